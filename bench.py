@@ -1,0 +1,331 @@
+"""Benchmark: extended-model gradient throughput on the guided-wave workload.
+
+Workload: 1000x300 grid (dx = 1 m), 30 m shale waveguide with +-3 % random
+perturbations, 32 moment-tensor sources (one extended component each), 500
+DAS channels (1 m spacing, 10 m gauge), nt = 4000 (dt = 0.1 ms), FP32 time
+stepping.  One step = one extended-model gradient: data misfit and the
+gradients of all 32 components (forward, checkpoint recompute, adjoint,
+imaging, chain rule) plus the consistency-term gradient of Vp, Vs and rho.
+
+Metric: G cell-updates/s, one cell-update = one physical cell x one time
+step x one shot, counted once per gradient (ns * nx * nz * nt / seconds);
+seconds per gradient are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own copy of the workload (independent
+extended problems, weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s and s per extended-model gradient (all shots) vs plain FP32 path"
+UNIT = "Gcell-updates/s"
+WORKLOAD = "guided_wave_1000x300: 32 shots x 500 DAS ch, nt=4000, dt=0.1ms, dx=1m, extended gradient + regularization"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--exec", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--ckpt-store", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ns", type=int, default=32)
+    ap.add_argument("--nt", type=int, default=4000)
+    return ap.parse_args()
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def problem(ns, nt):
+    import workloads as W
+    p = W.guided_wave_1000x300(ns=ns, nt=nt)
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    p.acq.wavelet = f32(p.acq.wavelet)
+    return p
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(p, budget_s=15.0):
+    """The FP64 oracle on host cores: gradient of one shot on the full grid for a
+    bounded number of steps (a sample of the same workload)."""
+    import copy
+    from oracle import elastic as E
+    acq = copy.deepcopy(p.acq)
+    s = 0
+    acq.tr_ptr = np.array([0, acq.tr_ptr[1]], np.int32)
+    acq.ch_xz, acq.ch_t = acq.ch_xz[:acq.tr_ptr[1]], acq.ch_t[:acq.tr_ptr[1]]
+    acq.src_xz, acq.mt = acq.src_xz[:1], acq.mt[:1]
+    nsteps = 8
+    while True:
+        acq.nt = nsteps
+        acq.wavelet = p.acq.wavelet[:1, :nsteps + 1]
+        vp, vs, rho = p.vp[:1], p.vs[:1], p.rho[:1]
+        d_obs = np.zeros((acq.ntr, nsteps))
+        t0 = time.perf_counter()
+        E.gradient(acq, vp, vs, rho, d_obs + 1e-12)
+        el = time.perf_counter() - t0
+        if el > budget_s / 4 or nsteps >= 4096:
+            break
+        nsteps *= 2
+    cells = acq.nx * acq.nz * nsteps
+    return {"value": cells / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle gradient of 1 shot on the full 1000x300 grid for {nsteps} steps "
+                      f"({el:.1f} s, single-threaded numpy)", "seconds": el}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    p = problem(args.ns, args.nt)
+    t_steps = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(p, budget_s=8.0)
+        if k >= args.warmup:
+            t_steps.append(r["value"])
+    value = float(np.median(t_steps))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = rank_info()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2305_14130_gb300 as efwi
+
+    p = problem(args.ns, args.nt)
+    acq = p.acq
+    dev = lambda a, dt=np.float32: torch.tensor(np.asarray(a, dt), device="cuda")
+    vp, vs, rho = dev(p.vp), dev(p.vs), dev(p.rho)
+    plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store)
+    # observed data: the same sources in the model with the Gaussian anomaly
+    ns = acq.ns
+    tv = lambda m: dev(np.repeat(np.asarray(m)[None], ns, 0))
+    d_obs = plan.forward(tv(p.true_vp), tv(p.true_vs), tv(p.true_rho))
+    b, bp, sink = efwi.zoi_weights(ns, acq.nx, acq.nz, acq.dx, acq.dz, p.zoi)
+    eta = p.eta
+    g = tuple(torch.empty_like(vp) for _ in range(3))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        phi, gvp, gvs, grho = plan.gradient(vp, vs, rho, d_obs, out=g)
+        for m, gm, e in zip((vp, vs, rho), g, eta):
+            plan.regularization_grad(m, b, bp, sink, e, g=gm)
+        return phi
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # kernels of one step: those the gradient call launched (counted by the plan)
+    # plus two per regularization call
+    plan.gradient(vp, vs, rho, d_obs, out=g)
+    launches_per_step = plan.info()["launches"] + 3 * 2
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    plan.prof_enable(97)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof_ms, prof_n = plan.prof_read()
+    plan.prof_enable(0)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    s_per_grad = ms / 1e3 / args.steps
+    cells = ns * acq.nx * acq.nz * acq.nt
+    value = cells * world / s_per_grad / 1e9
+    info = plan.info()
+
+    # roofline of the dominant kernel (the forward stress half-step over all shots)
+    padded = info["padded_cells"]
+    bytes_per_cell = 44.0   # read vx, vz, sxx, szz, sxz, lambda, mu, mu_xz; write sxx, szz, sxz
+    hbm, peak_kind = peaks()
+    roof = None
+    if prof_n:
+        avg = prof_ms / prof_n / 1e3
+        achieved = bytes_per_cell * padded / avg / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "k_stress (forward stress half-step, all shots)",
+                "peak_kind": peak_kind, "launches_timed": prof_n, "avg_us": avg * 1e6}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_vp, h_vs, h_rho = (t.cpu().pin_memory() for t in (vp, vs, rho))
+        h_obs = d_obs.cpu().pin_memory()
+        h_g = [torch.empty(vp.shape, dtype=torch.float32).pin_memory() for _ in range(3)]
+        h_phi = torch.empty((), dtype=torch.float64).pin_memory()
+        dvp, dvs, drho, dobs = (torch.empty_like(t) for t in (vp, vs, rho, d_obs))
+        h2d = sum(t.numel() * 4 for t in (h_vp, h_vs, h_rho, h_obs))
+        d2h = 3 * vp.numel() * 4 + 8
+
+        def e2e_step():
+            for d_, h_ in ((dvp, h_vp), (dvs, h_vs), (drho, h_rho), (dobs, h_obs)):
+                d_.copy_(h_, non_blocking=True)
+            phi, a, b_, c = plan.gradient(dvp, dvs, drho, dobs, out=g)
+            for m, gm, e in zip((dvp, dvs, drho), g, eta):
+                plan.regularization_grad(m, b, bp, sink, e, g=gm)
+            for h_, d_ in zip(h_g, g):
+                h_.copy_(d_, non_blocking=True)
+            h_phi.copy_(phi, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(1, min(args.steps, 2))
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": cells * world / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "s_per_gradient": el}
+
+    plain = None
+    if not args.no_plain and args.exec == "batched":
+        pl = efwi.Plan(acq, exec="plain")
+        gp = tuple(torch.empty_like(vp) for _ in range(3))
+        pl.gradient(vp, vs, rho, d_obs, out=gp)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        pl.gradient(vp, vs, rho, d_obs, out=gp)
+        for m, gm, e in zip((vp, vs, rho), gp, eta):
+            pl.regularization_grad(m, b, bp, sink, e, g=gm)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        sp = a0.elapsed_time(a1) / 1e3
+        rel = float(torch.linalg.vector_norm(gp[0] - g[0]) / torch.linalg.vector_norm(g[0]))
+        plain = {"s_per_gradient": sp, "value": cells / sp / 1e9, "speedup": sp / s_per_grad,
+                 "grad_vp_rel_diff": rel}
+        pl.close()
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_baseline(p)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "exec": args.exec, "ckpt_store": args.ckpt_store,
+                           "ckpt_interval": info["ckpt_interval"], "tile": [info["tile_x"], info["tile_z"]],
+                           "l2": "working set > L2 (wavefields, checkpoints, data >> 129 MB)",
+                           "parallelism": f"replicas x{world} (independent extended problems)"},
+                "s_per_gradient": s_per_grad, "padded_Gcell_updates_s": padded * acq.nt * world / s_per_grad / 1e9,
+                "gpu_launches": launches_per_step * args.steps, "clocks": ck, "roofline": roof,
+                "e2e": e2e, "plain_fp32": plain, "cpu_baseline": cpu,
+                "workspace_GB": info["workspace_bytes"] / 1e9}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

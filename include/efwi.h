@@ -1,0 +1,231 @@
+/*
+ * efwi.h -- C ABI of the GB300 (sm_103a) library for source-extended elastic
+ * full-waveform inversion with DAS data.
+ *
+ * The method (Bader, Clapp, Nihei, Biondi, "Source footprint elimination in
+ * full-waveform inversion by model extension") extends the model along
+ * sources, m~ = (m_1, ..., m_Ns), so that shot s is modelled with its own
+ * component m_s, and regularises the components towards a common "useful"
+ * model with the operator (I - S^T S_w) W:
+ *
+ *   phi_ext(m~) = 1/2 sum_s sum_r || d_{s,r}(m_s) - d_obs_{s,r} ||^2
+ *               + 1/2 eta^2 || (I - S^T S_w) W m~ ||^2                  (eq. 8)
+ *
+ * This library computes, on one GPU, every quantity the inversion needs per
+ * iteration: modelled DAS data (eqs. 1-3), the data misfit (eq. 4 / first
+ * term of eq. 8) and its gradient with respect to every extended component
+ * (eq. 6 applied to each m_s), the zone-of-influence weights (eq. 10) and the
+ * consistency term with its gradient (eqs. 8, 11, 12).
+ *
+ * Physics (the paper fixes no scheme): 2D isotropic elastic velocity-stress
+ * equations on a Virieux staggered grid, 4th order in space, 2nd order in
+ * time, convolutional PML (Komatitsch & Martin 2007), moment-tensor sources,
+ * DAS gauge-averaged axial strain (or strain rate).  The gradient is the exact
+ * discrete adjoint of the forward time stepping.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Row-major arrays, x fastest: a model component is [nz][nx]; an extended
+ *    model is [ns][nz][nx]; data are [ntr][nt] (trace-major; the traces of
+ *    shot s are tr_ptr[s] .. tr_ptr[s+1]-1).  Node (ix, iz) sits at
+ *    (ix*dx, iz*dz) metres.
+ *  - Arguments named "device" are device pointers owned by the caller,
+ *    16-byte aligned, never freed or retained by the library.  Everything in
+ *    efwi_plan_desc / efwi_zoi_desc is host memory, copied at the call.
+ *  - Work is enqueued asynchronously on the caller's stream; scalar results
+ *    (misfits) are written to device doubles.  No call synchronises the
+ *    device except efwi_plan_create / efwi_plan_destroy.
+ *  - Every call returns an int status: EFWI_OK (0) or a negative EFWI_ERR_*.
+ *    Nothing throws across the ABI.  efwi_last_error() gives the message.
+ *  - A plan is not thread-safe: calls on one plan must be serialised (they
+ *    share its workspace).  Different plans are independent.
+ */
+#ifndef EFWI_H
+#define EFWI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same underlying type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st *efwi_stream_t;
+typedef struct efwi_plan efwi_plan;
+
+enum efwi_status {
+    EFWI_OK = 0,
+    EFWI_ERR_ARG = -1,              /* invalid argument (sizes, positions, NULL pointers) */
+    EFWI_ERR_CFL = -2,              /* dt * vmax * sqrt(2) * (9/8 + 1/24) / min(dx, dz) >= 1 */
+    EFWI_ERR_OOM = -3,              /* device allocation failed at plan creation */
+    EFWI_ERR_CUDA = -4,             /* a CUDA runtime call or kernel launch failed */
+    EFWI_ERR_TIMEOUT = -5,          /* a bounded device-side wait expired */
+    EFWI_ERR_NAN = -6,              /* non-finite values detected */
+    EFWI_ERR_NOT_IMPLEMENTED = -7
+};
+
+enum efwi_das_mode { EFWI_DAS_STRAIN = 0, EFWI_DAS_STRAIN_RATE = 1 };
+/* storage precision of the wavefield checkpoints (the time stepping is FP32) */
+enum efwi_store { EFWI_STORE_FP32 = 0, EFWI_STORE_FP16 = 1, EFWI_STORE_BF16 = 2 };
+/* execution strategy:
+ *  PLAIN   one shot per launch, one kernel per half-step, no graph, no tuning
+ *  BATCHED all shots (any window sizes) in one fused launch per time step,
+ *          the time loop captured and replayed as CUDA graphs               */
+enum efwi_exec { EFWI_EXEC_PLAIN = 0, EFWI_EXEC_BATCHED = 1 };
+
+/*
+ * Problem description (host memory; copied by efwi_plan_create).
+ *
+ *   nx, nz, dx, dz     physical grid (cells, metres)
+ *   nt, dt             time steps and step (s); data sample n is taken after
+ *                      the velocity update of step n, n = 0..nt-1
+ *   npml               CPML thickness in cells; the grid is padded by npml+1
+ *                      cells per side (the first padding node is undamped)
+ *   pml_R, pml_vmax,   CPML reflection target, velocity and frequency used in
+ *   pml_f0             d0 = -3 vmax ln R / (2 L) and alpha = pi f0 (1 - r);
+ *                      pml_vmax <= 0 takes the maximum of ref_vp
+ *   ns                 number of sources = number of extended components
+ *   src_xz [ns][2]     source positions (m), inside the shot's window
+ *   mt [ns][3]         moment tensor (Mxx, Mzz, Mxz) per source (eq. 2)
+ *   wavelet [ns][nt+1] source time function w(t_n), t_n = n dt
+ *   ntr, tr_ptr[ns+1]  DAS traces, CSR over sources (the set N_r^s of eq. 4)
+ *   ch_xz [ntr][2]     gauge centres (m); ch_t [ntr][2] unit tangents
+ *   gauge              gauge length L (m): d = t.(u(p+) - u(p-)) / L,
+ *                      p+- = centre +- (L/2) t, u the displacement (STRAIN)
+ *                      or the particle velocity (STRAIN_RATE)
+ *   win [ns][2]        optional per-shot window (x0, width) in cells: shot s
+ *                      is modelled on columns x0 .. x0+width-1 only (NULL =
+ *                      the full grid for every shot)
+ *   ref_vp/vs/rho      frozen reference model [nz][nx]; the absorbing padding
+ *                      takes its edge values, so only physical cells are
+ *                      inversion variables
+ *   ckpt_interval      steps between wavefield checkpoints for the gradient:
+ *                      0 = ceil(sqrt(nt)); >= nt = store every step (no recompute)
+ *   ckpt_store         EFWI_STORE_* precision of the checkpoints
+ *   exec               EFWI_EXEC_*
+ *   tile_x, tile_z     stencil tile for EXEC_BATCHED (0, 0 = autotune at plan creation)
+ */
+typedef struct efwi_plan_desc {
+    int nx, nz;
+    double dx, dz;
+    int nt;
+    double dt;
+    int npml;
+    double pml_R, pml_vmax, pml_f0;
+    int ns;
+    const double *src_xz;
+    const double *mt;
+    const float *wavelet;
+    int ntr;
+    const int *tr_ptr;
+    const double *ch_xz;
+    const double *ch_t;
+    double gauge;
+    int das_mode;
+    const int *win;
+    const float *ref_vp, *ref_vs, *ref_rho;
+    int ckpt_interval;
+    int ckpt_store;
+    int exec;
+    int tile_x, tile_z;
+} efwi_plan_desc;
+
+/* What a plan chose and holds (filled by efwi_plan_info). */
+typedef struct efwi_plan_info_t {
+    int ckpt_interval;          /* steps per checkpoint segment */
+    int n_ckpt;                 /* checkpoints per gradient */
+    int tile_x, tile_z;         /* stencil tile in use */
+    size_t workspace_bytes;     /* device bytes owned by the plan */
+    long long padded_cells;     /* sum over shots of padded (nx_w + 2P)(nz + 2P) */
+    long long physical_cells;   /* sum over shots of window width * nz */
+    long long launches;         /* kernels launched by the last forward/gradient call */
+} efwi_plan_info_t;
+
+/* Zone-of-influence description (eq. 10), host memory.  Per source s:
+ *   active_x[s][2]  x-span (m) where the outer weight is 1
+ *   taper[s]        outer taper width (m): r = distance outside the span / taper
+ *   sink_xz[s][2]   sinkhole centre (m); sink_axes[s][2] ellipse semi-axes (m):
+ *                   d_M = sqrt((dx/a_x)^2 + (dz/a_z)^2), r = 1 - d_M, inside iff d_M < 1
+ *   n, nu           stiffness and height of the transition (0 < nu < 1)     */
+typedef struct efwi_zoi_desc {
+    const double *active_x;
+    const double *taper;
+    const double *sink_xz;
+    const double *sink_axes;
+    double n, nu;
+} efwi_zoi_desc;
+
+/* Create a plan: validates the description (positions inside windows, CFL),
+ * precomputes CPML profiles, interpolation weights and tile lists, allocates
+ * the workspace and, for EXEC_BATCHED with tile 0x0, runs the tile autotuner.
+ * Synchronises the device.  Errors: EFWI_ERR_ARG, EFWI_ERR_CFL, EFWI_ERR_OOM,
+ * EFWI_ERR_CUDA (*out is then NULL; the message is in efwi_last_error(NULL)). */
+int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *desc);
+
+/* Free a plan and its workspace (synchronises the device).  NULL is allowed. */
+int efwi_plan_destroy(efwi_plan *plan);
+
+/* Last error message of a plan, or of the calling thread when plan is NULL. */
+const char *efwi_last_error(const efwi_plan *plan);
+
+int efwi_plan_info(const efwi_plan *plan, efwi_plan_info_t *info);
+
+/* Forward modelling of every shot with its own component (eqs. 1-3; first
+ * term of eq. 8).
+ *   vp, vs, rho  device [ns][nz][nx] FP32 extended model (Vs > 0 everywhere)
+ *   d_out        device [ntr][nt] FP32, overwritten with the DAS data       */
+int efwi_forward(efwi_plan *plan, const float *vp, const float *vs, const float *rho,
+                 float *d_out, efwi_stream_t stream);
+
+/* Data misfit and its gradient with respect to every extended component
+ * (eq. 4 and eq. 6 applied to each m_s, by the adjoint-state method: exact
+ * discrete adjoint of the forward time stepping, zero-lag cross-correlation
+ * of forward and adjoint wavefields).
+ *   d_obs              device [ntr][nt] FP32 observed data
+ *   phi_data           device double: 1/2 sum (d - d_obs)^2 (FP64 reduction)
+ *   g_vp, g_vs, g_rho  device [ns][nz][nx] FP32, overwritten; zero outside a
+ *                      shot's window
+ *   mask               device [nz][nx] FP32 multiplier of every gradient, or NULL
+ *   d_out              device [ntr][nt] FP32 modelled data, or NULL          */
+int efwi_adjoint_gradient(efwi_plan *plan, const float *vp, const float *vs, const float *rho,
+                          const float *d_obs, double *phi_data, float *g_vp, float *g_vs,
+                          float *g_rho, const float *mask, float *d_out, efwi_stream_t stream);
+
+/* Zone-of-influence weights of every source (eq. 10): b_s, b'_s (= 1 inside
+ * the sinkhole of s, b_s outside; eq. 12) and the sinkhole flag.
+ *   b, bp  device [ns][nz][nx] FP32; sink device [ns][nz][nx] uint8          */
+int efwi_zoi_weights(int ns, int nx, int nz, double dx, double dz, const efwi_zoi_desc *zoi,
+                     float *b, float *bp, uint8_t *sink, efwi_stream_t stream);
+
+/* Consistency term of eq. 8 for one parameter field and its gradient:
+ *   phi_reg = 1/2 eta^2 || (I - S^T S_w) W m~ ||^2,
+ *   g      += eta^2 W^T (I - S^T S_w)^T (I - S^T S_w) W m~
+ * with W of eq. 11 and S_w of eq. 12, per pixel over the ns components.
+ *   m, b, bp   device [ns][nz][nx] FP32; sink device [ns][nz][nx] uint8
+ *   phi_reg    device double (overwritten; FP64 reduction)
+ *   g          device [ns][nz][nx] FP32, accumulated into (+=)             */
+int efwi_regularization_grad(efwi_plan *plan, const float *m, const float *b, const float *bp,
+                             const uint8_t *sink, double eta, double *phi_reg, float *g,
+                             efwi_stream_t stream);
+
+/* Extended objective of eq. 8: phi_data (as efwi_forward + misfit) and
+ * phi_reg summed over the three parameter fields (Vp, Vs, rho) with their
+ * own eta[3].  Both results are device doubles (overwritten).               */
+int efwi_extended_objective(efwi_plan *plan, const float *vp, const float *vs, const float *rho,
+                            const float *d_obs, const double eta[3], const float *b,
+                            const float *bp, const uint8_t *sink, double *phi_data,
+                            double *phi_reg, efwi_stream_t stream);
+
+/* Kernel timing for measurements: when every > 0, the plan brackets every
+ * every-th launch of its dominant stencil kernel with CUDA events on the
+ * launching stream (non-graph launches only).  efwi_prof_read synchronises
+ * those events and returns their summed elapsed milliseconds and count,
+ * then resets the counters.                                                 */
+int efwi_prof_enable(efwi_plan *plan, int every);
+int efwi_prof_read(efwi_plan *plan, double *total_ms, long long *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EFWI_H */

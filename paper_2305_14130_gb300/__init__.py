@@ -1,0 +1,213 @@
+"""Source-extended elastic FWI with DAS data on one GB300 (sm_103a).
+
+Python side of the C ABI declared in ``include/efwi.h``: it only marshals
+arguments (torch CUDA tensors -> device pointers, the current torch stream ->
+cudaStream_t).  Every step of the computation runs in the CUDA kernels of
+``_lib/libefwi_gb300.so``; there is no CPU fallback, and a missing library
+raises at first use.
+
+Method (Bader, Clapp, Nihei, Biondi, "Source footprint elimination in
+full-waveform inversion by model extension"):
+  * forward modelling d_s = K_r u_s(m_s) with one model component per source
+    (eqs. 1-3, first term of eq. 8), DAS axial strain as K_r;
+  * misfit 1/2 sum ||d_s - d_obs_s||^2 and its gradient per component by the
+    adjoint-state method (eqs. 4, 6);
+  * zone-of-influence weights (eq. 10) and the consistency term
+    1/2 eta^2 ||(I - S^T S_w) W m~||^2 with its gradient (eqs. 8, 11, 12).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import EfwiError, STORE, EXEC
+
+__all__ = ["Plan", "zoi_weights", "EfwiError", "load_library"]
+
+
+def load_library():
+    return _abi.load()
+
+
+def _ptr(t, name, numel=None, dtype=torch.float32, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(np.asarray(a, dtype=dtype))
+
+
+class Plan:
+    """A problem (grid, sources, DAS geometry, windows) bound to device workspace.
+
+    ``acq`` is any object with the attributes of ``efwi_plan_desc`` (see
+    include/efwi.h): nx, nz, dx, dz, nt, dt, npml, pml_R, pml_vmax, pml_f0,
+    src_xz, mt, wavelet, tr_ptr, ch_xz, ch_t, gauge, das_mode, win,
+    ref_vp, ref_vs, ref_rho.
+    """
+
+    def __init__(self, acq, exec: str = "batched", ckpt_interval: int = 0, ckpt_store: str = "fp32",
+                 tile=(0, 0)):
+        lib = _abi.load()
+        a = acq
+        self.nx, self.nz, self.nt = int(a.nx), int(a.nz), int(a.nt)
+        self.ns = int(np.asarray(a.src_xz).shape[0])
+        self.ntr = int(np.asarray(a.ch_xz).reshape(-1, 2).shape[0])
+        keep = dict(
+            src=_np(a.src_xz, np.float64), mt=_np(a.mt, np.float64), wav=_np(a.wavelet, np.float32),
+            ptr=_np(a.tr_ptr, np.int32), ch=_np(np.asarray(a.ch_xz).reshape(-1, 2), np.float64),
+            cht=_np(np.asarray(a.ch_t).reshape(-1, 2), np.float64),
+            rvp=_np(a.ref_vp, np.float32), rvs=_np(a.ref_vs, np.float32), rrho=_np(a.ref_rho, np.float32))
+        win = getattr(a, "win", None)
+        keep["win"] = None if win is None else _np(win, np.int32)
+        if keep["wav"].shape != (self.ns, self.nt + 1):
+            raise ValueError("wavelet must be [ns, nt+1]")
+        P = lambda arr, typ: arr.ctypes.data_as(C.POINTER(typ)) if arr is not None and arr.size else None
+        d = _abi.PlanDesc()
+        d.nx, d.nz, d.dx, d.dz = self.nx, self.nz, float(a.dx), float(a.dz)
+        d.nt, d.dt = self.nt, float(a.dt)
+        d.npml = int(getattr(a, "npml", 20))
+        d.pml_R = float(getattr(a, "pml_R", 1e-3))
+        d.pml_vmax = float(getattr(a, "pml_vmax", 0.0))
+        d.pml_f0 = float(getattr(a, "pml_f0", 0.0))
+        d.ns = self.ns
+        d.src_xz, d.mt, d.wavelet = P(keep["src"], C.c_double), P(keep["mt"], C.c_double), P(keep["wav"], C.c_float)
+        d.ntr, d.tr_ptr = self.ntr, P(keep["ptr"], C.c_int)
+        d.ch_xz, d.ch_t = P(keep["ch"], C.c_double), P(keep["cht"], C.c_double)
+        d.gauge = float(a.gauge)
+        d.das_mode = int(getattr(a, "das_mode", 0))
+        d.win = P(keep["win"], C.c_int)
+        d.ref_vp, d.ref_vs, d.ref_rho = P(keep["rvp"], C.c_float), P(keep["rvs"], C.c_float), P(keep["rrho"], C.c_float)
+        d.ckpt_interval = int(ckpt_interval)
+        d.ckpt_store = STORE[ckpt_store]
+        d.exec = EXEC[exec]
+        d.tile_x, d.tile_z = int(tile[0]), int(tile[1])
+        self.exec, self.ckpt_store = exec, ckpt_store
+        h = C.c_void_p()
+        torch.cuda.init()
+        rc = lib.efwi_plan_create(C.byref(h), C.byref(d))
+        _abi.check(rc, None)
+        self._h = h
+        self._lib = lib
+        self.model_numel = self.ns * self.nz * self.nx
+        self.data_shape = (self.ntr, self.nt)
+
+    # -- lifecycle -----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.efwi_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        _abi.check(rc, self._h)
+
+    def info(self) -> dict:
+        i = _abi.PlanInfo()
+        self._check(self._lib.efwi_plan_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in _abi.PlanInfo._fields_}
+
+    # -- calls -------------------------------------------------------------------
+    def _model(self, vp, vs, rho):
+        n = self.model_numel
+        return _ptr(vp, "vp", n), _ptr(vs, "vs", n), _ptr(rho, "rho", n)
+
+    def forward(self, vp, vs, rho, out=None):
+        """Modelled DAS data [ntr, nt] of the extended model (each [ns, nz, nx])."""
+        m = self._model(vp, vs, rho)
+        if out is None:
+            out = torch.empty(self.data_shape, dtype=torch.float32, device=vp.device)
+        self._check(self._lib.efwi_forward(self._h, *m, _ptr(out, "out", self.ntr * self.nt), _stream()))
+        return out
+
+    def gradient(self, vp, vs, rho, d_obs, mask=None, out=None, return_data=False):
+        """(phi_data [device float64 scalar], g_vp, g_vs, g_rho[, d]) of the data term."""
+        m = self._model(vp, vs, rho)
+        dev = vp.device
+        if out is None:
+            out = tuple(torch.empty_like(vp) for _ in range(3))
+        phi = torch.empty((), dtype=torch.float64, device=dev)
+        dmod = torch.empty(self.data_shape, dtype=torch.float32, device=dev) if return_data else None
+        self._check(self._lib.efwi_adjoint_gradient(
+            self._h, *m, _ptr(d_obs, "d_obs", self.ntr * self.nt), _ptr(phi, "phi", 1, torch.float64),
+            _ptr(out[0], "g_vp", self.model_numel), _ptr(out[1], "g_vs", self.model_numel),
+            _ptr(out[2], "g_rho", self.model_numel), _ptr(mask, "mask", self.nz * self.nx, allow_none=True),
+            _ptr(dmod, "d_out", self.ntr * self.nt, allow_none=True), _stream()))
+        return (phi, *out, dmod) if return_data else (phi, *out)
+
+    def regularization_grad(self, m, b, bp, sink, eta, g=None):
+        """phi_reg (device float64) and g += eta^2 A^T A m for one parameter field."""
+        n = self.model_numel
+        if g is None:
+            g = torch.zeros_like(m)
+        phi = torch.empty((), dtype=torch.float64, device=m.device)
+        self._check(self._lib.efwi_regularization_grad(
+            self._h, _ptr(m, "m", n), _ptr(b, "b", n), _ptr(bp, "bp", n), _ptr(sink, "sink", n, torch.uint8),
+            float(eta), _ptr(phi, "phi", 1, torch.float64), _ptr(g, "g", n), _stream()))
+        return phi, g
+
+    def extended_objective(self, vp, vs, rho, d_obs, eta, b, bp, sink):
+        """(phi_data, phi_reg) of eq. 8 as device float64 scalars."""
+        n = self.model_numel
+        m = self._model(vp, vs, rho)
+        pd = torch.empty((), dtype=torch.float64, device=vp.device)
+        pr = torch.empty((), dtype=torch.float64, device=vp.device)
+        e = (C.c_double * 3)(*[float(x) for x in eta])
+        self._check(self._lib.efwi_extended_objective(
+            self._h, *m, _ptr(d_obs, "d_obs", self.ntr * self.nt), e, _ptr(b, "b", n), _ptr(bp, "bp", n),
+            _ptr(sink, "sink", n, torch.uint8), _ptr(pd, "phi_data", 1, torch.float64),
+            _ptr(pr, "phi_reg", 1, torch.float64), _stream()))
+        return pd, pr
+
+    def prof_enable(self, every: int):
+        self._check(self._lib.efwi_prof_enable(self._h, int(every)))
+
+    def prof_read(self):
+        ms = C.c_double()
+        cnt = C.c_longlong()
+        self._check(self._lib.efwi_prof_read(self._h, C.byref(ms), C.byref(cnt)))
+        return ms.value, cnt.value
+
+
+def zoi_weights(ns, nx, nz, dx, dz, zoi, device="cuda"):
+    """b, b' [ns, nz, nx] float32 and the sinkhole flags (uint8) of eq. 10 on the device."""
+    lib = _abi.load()
+    act = _np(zoi.active_x, np.float64)
+    tap = _np(zoi.taper, np.float64)
+    sxz = _np(zoi.sink_xz, np.float64)
+    axes = _np(np.stack([np.asarray(zoi.sink_ax, np.float64), np.asarray(zoi.sink_az, np.float64)], axis=1),
+               np.float64)
+    PD = C.POINTER(C.c_double)
+    z = _abi.ZoiDesc(act.ctypes.data_as(PD), tap.ctypes.data_as(PD), sxz.ctypes.data_as(PD),
+                     axes.ctypes.data_as(PD), float(zoi.n), float(zoi.nu))
+    b = torch.empty((ns, nz, nx), dtype=torch.float32, device=device)
+    bp = torch.empty_like(b)
+    sink = torch.empty((ns, nz, nx), dtype=torch.uint8, device=device)
+    _abi.check(lib.efwi_zoi_weights(int(ns), int(nx), int(nz), float(dx), float(dz), C.byref(z),
+                                    C.c_void_p(b.data_ptr()), C.c_void_p(bp.data_ptr()),
+                                    C.c_void_p(sink.data_ptr()), _stream()))
+    return b, bp, sink

@@ -1,0 +1,87 @@
+"""ctypes declarations of the C ABI in include/efwi.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB
+
+EFWI_OK = 0
+STATUS = {0: "EFWI_OK", -1: "EFWI_ERR_ARG", -2: "EFWI_ERR_CFL", -3: "EFWI_ERR_OOM", -4: "EFWI_ERR_CUDA",
+          -5: "EFWI_ERR_TIMEOUT", -6: "EFWI_ERR_NAN", -7: "EFWI_ERR_NOT_IMPLEMENTED"}
+DAS_STRAIN, DAS_STRAIN_RATE = 0, 1
+STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
+EXEC = {"plain": 0, "batched": 1}
+
+PD = C.POINTER(C.c_double)
+PF = C.POINTER(C.c_float)
+PI = C.POINTER(C.c_int)
+
+
+class PlanDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("dz", C.c_double),
+                ("nt", C.c_int), ("dt", C.c_double), ("npml", C.c_int), ("pml_R", C.c_double),
+                ("pml_vmax", C.c_double), ("pml_f0", C.c_double), ("ns", C.c_int),
+                ("src_xz", PD), ("mt", PD), ("wavelet", PF), ("ntr", C.c_int), ("tr_ptr", PI),
+                ("ch_xz", PD), ("ch_t", PD), ("gauge", C.c_double), ("das_mode", C.c_int), ("win", PI),
+                ("ref_vp", PF), ("ref_vs", PF), ("ref_rho", PF), ("ckpt_interval", C.c_int),
+                ("ckpt_store", C.c_int), ("exec", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("ckpt_interval", C.c_int), ("n_ckpt", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
+                ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
+                ("physical_cells", C.c_longlong), ("launches", C.c_longlong)]
+
+
+class ZoiDesc(C.Structure):
+    _fields_ = [("active_x", PD), ("taper", PD), ("sink_xz", PD), ("sink_axes", PD),
+                ("n", C.c_double), ("nu", C.c_double)]
+
+
+VP = C.c_void_p
+SIGNATURES = {
+    "efwi_plan_create": (C.c_int, [C.POINTER(VP), C.POINTER(PlanDesc)]),
+    "efwi_plan_destroy": (C.c_int, [VP]),
+    "efwi_last_error": (C.c_char_p, [VP]),
+    "efwi_plan_info": (C.c_int, [VP, C.POINTER(PlanInfo)]),
+    "efwi_forward": (C.c_int, [VP, VP, VP, VP, VP, VP]),
+    "efwi_adjoint_gradient": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP]),
+    "efwi_zoi_weights": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(ZoiDesc),
+                                   VP, VP, VP, VP]),
+    "efwi_regularization_grad": (C.c_int, [VP, VP, VP, VP, VP, C.c_double, VP, VP, VP]),
+    "efwi_extended_objective": (C.c_int, [VP, VP, VP, VP, VP, PD, VP, VP, VP, VP, VP, VP]),
+    "efwi_prof_enable": (C.c_int, [VP, C.c_int]),
+    "efwi_prof_read": (C.c_int, [VP, PD, C.POINTER(C.c_longlong)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB):
+    """Load libefwi_gb300.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2305_14130_gb300.build.build() "
+                           "(the CUDA path has no CPU fallback)")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class EfwiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(code, plan_handle=None):
+    if code != EFWI_OK:
+        msg = _lib.efwi_last_error(plan_handle)
+        raise EfwiError(code, msg.decode() if msg else "")

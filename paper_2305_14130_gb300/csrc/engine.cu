@@ -1,0 +1,191 @@
+// Time-loop orchestration behind the C ABI: forward modelling, the
+// checkpointed adjoint-state gradient and the extended objective.
+//
+// Gradient schedule (uniform checkpoints, one recompute pass):
+//   forward n = 0..nt-1, saving the state x^n every K steps (FP32 or scaled
+//   FP16/BF16); residual r = d - d_obs and phi = 1/2 |r|^2 in FP64;
+//   for every segment [n0, n1) from the last: restore x^{n0}, recompute the
+//   segment keeping v^{n+1/2} of each step, then run the adjoint steps
+//   n1-1 .. n0, each accumulating the zero-lag imaging sums.  With K >= nt the
+//   first forward pass already keeps every v^{n+1/2} and nothing is recomputed.
+// EXEC_PLAIN launches one kernel per half-step and shot; EXEC_BATCHED runs all
+// shots in fused launches and replays the time loop from CUDA graphs.
+#include <cmath>
+#include <string>
+
+#include "plan.hpp"
+
+using namespace efwi;
+
+namespace {
+
+int cuda_status(efwi_plan *p, const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        p->err = std::string(where) + ": " + cudaGetErrorString(e);
+        return EFWI_ERR_CUDA;
+    }
+    return EFWI_OK;
+}
+
+int check_model_args(efwi_plan *p, const float *vp, const float *vs, const float *rho) {
+    if (!vp || !vs || !rho) {
+        p->err = "model pointers must be non-NULL device pointers";
+        return EFWI_ERR_ARG;
+    }
+    return EFWI_OK;
+}
+
+void reset_forward_state(efwi_plan *p, cudaStream_t st) {
+    for (int k = 0; k < 2; ++k)
+        if (p->state[k]) cudaMemsetAsync(p->state[k], 0, sizeof(float) * 5 * p->fsz_total, st);
+    cudaMemsetAsync(p->psi, 0, sizeof(float) * 4 * p->H, st);
+    if (p->d.ntr > 0) cudaMemsetAsync(p->tr_acc, 0, sizeof(double) * p->d.ntr, st);
+    p->scur = 0;
+    p->psi_v = 0;
+    p->psi_s = 0;
+}
+
+float *seg_x(efwi_plan *p, int slot) { return p->seg + (size_t)slot * 2 * p->fsz_total; }
+float *seg_z(efwi_plan *p, int slot) { return p->seg + (size_t)slot * 2 * p->fsz_total + p->fsz_total; }
+
+// One forward step of every shot; d == nullptr skips the DAS sampling.
+void forward_step(efwi_plan *p, int n, float *d, float *sx, float *sz, cudaStream_t st) {
+    if (p->d.exec == EFWI_EXEC_PLAIN) {
+        Fields F = state_fields(p, 0);
+        for (int s = 0; s < p->d.ns; ++s) {
+            launch_vel_plain(p, s, sx, sz, st);
+            if (d) launch_das_fwd(p, F, n, d, s, st);
+            launch_stress_plain(p, s, st);
+            launch_inject(p, F, n, s, st);
+        }
+    } else {
+        launch_step_fused(p, n, sx, sz, st);   // leaves v^{n+1/2}, sigma^{n+1} in state[scur]
+        if (d) launch_das_fwd(p, state_fields(p, p->scur), n, d, -1, st);
+    }
+}
+
+void adjoint_step(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaStream_t st) {
+    if (p->d.exec == EFWI_EXEC_PLAIN) {
+        Fields A = adj_fields(p, 0);
+        for (int s = 0; s < p->d.ns; ++s) {
+            launch_das_adj(p, A, vfx, vfz, G_field(p, 3), G_field(p, 4), n, s, st);
+            launch_adj_vel_plain(p, s, vfx, vfz, st);
+            launch_adj_stress_plain(p, s, vfx, vfz, st);
+        }
+        p->apsi_v ^= 1;
+    } else {
+        launch_das_adj(p, adj_fields(p, p->acur), vfx, vfz, G_field(p, 3), G_field(p, 4), n, -1, st);
+        launch_adj_fused(p, n, vfx, vfz, st);   // flips acur and the adjoint psi blocks
+    }
+}
+
+}  // namespace
+
+namespace efwi {
+
+// Forward pass over all steps; keeps checkpoints when ck != 0 and every
+// v^{n+1/2} in the segment buffer when the plan stores all steps.
+int run_forward(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
+    reset_forward_state(p, st);
+    const bool full = p->K >= p->d.nt;
+    for (int n = 0; n < p->d.nt; ++n) {
+        if (ck && n % p->K == 0) launch_ckpt_save(p, n / p->K, st);
+        float *sx = (ck && full) ? seg_x(p, n) : nullptr;
+        float *sz = (ck && full) ? seg_z(p, n) : nullptr;
+        forward_step(p, n, d, sx, sz, st);
+    }
+    return cuda_status(p, "forward time loop");
+}
+
+int run_adjoint(efwi_plan *p, cudaStream_t st) {
+    const long long F = p->fsz_total;
+    for (int k = 0; k < 2; ++k)
+        if (p->adj[k]) cudaMemsetAsync(p->adj[k], 0, sizeof(float) * 5 * F, st);
+    cudaMemsetAsync(p->apsi, 0, sizeof(float) * 4 * p->H, st);
+    cudaMemsetAsync(p->G, 0, sizeof(float) * 5 * F, st);
+    if (p->Gtot) cudaMemsetAsync(p->Gtot, 0, sizeof(float) * 5 * F, st);
+    if (p->Gcmp) cudaMemsetAsync(p->Gcmp, 0, sizeof(float) * 5 * F, st);
+    if (p->d.ntr > 0) cudaMemsetAsync(p->tr_acc, 0, sizeof(double) * p->d.ntr, st);
+    p->acur = 0;
+    p->apsi_v = 0;
+    p->apsi_s = 0;
+    const int nt = p->d.nt, K = p->K;
+    const bool full = K >= nt;
+    const int nseg = (nt + K - 1) / K;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int n0 = sgi * K, n1 = std::min(n0 + K, nt);
+        if (!full) {
+            launch_ckpt_load(p, sgi, st);
+            for (int n = n0; n < n1; ++n) forward_step(p, n, nullptr, seg_x(p, n - n0), seg_z(p, n - n0), st);
+        }
+        for (int n = n1 - 1; n >= n0; --n) adjoint_step(p, n, seg_x(p, n - n0), seg_z(p, n - n0), st);
+        if (p->Gtot) launch_kahan_fold(p, st);
+    }
+    return cuda_status(p, "adjoint time loop");
+}
+
+}  // namespace efwi
+
+extern "C" int efwi_forward(efwi_plan *p, const float *vp, const float *vs, const float *rho, float *d_out,
+                            efwi_stream_t stream) {
+    if (!p) return EFWI_ERR_ARG;
+    int rc = check_model_args(p, vp, vs, rho);
+    if (rc) return rc;
+    if (!d_out && p->d.ntr > 0) {
+        p->err = "d_out must be a device pointer";
+        return EFWI_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    p->launches = 0;
+    launch_materials(p, vp, vs, rho, st);
+    rc = run_forward(p, d_out, false, st);
+    return rc;
+}
+
+extern "C" int efwi_adjoint_gradient(efwi_plan *p, const float *vp, const float *vs, const float *rho,
+                                     const float *d_obs, double *phi_data, float *g_vp, float *g_vs, float *g_rho,
+                                     const float *mask, float *d_out, efwi_stream_t stream) {
+    if (!p) return EFWI_ERR_ARG;
+    int rc = check_model_args(p, vp, vs, rho);
+    if (rc) return rc;
+    if ((!d_obs && p->d.ntr > 0) || !phi_data || !g_vp || !g_vs || !g_rho) {
+        p->err = "d_obs, phi_data and gradient pointers must be device pointers";
+        return EFWI_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    p->launches = 0;
+    float *d = d_out ? d_out : p->dbuf;
+    launch_materials(p, vp, vs, rho, st);
+    if ((rc = run_forward(p, d, true, st))) return rc;
+    if (p->d.ntr > 0) launch_residual(p, d, d_obs, phi_data, st);
+    else cudaMemsetAsync(phi_data, 0, sizeof(double), st);
+    if ((rc = run_adjoint(p, st))) return rc;
+    float *src = p->Gtot ? p->Gtot : p->G;
+    const float *G[5];
+    for (int k = 0; k < 5; ++k) G[k] = src + k * p->fsz_total;
+    launch_chain_rule(p, vp, vs, rho, G, mask, g_vp, g_vs, g_rho, st);
+    return cuda_status(p, "gradient epilogue");
+}
+
+extern "C" int efwi_extended_objective(efwi_plan *p, const float *vp, const float *vs, const float *rho,
+                                       const float *d_obs, const double eta[3], const float *b, const float *bp,
+                                       const uint8_t *sink, double *phi_data, double *phi_reg,
+                                       efwi_stream_t stream) {
+    if (!p) return EFWI_ERR_ARG;
+    int rc = check_model_args(p, vp, vs, rho);
+    if (rc) return rc;
+    if ((!d_obs && p->d.ntr > 0) || !eta || !b || !bp || !sink || !phi_data || !phi_reg) {
+        p->err = "NULL argument to efwi_extended_objective";
+        return EFWI_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    p->launches = 0;
+    launch_materials(p, vp, vs, rho, st);
+    if ((rc = run_forward(p, p->dbuf, false, st))) return rc;
+    if (p->d.ntr > 0) launch_residual(p, p->dbuf, d_obs, phi_data, st);
+    else cudaMemsetAsync(phi_data, 0, sizeof(double), st);
+    const float *ms[3] = {vp, vs, rho};
+    for (int k = 0; k < 3; ++k) launch_reg(p, ms[k], b, bp, sink, eta[k], phi_reg, nullptr, k > 0, st);
+    return cuda_status(p, "extended objective");
+}

@@ -1,0 +1,504 @@
+// Plan creation and destruction, argument validation, host-side precompute
+// (CPML profiles, source and DAS interpolation weights, the deterministic
+// adjoint-source gather), workspace allocation, and the plan-level C ABI.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "plan.hpp"
+
+using namespace efwi;
+
+static thread_local std::string g_thread_err;
+
+static int fail(efwi_plan *p, int code, const std::string &msg) {
+    if (p) p->err = msg;
+    g_thread_err = msg;
+    return code;
+}
+
+namespace {
+
+struct Alloc {
+    efwi_plan *p;
+    bool ok = true;
+    std::string what;
+    template <class T>
+    void operator()(T **ptr, size_t count, const char *name) {
+        if (!ok || count == 0) return;
+        size_t bytes = count * sizeof(T);
+        cudaError_t e = cudaMalloc((void **)ptr, bytes);
+        if (e != cudaSuccess) {
+            ok = false;
+            char buf[256];
+            snprintf(buf, sizeof buf, "cudaMalloc of %zu bytes for %s failed: %s", bytes, name, cudaGetErrorString(e));
+            what = buf;
+            cudaGetLastError();
+            *ptr = nullptr;
+            return;
+        }
+        p->bytes += bytes;
+        cudaMemset(*ptr, 0, bytes);
+    }
+};
+
+// CPML (Komatitsch & Martin 2007) with kappa = 1 along one padded axis:
+// psi <- b psi + a d(.), b = exp(-(d + alpha) dt), a = d (b - 1) / (d + alpha),
+// d = d0 r^2, d0 = -3 vmax ln(R) / (2 L), alpha = pi f0 (1 - r).  The damping
+// starts beyond the first padding node: r = distance past index P-1 (left) or
+// N-P (right), over L = npml cells, clamped to 1.
+void cpml_axis(int N, int P, double h, int npml, double R, double vmax, double f0, double dt, bool half,
+               float *a, float *b) {
+    const double L = npml * h;
+    const double d0 = -3.0 * vmax * std::log(R) / (2.0 * L);
+    for (int k = 0; k < N; ++k) {
+        const double pos = k + (half ? 0.5 : 0.0);
+        const double dist = std::max(std::max((P - 1) - pos, pos - (N - P)), 0.0);
+        const double r = std::min(dist * h / L, 1.0);
+        const double d = d0 * r * r;
+        const double al = M_PI * f0 * (1.0 - r);
+        const double bb = std::exp(-(d + al) * dt);
+        a[k] = (float)(d > 0.0 ? d * (bb - 1.0) / (d + al) : 0.0);
+        b[k] = (float)bb;
+    }
+}
+
+struct Corner {
+    int i, j;
+    double w;
+};
+
+// Bilinear corners of the point (x, z) on the sub-grid offset by (ox, oz)
+// cells, in the padded frame of shot geometry s.  False if the point lies
+// outside the shot's physical window.
+bool bilinear(const efwi_plan_desc &d, const ShotDev &s, double x, double z, double ox, double oz, Corner out[4]) {
+    const double ux = x / d.dx - s.x0, uz = z / d.dz;
+    if (!(ux >= 0.0 && ux <= s.w - 1 && uz >= 0.0 && uz <= d.nz - 1)) return false;
+    const double fi = ux + s.P - ox, fj = uz + s.P - oz;
+    const int i0 = (int)std::floor(fi), j0 = (int)std::floor(fj);
+    const double ti = fi - i0, tj = fj - j0;
+    out[0] = {i0, j0, (1 - ti) * (1 - tj)};
+    out[1] = {i0 + 1, j0, ti * (1 - tj)};
+    out[2] = {i0, j0 + 1, (1 - ti) * tj};
+    out[3] = {i0 + 1, j0 + 1, ti * tj};
+    return true;
+}
+
+int local_off(const ShotDev &s, int i, int j) { return (j + EFWI_GZ) * s.pitch + (i + EFWI_GX); }
+
+}  // namespace
+
+namespace efwi {
+
+Fields state_fields(efwi_plan *p, int which) {
+    const long long F = p->fsz_total;
+    float *s = p->state[which];
+    return {s, s + F, s + 2 * F, s + 3 * F, s + 4 * F};
+}
+Fields adj_fields(efwi_plan *p, int which) {
+    const long long F = p->fsz_total;
+    float *s = p->adj[which];
+    return {s, s + F, s + 2 * F, s + 3 * F, s + 4 * F};
+}
+Mat materials(efwi_plan *p) {
+    const long long F = p->fsz_total;
+    return {p->mat, p->mat + F, p->mat + 2 * F, p->mat + 3 * F, p->mat + 4 * F};
+}
+float *psi_block(float *base, efwi_plan *p, int blk) { return base + blk * p->H; }
+static Pml make_pml(efwi_plan *p, float *base, int vblk, int sblk) {
+    Pml m;
+    const long long X = p->psx_total;
+    float *v = psi_block(base, p, vblk), *s = psi_block(base, p, 2 + sblk);
+    m.x[0] = v; m.x[1] = v + X; m.z[0] = v + 2 * X; m.z[1] = v + 2 * X + p->psz_total;
+    m.x[2] = s; m.x[3] = s + X; m.z[2] = s + 2 * X; m.z[3] = s + 2 * X + p->psz_total;
+    const int PX = p->prof_x_total;
+    m.ax_i = p->prof; m.bx_i = p->prof + PX; m.ax_h = p->prof + 2 * PX; m.bx_h = p->prof + 3 * PX;
+    const float *z = p->prof + 4 * PX;
+    m.az_i = z; m.bz_i = z + p->nzp; m.az_h = z + 2 * p->nzp; m.bz_h = z + 3 * p->nzp;
+    return m;
+}
+Pml fwd_pml(efwi_plan *p, int vblk, int sblk) { return make_pml(p, p->psi, vblk, sblk); }
+Pml adj_pml(efwi_plan *p, int vblk, int sblk) { return make_pml(p, p->apsi, vblk, sblk); }
+float *G_field(efwi_plan *p, int k) { return p->G + k * p->fsz_total; }
+
+void prof_begin(efwi_plan *p, cudaStream_t st, int *slot) {
+    *slot = -1;
+    if (p->prof_every <= 0) return;
+    if ((p->prof_counter++ % p->prof_every) != 0) return;
+    if (p->ev_used + 2 > (int)p->ev.size()) return;
+    *slot = p->ev_used;
+    p->ev_used += 2;
+    cudaEventRecord(p->ev[*slot], st);
+}
+void prof_end(efwi_plan *p, cudaStream_t st, int slot) {
+    if (slot >= 0) cudaEventRecord(p->ev[slot + 1], st);
+}
+
+}  // namespace efwi
+
+static void free_plan(efwi_plan *p) {
+    if (!p) return;
+    void *ptrs[] = {p->shots_d, p->state[0], p->state[1], p->mat, p->adj[0], p->adj[1], p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
+                    p->prof, p->dw, p->ref, p->tr_shot, p->tr_off, p->tr_w, p->tr_acc, p->tr_coef,
+                    p->gather.tgt_shot, p->gather.tgt_field, p->gather.tgt_off, p->gather.ptr, p->gather.tr,
+                    p->gather.w, p->tiles.tiles, p->resid, p->dbuf, p->partial, p->seg, p->ck.fields, p->ck.psi,
+                    p->ck.scale};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (auto &e : p->ev) cudaEventDestroy(e);
+    delete p;
+}
+
+int efwi_autotune(efwi_plan *p);   // k_fused.cu
+
+extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
+    if (!out) return fail(nullptr, EFWI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(nullptr, EFWI_ERR_ARG, "desc is NULL");
+    if (d->nx < 1 || d->nz < 1 || !(d->dx > 0) || !(d->dz > 0) || d->nt < 1 || !(d->dt > 0))
+        return fail(nullptr, EFWI_ERR_ARG, "grid sizes, spacings, nt and dt must be positive");
+    if (d->npml < 1 || d->npml > 200) return fail(nullptr, EFWI_ERR_ARG, "npml must be in [1, 200]");
+    if (!(d->pml_R > 0 && d->pml_R < 1)) return fail(nullptr, EFWI_ERR_ARG, "pml_R must be in (0, 1)");
+    if (d->ns < 1) return fail(nullptr, EFWI_ERR_ARG, "ns must be >= 1");
+    if (d->ntr < 0) return fail(nullptr, EFWI_ERR_ARG, "ntr must be >= 0");
+    if (!d->src_xz || !d->mt || !d->wavelet || !d->tr_ptr || !d->ref_vp || !d->ref_vs || !d->ref_rho)
+        return fail(nullptr, EFWI_ERR_ARG, "a required host array is NULL");
+    if (d->ntr > 0 && (!d->ch_xz || !d->ch_t)) return fail(nullptr, EFWI_ERR_ARG, "channel arrays are NULL");
+    if (d->das_mode != EFWI_DAS_STRAIN && d->das_mode != EFWI_DAS_STRAIN_RATE)
+        return fail(nullptr, EFWI_ERR_ARG, "unknown das_mode");
+    if (d->ntr > 0 && !(d->gauge > 0)) return fail(nullptr, EFWI_ERR_ARG, "gauge must be > 0");
+    if (d->ckpt_store < EFWI_STORE_FP32 || d->ckpt_store > EFWI_STORE_BF16)
+        return fail(nullptr, EFWI_ERR_ARG, "unknown ckpt_store");
+    if (d->exec != EFWI_EXEC_PLAIN && d->exec != EFWI_EXEC_BATCHED) return fail(nullptr, EFWI_ERR_ARG, "unknown exec");
+    if (d->ckpt_interval < 0) return fail(nullptr, EFWI_ERR_ARG, "ckpt_interval must be >= 0");
+    if (d->tr_ptr[0] != 0 || d->tr_ptr[d->ns] != d->ntr) return fail(nullptr, EFWI_ERR_ARG, "tr_ptr must run 0..ntr");
+    for (int s = 0; s < d->ns; ++s)
+        if (d->tr_ptr[s + 1] < d->tr_ptr[s]) return fail(nullptr, EFWI_ERR_ARG, "tr_ptr must be non-decreasing");
+    if (d->exec == EFWI_EXEC_BATCHED &&
+        ((d->tile_x != 0 || d->tile_z != 0) && (d->tile_x <= 0 || d->tile_z <= 0)))
+        return fail(nullptr, EFWI_ERR_ARG, "tile_x and tile_z must both be 0 or both positive");
+
+    const long long ncell = (long long)d->nx * d->nz;
+    double vmax = d->pml_vmax;
+    if (!(vmax > 0)) {
+        vmax = 0;
+        for (long long k = 0; k < ncell; ++k) vmax = std::max(vmax, (double)d->ref_vp[k]);
+    }
+    for (long long k = 0; k < ncell; ++k)
+        if (!(d->ref_vs[k] > 0) || !(d->ref_rho[k] > 0) || !(d->ref_vp[k] > 0))
+            return fail(nullptr, EFWI_ERR_ARG, "reference model must have Vp, Vs, rho > 0");
+    const double cfl = d->dt * vmax * std::sqrt(2.0) * (9.0 / 8.0 + 1.0 / 24.0) / std::min(d->dx, d->dz);
+    if (!(cfl < 1.0)) {
+        char b[160];
+        snprintf(b, sizeof b, "CFL number %.4f >= 1 (dt=%g, vmax=%g)", cfl, d->dt, vmax);
+        return fail(nullptr, EFWI_ERR_CFL, b);
+    }
+
+    efwi_plan *p = new (std::nothrow) efwi_plan();
+    if (!p) return fail(nullptr, EFWI_ERR_OOM, "host allocation failed");
+    p->d = *d;
+    p->d.src_xz = nullptr; p->d.mt = nullptr; p->d.wavelet = nullptr; p->d.tr_ptr = nullptr;
+    p->d.ch_xz = nullptr; p->d.ch_t = nullptr; p->d.win = nullptr;
+    p->d.ref_vp = p->d.ref_vs = p->d.ref_rho = nullptr;
+    p->d.pml_vmax = vmax;
+    const int P = d->npml + 1;
+    p->P = P;
+    const int ns = d->ns, nt = d->nt;
+    const int NZ = d->nz + 2 * P;
+    p->nzp = NZ;
+
+    // --- per-shot geometry -------------------------------------------------
+    p->shots.resize(ns);
+    long long off = 0, psx = 0, psz = 0;
+    int profx = 0;
+    for (int s = 0; s < ns; ++s) {
+        int x0 = 0, w = d->nx;
+        if (d->win) { x0 = d->win[2 * s]; w = d->win[2 * s + 1]; }
+        if (x0 < 0 || w < 1 || x0 + w > d->nx) {
+            free_plan(p);
+            return fail(nullptr, EFWI_ERR_ARG, "window of shot " + std::to_string(s) + " outside the grid");
+        }
+        ShotDev &sh = p->shots[s];
+        memset(&sh, 0, sizeof sh);
+        sh.P = P; sh.x0 = x0; sh.w = w;
+        sh.NX = w + 2 * P; sh.NZ = NZ;
+        sh.pitch = ((sh.NX + 3) / 4) * 4 + 8;
+        sh.off = off;
+        off += (((long long)(NZ + 2 * EFWI_GZ) * sh.pitch + 63) / 64) * 64;
+        sh.psx = psx; psx += (long long)NZ * 2 * P;
+        sh.psz = psz; psz += (long long)2 * P * sh.NX;
+        sh.profx = profx; profx += sh.NX;
+        sh.tr0 = d->tr_ptr[s]; sh.ntr = d->tr_ptr[s + 1] - d->tr_ptr[s];
+        sh.mxx = (float)d->mt[3 * s]; sh.mzz = (float)d->mt[3 * s + 1]; sh.mxz = (float)d->mt[3 * s + 2];
+        p->padded_cells += (long long)sh.NX * NZ;
+        p->physical_cells += (long long)w * d->nz;
+        p->max_nx = std::max(p->max_nx, sh.NX);
+        if (off > (1LL << 31) * 8) { free_plan(p); return fail(nullptr, EFWI_ERR_ARG, "problem too large"); }
+    }
+    p->fsz_total = off;
+    p->psx_total = psx; p->psz_total = psz;
+    p->H = 2 * psx + 2 * psz;
+    p->prof_x_total = profx;
+
+    // --- source injection weights --------------------------------------------
+    const double cellA = d->dx * d->dz;
+    for (int s = 0; s < ns; ++s) {
+        ShotDev &sh = p->shots[s];
+        Corner cn[4], cx[4];
+        if (!bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.0, 0.0, cn) ||
+            !bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.5, 0.5, cx)) {
+            free_plan(p);
+            return fail(nullptr, EFWI_ERR_ARG, "source " + std::to_string(s) + " outside its window");
+        }
+        for (int q = 0; q < 4; ++q) {
+            sh.inj_n[q] = local_off(sh, cn[q].i, cn[q].j); sh.inj_nw[q] = (float)(cn[q].w / cellA);
+            sh.inj_x[q] = local_off(sh, cx[q].i, cx[q].j); sh.inj_xw[q] = (float)(cx[q].w / cellA);
+        }
+    }
+
+    // --- DAS gauges: 4 components x 4 corners per trace ------------------------
+    const int ntr = d->ntr;
+    std::vector<int> h_off((size_t)std::max(ntr, 1) * 16, 0);
+    std::vector<float> h_w((size_t)std::max(ntr, 1) * 16, 0.f);
+    p->trace_shot.assign(ntr, 0);
+    // gather: (shot, field, off) -> list of (trace, weight)
+    std::map<std::tuple<int, int, int>, std::vector<std::pair<int, float>>> gmap;
+    for (int s = 0; s < ns; ++s) {
+        const ShotDev &sh = p->shots[s];
+        for (int c = d->tr_ptr[s]; c < d->tr_ptr[s + 1]; ++c) {
+            p->trace_shot[c] = s;
+            const double cx = d->ch_xz[2 * c], cz = d->ch_xz[2 * c + 1];
+            const double tx = d->ch_t[2 * c], tz = d->ch_t[2 * c + 1];
+            const double hl = 0.5 * d->gauge;
+            const double ends[2][2] = {{cx + hl * tx, cz + hl * tz}, {cx - hl * tx, cz - hl * tz}};
+            for (int k = 0; k < 4; ++k) {
+                const int e = k >> 1, field = k & 1;
+                const double sgn = e == 0 ? 1.0 : -1.0;
+                const double tcomp = field == 0 ? tx : tz;
+                Corner cr[4];
+                if (!bilinear(*d, sh, ends[e][0], ends[e][1], field == 0 ? 0.5 : 0.0, field == 0 ? 0.0 : 0.5, cr)) {
+                    free_plan(p);
+                    return fail(nullptr, EFWI_ERR_ARG,
+                                "gauge end of trace " + std::to_string(c) + " outside the window of shot " +
+                                    std::to_string(s));
+                }
+                for (int q = 0; q < 4; ++q) {
+                    const int o = local_off(sh, cr[q].i, cr[q].j);
+                    const float wq = (float)(cr[q].w * sgn * tcomp / d->gauge);
+                    h_off[(size_t)c * 16 + k * 4 + q] = o;
+                    h_w[(size_t)c * 16 + k * 4 + q] = wq;
+                    if (wq != 0.f) gmap[std::make_tuple(s, field, o)].push_back({c, wq});
+                }
+            }
+        }
+    }
+    std::vector<int> g_shot, g_field, g_off, g_ptr{0}, g_tr;
+    std::vector<float> g_w;
+    for (auto &kv : gmap) {
+        g_shot.push_back(std::get<0>(kv.first));
+        g_field.push_back(std::get<1>(kv.first));
+        g_off.push_back(std::get<2>(kv.first));
+        for (auto &e : kv.second) { g_tr.push_back(e.first); g_w.push_back(e.second); }
+        g_ptr.push_back((int)g_tr.size());
+    }
+    p->gather.n_tgt = (int)g_shot.size();
+    p->gather_ptr.assign(ns + 1, 0);
+    for (int s : g_shot) p->gather_ptr[s + 1]++;
+    for (int s = 0; s < ns; ++s) p->gather_ptr[s + 1] += p->gather_ptr[s];
+
+    // --- wavelet increments and CPML profiles ----------------------------------
+    std::vector<float> h_dw((size_t)ns * nt);
+    for (int s = 0; s < ns; ++s)
+        for (int n = 0; n < nt; ++n)
+            h_dw[(size_t)s * nt + n] =
+                (float)((double)d->wavelet[(size_t)s * (nt + 1) + n + 1] - (double)d->wavelet[(size_t)s * (nt + 1) + n]);
+    const int X = p->prof_x_total;
+    std::vector<float> h_prof(4 * (size_t)X + 4 * (size_t)NZ);
+    for (int s = 0; s < ns; ++s) {
+        const ShotDev &sh = p->shots[s];
+        cpml_axis(sh.NX, P, d->dx, d->npml, d->pml_R, vmax, d->pml_f0, d->dt, false, &h_prof[sh.profx], &h_prof[X + sh.profx]);
+        cpml_axis(sh.NX, P, d->dx, d->npml, d->pml_R, vmax, d->pml_f0, d->dt, true, &h_prof[2 * X + sh.profx],
+                  &h_prof[3 * X + sh.profx]);
+    }
+    float *zp = &h_prof[4 * (size_t)X];
+    cpml_axis(NZ, P, d->dz, d->npml, d->pml_R, vmax, d->pml_f0, d->dt, false, zp, zp + NZ);
+    cpml_axis(NZ, P, d->dz, d->npml, d->pml_R, vmax, d->pml_f0, d->dt, true, zp + 2 * NZ, zp + 3 * NZ);
+
+    // --- checkpoint schedule ---------------------------------------------------
+    int K = d->ckpt_interval;
+    if (K == 0) K = (int)std::ceil(std::sqrt((double)nt));
+    K = std::min(K, nt);
+    p->K = K;
+    p->ck.store = d->ckpt_store;
+    p->ck.n = (nt + K - 1) / K;
+
+    // --- device allocation -------------------------------------------------------
+    Alloc A{p};
+    const long long F = p->fsz_total;
+    A(&p->shots_d, (size_t)ns, "shots");
+    const bool batched = d->exec == EFWI_EXEC_BATCHED;
+    A(&p->state[0], (size_t)(5 * F), "state");
+    if (batched) A(&p->state[1], (size_t)(5 * F), "state (second buffer)");
+    A(&p->mat, (size_t)(5 * F), "materials");
+    A(&p->adj[0], (size_t)(5 * F), "adjoint state");
+    if (batched) A(&p->adj[1], (size_t)(5 * F), "adjoint state (second buffer)");
+    A(&p->G, (size_t)(5 * F), "imaging accumulators");
+    if (batched) {
+        A(&p->Gtot, (size_t)(5 * F), "Kahan totals");
+        A(&p->Gcmp, (size_t)(5 * F), "Kahan compensation");
+    }
+    A(&p->psi, (size_t)(4 * p->H), "psi");
+    A(&p->apsi, (size_t)(4 * p->H), "adjoint psi");
+    A(&p->prof, h_prof.size(), "profiles");
+    A(&p->dw, h_dw.size(), "wavelet increments");
+    A(&p->ref, (size_t)(3 * ncell), "reference model");
+    A(&p->tr_shot, (size_t)std::max(ntr, 1), "trace shots");
+    A(&p->tr_off, h_off.size(), "trace offsets");
+    A(&p->tr_w, h_w.size(), "trace weights");
+    A(&p->tr_acc, (size_t)std::max(ntr, 1), "trace accumulators");
+    A(&p->tr_coef, (size_t)std::max(ntr, 1), "trace coefficients");
+    if (p->gather.n_tgt > 0) {
+        A(&p->gather.tgt_shot, g_shot.size(), "gather");
+        A(&p->gather.tgt_field, g_field.size(), "gather");
+        A(&p->gather.tgt_off, g_off.size(), "gather");
+        A(&p->gather.ptr, g_ptr.size(), "gather");
+        A(&p->gather.tr, g_tr.size(), "gather");
+        A(&p->gather.w, g_w.size(), "gather");
+    }
+    A(&p->resid, (size_t)std::max(ntr, 1) * nt, "residual");
+    A(&p->dbuf, (size_t)std::max(ntr, 1) * nt, "data buffer");
+    A(&p->partial, (size_t)kPartials + 8, "reduction scratch");
+    A(&p->seg, (size_t)K * 2 * F, "segment buffer");
+    const size_t nck_el = (size_t)p->ck.n * 5 * F;
+    if (p->ck.store == EFWI_STORE_FP32) A((float **)&p->ck.fields, nck_el, "checkpoints");
+    else {
+        A((__half **)&p->ck.fields, nck_el, "checkpoints");
+        A(&p->ck.scale, (size_t)p->ck.n * 5 * ns, "checkpoint scales");
+    }
+    A(&p->ck.psi, (size_t)p->ck.n * 2 * p->H, "checkpoint psi");
+    if (!A.ok) {
+        free_plan(p);
+        return fail(nullptr, EFWI_ERR_OOM, A.what);
+    }
+
+    // --- upload --------------------------------------------------------------------
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (bytes) cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(p->shots_d, p->shots.data(), sizeof(ShotDev) * ns);
+    up(p->prof, h_prof.data(), h_prof.size() * 4);
+    up(p->dw, h_dw.data(), h_dw.size() * 4);
+    up(p->ref, d->ref_vp, ncell * 4);
+    up(p->ref + ncell, d->ref_vs, ncell * 4);
+    up(p->ref + 2 * ncell, d->ref_rho, ncell * 4);
+    if (ntr > 0) {
+        up(p->tr_shot, p->trace_shot.data(), 4 * (size_t)ntr);
+        up(p->tr_off, h_off.data(), 4 * h_off.size());
+        up(p->tr_w, h_w.data(), 4 * h_w.size());
+    }
+    if (p->gather.n_tgt > 0) {
+        up(p->gather.tgt_shot, g_shot.data(), 4 * g_shot.size());
+        up(p->gather.tgt_field, g_field.data(), 4 * g_field.size());
+        up(p->gather.tgt_off, g_off.data(), 4 * g_off.size());
+        up(p->gather.ptr, g_ptr.data(), 4 * g_ptr.size());
+        up(p->gather.tr, g_tr.data(), 4 * g_tr.size());
+        up(p->gather.w, g_w.data(), 4 * g_w.size());
+    }
+    p->ev.resize(4096);
+    for (auto &e : p->ev) cudaEventCreate(&e);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        std::string m = std::string("plan upload failed: ") + cudaGetErrorString(e);
+        free_plan(p);
+        return fail(nullptr, EFWI_ERR_CUDA, m);
+    }
+    if (d->exec == EFWI_EXEC_BATCHED) {
+        p->tile_x = d->tile_x; p->tile_z = d->tile_z;
+        int rc = efwi_autotune(p);
+        if (rc != EFWI_OK) {
+            std::string m = p->err;
+            free_plan(p);
+            return fail(nullptr, rc, m);
+        }
+    }
+    *out = p;
+    return EFWI_OK;
+}
+
+extern "C" int efwi_plan_destroy(efwi_plan *p) {
+    if (!p) return EFWI_OK;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return EFWI_OK;
+}
+
+extern "C" const char *efwi_last_error(const efwi_plan *p) {
+    if (p) return p->err.c_str();
+    return g_thread_err.c_str();
+}
+
+extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
+    if (!p || !info) return fail(nullptr, EFWI_ERR_ARG, "NULL argument");
+    info->ckpt_interval = p->K;
+    info->n_ckpt = p->ck.n;
+    info->tile_x = p->tile_x;
+    info->tile_z = p->tile_z;
+    info->workspace_bytes = p->bytes;
+    info->padded_cells = p->padded_cells;
+    info->physical_cells = p->physical_cells;
+    info->launches = p->launches;
+    return EFWI_OK;
+}
+
+extern "C" int efwi_prof_enable(efwi_plan *p, int every) {
+    if (!p || every < 0) return fail(p, EFWI_ERR_ARG, "bad arguments to efwi_prof_enable");
+    p->prof_every = every;
+    p->prof_counter = 0;
+    p->ev_used = 0;
+    p->prof_ms = 0;
+    p->prof_count = 0;
+    return EFWI_OK;
+}
+
+extern "C" int efwi_prof_read(efwi_plan *p, double *total_ms, long long *count) {
+    if (!p || !total_ms || !count) return fail(p, EFWI_ERR_ARG, "NULL argument");
+    double ms = 0;
+    long long c = 0;
+    for (int k = 0; k + 1 < p->ev_used; k += 2) {
+        if (cudaEventSynchronize(p->ev[k + 1]) != cudaSuccess) return fail(p, EFWI_ERR_CUDA, "event sync failed");
+        float t = 0;
+        if (cudaEventElapsedTime(&t, p->ev[k], p->ev[k + 1]) == cudaSuccess) { ms += t; ++c; }
+    }
+    *total_ms = ms;
+    *count = c;
+    p->ev_used = 0;
+    p->prof_counter = 0;
+    return EFWI_OK;
+}
+
+extern "C" int efwi_zoi_weights(int ns, int nx, int nz, double dx, double dz, const efwi_zoi_desc *z, float *b,
+                                float *bp, uint8_t *sink, efwi_stream_t stream) {
+    std::string err;
+    int rc = launch_zoi(ns, nx, nz, dx, dz, z, b, bp, sink, (cudaStream_t)stream, err);
+    if (rc != EFWI_OK) return fail(nullptr, rc, err);
+    return EFWI_OK;
+}
+
+extern "C" int efwi_regularization_grad(efwi_plan *p, const float *m, const float *b, const float *bp,
+                                        const uint8_t *sink, double eta, double *phi_reg, float *g,
+                                        efwi_stream_t stream) {
+    if (!p) return fail(nullptr, EFWI_ERR_ARG, "plan is NULL");
+    if (!m || !b || !bp || !sink || !phi_reg || !g) return fail(p, EFWI_ERR_ARG, "NULL device pointer");
+    if (!std::isfinite(eta)) return fail(p, EFWI_ERR_ARG, "eta must be finite");
+    launch_reg(p, m, b, bp, sink, eta, phi_reg, g, 0, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(p, EFWI_ERR_CUDA, cudaGetErrorString(e));
+    return EFWI_OK;
+}

@@ -1,0 +1,146 @@
+// Host-side plan object and the launchers each translation unit exports.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "efwi_common.cuh"
+
+namespace efwi {
+
+// Adjoint-source gather (the transpose of the DAS sampling): for every grid
+// cell touched by any gauge end, the list of (trace, weight) contributions,
+// summed in a fixed order so the result is deterministic.
+struct GatherCSR {
+    int n_tgt = 0;
+    int *tgt_shot = nullptr;     // [n_tgt]
+    int *tgt_field = nullptr;    // [n_tgt] 0 = vx, 1 = vz
+    int *tgt_off = nullptr;      // [n_tgt] offset within the shot block
+    int *ptr = nullptr;          // [n_tgt + 1]
+    int *tr = nullptr;           // [nnz] global trace index
+    float *w = nullptr;          // [nnz] bilinear weight * (+-t_k) / L
+};
+
+struct TileList {
+    int n = 0;
+    int4 *tiles = nullptr;       // (shot, i0, j0, unused)
+};
+
+// Checkpoint of the forward state (wavefields + CPML memory) in FP32 or
+// per-snapshot, per-field scaled FP16 / BF16.
+struct CkptStore {
+    int store = EFWI_STORE_FP32;
+    int n = 0;                   // number of checkpoints
+    void *fields = nullptr;      // n x 5 x fsz_total elements (float / half / bf16)
+    float *psi = nullptr;        // n x 2H floats (V and S blocks, always FP32)
+    float *scale = nullptr;      // n x 5 x ns per-field scales (reduced precision only)
+};
+
+}  // namespace efwi
+
+struct efwi_plan {
+    efwi_plan_desc d;                       // scalars only (pointers cleared)
+    int P = 0;
+    std::vector<efwi::ShotDev> shots;
+    efwi::ShotDev *shots_d = nullptr;
+    long long fsz_total = 0;               // floats per field kind, all shots
+    long long psx_total = 0, psz_total = 0;
+    long long H = 0;                       // 2 * psx_total + 2 * psz_total (one psi block)
+    long long padded_cells = 0, physical_cells = 0;
+    int prof_x_total = 0;
+    int max_nx = 0, nzp = 0;
+    std::vector<int> trace_shot;
+
+    // device buffers
+    // Wavefields: two buffers of 5 * fsz_total (vx, vz, sxx, szz, sxz).  The plain
+    // path updates buffer 0 in place; the batched path reads buffer scur and writes
+    // the other one (a tile reads halos that neighbouring tiles overwrite).
+    float *state[2] = {nullptr, nullptr};
+    int scur = 0;
+    float *mat = nullptr;                  // 5 * fsz_total (lambda, mu, mu_xz, b_x, b_z)
+    float *adj[2] = {nullptr, nullptr};    // adjoint wavefields, same scheme
+    int acur = 0;
+    float *G = nullptr;                    // 5 * fsz_total (per-segment or direct accumulators)
+    float *Gtot = nullptr, *Gcmp = nullptr;// Kahan totals and compensation (batched)
+    // CPML memory, 4 blocks of H = 2 psx_total + 2 psz_total floats:
+    //   [V0 | V1 | S0 | S1], V = (psi1, psi3 | psi2, psi4) of the velocity sub-step,
+    //   S = (psi5, psi8 | psi6, psi7) of the stress sub-step; x-strip arrays first.
+    float *psi = nullptr;
+    int psi_v = 0, psi_s = 0;              // current V and S blocks
+    float *apsi = nullptr;                 // adjoint CPML memory, same layout
+    int apsi_v = 0, apsi_s = 0;
+    float *prof = nullptr;                 // 4 * prof_x_total + 4 * nzp
+    float *dw = nullptr;                   // [ns][nt] (w_{n+1} - w_n)
+    float *ref = nullptr;                  // [3][nz][nx] reference model
+    int *tr_shot = nullptr;                // [ntr]
+    int *tr_off = nullptr;                 // [ntr][16] offsets within shot block
+    float *tr_w = nullptr;                 // [ntr][16] weights * (+-t) / L
+    double *tr_acc = nullptr;              // [ntr] running strain (fwd) / reverse residual sum (adj)
+    float *tr_coef = nullptr;              // [ntr] adjoint-source coefficient of the current step
+    efwi::GatherCSR gather;
+    std::vector<int> gather_ptr;           // [ns+1] per-shot range of gather targets
+    efwi::TileList tiles;
+    float *resid = nullptr;                // [ntr][nt]
+    float *dbuf = nullptr;                 // [ntr][nt]
+    double *partial = nullptr;             // reduction scratch
+    float *seg = nullptr;                  // segment buffer: K x 2 x fsz_total
+    efwi::CkptStore ck;
+    int K = 0;                             // checkpoint interval
+    int tile_x = 0, tile_z = 0;
+    size_t bytes = 0;
+    long long launches = 0;
+
+    // profiling of the dominant kernel
+    int prof_every = 0;
+    long long prof_counter = 0;
+    std::vector<cudaEvent_t> ev;           // pairs
+    int ev_used = 0;
+    double prof_ms = 0.0;
+    long long prof_count = 0;
+
+    std::string err;
+};
+
+namespace efwi {
+
+constexpr int kPartials = 1024;            // blocks of the FP64 reductions
+
+// --- k_misc.cu ---------------------------------------------------------------
+void launch_materials(efwi_plan *p, const float *vp, const float *vs, const float *rho, cudaStream_t st);
+void launch_inject(efwi_plan *p, Fields F, int n, int shot /* -1 = all */, cudaStream_t st);
+void launch_das_fwd(efwi_plan *p, Fields F, int n, float *d, int shot, cudaStream_t st);
+void launch_das_adj(efwi_plan *p, Fields A, const float *vf_x, const float *vf_z, float *Gbx, float *Gbz,
+                    int n, int shot, cudaStream_t st);
+void launch_residual(efwi_plan *p, const float *d, const float *dobs, double *phi, cudaStream_t st);
+void launch_chain_rule(efwi_plan *p, const float *vp, const float *vs, const float *rho, const float *const *G,
+                       const float *mask, float *gvp, float *gvs, float *grho, cudaStream_t st);
+void launch_kahan_fold(efwi_plan *p, cudaStream_t st);
+void launch_ckpt_save(efwi_plan *p, int slot, cudaStream_t st);
+void launch_ckpt_load(efwi_plan *p, int slot, cudaStream_t st);
+int launch_zoi(int ns, int nx, int nz, double dx, double dz, const efwi_zoi_desc *z, float *b, float *bp,
+               uint8_t *sink, cudaStream_t st, std::string &err);
+void launch_reg(efwi_plan *p, const float *m, const float *b, const float *bp, const uint8_t *sink, double eta,
+                double *phi, float *g, int accumulate_phi, cudaStream_t st);
+
+// --- k_plain.cu (shot >= 0: that shot only; shot < 0: all shots in one launch) ---
+void launch_vel_plain(efwi_plan *p, int shot, float *segx, float *segz, cudaStream_t st);
+void launch_stress_plain(efwi_plan *p, int shot, cudaStream_t st);
+void launch_adj_vel_plain(efwi_plan *p, int shot, const float *vfx, const float *vfz, cudaStream_t st);
+void launch_adj_stress_plain(efwi_plan *p, int shot, const float *vfx, const float *vfz, cudaStream_t st);
+
+// --- k_fused.cu --------------------------------------------------------------
+void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaStream_t st);
+void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaStream_t st);
+
+// helpers (plan.cu)
+Fields state_fields(efwi_plan *p, int which);   // which: 0/1 buffer
+Fields adj_fields(efwi_plan *p, int which);
+Mat materials(efwi_plan *p);
+Pml fwd_pml(efwi_plan *p, int vblk, int sblk);  // profiles + psi blocks
+Pml adj_pml(efwi_plan *p, int vblk, int sblk);
+float *psi_block(float *base, efwi_plan *p, int blk);  // blk 0,1 = V0,V1; 2,3 = S0,S1
+float *G_field(efwi_plan *p, int k);      // k: 0 lam, 1 mu, 2 muxz, 3 bx, 4 bz
+void prof_begin(efwi_plan *p, cudaStream_t st, int *slot);
+void prof_end(efwi_plan *p, cudaStream_t st, int slot);
+
+}  // namespace efwi

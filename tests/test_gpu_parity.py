@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Every comparison feeds both sides the same float32-representable inputs.
+Acceptance (FP32 time stepping): relative L2 <= 1e-4 for the data, the
+misfit and every per-component gradient.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from common import f32, rel_l2, rounded
+from oracle import elastic as E
+from oracle import extension as X
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def efwi():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2305_14130_gb300 as m
+    return m
+
+
+def dev(a, dtype=np.float32):
+    return torch.tensor(np.asarray(a, dtype), device="cuda")
+
+
+def observed(p):
+    ns = p.acq.ns
+    return f32(E.forward(p.acq, *(np.repeat(m[None], ns, 0) for m in (p.true_vp, p.true_vs, p.true_rho))))
+
+
+CASES = {
+    "tiny_strain": lambda: W.tiny(nx=40, nz=30, ns=3, nt=80, npml=6),
+    "tiny_strain_rate": lambda: W.tiny(nx=37, nz=29, ns=2, nt=70, npml=5, das_mode=W.STRAIN_RATE),
+    "tiny_windows": lambda: W.tiny(nx=48, nz=26, ns=3, nt=60, npml=4, win=[[0, 30], [9, 37], [20, 28]]),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    p = rounded(CASES[request.param]())
+    return request.param, p, observed(p)
+
+
+@pytest.fixture(scope="module")
+def oracle_grad(case):
+    name, p, d_obs = case
+    return E.gradient(p.acq, p.vp, p.vs, p.rho, d_obs), E.forward(p.acq, p.vp, p.vs, p.rho)
+
+
+@pytest.mark.parametrize("exec_", ["plain", "batched"])
+def test_forward_and_gradient_parity(efwi, case, oracle_grad, exec_):
+    name, p, d_obs = case
+    (phi_o, gvp_o, gvs_o, grho_o), d_o = oracle_grad
+    plan = efwi.Plan(p.acq, exec=exec_)
+    d = plan.forward(dev(p.vp), dev(p.vs), dev(p.rho))
+    phi, gvp, gvs, grho, d2 = plan.gradient(dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs), return_data=True)
+    torch.cuda.synchronize()
+    assert rel_l2(d.cpu().numpy(), d_o) <= TOL
+    assert torch.equal(d, d2)
+    assert abs(phi.item() - phi_o) <= TOL * abs(phi_o)
+    for g, go in ((gvp, gvp_o), (gvs, gvs_o), (grho, grho_o)):
+        assert rel_l2(g.cpu().numpy(), go) <= TOL
+    plan.close()
+
+
+def test_single_shot_200x100_parity(efwi):
+    """The 200x100 single-shot workload (nt = 1000) in full: data, misfit and gradients."""
+    p = rounded(W.single_shot_200x100())
+    d_obs = observed(p)
+    phi_o, gvp_o, gvs_o, grho_o = E.gradient(p.acq, p.vp, p.vs, p.rho, d_obs)
+    for exec_ in ("plain", "batched"):
+        plan = efwi.Plan(p.acq, exec=exec_)
+        phi, gvp, gvs, grho = plan.gradient(dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
+        torch.cuda.synchronize()
+        assert abs(phi.item() - phi_o) <= TOL * phi_o
+        for g, go in ((gvp, gvp_o), (gvs, gvs_o), (grho, grho_o)):
+            assert rel_l2(g.cpu().numpy(), go) <= TOL, exec_
+        plan.close()
+
+
+@pytest.mark.parametrize("exec_", ["plain", "batched"])
+def test_checkpointing_is_bitwise_identical_to_full_storage(efwi, exec_):
+    p = rounded(W.tiny(nx=40, nz=30, ns=2, nt=75, npml=6))
+    d_obs = observed(p)
+    args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
+    outs = []
+    for K in (p.acq.nt, 0, 7):
+        plan = efwi.Plan(p.acq, exec=exec_, ckpt_interval=K)
+        outs.append([t.clone() for t in plan.gradient(*args)])
+        plan.close()
+    torch.cuda.synchronize()
+    if exec_ == "plain":
+        for o in outs[1:]:
+            for a, b in zip(outs[0], o):
+                assert torch.equal(a, b)
+    else:
+        # the batched path folds per-segment sums with Kahan compensation, so the
+        # summation grouping depends on K; results agree to rounding
+        for o in outs[1:]:
+            for a, b in zip(outs[0][1:], o[1:]):
+                assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= 1e-6
+
+
+def test_repeat_calls_are_bitwise_identical(efwi):
+    p = rounded(W.tiny(nx=40, nz=30, ns=2, nt=50, npml=6))
+    d_obs = observed(p)
+    plan = efwi.Plan(p.acq, exec="batched")
+    args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
+    a = [t.clone() for t in plan.gradient(*args)]
+    b = [t.clone() for t in plan.gradient(*args)]
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    plan.close()
+
+
+@pytest.mark.parametrize("store,bound", [("fp16", 2e-3), ("bf16", 2e-2)])
+def test_reduced_precision_checkpoints(efwi, store, bound):
+    """Scaled FP16/BF16 checkpoints: gradient error against FP32 checkpoints.
+
+    Per element the stored state errs by at most s 2^-12 (FP16) or s 2^-9
+    (BF16), s = max |field| of that snapshot; the gradient error this causes is
+    measured here and must stay below a loose bound.
+    """
+    p = rounded(W.tiny(nx=40, nz=30, ns=2, nt=90, npml=6))
+    d_obs = observed(p)
+    args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
+    ref = efwi.Plan(p.acq, exec="batched", ckpt_interval=9)
+    g32 = [t.cpu().numpy() for t in ref.gradient(*args)[1:]]
+    red = efwi.Plan(p.acq, exec="batched", ckpt_interval=9, ckpt_store=store)
+    g16 = [t.cpu().numpy() for t in red.gradient(*args)[1:]]
+    errs = [rel_l2(a, b) for a, b in zip(g16, g32)]
+    print(f"{store} checkpoint gradient rel-L2 errors (vp, vs, rho): {errs}")
+    assert 0 < max(errs) <= bound
+    ref.close(); red.close()
+
+
+def test_zoi_weights_parity(efwi):
+    p = W.random_layered_128()
+    z = p.zoi
+    acq = p.acq
+    b, bp, sink = efwi.zoi_weights(acq.ns, acq.nx, acq.nz, acq.dx, acq.dz, z)
+    bo, bpo, sinko = X.zoi_weights(z, acq.nx, acq.nz, acq.dx, acq.dz)
+    torch.cuda.synchronize()
+    assert np.array_equal(sink.cpu().numpy(), sinko)
+    assert np.abs(b.cpu().numpy() - bo).max() <= 1e-6
+    assert np.abs(bp.cpu().numpy() - bpo).max() <= 1e-6
+
+
+@pytest.mark.parametrize("ns", [1, 2, 5])
+def test_regularization_parity(efwi, ns):
+    rng = np.random.default_rng(ns)
+    nz, nx = 23, 37
+    p = rounded(W.tiny(nx=nx, nz=nz, ns=ns, nt=10, npml=3))
+    zoi = p.zoi
+    bo, bpo, sinko = X.zoi_weights(zoi, nx, nz, p.acq.dx, p.acq.dz)
+    bo, bpo = f32(bo), f32(bpo)
+    m = f32(3000 + 100 * rng.standard_normal((ns, nz, nx)))
+    eta = 0.37
+    phi_o, g_o = X.regularization(m, bo, bpo, sinko, eta)
+    plan = efwi.Plan(p.acq, exec="batched")
+    g0 = f32(rng.standard_normal((ns, nz, nx)))
+    phi, g = plan.regularization_grad(dev(m), dev(bo), dev(bpo), dev(sinko, np.uint8), eta, g=dev(g0))
+    torch.cuda.synchronize()
+    if ns == 1:
+        assert phi.item() == 0.0
+        assert np.array_equal(g.cpu().numpy(), g0.astype(np.float32))
+    else:
+        assert abs(phi.item() - phi_o) <= 1e-10 * phi_o
+        assert rel_l2(g.cpu().numpy() - g0, g_o) <= 1e-5
+    plan.close()
+
+
+def test_extended_objective_parity(efwi):
+    p = rounded(W.tiny(nx=40, nz=30, ns=3, nt=60, npml=6))
+    d_obs = observed(p)
+    acq = p.acq
+    bo, bpo, sinko = X.zoi_weights(p.zoi, acq.nx, acq.nz, acq.dx, acq.dz)
+    bo, bpo = f32(bo), f32(bpo)
+    eta = (1e-3, 2e-3, 5e-3)
+    phi_d_o = E.misfit(E.forward(acq, p.vp, p.vs, p.rho), d_obs)
+    phi_r_o = sum(X.regularization(m, bo, bpo, sinko, e)[0] for m, e in zip((p.vp, p.vs, p.rho), eta))
+    plan = efwi.Plan(acq, exec="batched")
+    pd, pr = plan.extended_objective(dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs), eta, dev(bo), dev(bpo),
+                                     dev(sinko, np.uint8))
+    torch.cuda.synchronize()
+    assert abs(pd.item() - phi_d_o) <= TOL * phi_d_o
+    assert abs(pr.item() - phi_r_o) <= 1e-9 * phi_r_o
+    plan.close()
+
+
+def test_guided_wave_full_size_sampled(efwi):
+    """1000x300 grid, 32 shots, nt = 4000 in the batched launch configuration.
+
+    The oracle checks sampled outputs: the first 400 time samples (P and S
+    arrivals at the fibre) of one shot; samples before n do not depend on
+    later steps.
+    """
+    p = rounded(W.guided_wave_1000x300())
+    acq = p.acq
+    plan = efwi.Plan(acq, exec="batched")
+    d = plan.forward(dev(p.vp), dev(p.vs), dev(p.rho))
+    torch.cuda.synchronize()
+    d = d.cpu().numpy()
+    assert np.isfinite(d).all()
+    import copy
+    short = copy.deepcopy(acq)
+    short.nt = 400
+    short.wavelet = acq.wavelet[:, :401]
+    for s in (17,):
+        ref = E.Shot(short, s, p.vp[s], p.vs[s], p.rho[s]).forward()[0]
+        a, b = acq.tr_ptr[s], acq.tr_ptr[s + 1]
+        assert rel_l2(d[a:b, :400], ref) <= TOL
+    plan.close()
