@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--ckpt-store", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--ns", type=int, default=32)
     ap.add_argument("--nt", type=int, default=4000)
     return ap.parse_args()
@@ -110,6 +111,45 @@ def peaks():
         return float(j["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# Algorithmic bytes per padded cell of one launch of the two stencil kernels
+# (FP32 words each launch must move at least once):
+#   fused forward step: read vx vz sxx szz sxz + lambda mu mu_xz b_x b_z, write 5 = 15 words
+#   fused adjoint step: read 5 adjoint fields + 5 materials + forward vx vz + 5 imaging
+#                       sums, write 5 adjoint fields + 5 imaging sums = 27 words
+#   plain stress half-step: read vx vz + 3 stresses + lambda mu mu_xz, write 3 = 11 words
+#   plain adjoint stress half-step: read 2 + 2 + 3 + 3 + 2 + 3, write 3 + 3 = 21 words
+KERNELS = {
+    ("batched", "step"): ("k_step_fused (forward time step, all shots)", 60.0),
+    ("batched", "adj"): ("k_adj_fused (adjoint time step + imaging, all shots)", 108.0),
+    ("plain", "step"): ("k_stress (forward stress half-step, one shot)", 44.0),
+    ("plain", "adj"): ("k_adj_stress (adjoint stress half-step + imaging, one shot)", 84.0),
+}
+
+
+def roofline(exec_, info, prof, nt, ns):
+    """Roofline entries of the dominant and of the other stencil kernel."""
+    hbm, peak_kind = peaks()
+    cells = info["padded_cells"] if exec_ == "batched" else info["padded_cells"] / ns
+    per_grad = {"step": 2 * nt if info["ckpt_interval"] < nt else nt, "adj": nt}
+    out = []
+    for k in ("step", "adj"):
+        ms, n = prof[k]
+        if not n:
+            continue
+        name, bpc = KERNELS[(exec_, k)]
+        avg = ms / n / 1e3
+        achieved = bpc * cells / avg / 1e9
+        out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": None, "kernel": name, "bytes_per_cell": bpc, "cells_per_launch": cells,
+                    "peak_kind": peak_kind, "launches_timed": n, "avg_us": avg * 1e6,
+                    "time_share_est": avg * per_grad[k]})
+    tot = sum(r["time_share_est"] for r in out) or 1.0
+    for r in out:
+        r["time_share_est"] = r["time_share_est"] / tot
+    out.sort(key=lambda r: -r["time_share_est"])
+    return (out + [None, None])[:2]
 
 
 def cpu_baseline(p, budget_s=15.0):
@@ -221,7 +261,7 @@ def run_ours(args):
         dist.barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    prof_ms, prof_n = plan.prof_read()
+    prof = {k: plan.prof_read(k) for k in ("step", "adj")}
     plan.prof_enable(0)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -231,18 +271,7 @@ def run_ours(args):
     cells = ns * acq.nx * acq.nz * acq.nt
     value = cells * world / s_per_grad / 1e9
     info = plan.info()
-
-    # roofline of the dominant kernel (the forward stress half-step over all shots)
-    padded = info["padded_cells"]
-    bytes_per_cell = 44.0   # read vx, vz, sxx, szz, sxz, lambda, mu, mu_xz; write sxx, szz, sxz
-    hbm, peak_kind = peaks()
-    roof = None
-    if prof_n:
-        avg = prof_ms / prof_n / 1e3
-        achieved = bytes_per_cell * padded / avg / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "k_stress (forward stress half-step, all shots)",
-                "peak_kind": peak_kind, "launches_timed": prof_n, "avg_us": avg * 1e6}
+    roofs = roofline(args.exec, info, prof, acq.nt, ns)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -298,7 +327,7 @@ def run_ours(args):
         pl.close()
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(p)
 
     if rank == 0:
@@ -307,10 +336,13 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "exec": args.exec, "ckpt_store": args.ckpt_store,
                            "ckpt_interval": info["ckpt_interval"], "tile": [info["tile_x"], info["tile_z"]],
+                           "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
                            "l2": "working set > L2 (wavefields, checkpoints, data >> 129 MB)",
                            "parallelism": f"replicas x{world} (independent extended problems)"},
-                "s_per_gradient": s_per_grad, "padded_Gcell_updates_s": padded * acq.nt * world / s_per_grad / 1e9,
-                "gpu_launches": launches_per_step * args.steps, "clocks": ck, "roofline": roof,
+                "s_per_gradient": s_per_grad,
+                "padded_Gcell_updates_s": info["padded_cells"] * acq.nt * world / s_per_grad / 1e9,
+                "gpu_launches": launches_per_step * args.steps, "clocks": ck, "roofline": roofs[0],
+                "roofline_other": roofs[1],
                 "e2e": e2e, "plain_fp32": plain, "cpu_baseline": cpu,
                 "workspace_GB": info["workspace_bytes"] / 1e9}
         print(json.dumps(line), flush=True)

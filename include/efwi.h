@@ -135,7 +135,8 @@ typedef struct efwi_plan_desc {
 typedef struct efwi_plan_info_t {
     int ckpt_interval;          /* steps per checkpoint segment */
     int n_ckpt;                 /* checkpoints per gradient */
-    int tile_x, tile_z;         /* stencil tile in use */
+    int tile_x, tile_z;         /* forward stencil tile in use (EXEC_BATCHED) */
+    int adj_tile_x, adj_tile_z; /* adjoint stencil tile in use (EXEC_BATCHED) */
     size_t workspace_bytes;     /* device bytes owned by the plan */
     long long padded_cells;     /* sum over shots of padded (nx_w + 2P)(nz + 2P) */
     long long physical_cells;   /* sum over shots of window width * nz */
@@ -217,13 +218,16 @@ int efwi_extended_objective(efwi_plan *plan, const float *vp, const float *vs, c
                             const float *bp, const uint8_t *sink, double *phi_data,
                             double *phi_reg, efwi_stream_t stream);
 
-/* Kernel timing for measurements: when every > 0, the plan brackets every
- * every-th launch of its dominant stencil kernel with CUDA events on the
- * launching stream (non-graph launches only).  efwi_prof_read synchronises
- * those events and returns their summed elapsed milliseconds and count,
- * then resets the counters.                                                 */
+/* Kernel timing for measurements.  When every > 0 the plan brackets every
+ * every-th launch of its two dominant stencil kernels with CUDA events on the
+ * launching stream (inside the captured graphs too, where each replay
+ * re-records them).  efwi_prof_read synchronises the events of one kernel
+ * (EFWI_KERNEL_STEP: the forward time step; EFWI_KERNEL_ADJ: the adjoint time
+ * step) and returns their summed elapsed milliseconds and the number of timed
+ * launches.  efwi_prof_enable drops the cached graphs.                     */
+enum efwi_kernel { EFWI_KERNEL_STEP = 0, EFWI_KERNEL_ADJ = 1 };
 int efwi_prof_enable(efwi_plan *plan, int every);
-int efwi_prof_read(efwi_plan *plan, double *total_ms, long long *count);
+int efwi_prof_read(efwi_plan *plan, int kernel, double *total_ms, long long *count);
 
 #ifdef __cplusplus
 }

@@ -186,10 +186,12 @@ class Plan:
     def prof_enable(self, every: int):
         self._check(self._lib.efwi_prof_enable(self._h, int(every)))
 
-    def prof_read(self):
+    def prof_read(self, kernel: str = "step"):
+        """(summed ms, launches timed) of the 'step' (forward) or 'adj' stencil kernel."""
         ms = C.c_double()
         cnt = C.c_longlong()
-        self._check(self._lib.efwi_prof_read(self._h, C.byref(ms), C.byref(cnt)))
+        k = {"step": 0, "adj": 1}[kernel]
+        self._check(self._lib.efwi_prof_read(self._h, k, C.byref(ms), C.byref(cnt)))
         return ms.value, cnt.value
 
 

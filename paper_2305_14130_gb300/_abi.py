@@ -30,6 +30,7 @@ class PlanDesc(C.Structure):
 
 class PlanInfo(C.Structure):
     _fields_ = [("ckpt_interval", C.c_int), ("n_ckpt", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
+                ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong)]
 
@@ -52,7 +53,7 @@ SIGNATURES = {
     "efwi_regularization_grad": (C.c_int, [VP, VP, VP, VP, VP, C.c_double, VP, VP, VP]),
     "efwi_extended_objective": (C.c_int, [VP, VP, VP, VP, VP, PD, VP, VP, VP, VP, VP, VP]),
     "efwi_prof_enable": (C.c_int, [VP, C.c_int]),
-    "efwi_prof_read": (C.c_int, [VP, PD, C.POINTER(C.c_longlong)]),
+    "efwi_prof_read": (C.c_int, [VP, C.c_int, PD, C.POINTER(C.c_longlong)]),
 }
 
 _lib = None

@@ -20,7 +20,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libefwi_gb300.so")
 SOURCES = ["plan.cu", "engine.cu", "k_plain.cu", "k_misc.cu", "k_fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+# -fmad=false: no implicit multiply-add contraction, so every kernel (plain and
+# fused, every tile-shape instantiation) rounds each expression identically and
+# results do not depend on the work decomposition.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+         "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc_path() -> str:
@@ -51,6 +55,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     nvcc = nvcc_path()
     deps = _deps()
+    stamp = os.path.join(BUILD, "flags.txt")
+    sig = " ".join(ARCH + FLAGS + list(extra_flags) + [nvcc])
+    if not os.path.exists(stamp) or open(stamp).read() != sig:
+        force = True
     objs = []
     jobs = []
     for src in SOURCES:
@@ -74,6 +82,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         tmp = LIB + ".tmp"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(sig)
     return LIB
 
 

@@ -10,6 +10,7 @@
 //   first forward pass already keeps every v^{n+1/2} and nothing is recomputed.
 // EXEC_PLAIN launches one kernel per half-step and shot; EXEC_BATCHED runs all
 // shots in fused launches and replays the time loop from CUDA graphs.
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -84,9 +85,9 @@ void adjoint_step(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaS
 
 namespace efwi {
 
-// Forward pass over all steps; keeps checkpoints when ck != 0 and every
-// v^{n+1/2} in the segment buffer when the plan stores all steps.
-int run_forward(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
+// Forward pass over all steps; keeps checkpoints when ck and every v^{n+1/2}
+// in the segment buffer when the plan stores all steps.
+void forward_loop(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
     reset_forward_state(p, st);
     const bool full = p->K >= p->d.nt;
     for (int n = 0; n < p->d.nt; ++n) {
@@ -95,10 +96,9 @@ int run_forward(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
         float *sz = (ck && full) ? seg_z(p, n) : nullptr;
         forward_step(p, n, d, sx, sz, st);
     }
-    return cuda_status(p, "forward time loop");
 }
 
-int run_adjoint(efwi_plan *p, cudaStream_t st) {
+void adjoint_loop(efwi_plan *p, cudaStream_t st) {
     const long long F = p->fsz_total;
     for (int k = 0; k < 2; ++k)
         if (p->adj[k]) cudaMemsetAsync(p->adj[k], 0, sizeof(float) * 5 * F, st);
@@ -121,6 +121,52 @@ int run_adjoint(efwi_plan *p, cudaStream_t st) {
         }
         for (int n = n1 - 1; n >= n0; --n) adjoint_step(p, n, seg_x(p, n - n0), seg_z(p, n - n0), st);
         if (p->Gtot) launch_kahan_fold(p, st);
+    }
+}
+
+// Capture body() once into gc (on the plan's capture stream), then replay it on st.
+template <class Body>
+int replay(efwi_plan *p, GraphCache &gc, cudaStream_t st, Body body) {
+    if (!gc.exec) {
+        const long long l0 = p->launches;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return cuda_status(p, "begin graph capture");
+        body(p->cap);
+        if (cudaStreamEndCapture(p->cap, &g) != cudaSuccess || !g) return cuda_status(p, "end graph capture");
+        cudaError_t e = cudaGraphInstantiate(&gc.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            gc.exec = nullptr;
+            return cuda_status(p, "graph instantiate");
+        }
+        gc.launches = p->launches - l0;
+        p->launches = l0;
+    }
+    if (cudaGraphLaunch(gc.exec, st) != cudaSuccess) return cuda_status(p, "graph launch");
+    p->launches += gc.launches;
+    return EFWI_OK;
+}
+
+int run_forward(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
+    if (p->d.exec == EFWI_EXEC_BATCHED && p->use_graphs) {
+        int rc = replay(p, ck ? p->g_fwd_ck : p->g_fwd, st,
+                        [&](cudaStream_t cs) { forward_loop(p, p->dbuf, ck, cs); });
+        if (rc) return rc;
+        if (d && d != p->dbuf && p->d.ntr > 0)
+            cudaMemcpyAsync(d, p->dbuf, sizeof(float) * (size_t)p->d.ntr * p->d.nt, cudaMemcpyDeviceToDevice, st);
+    } else {
+        forward_loop(p, d, ck, st);
+    }
+    return cuda_status(p, "forward time loop");
+}
+
+int run_adjoint(efwi_plan *p, cudaStream_t st) {
+    if (p->d.exec == EFWI_EXEC_BATCHED && p->use_graphs) {
+        int rc = replay(p, p->g_adj, st, [&](cudaStream_t cs) { adjoint_loop(p, cs); });
+        if (rc) return rc;
+    } else {
+        adjoint_loop(p, st);
     }
     return cuda_status(p, "adjoint time loop");
 }

@@ -331,7 +331,7 @@ void launch_stress_plain(efwi_plan *p, int shot, cudaStream_t st) {
     StepArgs a = step_args(p, shot, nullptr, nullptr);
     dim3 b(32, 8);
     int slot;
-    prof_begin(p, st, &slot);
+    prof_begin(p, st, &slot, EFWI_KERNEL_STEP);
     k_stress<<<grid_of(p, shot, b), b, 0, st>>>(a);
     prof_end(p, st, slot);
     p->launches++;
@@ -347,7 +347,10 @@ void launch_adj_vel_plain(efwi_plan *p, int shot, const float *vfx, const float 
 void launch_adj_stress_plain(efwi_plan *p, int shot, const float *vfx, const float *vfz, cudaStream_t st) {
     AdjArgs a = adj_args(p, shot, vfx, vfz);
     dim3 b(32, 8);
+    int slot;
+    prof_begin(p, st, &slot, EFWI_KERNEL_ADJ);
     k_adj_stress<<<grid_of(p, shot, b), b, 0, st>>>(a);
+    prof_end(p, st, slot);
     p->launches++;
 }
 

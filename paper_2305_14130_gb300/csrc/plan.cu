@@ -128,17 +128,27 @@ Pml fwd_pml(efwi_plan *p, int vblk, int sblk) { return make_pml(p, p->psi, vblk,
 Pml adj_pml(efwi_plan *p, int vblk, int sblk) { return make_pml(p, p->apsi, vblk, sblk); }
 float *G_field(efwi_plan *p, int k) { return p->G + k * p->fsz_total; }
 
-void prof_begin(efwi_plan *p, cudaStream_t st, int *slot) {
+// Inside a stream capture an event record becomes a graph node (re-recorded by
+// every replay) only with cudaEventRecordExternal.
+static void record_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+}
+
+void prof_begin(efwi_plan *p, cudaStream_t st, int *slot, int kind) {
     *slot = -1;
     if (p->prof_every <= 0) return;
-    if ((p->prof_counter++ % p->prof_every) != 0) return;
+    if ((p->prof_counter[kind]++ % p->prof_every) != 0) return;
     if (p->ev_used + 2 > (int)p->ev.size()) return;
     *slot = p->ev_used;
+    p->ev_kind[*slot / 2] = kind;
     p->ev_used += 2;
-    cudaEventRecord(p->ev[*slot], st);
+    record_event(p->ev[*slot], st);
 }
 void prof_end(efwi_plan *p, cudaStream_t st, int slot) {
-    if (slot >= 0) cudaEventRecord(p->ev[slot + 1], st);
+    if (slot >= 0) record_event(p->ev[slot + 1], st);
 }
 
 }  // namespace efwi
@@ -148,10 +158,13 @@ static void free_plan(efwi_plan *p) {
     void *ptrs[] = {p->shots_d, p->state[0], p->state[1], p->mat, p->adj[0], p->adj[1], p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
                     p->prof, p->dw, p->ref, p->tr_shot, p->tr_off, p->tr_w, p->tr_acc, p->tr_coef,
                     p->gather.tgt_shot, p->gather.tgt_field, p->gather.tgt_off, p->gather.ptr, p->gather.tr,
-                    p->gather.w, p->tiles.tiles, p->resid, p->dbuf, p->partial, p->seg, p->ck.fields, p->ck.psi,
+                    p->gather.w, p->tiles.tiles, p->adj_tiles.tiles, p->resid, p->dbuf, p->partial, p->seg, p->ck.fields, p->ck.psi,
                     p->ck.scale};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj})
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (p->cap) cudaStreamDestroy(p->cap);
     for (auto &e : p->ev) cudaEventDestroy(e);
     delete p;
 }
@@ -411,7 +424,9 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
         up(p->gather.tr, g_tr.data(), 4 * g_tr.size());
         up(p->gather.w, g_w.data(), 4 * g_w.size());
     }
-    p->ev.resize(4096);
+    p->ev.resize(8192);
+    p->ev_kind.assign(4096, 0);
+    cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
     for (auto &e : p->ev) cudaEventCreate(&e);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -450,6 +465,8 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->n_ckpt = p->ck.n;
     info->tile_x = p->tile_x;
     info->tile_z = p->tile_z;
+    info->adj_tile_x = p->adj_tile_x;
+    info->adj_tile_z = p->adj_tile_z;
     info->workspace_bytes = p->bytes;
     info->padded_cells = p->padded_cells;
     info->physical_cells = p->physical_cells;
@@ -459,27 +476,27 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
 
 extern "C" int efwi_prof_enable(efwi_plan *p, int every) {
     if (!p || every < 0) return fail(p, EFWI_ERR_ARG, "bad arguments to efwi_prof_enable");
+    cudaDeviceSynchronize();
+    for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj})
+        if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
     p->prof_every = every;
-    p->prof_counter = 0;
+    p->prof_counter[0] = p->prof_counter[1] = 0;
     p->ev_used = 0;
-    p->prof_ms = 0;
-    p->prof_count = 0;
     return EFWI_OK;
 }
 
-extern "C" int efwi_prof_read(efwi_plan *p, double *total_ms, long long *count) {
-    if (!p || !total_ms || !count) return fail(p, EFWI_ERR_ARG, "NULL argument");
+extern "C" int efwi_prof_read(efwi_plan *p, int kernel, double *total_ms, long long *count) {
+    if (!p || !total_ms || !count || kernel < 0 || kernel > 1) return fail(p, EFWI_ERR_ARG, "bad arguments to efwi_prof_read");
     double ms = 0;
     long long c = 0;
     for (int k = 0; k + 1 < p->ev_used; k += 2) {
+        if (p->ev_kind[k / 2] != kernel) continue;
         if (cudaEventSynchronize(p->ev[k + 1]) != cudaSuccess) return fail(p, EFWI_ERR_CUDA, "event sync failed");
         float t = 0;
         if (cudaEventElapsedTime(&t, p->ev[k], p->ev[k + 1]) == cudaSuccess) { ms += t; ++c; }
     }
     *total_ms = ms;
     *count = c;
-    p->ev_used = 0;
-    p->prof_counter = 0;
     return EFWI_OK;
 }
 

@@ -21,8 +21,15 @@ struct GatherCSR {
     float *w = nullptr;          // [nnz] bilinear weight * (+-t_k) / L
 };
 
+// An instantiated CUDA graph of a time loop and the kernels it launches.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+};
+
 struct TileList {
     int n = 0;
+    int tx = 0, tz = 0;          // tile shape
     int4 *tiles = nullptr;       // (shot, i0, j0, unused)
 };
 
@@ -79,24 +86,30 @@ struct efwi_plan {
     float *tr_coef = nullptr;              // [ntr] adjoint-source coefficient of the current step
     efwi::GatherCSR gather;
     std::vector<int> gather_ptr;           // [ns+1] per-shot range of gather targets
-    efwi::TileList tiles;
+    efwi::TileList tiles;                  // forward fused-step work items
+    efwi::TileList adj_tiles;              // adjoint fused-step work items
     float *resid = nullptr;                // [ntr][nt]
     float *dbuf = nullptr;                 // [ntr][nt]
     double *partial = nullptr;             // reduction scratch
     float *seg = nullptr;                  // segment buffer: K x 2 x fsz_total
     efwi::CkptStore ck;
     int K = 0;                             // checkpoint interval
-    int tile_x = 0, tile_z = 0;
+    int tile_x = 0, tile_z = 0;            // forward tile
+    int adj_tile_x = 0, adj_tile_z = 0;    // adjoint tile
     size_t bytes = 0;
     long long launches = 0;
 
-    // profiling of the dominant kernel
+    // batched path: time loops captured once and replayed
+    cudaStream_t cap = nullptr;            // capture stream (never executes work)
+    efwi::GraphCache g_fwd, g_fwd_ck, g_adj;
+    bool use_graphs = true;
+
+    // timing of the dominant kernels (event pairs, tagged by kernel kind)
     int prof_every = 0;
-    long long prof_counter = 0;
-    std::vector<cudaEvent_t> ev;           // pairs
+    long long prof_counter[2] = {0, 0};
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
     int ev_used = 0;
-    double prof_ms = 0.0;
-    long long prof_count = 0;
 
     std::string err;
 };
@@ -140,7 +153,7 @@ Pml fwd_pml(efwi_plan *p, int vblk, int sblk);  // profiles + psi blocks
 Pml adj_pml(efwi_plan *p, int vblk, int sblk);
 float *psi_block(float *base, efwi_plan *p, int blk);  // blk 0,1 = V0,V1; 2,3 = S0,S1
 float *G_field(efwi_plan *p, int k);      // k: 0 lam, 1 mu, 2 muxz, 3 bx, 4 bz
-void prof_begin(efwi_plan *p, cudaStream_t st, int *slot);
+void prof_begin(efwi_plan *p, cudaStream_t st, int *slot, int kind);
 void prof_end(efwi_plan *p, cudaStream_t st, int slot);
 
 }  // namespace efwi
