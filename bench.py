@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--stencil", default="auto", choices=["auto", "loads", "tma"])
+    ap.add_argument("--tile", default="0x0", help="forward tile, e.g. 32x16 (0x0 = autotune)")
     ap.add_argument("--ns", type=int, default=32)
     ap.add_argument("--nt", type=int, default=4000)
     return ap.parse_args()
@@ -220,7 +222,8 @@ def run_ours(args):
     acq = p.acq
     dev = lambda a, dt=np.float32: torch.tensor(np.asarray(a, dt), device="cuda")
     vp, vs, rho = dev(p.vp), dev(p.vs), dev(p.rho)
-    plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store)
+    tile = tuple(int(v) for v in args.tile.lower().split("x"))
+    plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store, stencil=args.stencil, tile=tile)
     # observed data: the same sources in the model with the Gaussian anomaly
     ns = acq.ns
     tv = lambda m: dev(np.repeat(np.asarray(m)[None], ns, 0))
@@ -337,6 +340,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "exec": args.exec, "ckpt_store": args.ckpt_store,
                            "ckpt_interval": info["ckpt_interval"], "tile": [info["tile_x"], info["tile_z"]],
                            "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
+                           "stencil": {1: "loads", 2: "tma"}.get(info["stencil"], "?"), "stages": info["stages"],
                            "l2": "working set > L2 (wavefields, checkpoints, data >> 129 MB)",
                            "parallelism": f"replicas x{world} (independent extended problems)"},
                 "s_per_gradient": s_per_grad,

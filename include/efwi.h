@@ -73,6 +73,9 @@ enum efwi_store { EFWI_STORE_FP32 = 0, EFWI_STORE_FP16 = 1, EFWI_STORE_BF16 = 2 
  *  BATCHED all shots (any window sizes) in one fused launch per time step,
  *          the time loop captured and replayed as CUDA graphs               */
 enum efwi_exec { EFWI_EXEC_PLAIN = 0, EFWI_EXEC_BATCHED = 1 };
+/* tile staging of the batched forward step: per-thread loads, or TMA bulk
+ * tensor copies into double-buffered shared memory (persistent CTAs)        */
+enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_TMA = 2 };
 
 /*
  * Problem description (host memory; copied by efwi_plan_create).
@@ -105,6 +108,9 @@ enum efwi_exec { EFWI_EXEC_PLAIN = 0, EFWI_EXEC_BATCHED = 1 };
  *   ckpt_store         EFWI_STORE_* precision of the checkpoints
  *   exec               EFWI_EXEC_*
  *   tile_x, tile_z     stencil tile for EXEC_BATCHED (0, 0 = autotune at plan creation)
+ *   stencil            EFWI_STENCIL_*: how EXEC_BATCHED stages a tile in shared
+ *                      memory (AUTO lets the autotuner choose); every choice gives
+ *                      bitwise-identical results
  */
 typedef struct efwi_plan_desc {
     int nx, nz;
@@ -129,6 +135,7 @@ typedef struct efwi_plan_desc {
     int ckpt_store;
     int exec;
     int tile_x, tile_z;
+    int stencil;
 } efwi_plan_desc;
 
 /* What a plan chose and holds (filled by efwi_plan_info). */
@@ -137,6 +144,8 @@ typedef struct efwi_plan_info_t {
     int n_ckpt;                 /* checkpoints per gradient */
     int tile_x, tile_z;         /* forward stencil tile in use (EXEC_BATCHED) */
     int adj_tile_x, adj_tile_z; /* adjoint stencil tile in use (EXEC_BATCHED) */
+    int stencil;                /* EFWI_STENCIL_* used by the forward step */
+    int stages;                 /* shared-memory pipeline depth of the TMA forward step */
     size_t workspace_bytes;     /* device bytes owned by the plan */
     long long padded_cells;     /* sum over shots of padded (nx_w + 2P)(nz + 2P) */
     long long physical_cells;   /* sum over shots of window width * nz */
@@ -171,6 +180,12 @@ int efwi_plan_destroy(efwi_plan *plan);
 const char *efwi_last_error(const efwi_plan *plan);
 
 int efwi_plan_info(const efwi_plan *plan, efwi_plan_info_t *info);
+
+/* Synchronise the stream and report device-side failures of earlier calls on
+ * this plan: EFWI_ERR_TIMEOUT if a kernel gave up a bounded wait (its results
+ * are then invalid), EFWI_ERR_CUDA for an asynchronous CUDA error.  The device
+ * flag is cleared.                                                           */
+int efwi_sync_status(efwi_plan *plan, efwi_stream_t stream);
 
 /* Forward modelling of every shot with its own component (eqs. 1-3; first
  * term of eq. 8).

@@ -23,7 +23,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import EfwiError, STORE, EXEC
+from ._abi import EfwiError, STORE, EXEC, STENCIL
 
 __all__ = ["Plan", "zoi_weights", "EfwiError", "load_library"]
 
@@ -66,7 +66,7 @@ class Plan:
     """
 
     def __init__(self, acq, exec: str = "batched", ckpt_interval: int = 0, ckpt_store: str = "fp32",
-                 tile=(0, 0)):
+                 tile=(0, 0), stencil: str = "auto"):
         lib = _abi.load()
         a = acq
         self.nx, self.nz, self.nt = int(a.nx), int(a.nz), int(a.nt)
@@ -101,6 +101,7 @@ class Plan:
         d.ckpt_store = STORE[ckpt_store]
         d.exec = EXEC[exec]
         d.tile_x, d.tile_z = int(tile[0]), int(tile[1])
+        d.stencil = STENCIL[stencil]
         self.exec, self.ckpt_store = exec, ckpt_store
         h = C.c_void_p()
         torch.cuda.init()
@@ -182,6 +183,10 @@ class Plan:
             _ptr(sink, "sink", n, torch.uint8), _ptr(pd, "phi_data", 1, torch.float64),
             _ptr(pr, "phi_reg", 1, torch.float64), _stream()))
         return pd, pr
+
+    def sync_status(self):
+        """Synchronise the current stream; raise on device-side failures of earlier calls."""
+        self._check(self._lib.efwi_sync_status(self._h, _stream()))
 
     def prof_enable(self, every: int):
         self._check(self._lib.efwi_prof_enable(self._h, int(every)))

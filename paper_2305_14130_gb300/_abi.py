@@ -12,6 +12,7 @@ STATUS = {0: "EFWI_OK", -1: "EFWI_ERR_ARG", -2: "EFWI_ERR_CFL", -3: "EFWI_ERR_OO
 DAS_STRAIN, DAS_STRAIN_RATE = 0, 1
 STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXEC = {"plain": 0, "batched": 1}
+STENCIL = {"auto": 0, "loads": 1, "tma": 2}
 
 PD = C.POINTER(C.c_double)
 PF = C.POINTER(C.c_float)
@@ -25,12 +26,14 @@ class PlanDesc(C.Structure):
                 ("src_xz", PD), ("mt", PD), ("wavelet", PF), ("ntr", C.c_int), ("tr_ptr", PI),
                 ("ch_xz", PD), ("ch_t", PD), ("gauge", C.c_double), ("das_mode", C.c_int), ("win", PI),
                 ("ref_vp", PF), ("ref_vs", PF), ("ref_rho", PF), ("ckpt_interval", C.c_int),
-                ("ckpt_store", C.c_int), ("exec", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int)]
+                ("ckpt_store", C.c_int), ("exec", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
+                ("stencil", C.c_int)]
 
 
 class PlanInfo(C.Structure):
     _fields_ = [("ckpt_interval", C.c_int), ("n_ckpt", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
-                ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int),
+                ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("stencil", C.c_int),
+                ("stages", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong)]
 
@@ -46,6 +49,7 @@ SIGNATURES = {
     "efwi_plan_destroy": (C.c_int, [VP]),
     "efwi_last_error": (C.c_char_p, [VP]),
     "efwi_plan_info": (C.c_int, [VP, C.POINTER(PlanInfo)]),
+    "efwi_sync_status": (C.c_int, [VP, VP]),
     "efwi_forward": (C.c_int, [VP, VP, VP, VP, VP, VP]),
     "efwi_adjoint_gradient": (C.c_int, [VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP]),
     "efwi_zoi_weights": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(ZoiDesc),

@@ -55,21 +55,25 @@ __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
 
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = a.tiles[t];
-        const ShotDev s = a.shots[tl.x];
+        const ShotDev *sp = a.shots + tl.x;
+        const int NX = sp->NX, NZ = sp->NZ, PP = sp->P, profx = sp->profx, pitch = sp->pitch;
+        const long long off = sp->off, psx = sp->psx, psz = sp->psz;
+        const bool edge = (tl.w & 2) != 0;
         const int i0 = tl.y, j0 = tl.z;
-        const long long P = s.pitch;
-        const int rowlim = s.pitch - EFWI_GX;
+        const int rowlim = pitch - EFWI_GX;
+        const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
 
         // 1. sigma^n with a 4-cell halo (zero outside the padded grid)
         constexpr int Q4 = SX / 4;
+#pragma unroll 4
         for (int q = tid; q < 3 * SZ * Q4; q += kThreads) {
             const int f = q / (SZ * Q4), r = q - f * SZ * Q4;
             const int y = r / Q4, x4 = r - y * Q4;
             const int i = i0 - 4 + 4 * x4, j = j0 - 4 + y;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (j >= 0 && j < s.NZ && i + 4 <= rowlim) {
+            if (j >= 0 && j < NZ && i + 4 <= rowlim) {
                 const float *src = f == 0 ? a.in.sxx : (f == 1 ? a.in.szz : a.in.sxz);
-                v = __ldg(reinterpret_cast<const float4 *>(src + cell_of(s, i, j)));
+                v = __ldg(reinterpret_cast<const float4 *>(src + off + (j + EFWI_GZ) * pitch + (i + EFWI_GX)));
             }
             reinterpret_cast<float4 *>(sm + f * SX * SZ + y * SX)[x4] = v;
         }
@@ -80,33 +84,36 @@ __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
             const int y = q / VX, x = q - y * VX;
             const int i = i0 - 2 + x, j = j0 - 2 + y;
             float vx = 0.f, vz = 0.f;
-            if (i >= 0 && i < s.NX && j >= 0 && j < s.NZ) {
-                const long long c = cell_of(s, i, j);
+            if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
+                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                 const int o = (y + 2) * SX + (x + 2);       // (i, j) in sigma staging
-                float e1 = (C1 * (sxx[o + 1] - sxx[o]) + C2 * (sxx[o + 2] - sxx[o - 1])) * a.rdx;
-                float e2 = (C1 * (sxz[o] - sxz[o - SX]) + C2 * (sxz[o + SX] - sxz[o - 2 * SX])) * a.rdz;
-                float e3 = (C1 * (sxz[o] - sxz[o - 1]) + C2 * (sxz[o + 1] - sxz[o - 2])) * a.rdx;
-                float e4 = (C1 * (szz[o + SX] - szz[o]) + C2 * (szz[o + 2 * SX] - szz[o - SX])) * a.rdz;
-                const bool own = i >= i0 && i < i0 + TX && j >= j0 && j < j0 + TZ;
-                const int xs = xstrip(s, i), zs = zstrip(s, j);
-                if (xs >= 0) {
-                    const long long k = s.psx + (long long)j * 2 * s.P + xs;
-                    const int pq = s.profx + i;
-                    const float p1 = a.pml.bx_h[pq] * a.pml.x[0][k] + a.pml.ax_h[pq] * e1;
-                    const float p3 = a.pml.bx_i[pq] * a.pml.x[1][k] + a.pml.ax_i[pq] * e3;
-                    if (own) { a.n1[k] = p1; a.n3[k] = p3; }
-                    e1 += p1; e3 += p3;
+                float e1 = (C1 * (sxx[o + 1] - sxx[o]) + C2 * (sxx[o + 2] - sxx[o - 1])) * rdx;
+                float e2 = (C1 * (sxz[o] - sxz[o - SX]) + C2 * (sxz[o + SX] - sxz[o - 2 * SX])) * rdz;
+                float e3 = (C1 * (sxz[o] - sxz[o - 1]) + C2 * (sxz[o + 1] - sxz[o - 2])) * rdx;
+                float e4 = (C1 * (szz[o + SX] - szz[o]) + C2 * (szz[o + 2 * SX] - szz[o - SX])) * rdz;
+                const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2;
+                if (edge) {
+                    const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                    const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                    if (xs >= 0) {
+                        const long long k = psx + (long long)j * 2 * PP + xs;
+                        const int pq = profx + i;
+                        const float p1 = a.pml.bx_h[pq] * a.pml.x[0][k] + a.pml.ax_h[pq] * e1;
+                        const float p3 = a.pml.bx_i[pq] * a.pml.x[1][k] + a.pml.ax_i[pq] * e3;
+                        if (own) { a.n1[k] = p1; a.n3[k] = p3; }
+                        e1 += p1; e3 += p3;
+                    }
+                    if (zs >= 0) {
+                        const long long k = psz + (long long)zs * NX + i;
+                        const float p2 = a.pml.bz_i[j] * a.pml.z[0][k] + a.pml.az_i[j] * e2;
+                        const float p4 = a.pml.bz_h[j] * a.pml.z[1][k] + a.pml.az_h[j] * e4;
+                        if (own) { a.n2[k] = p2; a.n4[k] = p4; }
+                        e2 += p2; e4 += p4;
+                    }
                 }
-                if (zs >= 0) {
-                    const long long k = s.psz + (long long)zs * s.NX + i;
-                    const float p2 = a.pml.bz_i[j] * a.pml.z[0][k] + a.pml.az_i[j] * e2;
-                    const float p4 = a.pml.bz_h[j] * a.pml.z[1][k] + a.pml.az_h[j] * e4;
-                    if (own) { a.n2[k] = p2; a.n4[k] = p4; }
-                    e2 += p2; e4 += p4;
-                }
-                vx = __ldg(a.in.vx + c) + a.dt * __ldg(a.M.bx + c) * (e1 + e2);
-                vz = __ldg(a.in.vz + c) + a.dt * __ldg(a.M.bz + c) * (e3 + e4);
-                if (own) {
+                vx = __ldg(a.in.vx + c) + dt * __ldg(a.M.bx + c) * (e1 + e2);
+                vz = __ldg(a.in.vz + c) + dt * __ldg(a.M.bz + c) * (e3 + e4);
+                if (own && (!edge || (i < NX && j < NZ))) {
                     a.out.vx[c] = vx;
                     a.out.vz[c] = vz;
                     if (a.segx) { a.segx[c] = vx; a.segz[c] = vz; }
@@ -118,47 +125,53 @@ __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
         __syncthreads();
 
         // 3. sigma^{n+1} on the tile, then the moment-tensor source
-        const float dwn = a.dw[(long long)tl.x * a.nt + a.n];
+        const bool inj = (tl.w & 1) != 0;
+        const float dwn = inj ? a.dw[(long long)tl.x * a.nt + a.n] : 0.f;
         for (int q = tid; q < TX * TZ; q += kThreads) {
             const int y = q / TX, x = q - y * TX;
             const int i = i0 + x, j = j0 + y;
-            if (i >= s.NX || j >= s.NZ) continue;
-            const long long c = cell_of(s, i, j);
+            if (edge && (i >= NX || j >= NZ)) continue;
+            const int lc = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+            const long long c = off + lc;
             const int o = (y + 2) * VX + (x + 2);           // (i, j) in velocity staging
-            float f1 = (C1 * (svx[o] - svx[o - 1]) + C2 * (svx[o + 1] - svx[o - 2])) * a.rdx;
-            float f2 = (C1 * (svz[o] - svz[o - VX]) + C2 * (svz[o + VX] - svz[o - 2 * VX])) * a.rdz;
-            float f3 = (C1 * (svx[o + VX] - svx[o]) + C2 * (svx[o + 2 * VX] - svx[o - VX])) * a.rdz;
-            float f4 = (C1 * (svz[o + 1] - svz[o]) + C2 * (svz[o + 2] - svz[o - 1])) * a.rdx;
-            const int xs = xstrip(s, i), zs = zstrip(s, j);
-            if (xs >= 0) {
-                const long long k = s.psx + (long long)j * 2 * s.P + xs;
-                const int pq = s.profx + i;
-                const float p5 = a.pml.bx_i[pq] * a.pml.x[2][k] + a.pml.ax_i[pq] * f1;
-                const float p8 = a.pml.bx_h[pq] * a.pml.x[3][k] + a.pml.ax_h[pq] * f4;
-                a.pml.x[2][k] = p5; a.pml.x[3][k] = p8;
-                f1 += p5; f4 += p8;
-            }
-            if (zs >= 0) {
-                const long long k = s.psz + (long long)zs * s.NX + i;
-                const float p6 = a.pml.bz_i[j] * a.pml.z[2][k] + a.pml.az_i[j] * f2;
-                const float p7 = a.pml.bz_h[j] * a.pml.z[3][k] + a.pml.az_h[j] * f3;
-                a.pml.z[2][k] = p6; a.pml.z[3][k] = p7;
-                f2 += p6; f3 += p7;
+            float f1 = (C1 * (svx[o] - svx[o - 1]) + C2 * (svx[o + 1] - svx[o - 2])) * rdx;
+            float f2 = (C1 * (svz[o] - svz[o - VX]) + C2 * (svz[o + VX] - svz[o - 2 * VX])) * rdz;
+            float f3 = (C1 * (svx[o + VX] - svx[o]) + C2 * (svx[o + 2 * VX] - svx[o - VX])) * rdz;
+            float f4 = (C1 * (svz[o + 1] - svz[o]) + C2 * (svz[o + 2] - svz[o - 1])) * rdx;
+            if (edge) {
+                const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                if (xs >= 0) {
+                    const long long k = psx + (long long)j * 2 * PP + xs;
+                    const int pq = profx + i;
+                    const float p5 = a.pml.bx_i[pq] * a.pml.x[2][k] + a.pml.ax_i[pq] * f1;
+                    const float p8 = a.pml.bx_h[pq] * a.pml.x[3][k] + a.pml.ax_h[pq] * f4;
+                    a.pml.x[2][k] = p5; a.pml.x[3][k] = p8;
+                    f1 += p5; f4 += p8;
+                }
+                if (zs >= 0) {
+                    const long long k = psz + (long long)zs * NX + i;
+                    const float p6 = a.pml.bz_i[j] * a.pml.z[2][k] + a.pml.az_i[j] * f2;
+                    const float p7 = a.pml.bz_h[j] * a.pml.z[3][k] + a.pml.az_h[j] * f3;
+                    a.pml.z[2][k] = p6; a.pml.z[3][k] = p7;
+                    f2 += p6; f3 += p7;
+                }
             }
             const int os = (y + 4) * SX + (x + 4);          // (i, j) in sigma staging
             const float lam = __ldg(a.M.lam + c), mu2 = 2.f * __ldg(a.M.mu + c);
             const float tr = lam * (f1 + f2);
-            float nxx = sxx[os] + a.dt * (tr + mu2 * f1);
-            float nzz = szz[os] + a.dt * (tr + mu2 * f2);
-            float nxz = sxz[os] + a.dt * __ldg(a.M.muxz + c) * (f3 + f4);
-            const int lc = (int)(c - s.off);
+            float nxx = sxx[os] + dt * (tr + mu2 * f1);
+            float nzz = szz[os] + dt * (tr + mu2 * f2);
+            float nxz = sxz[os] + dt * __ldg(a.M.muxz + c) * (f3 + f4);
+            if (inj) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (lc == s.inj_n[k]) {
-                    nxx -= s.mxx * dwn * s.inj_nw[k];
-                    nzz -= s.mzz * dwn * s.inj_nw[k];
+                for (int k = 0; k < 4; ++k) {
+                    if (lc == sp->inj_n[k]) {
+                        nxx -= sp->mxx * dwn * sp->inj_nw[k];
+                        nzz -= sp->mzz * dwn * sp->inj_nw[k];
+                    }
+                    if (lc == sp->inj_x[k]) nxz -= sp->mxz * dwn * sp->inj_xw[k];
                 }
-                if (lc == s.inj_x[k]) nxz -= s.mxz * dwn * s.inj_xw[k];
             }
             a.out.sxx[c] = nxx;
             a.out.szz[c] = nzz;
@@ -194,44 +207,50 @@ __global__ void __launch_bounds__(kThreads) k_adj_fused(AdjArgsF a) {
 
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = a.tiles[t];
-        const ShotDev s = a.shots[tl.x];
+        const ShotDev *sp = a.shots + tl.x;
+        const int NX = sp->NX, NZ = sp->NZ, PP = sp->P, profx = sp->profx, pitch = sp->pitch, w = sp->w;
+        const long long off = sp->off, psx = sp->psx, psz = sp->psz;
+        const bool edge = (tl.w & 4) != 0;      // 4-cell halo touches a strip or the grid edge
         const int i0 = tl.y, j0 = tl.z;
-        const long long P = s.pitch;
+        const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
 
         // 1. f^ on the tile + 4-cell halo; the tile's stress-sub-step PML memory advances
         for (int q = tid; q < SX * SZ; q += kThreads) {
             const int y = q / SX, x = q - y * SX;
             const int i = i0 - 4 + x, j = j0 - 4 + y;
             float g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f;
-            if (i >= 0 && i < s.NX && j >= 0 && j < s.NZ) {
-                const long long c = cell_of(s, i, j);
+            if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
+                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                 const float hxx = __ldg(a.in.sxx + c), hzz = __ldg(a.in.szz + c), hxz = __ldg(a.in.sxz + c);
                 const float lam = __ldg(a.M.lam + c), l2m = lam + 2.f * __ldg(a.M.mu + c);
-                const float Ex = a.dt * (l2m * hxx + lam * hzz);
-                const float Ez = a.dt * (lam * hxx + l2m * hzz);
-                const float Exz = a.dt * __ldg(a.M.muxz + c) * hxz;
+                const float Ex = dt * (l2m * hxx + lam * hzz);
+                const float Ez = dt * (lam * hxx + l2m * hzz);
+                const float Exz = dt * __ldg(a.M.muxz + c) * hxz;
                 g1 = Ex; g2 = Ez; g3 = Exz; g4 = Exz;
-                const bool own = i >= i0 && i < i0 + TX && j >= j0 && j < j0 + TZ;
-                const int xs = xstrip(s, i), zs = zstrip(s, j);
-                if (xs >= 0) {
-                    const long long k = s.psx + (long long)j * 2 * s.P + xs;
-                    const int pq = s.profx + i;
-                    const float P5 = a.pml.x[2][k], P8 = a.pml.x[3][k];
-                    g1 += a.pml.ax_i[pq] * (P5 + Ex);
-                    g4 += a.pml.ax_h[pq] * (P8 + Exz);
-                    if (own) {
-                        a.n5[k] = a.pml.bx_i[pq] * (P5 + Ex);
-                        a.n8[k] = a.pml.bx_h[pq] * (P8 + Exz);
+                if (edge) {
+                    const bool own = x >= 4 && x < TX + 4 && y >= 4 && y < TZ + 4;
+                    const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                    const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                    if (xs >= 0) {
+                        const long long k = psx + (long long)j * 2 * PP + xs;
+                        const int pq = profx + i;
+                        const float P5 = a.pml.x[2][k], P8 = a.pml.x[3][k];
+                        g1 += a.pml.ax_i[pq] * (P5 + Ex);
+                        g4 += a.pml.ax_h[pq] * (P8 + Exz);
+                        if (own) {
+                            a.n5[k] = a.pml.bx_i[pq] * (P5 + Ex);
+                            a.n8[k] = a.pml.bx_h[pq] * (P8 + Exz);
+                        }
                     }
-                }
-                if (zs >= 0) {
-                    const long long k = s.psz + (long long)zs * s.NX + i;
-                    const float P6 = a.pml.z[2][k], P7 = a.pml.z[3][k];
-                    g2 += a.pml.az_i[j] * (P6 + Ez);
-                    g3 += a.pml.az_h[j] * (P7 + Exz);
-                    if (own) {
-                        a.n6[k] = a.pml.bz_i[j] * (P6 + Ez);
-                        a.n7[k] = a.pml.bz_h[j] * (P7 + Exz);
+                    if (zs >= 0) {
+                        const long long k = psz + (long long)zs * NX + i;
+                        const float P6 = a.pml.z[2][k], P7 = a.pml.z[3][k];
+                        g2 += a.pml.az_i[j] * (P6 + Ez);
+                        g3 += a.pml.az_h[j] * (P7 + Exz);
+                        if (own) {
+                            a.n6[k] = a.pml.bz_i[j] * (P6 + Ez);
+                            a.n7[k] = a.pml.bz_h[j] * (P7 + Exz);
+                        }
                     }
                 }
             }
@@ -244,44 +263,47 @@ __global__ void __launch_bounds__(kThreads) k_adj_fused(AdjArgsF a) {
             const int y = q / VX, x = q - y * VX;
             const int i = i0 - 2 + x, j = j0 - 2 + y;
             float h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f;
-            if (i >= 0 && i < s.NX && j >= 0 && j < s.NZ) {
-                const long long c = cell_of(s, i, j);
+            if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
+                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                 const int o = (y + 2) * SX + (x + 2);
-                const float inc_x = -(C1 * (f1s[o + 1] - f1s[o]) + C2 * (f1s[o + 2] - f1s[o - 1])) * a.rdx
-                                    - (C1 * (f3s[o] - f3s[o - SX]) + C2 * (f3s[o + SX] - f3s[o - 2 * SX])) * a.rdz;
-                const float inc_z = -(C1 * (f2s[o + SX] - f2s[o]) + C2 * (f2s[o + 2 * SX] - f2s[o - SX])) * a.rdz
-                                    - (C1 * (f4s[o] - f4s[o - 1]) + C2 * (f4s[o + 1] - f4s[o - 2])) * a.rdx;
+                const float inc_x = -(C1 * (f1s[o + 1] - f1s[o]) + C2 * (f1s[o + 2] - f1s[o - 1])) * rdx
+                                    - (C1 * (f3s[o] - f3s[o - SX]) + C2 * (f3s[o + SX] - f3s[o - 2 * SX])) * rdz;
+                const float inc_z = -(C1 * (f2s[o + SX] - f2s[o]) + C2 * (f2s[o + 2 * SX] - f2s[o - SX])) * rdz
+                                    - (C1 * (f4s[o] - f4s[o - 1]) + C2 * (f4s[o + 1] - f4s[o - 2])) * rdx;
                 const float vx = __ldg(a.in.vx + c) + inc_x;
                 const float vz = __ldg(a.in.vz + c) + inc_z;
-                const float qx = a.dt * __ldg(a.M.bx + c) * vx, qz = a.dt * __ldg(a.M.bz + c) * vz;
+                const float qx = dt * __ldg(a.M.bx + c) * vx, qz = dt * __ldg(a.M.bz + c) * vz;
                 h1 = qx; h2 = qx; h3 = qz; h4 = qz;
-                const bool own = i >= i0 && i < i0 + TX && j >= j0 && j < j0 + TZ;
-                const int xs = xstrip(s, i), zs = zstrip(s, j);
-                if (xs >= 0) {
-                    const long long k = s.psx + (long long)j * 2 * s.P + xs;
-                    const int pq = s.profx + i;
-                    const float P1 = a.pml.x[0][k], P3 = a.pml.x[1][k];
-                    h1 += a.pml.ax_h[pq] * (P1 + qx);
-                    h3 += a.pml.ax_i[pq] * (P3 + qz);
-                    if (own) {
-                        a.n1[k] = a.pml.bx_h[pq] * (P1 + qx);
-                        a.n3[k] = a.pml.bx_i[pq] * (P3 + qz);
+                const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
+                if (edge) {
+                    const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                    const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                    if (xs >= 0) {
+                        const long long k = psx + (long long)j * 2 * PP + xs;
+                        const int pq = profx + i;
+                        const float P1 = a.pml.x[0][k], P3 = a.pml.x[1][k];
+                        h1 += a.pml.ax_h[pq] * (P1 + qx);
+                        h3 += a.pml.ax_i[pq] * (P3 + qz);
+                        if (own) {
+                            a.n1[k] = a.pml.bx_h[pq] * (P1 + qx);
+                            a.n3[k] = a.pml.bx_i[pq] * (P3 + qz);
+                        }
                     }
-                }
-                if (zs >= 0) {
-                    const long long k = s.psz + (long long)zs * s.NX + i;
-                    const float P2 = a.pml.z[0][k], P4 = a.pml.z[1][k];
-                    h2 += a.pml.az_i[j] * (P2 + qx);
-                    h4 += a.pml.az_h[j] * (P4 + qz);
-                    if (own) {
-                        a.n2[k] = a.pml.bz_i[j] * (P2 + qx);
-                        a.n4[k] = a.pml.bz_h[j] * (P4 + qz);
+                    if (zs >= 0) {
+                        const long long k = psz + (long long)zs * NX + i;
+                        const float P2 = a.pml.z[0][k], P4 = a.pml.z[1][k];
+                        h2 += a.pml.az_i[j] * (P2 + qx);
+                        h4 += a.pml.az_h[j] * (P4 + qz);
+                        if (own) {
+                            a.n2[k] = a.pml.bz_i[j] * (P2 + qx);
+                            a.n4[k] = a.pml.bz_h[j] * (P4 + qz);
+                        }
                     }
                 }
                 if (own) {
                     a.out.vx[c] = vx;
                     a.out.vz[c] = vz;
-                    if (i >= s.P - 1 && i <= s.P + s.w && j >= s.P - 1 && j <= s.NZ - s.P) {
+                    if (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP)) {
                         a.Gbx[c] += __ldg(a.vfx + c) * inc_x;
                         a.Gbz[c] += __ldg(a.vfz + c) * inc_z;
                     }
@@ -295,24 +317,24 @@ __global__ void __launch_bounds__(kThreads) k_adj_fused(AdjArgsF a) {
         for (int q = tid; q < TX * TZ; q += kThreads) {
             const int y = q / TX, x = q - y * TX;
             const int i = i0 + x, j = j0 + y;
-            if (i >= s.NX || j >= s.NZ) continue;
-            const long long c = cell_of(s, i, j);
+            if (edge && (i >= NX || j >= NZ)) continue;
+            const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
             const float hxx = __ldg(a.in.sxx + c), hzz = __ldg(a.in.szz + c), hxz = __ldg(a.in.sxz + c);
-            if (i >= s.P && i < s.P + s.w && j >= s.P && j < s.NZ - s.P) {
-                const float fx = dbwd(a.vfx, c, 1) * a.rdx;
-                const float fz = dbwd(a.vfz, c, P) * a.rdz;
-                a.Glam[c] += a.dt * (hxx + hzz) * (fx + fz);
-                a.Gmu[c] += 2.f * a.dt * (hxx * fx + hzz * fz);
+            if (!edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP)) {
+                const float fx = dbwd(a.vfx, c, 1) * rdx;
+                const float fz = dbwd(a.vfz, c, pitch) * rdz;
+                a.Glam[c] += dt * (hxx + hzz) * (fx + fz);
+                a.Gmu[c] += 2.f * dt * (hxx * fx + hzz * fz);
             }
-            if (i >= s.P - 1 && i < s.P + s.w && j >= s.P - 1 && j < s.NZ - s.P) {
-                const float fxz = dfwd(a.vfx, c, P) * a.rdz + dfwd(a.vfz, c, 1) * a.rdx;
-                a.Gmuxz[c] += a.dt * hxz * fxz;
+            if (!edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP)) {
+                const float fxz = dfwd(a.vfx, c, pitch) * rdz + dfwd(a.vfz, c, 1) * rdx;
+                a.Gmuxz[c] += dt * hxz * fxz;
             }
             const int o = (y + 2) * VX + (x + 2);
-            a.out.sxx[c] = hxx - (C1 * (e1s[o] - e1s[o - 1]) + C2 * (e1s[o + 1] - e1s[o - 2])) * a.rdx;
-            a.out.szz[c] = hzz - (C1 * (e4s[o] - e4s[o - VX]) + C2 * (e4s[o + VX] - e4s[o - 2 * VX])) * a.rdz;
-            a.out.sxz[c] = hxz - (C1 * (e2s[o + VX] - e2s[o]) + C2 * (e2s[o + 2 * VX] - e2s[o - VX])) * a.rdz
-                               - (C1 * (e3s[o + 1] - e3s[o]) + C2 * (e3s[o + 2] - e3s[o - 1])) * a.rdx;
+            a.out.sxx[c] = hxx - (C1 * (e1s[o] - e1s[o - 1]) + C2 * (e1s[o + 1] - e1s[o - 2])) * rdx;
+            a.out.szz[c] = hzz - (C1 * (e4s[o] - e4s[o - VX]) + C2 * (e4s[o + VX] - e4s[o - 2 * VX])) * rdz;
+            a.out.sxz[c] = hxz - (C1 * (e2s[o + VX] - e2s[o]) + C2 * (e2s[o + 2 * VX] - e2s[o - VX])) * rdz
+                               - (C1 * (e3s[o + 1] - e3s[o]) + C2 * (e3s[o + 2] - e3s[o - 1])) * rdx;
         }
         __syncthreads();
     }
@@ -370,15 +392,32 @@ bool shape_ok(int tx, int tz) {
     return false;
 }
 
+// Work items (shot, i0, j0, flags).  flags bit 0: the tile holds a source
+// injection cell; bit 1 (bit 2): the tile or its 2-cell (4-cell) halo touches
+// a CPML strip or leaves the padded grid, so kernels take the checked path.
 std::vector<int4> make_tiles(efwi_plan *p, int tx, int tz) {
     std::vector<int4> t;
     for (int s = 0; s < p->d.ns; ++s) {
         const ShotDev &sh = p->shots[s];
         for (int j0 = 0; j0 < sh.NZ; j0 += tz)
-            for (int i0 = 0; i0 < sh.NX; i0 += tx) t.push_back(make_int4(s, i0, j0, 0));
+            for (int i0 = 0; i0 < sh.NX; i0 += tx) {
+                int flags = 0;
+                for (int q = 0; q < 4; ++q)
+                    for (int o : {sh.inj_n[q], sh.inj_x[q]}) {
+                        const int j = o / sh.pitch - EFWI_GZ, i = o % sh.pitch - EFWI_GX;
+                        if (i >= i0 && i < i0 + tx && j >= j0 && j < j0 + tz) flags |= 1;
+                    }
+                for (int h : {2, 4}) {
+                    const int xa = i0 - h, xb = i0 + tx + h, za = j0 - h, zb = j0 + tz + h;
+                    if (xa < sh.P || xb > sh.NX - sh.P || za < sh.P || zb > sh.NZ - sh.P) flags |= h;
+                }
+                t.push_back(make_int4(s, i0, j0, flags));
+            }
     }
     return t;
 }
+
+}  // namespace
 
 int upload_tiles(efwi_plan *p, TileList &tl, int tx, int tz) {
     std::vector<int4> t = make_tiles(p, tx, tz);
@@ -391,6 +430,8 @@ int upload_tiles(efwi_plan *p, TileList &tl, int tx, int tz) {
     tl.tz = tz;
     return EFWI_OK;
 }
+
+namespace {
 
 FwdArgs fwd_args(efwi_plan *p, int n, float *segx, float *segz) {
     FwdArgs a;
@@ -438,10 +479,14 @@ AdjArgsF adj_args_f(efwi_plan *p, const float *vfx, const float *vfz) {
 }  // namespace
 
 void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaStream_t st) {
-    FwdArgs a = fwd_args(p, n, vseg_x, vseg_z);
     int slot;
     prof_begin(p, st, &slot, EFWI_KERNEL_STEP);
-    EFWI_DISPATCH(p->tiles.tx, p->tiles.tz, fwd_launch, a, a.ntiles, st);
+    if (p->stencil == EFWI_STENCIL_TMA) {
+        launch_step_tma(p, n, vseg_x, vseg_z, st);
+    } else {
+        FwdArgs a = fwd_args(p, n, vseg_x, vseg_z);
+        EFWI_DISPATCH(p->tiles.tx, p->tiles.tz, fwd_launch, a, a.ntiles, st);
+    }
     prof_end(p, st, slot);
     p->launches++;
     p->scur ^= 1;
@@ -465,57 +510,88 @@ void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, c
 
 using namespace efwi;
 
-// Tile autotuner: times a few fused forward steps and adjoint steps of the
-// plan's own shots for every compiled tile shape and keeps the fastest (the
-// shapes change no arithmetic, only the work decomposition).
+// Tile autotuner: times a few fused forward and adjoint steps of the plan's
+// own shots for every compiled variant (staging kind x tile shape) and keeps
+// the fastest.  Variants change only the work decomposition and staging, never
+// the arithmetic, so the choice does not change results.
+namespace {
+
+struct Variant {
+    int kind, tx, tz, nst;
+};
+
+float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+    float *vs_x = p->seg, *vs_z = p->seg + p->fsz_total;
+    const int reps = 3;
+    float t = 0;
+    for (int w = 0; w < 2; ++w) {              // warm-up, then timed
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r) {
+            if (adj) launch_adj_fused(p, 0, vs_x, vs_z, st);
+            else launch_step_fused(p, 0, vs_x, vs_z, st);
+        }
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t, e0, e1);
+    }
+    return cudaGetLastError() == cudaSuccess ? t : 1e30f;
+}
+
+int select_fwd(efwi_plan *p, const Variant &v) {
+    p->stencil = v.kind;
+    int rc = upload_tiles(p, p->tiles, v.tx, v.tz);
+    if (!rc && v.kind == EFWI_STENCIL_TMA) rc = tma_prepare_fwd(p, v.tx, v.tz, v.nst);
+    p->tile_x = v.tx;
+    p->tile_z = v.tz;
+    return rc;
+}
+
+}  // namespace
+
 int efwi_autotune(efwi_plan *p) {
     set_all_attrs();
+    const int want = p->d.stencil;
     const bool fixed = p->tile_x > 0 && p->tile_z > 0;
-    if (fixed && !shape_ok(p->tile_x, p->tile_z)) {
-        p->err = "tile shape not among the compiled shapes (32x8, 32x16, 64x8, 64x16, 32x32, 128x8, 64x32)";
+    std::vector<Variant> fwd, adj;
+    for (auto &s : kShapes) {
+        if (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)) continue;
+        if (want != EFWI_STENCIL_TMA) fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        for (int nst = 2; nst <= 4; ++nst)
+            if (want != EFWI_STENCIL_LOADS && tma_shape_ok(s.tx, s.tz, nst))
+                fwd.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, nst});
+        adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+    }
+    if (fwd.empty() || adj.empty()) {
+        p->err = "no compiled stencil variant matches the requested tile/stencil "
+                 "(loads: 32x8 32x16 64x8 64x16 32x32 128x8 64x32; tma: 32x8 32x16 64x8 64x16)";
         return EFWI_ERR_ARG;
     }
-    if (fixed) {
-        int rc = upload_tiles(p, p->tiles, p->tile_x, p->tile_z);
-        if (!rc) rc = upload_tiles(p, p->adj_tiles, p->tile_x, p->tile_z);
-        p->adj_tile_x = p->tile_x; p->adj_tile_z = p->tile_z;
-        return rc;
-    }
-    cudaStream_t st;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best_f = 1e30f, best_a = 1e30f;
-    int bf = 0, ba = 0;
-    const int reps = 3;
-    for (int k = 0; k < kNumShapes; ++k) {
-        const int tx = kShapes[k].tx, tz = kShapes[k].tz;
-        if (upload_tiles(p, p->tiles, tx, tz) || upload_tiles(p, p->adj_tiles, tx, tz)) continue;
-        float *vs_x = p->seg, *vs_z = p->seg + p->fsz_total;
-        for (int w = 0; w < 2; ++w) {          // warm-up, then timed
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < reps; ++r) launch_step_fused(p, 0, vs_x, vs_z, st);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
+    int rc = EFWI_OK;
+    Variant bf = fwd[0], ba = adj[0];
+    if (fwd.size() > 1 || adj.size() > 1) {
+        cudaStream_t st;
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (auto &v : fwd) {
+            if (select_fwd(p, v)) continue;
+            const float t = time_steps(p, false, st, e0, e1);
+            if (t < best) { best = t; bf = v; }
         }
-        float tf = 0;
-        cudaEventElapsedTime(&tf, e0, e1);
-        for (int w = 0; w < 2; ++w) {
-            cudaEventRecord(e0, st);
-            for (int r = 0; r < reps; ++r) launch_adj_fused(p, 0, vs_x, vs_z, st);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
+        best = 1e30f;
+        for (auto &v : adj) {
+            if (upload_tiles(p, p->adj_tiles, v.tx, v.tz)) continue;
+            const float t = time_steps(p, true, st, e0, e1);
+            if (t < best) { best = t; ba = v; }
         }
-        float ta = 0;
-        cudaEventElapsedTime(&ta, e0, e1);
-        if (tf < best_f) { best_f = tf; bf = k; }
-        if (ta < best_a) { best_a = ta; ba = k; }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaStreamDestroy(st);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaStreamDestroy(st);
-    // the tuning runs touched workspace only; clear what the next call expects zeroed
+    // the timing runs touched workspace only; clear what the next call expects zeroed
+    cudaDeviceSynchronize();
     for (int k = 0; k < 2; ++k)
         if (p->state[k]) cudaMemset(p->state[k], 0, sizeof(float) * 5 * p->fsz_total);
     for (int k = 0; k < 2; ++k)
@@ -524,16 +600,20 @@ int efwi_autotune(efwi_plan *p) {
     cudaMemset(p->apsi, 0, sizeof(float) * 4 * p->H);
     cudaMemset(p->G, 0, sizeof(float) * 5 * p->fsz_total);
     cudaMemset(p->seg, 0, sizeof(float) * 2 * p->fsz_total);
+    cudaMemset(p->dev_err, 0, sizeof(int));
     p->scur = p->acur = p->psi_v = p->psi_s = p->apsi_v = p->apsi_s = 0;
     p->launches = 0;
-    p->tile_x = kShapes[bf].tx; p->tile_z = kShapes[bf].tz;
-    p->adj_tile_x = kShapes[ba].tx; p->adj_tile_z = kShapes[ba].tz;
-    int rc = upload_tiles(p, p->tiles, p->tile_x, p->tile_z);
-    if (!rc) rc = upload_tiles(p, p->adj_tiles, p->adj_tile_x, p->adj_tile_z);
+    p->prof_counter[0] = p->prof_counter[1] = 0;
+    p->ev_used = 0;
+    rc = select_fwd(p, bf);
+    if (!rc) rc = upload_tiles(p, p->adj_tiles, ba.tx, ba.tz);
+    p->adj_tile_x = ba.tx;
+    p->adj_tile_z = ba.tz;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         p->err = std::string("autotune: ") + cudaGetErrorString(e);
         return EFWI_ERR_CUDA;
     }
+    if (rc && p->err.empty()) p->err = "autotune: could not prepare the selected variant";
     return rc;
 }

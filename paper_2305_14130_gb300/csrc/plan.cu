@@ -155,7 +155,7 @@ void prof_end(efwi_plan *p, cudaStream_t st, int slot) {
 
 static void free_plan(efwi_plan *p) {
     if (!p) return;
-    void *ptrs[] = {p->shots_d, p->state[0], p->state[1], p->mat, p->adj[0], p->adj[1], p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
+    void *ptrs[] = {p->shots_d, p->state[0], p->mat, p->adj[0], p->fwd_maps, p->dev_err, p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
                     p->prof, p->dw, p->ref, p->tr_shot, p->tr_off, p->tr_w, p->tr_acc, p->tr_coef,
                     p->gather.tgt_shot, p->gather.tgt_field, p->gather.tgt_off, p->gather.ptr, p->gather.tr,
                     p->gather.w, p->tiles.tiles, p->adj_tiles.tiles, p->resid, p->dbuf, p->partial, p->seg, p->ck.fields, p->ck.psi,
@@ -197,6 +197,8 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (d->exec == EFWI_EXEC_BATCHED &&
         ((d->tile_x != 0 || d->tile_z != 0) && (d->tile_x <= 0 || d->tile_z <= 0)))
         return fail(nullptr, EFWI_ERR_ARG, "tile_x and tile_z must both be 0 or both positive");
+    if (d->stencil < EFWI_STENCIL_AUTO || d->stencil > EFWI_STENCIL_TMA)
+        return fail(nullptr, EFWI_ERR_ARG, "unknown stencil");
 
     const long long ncell = (long long)d->nx * d->nz;
     double vmax = d->pml_vmax;
@@ -357,11 +359,11 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     const long long F = p->fsz_total;
     A(&p->shots_d, (size_t)ns, "shots");
     const bool batched = d->exec == EFWI_EXEC_BATCHED;
-    A(&p->state[0], (size_t)(5 * F), "state");
-    if (batched) A(&p->state[1], (size_t)(5 * F), "state (second buffer)");
+    // the batched path's two state buffers are one allocation (one tensor map covers both)
+    A(&p->state[0], (size_t)((batched ? 10 : 5) * F), "state");
     A(&p->mat, (size_t)(5 * F), "materials");
-    A(&p->adj[0], (size_t)(5 * F), "adjoint state");
-    if (batched) A(&p->adj[1], (size_t)(5 * F), "adjoint state (second buffer)");
+    A(&p->adj[0], (size_t)((batched ? 10 : 5) * F), "adjoint state");
+    A(&p->dev_err, (size_t)1, "device error flag");
     A(&p->G, (size_t)(5 * F), "imaging accumulators");
     if (batched) {
         A(&p->Gtot, (size_t)(5 * F), "Kahan totals");
@@ -399,6 +401,10 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (!A.ok) {
         free_plan(p);
         return fail(nullptr, EFWI_ERR_OOM, A.what);
+    }
+    if (batched) {
+        p->state[1] = p->state[0] + 5 * F;
+        p->adj[1] = p->adj[0] + 5 * F;
     }
 
     // --- upload --------------------------------------------------------------------
@@ -467,10 +473,25 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->tile_z = p->tile_z;
     info->adj_tile_x = p->adj_tile_x;
     info->adj_tile_z = p->adj_tile_z;
+    info->stencil = p->stencil;
+    info->stages = p->stencil == EFWI_STENCIL_TMA ? p->tma_stages : 0;
     info->workspace_bytes = p->bytes;
     info->padded_cells = p->padded_cells;
     info->physical_cells = p->physical_cells;
     info->launches = p->launches;
+    return EFWI_OK;
+}
+
+extern "C" int efwi_sync_status(efwi_plan *p, efwi_stream_t stream) {
+    if (!p) return fail(nullptr, EFWI_ERR_ARG, "plan is NULL");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(p, EFWI_ERR_CUDA, std::string("stream sync: ") + cudaGetErrorString(e));
+    int flag = 0;
+    cudaMemcpy(&flag, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (flag) {
+        cudaMemset(p->dev_err, 0, sizeof(int));
+        return fail(p, EFWI_ERR_TIMEOUT, "a kernel gave up a bounded wait; results of that call are invalid");
+    }
     return EFWI_OK;
 }
 

@@ -8,6 +8,8 @@
 
 namespace efwi {
 
+struct FwdMaps;   // tensor maps of one shot (tma.cuh)
+
 // Adjoint-source gather (the transpose of the DAS sampling): for every grid
 // cell touched by any gauge end, the list of (trace, weight) contributions,
 // summed in a fixed order so the result is deterministic.
@@ -95,6 +97,11 @@ struct efwi_plan {
     efwi::CkptStore ck;
     int K = 0;                             // checkpoint interval
     int tile_x = 0, tile_z = 0;            // forward tile
+    int stencil = EFWI_STENCIL_LOADS;      // staging of the forward step (after tuning)
+    efwi::FwdMaps *fwd_maps = nullptr;     // [ns] tensor maps for EFWI_STENCIL_TMA
+    int tma_grid = 0;                      // persistent CTAs of the TMA forward step
+    int tma_stages = 2;                    // shared-memory pipeline depth of the TMA forward step
+    int *dev_err = nullptr;                // device flag: a bounded wait expired
     int adj_tile_x = 0, adj_tile_z = 0;    // adjoint tile
     size_t bytes = 0;
     long long launches = 0;
@@ -141,9 +148,15 @@ void launch_stress_plain(efwi_plan *p, int shot, cudaStream_t st);
 void launch_adj_vel_plain(efwi_plan *p, int shot, const float *vfx, const float *vfz, cudaStream_t st);
 void launch_adj_stress_plain(efwi_plan *p, int shot, const float *vfx, const float *vfz, cudaStream_t st);
 
+// --- k_tma.cu ----------------------------------------------------------------
+bool tma_shape_ok(int tx, int tz, int nst);
+int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst);
+void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t st);
+
 // --- k_fused.cu --------------------------------------------------------------
 void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaStream_t st);
 void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaStream_t st);
+int upload_tiles(efwi_plan *p, TileList &tl, int tx, int tz);
 
 // helpers (plan.cu)
 Fields state_fields(efwi_plan *p, int which);   // which: 0/1 buffer

@@ -221,27 +221,50 @@ def test_guided_wave_full_size_sampled(efwi):
 
 
 SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16), (32, 32), (128, 8), (64, 32)]
+TMA_SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16)]
+VARIANTS = [("loads", s) for s in SHAPES] + [("tma", s) for s in TMA_SHAPES]
 
 
-def test_tile_shapes_do_not_change_results(efwi):
-    """The autotuner's choice changes only the work decomposition: every
-    compiled tile shape gives bitwise-identical data and gradients (uneven
+def test_stencil_variants_do_not_change_results(efwi):
+    """The autotuner's choice changes only the work decomposition and the
+    shared-memory staging: every compiled variant (per-thread loads or TMA,
+    every tile shape) gives bitwise-identical data and gradients (uneven
     windows, ragged tiles)."""
     p = rounded(W.tiny(nx=70, nz=41, ns=3, nt=40, npml=5, win=[[0, 45], [13, 57], [30, 40]]))
     d_obs = observed(p)
     args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
     ref = None
-    for tx, tz in SHAPES:
-        plan = efwi.Plan(p.acq, exec="batched", tile=(tx, tz))
+    for stencil, (tx, tz) in VARIANTS:
+        plan = efwi.Plan(p.acq, exec="batched", tile=(tx, tz), stencil=stencil)
         info = plan.info()
         assert (info["tile_x"], info["tile_z"]) == (tx, tz)
+        assert info["stencil"] == {"loads": 1, "tma": 2}[stencil]
         out = [t.clone() for t in plan.gradient(*args, return_data=True)]
+        plan.sync_status()
         plan.close()
         if ref is None:
             ref = out
         else:
             for a, b in zip(ref, out):
-                assert torch.equal(a, b), (tx, tz)
+                assert torch.equal(a, b), (stencil, tx, tz)
+
+
+def test_tma_full_size_matches_loads(efwi):
+    """1000x300 grid, 32 shots: the TMA forward step and the per-thread-load step
+    give bitwise-identical data for 300 steps."""
+    import copy
+    p = rounded(W.guided_wave_1000x300())
+    acq = copy.deepcopy(p.acq)
+    acq.nt = 300
+    acq.wavelet = acq.wavelet[:, :301]
+    m = (dev(p.vp), dev(p.vs), dev(p.rho))
+    outs = []
+    for stencil in ("loads", "tma"):
+        plan = efwi.Plan(acq, exec="batched", stencil=stencil, ckpt_interval=300)
+        outs.append(plan.forward(*m).clone())
+        plan.sync_status()
+        plan.close()
+    assert torch.equal(outs[0], outs[1])
 
 
 def test_batched_matches_plain(efwi):
