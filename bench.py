@@ -341,6 +341,8 @@ def run_ours(args):
                            "ckpt_interval": info["ckpt_interval"], "tile": [info["tile_x"], info["tile_z"]],
                            "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
                            "stencil": {1: "loads", 2: "tma"}.get(info["stencil"], "?"), "stages": info["stages"],
+                           "adj_stencil": {1: "loads", 2: "tma"}.get(info["adj_stencil"], "?"),
+                           "adj_stages": info["adj_stages"],
                            "l2": "working set > L2 (wavefields, checkpoints, data >> 129 MB)",
                            "parallelism": f"replicas x{world} (independent extended problems)"},
                 "s_per_gradient": s_per_grad,

@@ -73,8 +73,8 @@ enum efwi_store { EFWI_STORE_FP32 = 0, EFWI_STORE_FP16 = 1, EFWI_STORE_BF16 = 2 
  *  BATCHED all shots (any window sizes) in one fused launch per time step,
  *          the time loop captured and replayed as CUDA graphs               */
 enum efwi_exec { EFWI_EXEC_PLAIN = 0, EFWI_EXEC_BATCHED = 1 };
-/* tile staging of the batched forward step: per-thread loads, or TMA bulk
- * tensor copies into double-buffered shared memory (persistent CTAs)        */
+/* tile staging of the batched forward and adjoint steps: per-thread loads, or
+ * TMA bulk tensor copies into pipelined shared memory (persistent CTAs)     */
 enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_TMA = 2 };
 
 /*
@@ -146,6 +146,8 @@ typedef struct efwi_plan_info_t {
     int adj_tile_x, adj_tile_z; /* adjoint stencil tile in use (EXEC_BATCHED) */
     int stencil;                /* EFWI_STENCIL_* used by the forward step */
     int stages;                 /* shared-memory pipeline depth of the TMA forward step */
+    int adj_stencil;            /* EFWI_STENCIL_* used by the adjoint step */
+    int adj_stages;             /* pipeline depth of the TMA adjoint step */
     size_t workspace_bytes;     /* device bytes owned by the plan */
     long long padded_cells;     /* sum over shots of padded (nx_w + 2P)(nz + 2P) */
     long long physical_cells;   /* sum over shots of window width * nz */

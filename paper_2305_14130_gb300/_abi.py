@@ -33,7 +33,7 @@ class PlanDesc(C.Structure):
 class PlanInfo(C.Structure):
     _fields_ = [("ckpt_interval", C.c_int), ("n_ckpt", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
                 ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("stencil", C.c_int),
-                ("stages", C.c_int),
+                ("stages", C.c_int), ("adj_stencil", C.c_int), ("adj_stages", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong)]
 

@@ -495,10 +495,14 @@ void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaSt
 
 void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaStream_t st) {
     (void)n;
-    AdjArgsF a = adj_args_f(p, vfx, vfz);
     int slot;
     prof_begin(p, st, &slot, EFWI_KERNEL_ADJ);
-    EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, a.ntiles, st);
+    if (p->adj_stencil == EFWI_STENCIL_TMA) {
+        launch_adj_tma(p, vfx, st);
+    } else {
+        AdjArgsF a = adj_args_f(p, vfx, vfz);
+        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, a.ntiles, st);
+    }
     prof_end(p, st, slot);
     p->launches++;
     p->acur ^= 1;
@@ -537,6 +541,15 @@ float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEv
     return cudaGetLastError() == cudaSuccess ? t : 1e30f;
 }
 
+int select_adj(efwi_plan *p, const Variant &v) {
+    p->adj_stencil = v.kind;
+    int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
+    if (!rc && v.kind == EFWI_STENCIL_TMA) rc = tma_prepare_adj(p, v.tx, v.tz, v.nst);
+    p->adj_tile_x = v.tx;
+    p->adj_tile_z = v.tz;
+    return rc;
+}
+
 int select_fwd(efwi_plan *p, const Variant &v) {
     p->stencil = v.kind;
     int rc = upload_tiles(p, p->tiles, v.tx, v.tz);
@@ -559,7 +572,16 @@ int efwi_autotune(efwi_plan *p) {
         for (int nst = 2; nst <= 4; ++nst)
             if (want != EFWI_STENCIL_LOADS && tma_shape_ok(s.tx, s.tz, nst))
                 fwd.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, nst});
-        adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        if (want != EFWI_STENCIL_TMA) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        for (int nst = 1; nst <= 2; ++nst)
+            if (want != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
+                adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, nst});
+    }
+    // a requested staging without an instantiation for this tile falls back to per-thread loads
+    for (auto &s : kShapes) {
+        if (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)) continue;
+        if (fwd.empty()) fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        if (adj.empty()) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
     }
     if (fwd.empty() || adj.empty()) {
         p->err = "no compiled stencil variant matches the requested tile/stencil "
@@ -582,7 +604,7 @@ int efwi_autotune(efwi_plan *p) {
         }
         best = 1e30f;
         for (auto &v : adj) {
-            if (upload_tiles(p, p->adj_tiles, v.tx, v.tz)) continue;
+            if (select_adj(p, v)) continue;
             const float t = time_steps(p, true, st, e0, e1);
             if (t < best) { best = t; ba = v; }
         }
@@ -606,9 +628,7 @@ int efwi_autotune(efwi_plan *p) {
     p->prof_counter[0] = p->prof_counter[1] = 0;
     p->ev_used = 0;
     rc = select_fwd(p, bf);
-    if (!rc) rc = upload_tiles(p, p->adj_tiles, ba.tx, ba.tz);
-    p->adj_tile_x = ba.tx;
-    p->adj_tile_z = ba.tz;
+    if (!rc) rc = select_adj(p, ba);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         p->err = std::string("autotune: ") + cudaGetErrorString(e);

@@ -243,6 +243,7 @@ template <int TX, int TZ, int NST>
 int occupancy() {
     cudaFuncSetAttribute(k_step_tma<TX, TZ, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)FwdLayout<TX, TZ, NST>::smem());
+    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<TX, TZ, NST>, kThreads,
                                                   FwdLayout<TX, TZ, NST>::smem());
@@ -328,6 +329,348 @@ void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t
     const int tx = p->tiles.tx, tz = p->tiles.tz, nst = p->tma_stages;
 #define EFWI_LAUNCH_X(a_, b_, c_) if (tx == a_ && tz == b_ && nst == c_) launch_tma<a_, b_, c_>(a, grid, st);
     EFWI_TMA_VARIANTS(EFWI_LAUNCH_X)
+#undef EFWI_LAUNCH_X
+}
+
+}  // namespace efwi
+
+// ===========================================================================
+// Adjoint time step with TMA staging: same persistent, pipelined structure.
+// Per tile, one thread copies (tile + 4-cell halo boxes) the 5 adjoint fields,
+// the 5 materials and the 2 forward velocities of step n into shared memory.
+// Then, in place over the staged fields:
+//   0. every thread keeps the adjoint stresses of its own tile cells;
+//   1. f^ = C sigma^ (+ PML) over the staged adjoint stresses;
+//   2. v^ += D^T f^ on the tile + 2-cell halo, e^ = dt b v^ (+ PML) over the
+//      staged adjoint velocities; b-imaging on the tile;
+//   3. sigma^ += D^T e^ on the tile with the C-imaging.
+// Inside CPML strips the four f^ (e^) components differ, and the extra
+// components go to a separate shared array.
+// ===========================================================================
+namespace efwi {
+namespace {
+
+struct TmaAdjArgs {
+    const ShotDev *shots;
+    const int4 *tiles;
+    const AdjMaps *maps;
+    int ntiles;
+    int acur;                   // adjoint buffer read (z offset 5 * acur)
+    int slot;                   // segment-buffer step of the forward velocities
+    Fields out;                 // adjoint buffer written
+    Pml pml;                    // current adjoint PML memory
+    float *n1, *n3, *n2, *n4;   // next V block
+    float *n5, *n8, *n6, *n7;   // next S block
+    float *Glam, *Gmu, *Gmuxz, *Gbx, *Gbz;
+    float dt, rdx, rdz;
+    int *err;
+};
+
+template <int TX, int TZ, int NST>
+struct AdjLayout {
+    static constexpr int SX = TX + 8, SZ = TZ + 8;
+    static constexpr int NS = SX * SZ;
+    static constexpr int BUF = 12 * NS;                 // 5 adjoint + 5 materials + 2 forward v
+    static constexpr unsigned BYTES = BUF * 4u;
+    static constexpr int EXTRA = 3 * NS;                 // f^4, e^2, e^4 inside CPML strips
+    static constexpr size_t smem() { return (NST * (size_t)BUF + EXTRA) * 4 + 128; }
+    static constexpr int PER = (TX * TZ + 255) / 256;    // own tile cells per thread
+};
+
+template <int TX, int TZ, int NST>
+__device__ __forceinline__ void issue_adj(const TmaAdjArgs &a, int t, float *buf, uint64_t *bar) {
+    using L = AdjLayout<TX, TZ, NST>;
+    const int4 tl = a.tiles[t];
+    const AdjMaps *m = a.maps + tl.x;
+    mbar_expect_tx(bar, L::BYTES);
+    tma_load_3d(buf, &m->ad, bar, tl.y, tl.z - 2, 5 * a.acur);
+    tma_load_3d(buf + 5 * L::NS, &m->m5, bar, tl.y, tl.z - 2, 0);
+    tma_load_3d(buf + 10 * L::NS, &m->sg, bar, tl.y, tl.z - 2, 2 * a.slot);
+}
+
+template <int TX, int TZ, int NST>
+__global__ void __launch_bounds__(256) k_adj_tma(TmaAdjArgs a) {
+    using L = AdjLayout<TX, TZ, NST>;
+    constexpr int SX = L::SX, NS = L::NS, PER = L::PER;
+    extern __shared__ float4 smem_raw[];
+    float *smb = align128(smem_raw);
+    float *xf4 = smb + NST * L::BUF, *xe2 = xf4 + NS, *xe4 = xe2 + NS;
+    __shared__ __align__(8) uint64_t bar[NST];
+    __shared__ int ok_s;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int b = 0; b < NST; ++b) mbar_init(&bar[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int b = 0; b < NST - 1; ++b) {
+            const int tb = blockIdx.x + b * gridDim.x;
+            if (tb < a.ntiles) issue_adj<TX, TZ, NST>(a, tb, smb + b * L::BUF, &bar[b]);
+        }
+    uint32_t phase = 0;
+    int t = blockIdx.x;
+    for (int k = 0; t < a.ntiles; t += gridDim.x, ++k) {
+        const int b = k % NST;
+        float *buf = smb + b * L::BUF;
+        const int tn = t + (NST - 1) * gridDim.x;
+        const int bn = (k + NST - 1) % NST;
+        if (NST > 1 && tid == 0 && tn < a.ntiles) issue_adj<TX, TZ, NST>(a, tn, smb + bn * L::BUF, &bar[bn]);
+        if (NST == 1 && tid == 0) issue_adj<TX, TZ, NST>(a, t, buf, &bar[0]);
+        if (tid == 0) ok_s = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+        __syncthreads();
+        if (!ok_s) {
+            if (tid == 0) atomicExch(a.err, 1);
+            return;
+        }
+        mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+        phase ^= 1u << b;
+
+        const int4 tl = a.tiles[t];
+        const ShotDev *sp = a.shots + tl.x;
+        const int NX = sp->NX, NZ = sp->NZ, PP = sp->P, profx = sp->profx, pitch = sp->pitch, w = sp->w;
+        const long long off = sp->off, psx = sp->psx, psz = sp->psz;
+        const bool edge = (tl.w & 4) != 0;
+        const int i0 = tl.y, j0 = tl.z;
+        const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
+        float *hvx = buf, *hvz = buf + NS, *hxx = buf + 2 * NS, *hzz = buf + 3 * NS, *hxz = buf + 4 * NS;
+        const float *mlam = buf + 5 * NS, *mmu = buf + 6 * NS, *mmxz = buf + 7 * NS, *mbx = buf + 8 * NS,
+                    *mbz = buf + 9 * NS, *fvx = buf + 10 * NS, *fvz = buf + 11 * NS;
+        float *f4s = edge ? xf4 : hxz;     // f^4 == f^3 away from the CPML
+        float *e2s = edge ? xe2 : hvx;     // e^2 == e^1
+        float *e4s = edge ? xe4 : hvz;     // e^4 == e^3
+
+        // 0. own tile cells: adjoint stresses and imaging sums into registers
+        float rxx[PER], rzz[PER], rxz[PER], gl[PER], gm[PER], gx[PER];
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int q = tid + r * 256;
+            const int y = q / TX, x = q - y * TX;
+            const int o = (y + 4) * SX + (x + 4);
+            rxx[r] = hxx[o]; rzz[r] = hzz[o]; rxz[r] = hxz[o];
+            const int i = i0 + x, j = j0 + y;
+            gl[r] = gm[r] = gx[r] = 0.f;
+            if (q < TX * TZ && (!edge || (i < NX && j < NZ))) {
+                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                gl[r] = a.Glam[c]; gm[r] = a.Gmu[c]; gx[r] = a.Gmuxz[c];
+            }
+        }
+        __syncthreads();
+
+        // 1. f^ over the staged adjoint stresses (tile + 4-cell halo)
+        for (int q = tid; q < NS; q += 256) {
+            const int y = q / SX, x = q - y * SX;
+            const int i = i0 - 4 + x, j = j0 - 4 + y;
+            const float sxx = hxx[q], szz = hzz[q], sxz = hxz[q];
+            const float lam = mlam[q], l2m = lam + 2.f * mmu[q];
+            const float Ex = dt * (l2m * sxx + lam * szz);
+            const float Ez = dt * (lam * sxx + l2m * szz);
+            const float Exz = dt * mmxz[q] * sxz;
+            float g1 = Ex, g2 = Ez, g3 = Exz, g4 = Exz;
+            if (edge) {
+                if (i >= 0 && i < NX && j >= 0 && j < NZ) {
+                    const bool own = x >= 4 && x < TX + 4 && y >= 4 && y < TZ + 4;
+                    const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                    const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                    if (xs >= 0) {
+                        const long long kk = psx + (long long)j * 2 * PP + xs;
+                        const int pq = profx + i;
+                        const float P5 = a.pml.x[2][kk], P8 = a.pml.x[3][kk];
+                        g1 += a.pml.ax_i[pq] * (P5 + Ex);
+                        g4 += a.pml.ax_h[pq] * (P8 + Exz);
+                        if (own) {
+                            a.n5[kk] = a.pml.bx_i[pq] * (P5 + Ex);
+                            a.n8[kk] = a.pml.bx_h[pq] * (P8 + Exz);
+                        }
+                    }
+                    if (zs >= 0) {
+                        const long long kk = psz + (long long)zs * NX + i;
+                        const float P6 = a.pml.z[2][kk], P7 = a.pml.z[3][kk];
+                        g2 += a.pml.az_i[j] * (P6 + Ez);
+                        g3 += a.pml.az_h[j] * (P7 + Exz);
+                        if (own) {
+                            a.n6[kk] = a.pml.bz_i[j] * (P6 + Ez);
+                            a.n7[kk] = a.pml.bz_h[j] * (P7 + Exz);
+                        }
+                    }
+                } else {
+                    g1 = g2 = g3 = g4 = 0.f;
+                }
+                f4s[q] = g4;
+            }
+            hxx[q] = g1; hzz[q] = g2; hxz[q] = g3;
+        }
+        __syncthreads();
+
+        // 2. v^ += D^T f^ on the tile + 2-cell halo; e^ over the staged adjoint velocities
+        float *__restrict__ gbx = a.Gbx + off;
+        float *__restrict__ gbz = a.Gbz + off;
+        constexpr int VX = TX + 4, VZ = TZ + 4;
+        for (int q = tid; q < VX * VZ; q += 256) {
+            const int y = q / VX, x = q - y * VX;
+            const int i = i0 - 2 + x, j = j0 - 2 + y;
+            const int o = (y + 2) * SX + (x + 2);
+            float h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f;
+            if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
+                const float inc_x = -(C1 * (hxx[o + 1] - hxx[o]) + C2 * (hxx[o + 2] - hxx[o - 1])) * rdx
+                                    - (C1 * (hxz[o] - hxz[o - SX]) + C2 * (hxz[o + SX] - hxz[o - 2 * SX])) * rdz;
+                const float inc_z = -(C1 * (hzz[o + SX] - hzz[o]) + C2 * (hzz[o + 2 * SX] - hzz[o - SX])) * rdz
+                                    - (C1 * (f4s[o] - f4s[o - 1]) + C2 * (f4s[o + 1] - f4s[o - 2])) * rdx;
+                const float vx = hvx[o] + inc_x;
+                const float vz = hvz[o] + inc_z;
+                const float qx = dt * mbx[o] * vx, qz = dt * mbz[o] * vz;
+                h1 = qx; h2 = qx; h3 = qz; h4 = qz;
+                const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
+                if (edge) {
+                    const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                    const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                    if (xs >= 0) {
+                        const long long kk = psx + (long long)j * 2 * PP + xs;
+                        const int pq = profx + i;
+                        const float P1 = a.pml.x[0][kk], P3 = a.pml.x[1][kk];
+                        h1 += a.pml.ax_h[pq] * (P1 + qx);
+                        h3 += a.pml.ax_i[pq] * (P3 + qz);
+                        if (own) {
+                            a.n1[kk] = a.pml.bx_h[pq] * (P1 + qx);
+                            a.n3[kk] = a.pml.bx_i[pq] * (P3 + qz);
+                        }
+                    }
+                    if (zs >= 0) {
+                        const long long kk = psz + (long long)zs * NX + i;
+                        const float P2 = a.pml.z[0][kk], P4 = a.pml.z[1][kk];
+                        h2 += a.pml.az_i[j] * (P2 + qx);
+                        h4 += a.pml.az_h[j] * (P4 + qz);
+                        if (own) {
+                            a.n2[kk] = a.pml.bz_i[j] * (P2 + qx);
+                            a.n4[kk] = a.pml.bz_h[j] * (P4 + qz);
+                        }
+                    }
+                }
+                if (own) {
+                    const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    a.out.vx[off + c] = vx;
+                    a.out.vz[off + c] = vz;
+                    if (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP)) {
+                        gbx[c] += fvx[o] * inc_x;
+                        gbz[c] += fvz[o] * inc_z;
+                    }
+                }
+            }
+            if (edge) { e2s[o] = h2; e4s[o] = h4; }
+            hvx[o] = h1;
+            hvz[o] = h3;
+        }
+        __syncthreads();
+
+        // 3. sigma^ += D^T e^ on the tile, with the C-imaging
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int q = tid + r * 256;
+            if (q >= TX * TZ) break;
+            const int y = q / TX, x = q - y * TX;
+            const int i = i0 + x, j = j0 + y;
+            if (edge && (i >= NX || j >= NZ)) continue;
+            const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+            const int o = (y + 4) * SX + (x + 4);
+            const float sxx = rxx[r], szz = rzz[r], sxz = rxz[r];
+            if (!edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP)) {
+                const float fx = (C1 * (fvx[o] - fvx[o - 1]) + C2 * (fvx[o + 1] - fvx[o - 2])) * rdx;
+                const float fz = (C1 * (fvz[o] - fvz[o - SX]) + C2 * (fvz[o + SX] - fvz[o - 2 * SX])) * rdz;
+                a.Glam[off + c] = gl[r] + dt * (sxx + szz) * (fx + fz);
+                a.Gmu[off + c] = gm[r] + 2.f * dt * (sxx * fx + szz * fz);
+            }
+            if (!edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP)) {
+                const float fxz = (C1 * (fvx[o + SX] - fvx[o]) + C2 * (fvx[o + 2 * SX] - fvx[o - SX])) * rdz +
+                                  (C1 * (fvz[o + 1] - fvz[o]) + C2 * (fvz[o + 2] - fvz[o - 1])) * rdx;
+                a.Gmuxz[off + c] = gx[r] + dt * sxz * fxz;
+            }
+            a.out.sxx[off + c] = sxx - (C1 * (hvx[o] - hvx[o - 1]) + C2 * (hvx[o + 1] - hvx[o - 2])) * rdx;
+            a.out.szz[off + c] = szz - (C1 * (e4s[o] - e4s[o - SX]) + C2 * (e4s[o + SX] - e4s[o - 2 * SX])) * rdz;
+            a.out.sxz[off + c] = sxz - (C1 * (e2s[o + SX] - e2s[o]) + C2 * (e2s[o + 2 * SX] - e2s[o - SX])) * rdz
+                                     - (C1 * (hvz[o + 1] - hvz[o]) + C2 * (hvz[o + 2] - hvz[o - 1])) * rdx;
+        }
+        __syncthreads();
+    }
+}
+
+template <int TX, int TZ, int NST>
+void launch_adj_tma_t(const TmaAdjArgs &a, int grid, cudaStream_t st) {
+    k_adj_tma<TX, TZ, NST><<<grid, 256, AdjLayout<TX, TZ, NST>::smem(), st>>>(a);
+}
+
+template <int TX, int TZ, int NST>
+int adj_occupancy() {
+    cudaFuncSetAttribute(k_adj_tma<TX, TZ, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)AdjLayout<TX, TZ, NST>::smem());
+    cudaFuncSetAttribute(k_adj_tma<TX, TZ, NST>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_tma<TX, TZ, NST>, 256, AdjLayout<TX, TZ, NST>::smem());
+    return nb;
+}
+
+#define EFWI_TMA_ADJ_VARIANTS(X) X(32, 8, 1) X(32, 8, 2) X(32, 16, 1) X(32, 16, 2) X(64, 8, 1) X(64, 8, 2)
+
+}  // namespace
+
+bool tma_adj_shape_ok(int tx, int tz, int nst) {
+#define EFWI_OK_X(a_, b_, c_) if (tx == a_ && tz == b_ && nst == c_) return true;
+    EFWI_TMA_ADJ_VARIANTS(EFWI_OK_X)
+#undef EFWI_OK_X
+    return false;
+}
+
+int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst) {
+    std::vector<AdjMaps> h(p->d.ns);
+    const long long F = p->fsz_total;
+    for (int s = 0; s < p->d.ns; ++s) {
+        const ShotDev &sh = p->shots[s];
+        int rc = encode_map(&h[s].ad, p->adj[0], sh, F, 10, tx + 8, tz + 8, 5);
+        if (!rc) rc = encode_map(&h[s].m5, p->mat, sh, F, 5, tx + 8, tz + 8, 5);
+        if (!rc) rc = encode_map(&h[s].sg, p->seg, sh, F, 2 * p->K, tx + 8, tz + 8, 2);
+        if (rc) {
+            p->err = "cuTensorMapEncodeTiled failed for the adjoint maps";
+            return rc;
+        }
+    }
+    if (!p->adj_maps && cudaMalloc((void **)&p->adj_maps, sizeof(AdjMaps) * p->d.ns) != cudaSuccess)
+        return EFWI_ERR_OOM;
+    cudaMemcpy(p->adj_maps, h.data(), sizeof(AdjMaps) * p->d.ns, cudaMemcpyHostToDevice);
+    int nb = 0;
+#define EFWI_OCC_X(a_, b_, c_) if (tx == a_ && tz == b_ && nst == c_) nb = adj_occupancy<a_, b_, c_>();
+    EFWI_TMA_ADJ_VARIANTS(EFWI_OCC_X)
+#undef EFWI_OCC_X
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    p->tma_adj_grid = std::max(1, nb) * sms;
+    p->tma_adj_stages = nst;
+    return EFWI_OK;
+}
+
+void launch_adj_tma(efwi_plan *p, const float *vfx, cudaStream_t st) {
+    TmaAdjArgs a;
+    a.shots = p->shots_d;
+    a.tiles = p->adj_tiles.tiles;
+    a.maps = p->adj_maps;
+    a.ntiles = p->adj_tiles.n;
+    a.acur = p->acur;
+    a.slot = (int)((vfx - p->seg) / (2 * p->fsz_total));
+    a.out = adj_fields(p, 1 - p->acur);
+    a.pml = adj_pml(p, p->apsi_v, p->apsi_s);
+    const long long X = p->psx_total, Z = p->psz_total;
+    float *vn = psi_block(p->apsi, p, 1 - p->apsi_v), *sn = psi_block(p->apsi, p, 2 + (1 - p->apsi_s));
+    a.n1 = vn; a.n3 = vn + X; a.n2 = vn + 2 * X; a.n4 = vn + 2 * X + Z;
+    a.n5 = sn; a.n8 = sn + X; a.n6 = sn + 2 * X; a.n7 = sn + 2 * X + Z;
+    a.Glam = G_field(p, 0); a.Gmu = G_field(p, 1); a.Gmuxz = G_field(p, 2);
+    a.Gbx = G_field(p, 3); a.Gbz = G_field(p, 4);
+    a.dt = (float)p->d.dt;
+    a.rdx = (float)(1.0 / p->d.dx);
+    a.rdz = (float)(1.0 / p->d.dz);
+    a.err = p->dev_err;
+    const int grid = std::min(p->tma_adj_grid, a.ntiles);
+    const int tx = p->adj_tiles.tx, tz = p->adj_tiles.tz, nst = p->tma_adj_stages;
+#define EFWI_LAUNCH_X(a_, b_, c_) if (tx == a_ && tz == b_ && nst == c_) launch_adj_tma_t<a_, b_, c_>(a, grid, st);
+    EFWI_TMA_ADJ_VARIANTS(EFWI_LAUNCH_X)
 #undef EFWI_LAUNCH_X
 }
 

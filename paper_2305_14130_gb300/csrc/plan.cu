@@ -155,7 +155,7 @@ void prof_end(efwi_plan *p, cudaStream_t st, int slot) {
 
 static void free_plan(efwi_plan *p) {
     if (!p) return;
-    void *ptrs[] = {p->shots_d, p->state[0], p->mat, p->adj[0], p->fwd_maps, p->dev_err, p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
+    void *ptrs[] = {p->shots_d, p->state[0], p->mat, p->adj[0], p->fwd_maps, p->adj_maps, p->dev_err, p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
                     p->prof, p->dw, p->ref, p->tr_shot, p->tr_off, p->tr_w, p->tr_acc, p->tr_coef,
                     p->gather.tgt_shot, p->gather.tgt_field, p->gather.tgt_off, p->gather.ptr, p->gather.tr,
                     p->gather.w, p->tiles.tiles, p->adj_tiles.tiles, p->resid, p->dbuf, p->partial, p->seg, p->ck.fields, p->ck.psi,
@@ -475,6 +475,8 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->adj_tile_z = p->adj_tile_z;
     info->stencil = p->stencil;
     info->stages = p->stencil == EFWI_STENCIL_TMA ? p->tma_stages : 0;
+    info->adj_stencil = p->adj_stencil;
+    info->adj_stages = p->adj_stencil == EFWI_STENCIL_TMA ? p->tma_adj_stages : 0;
     info->workspace_bytes = p->bytes;
     info->padded_cells = p->padded_cells;
     info->physical_cells = p->physical_cells;

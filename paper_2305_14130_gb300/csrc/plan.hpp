@@ -9,6 +9,7 @@
 namespace efwi {
 
 struct FwdMaps;   // tensor maps of one shot (tma.cuh)
+struct AdjMaps;
 
 // Adjoint-source gather (the transpose of the DAS sampling): for every grid
 // cell touched by any gauge end, the list of (trace, weight) contributions,
@@ -101,6 +102,9 @@ struct efwi_plan {
     efwi::FwdMaps *fwd_maps = nullptr;     // [ns] tensor maps for EFWI_STENCIL_TMA
     int tma_grid = 0;                      // persistent CTAs of the TMA forward step
     int tma_stages = 2;                    // shared-memory pipeline depth of the TMA forward step
+    int adj_stencil = EFWI_STENCIL_LOADS;  // staging of the adjoint step (after tuning)
+    efwi::AdjMaps *adj_maps = nullptr;
+    int tma_adj_grid = 0, tma_adj_stages = 1;
     int *dev_err = nullptr;                // device flag: a bounded wait expired
     int adj_tile_x = 0, adj_tile_z = 0;    // adjoint tile
     size_t bytes = 0;
@@ -152,6 +156,9 @@ void launch_adj_stress_plain(efwi_plan *p, int shot, const float *vfx, const flo
 bool tma_shape_ok(int tx, int tz, int nst);
 int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst);
 void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t st);
+bool tma_adj_shape_ok(int tx, int tz, int nst);
+int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst);
+void launch_adj_tma(efwi_plan *p, const float *vfx, cudaStream_t st);
 
 // --- k_fused.cu --------------------------------------------------------------
 void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaStream_t st);

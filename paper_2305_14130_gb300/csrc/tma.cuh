@@ -14,6 +14,13 @@ struct __align__(64) FwdMaps {
     CUtensorMap st, mb, mc;
 };
 
+// Tensor maps of one shot for the adjoint step: adjoint state (both buffers,
+// 10 fields) and the 5 materials on the halo box, the forward velocities of
+// the segment buffer (2 fields per stored step) on the halo box.
+struct __align__(64) AdjMaps {
+    CUtensorMap ad, m5, sg;
+};
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

@@ -239,6 +239,7 @@ def test_stencil_variants_do_not_change_results(efwi):
         info = plan.info()
         assert (info["tile_x"], info["tile_z"]) == (tx, tz)
         assert info["stencil"] == {"loads": 1, "tma": 2}[stencil]
+        assert info["adj_stencil"] in (1, 2)
         out = [t.clone() for t in plan.gradient(*args, return_data=True)]
         plan.sync_status()
         plan.close()
@@ -250,8 +251,9 @@ def test_stencil_variants_do_not_change_results(efwi):
 
 
 def test_tma_full_size_matches_loads(efwi):
-    """1000x300 grid, 32 shots: the TMA forward step and the per-thread-load step
-    give bitwise-identical data for 300 steps."""
+    """1000x300 grid, 32 shots, 300 steps: the TMA-staged forward and adjoint
+    steps and the per-thread-load ones give bitwise-identical data, misfit and
+    gradients (checkpoint recompute included)."""
     import copy
     p = rounded(W.guided_wave_1000x300())
     acq = copy.deepcopy(p.acq)
@@ -259,12 +261,14 @@ def test_tma_full_size_matches_loads(efwi):
     acq.wavelet = acq.wavelet[:, :301]
     m = (dev(p.vp), dev(p.vs), dev(p.rho))
     outs = []
+    d_obs = torch.zeros((acq.ntr, acq.nt), device="cuda")
     for stencil in ("loads", "tma"):
-        plan = efwi.Plan(acq, exec="batched", stencil=stencil, ckpt_interval=300)
-        outs.append(plan.forward(*m).clone())
+        plan = efwi.Plan(acq, exec="batched", stencil=stencil, ckpt_interval=30)
+        outs.append([t.clone() for t in plan.gradient(*m, d_obs, return_data=True)])
         plan.sync_status()
         plan.close()
-    assert torch.equal(outs[0], outs[1])
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
 
 
 def test_batched_matches_plain(efwi):
