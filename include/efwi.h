@@ -227,6 +227,23 @@ int efwi_regularization_grad(efwi_plan *plan, const float *m, const float *b, co
                              const uint8_t *sink, double eta, double *phi_reg, float *g,
                              efwi_stream_t stream);
 
+/* Allocation-free variant of efwi_regularization_grad (no counterpart in the
+ * paper; it exists for callers that cannot let a library allocate device
+ * memory, e.g. applications that own all device memory through their own
+ * pool or budget, and for callers that want the regularization without
+ * creating a plan, whose creation allocates the whole workspace).  Same
+ * arguments and results as efwi_regularization_grad but no plan: ns, nx, nz
+ * give the sizes of the [ns][nz][nx] arrays.  It calls no cudaMalloc or
+ * cudaFree.  Its only scratch (FP64 block partials of phi_reg) is a static
+ * 32 KB device array that every GPU loading the library holds until exit;
+ * the first call on each device looks up that array's address (call it once
+ * before any stream capture).  Limit: nx * nz <= 1048576 pixels, larger
+ * sizes return EFWI_ERR_ARG without launching anything.  All calls share the
+ * array, so calls that overlap on the GPU race on it.                       */
+int efwi_regularization_grad_noalloc(int ns, int nx, int nz, const float *m, const float *b,
+                                     const float *bp, const uint8_t *sink, double eta,
+                                     double *phi_reg, float *g, efwi_stream_t stream);
+
 /* Extended objective of eq. 8: phi_data (as efwi_forward + misfit) and
  * phi_reg summed over the three parameter fields (Vp, Vs, rho) with their
  * own eta[3].  Both results are device doubles (overwritten).               */

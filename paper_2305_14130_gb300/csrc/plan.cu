@@ -97,6 +97,8 @@ int local_off(const ShotDev &s, int i, int j) { return (j + EFWI_GZ) * s.pitch +
 
 namespace efwi {
 
+void set_thread_error(const std::string &msg) { g_thread_err = msg; }
+
 Fields state_fields(efwi_plan *p, int which) {
     const long long F = p->fsz_total;
     float *s = p->state[which];

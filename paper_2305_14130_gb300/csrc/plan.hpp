@@ -166,6 +166,7 @@ void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, c
 int upload_tiles(efwi_plan *p, TileList &tl, int tx, int tz);
 
 // helpers (plan.cu)
+void set_thread_error(const std::string &msg);  // message for efwi_last_error(NULL)
 Fields state_fields(efwi_plan *p, int which);   // which: 0/1 buffer
 Fields adj_fields(efwi_plan *p, int which);
 Mat materials(efwi_plan *p);
