@@ -75,7 +75,8 @@ enum efwi_store { EFWI_STORE_FP32 = 0, EFWI_STORE_FP16 = 1, EFWI_STORE_BF16 = 2 
 enum efwi_exec { EFWI_EXEC_PLAIN = 0, EFWI_EXEC_BATCHED = 1 };
 /* tile staging of the batched forward and adjoint steps: per-thread loads, or
  * TMA bulk tensor copies into pipelined shared memory (persistent CTAs)     */
-enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_TMA = 2 };
+enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_TMA = 2,
+                    EFWI_STENCIL_TMA_PAIRS = 3 /* TMA, two adjacent cells per thread (forward step) */ };
 
 /*
  * Problem description (host memory; copied by efwi_plan_create).

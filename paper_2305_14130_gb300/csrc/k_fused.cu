@@ -481,7 +481,7 @@ AdjArgsF adj_args_f(efwi_plan *p, const float *vfx, const float *vfz) {
 void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaStream_t st) {
     int slot;
     prof_begin(p, st, &slot, EFWI_KERNEL_STEP);
-    if (p->stencil == EFWI_STENCIL_TMA) {
+    if (p->stencil >= EFWI_STENCIL_TMA) {
         launch_step_tma(p, n, vseg_x, vseg_z, st);
     } else {
         FwdArgs a = fwd_args(p, n, vseg_x, vseg_z);
@@ -521,7 +521,7 @@ using namespace efwi;
 namespace {
 
 struct Variant {
-    int kind, tx, tz, nst;
+    int kind, tx, tz, nst, vec = 1;
 };
 
 float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
@@ -553,7 +553,7 @@ int select_adj(efwi_plan *p, const Variant &v) {
 int select_fwd(efwi_plan *p, const Variant &v) {
     p->stencil = v.kind;
     int rc = upload_tiles(p, p->tiles, v.tx, v.tz);
-    if (!rc && v.kind == EFWI_STENCIL_TMA) rc = tma_prepare_fwd(p, v.tx, v.tz, v.nst);
+    if (!rc && v.kind >= EFWI_STENCIL_TMA) rc = tma_prepare_fwd(p, v.tx, v.tz, v.nst, v.vec);
     p->tile_x = v.tx;
     p->tile_z = v.tz;
     return rc;
@@ -568,11 +568,14 @@ int efwi_autotune(efwi_plan *p) {
     std::vector<Variant> fwd, adj;
     for (auto &s : kShapes) {
         if (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)) continue;
-        if (want != EFWI_STENCIL_TMA) fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-        for (int nst = 2; nst <= 4; ++nst)
-            if (want != EFWI_STENCIL_LOADS && tma_shape_ok(s.tx, s.tz, nst))
-                fwd.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, nst});
-        if (want != EFWI_STENCIL_TMA) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        if (want == EFWI_STENCIL_AUTO || want == EFWI_STENCIL_LOADS) fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        for (int vec = 1; vec <= 2; ++vec) {
+            const int kind = vec == 1 ? EFWI_STENCIL_TMA : EFWI_STENCIL_TMA_PAIRS;
+            if (want != EFWI_STENCIL_AUTO && want != kind) continue;
+            for (int nst = 2; nst <= 4; ++nst)
+                if (tma_shape_ok(s.tx, s.tz, nst, vec)) fwd.push_back({kind, s.tx, s.tz, nst, vec});
+        }
+        if (want == EFWI_STENCIL_AUTO || want == EFWI_STENCIL_LOADS) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
         for (int nst = 1; nst <= 2; ++nst)
             if (want != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
                 adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, nst});

@@ -199,7 +199,7 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (d->exec == EFWI_EXEC_BATCHED &&
         ((d->tile_x != 0 || d->tile_z != 0) && (d->tile_x <= 0 || d->tile_z <= 0)))
         return fail(nullptr, EFWI_ERR_ARG, "tile_x and tile_z must both be 0 or both positive");
-    if (d->stencil < EFWI_STENCIL_AUTO || d->stencil > EFWI_STENCIL_TMA)
+    if (d->stencil < EFWI_STENCIL_AUTO || d->stencil > EFWI_STENCIL_TMA_PAIRS)
         return fail(nullptr, EFWI_ERR_ARG, "unknown stencil");
 
     const long long ncell = (long long)d->nx * d->nz;
@@ -476,7 +476,7 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->adj_tile_x = p->adj_tile_x;
     info->adj_tile_z = p->adj_tile_z;
     info->stencil = p->stencil;
-    info->stages = p->stencil == EFWI_STENCIL_TMA ? p->tma_stages : 0;
+    info->stages = p->stencil >= EFWI_STENCIL_TMA ? p->tma_stages : 0;
     info->adj_stencil = p->adj_stencil;
     info->adj_stages = p->adj_stencil == EFWI_STENCIL_TMA ? p->tma_adj_stages : 0;
     info->workspace_bytes = p->bytes;

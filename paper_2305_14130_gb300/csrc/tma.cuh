@@ -29,6 +29,10 @@ __device__ __forceinline__ float *align128(void *p) {
     return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(p) + 127) & ~(uintptr_t)127);
 }
 
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ __forceinline__ void st2g(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
