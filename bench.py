@@ -123,8 +123,8 @@ def peaks():
 #   plain stress half-step: read vx vz + 3 stresses + lambda mu mu_xz, write 3 = 11 words
 #   plain adjoint stress half-step: read 2 + 2 + 3 + 3 + 2 + 3, write 3 + 3 = 21 words
 KERNELS = {
-    ("batched", "step"): ("k_step_fused (forward time step, all shots)", 60.0),
-    ("batched", "adj"): ("k_adj_fused (adjoint time step + imaging, all shots)", 108.0),
+    ("batched", "step"): ("forward_step (velocity + stress + source, all shots)", 60.0),
+    ("batched", "adj"): ("adjoint_step (transposed step + imaging, all shots)", 108.0),
     ("plain", "step"): ("k_stress (forward stress half-step, one shot)", 44.0),
     ("plain", "adj"): ("k_adj_stress (adjoint stress half-step + imaging, one shot)", 84.0),
 }
@@ -141,6 +141,11 @@ def roofline(exec_, info, prof, nt, ns):
         if not n:
             continue
         name, bpc = KERNELS[(exec_, k)]
+        if exec_ == "batched":
+            kind = info["stencil"] if k == "step" else info["adj_stencil"]
+            tile = (info["tile_x"], info["tile_z"]) if k == "step" else (info["adj_tile_x"], info["adj_tile_z"])
+            staging = {1: "per-thread loads", 2: "TMA", 3: "TMA, cell pairs"}.get(kind, "?")
+            name = f"{name.split(' ')[0]} [{staging}, tile {tile[0]}x{tile[1]}] {' '.join(name.split(' ')[1:])}"
         avg = ms / n / 1e3
         achieved = bpc * cells / avg / 1e9
         out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

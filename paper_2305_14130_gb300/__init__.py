@@ -25,7 +25,10 @@ import torch
 from . import _abi
 from ._abi import EfwiError, STORE, EXEC, STENCIL
 
-__all__ = ["Plan", "zoi_weights", "EfwiError", "load_library"]
+__all__ = ["Plan", "zoi_weights", "EfwiError", "load_library", "DataMisfit", "Consistency", "extended_objective"]
+
+
+from .autograd import DataMisfit, Consistency, extended_objective  # noqa: E402
 
 
 def load_library():
