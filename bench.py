@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--stencil", default="auto", choices=["auto", "loads", "tma", "tma_pairs"])
     ap.add_argument("--tile", default="0x0", help="forward tile, e.g. 32x16 (0x0 = autotune)")
+    ap.add_argument("--adj-stencil", default="auto", choices=["auto", "loads", "tma"])
+    ap.add_argument("--adj-tile", default="0x0", help="adjoint tile (0x0 = autotune)")
     ap.add_argument("--ns", type=int, default=32)
     ap.add_argument("--nt", type=int, default=4000)
     return ap.parse_args()
@@ -130,6 +132,15 @@ KERNELS = {
 }
 
 
+# DRAM traffic per padded cell of one launch, from the ncu captures summarised in
+# profiles/ (8-shot case, same kernel variant; scaled to a launch by its cells).
+# Keyed by (kernel, staging, tile); any other variant reports traffic null.
+TRAFFIC_PER_CELL = {
+    ("step", 3, 32, 16): 54.66,   # TMA, cell pairs, 32x16 (profiles/k_step_tma_guided_wave_8shots.md)
+    ("adj", 1, 64, 8): 94.87,     # per-thread loads, 64x8 (profiles/k_adj_fused_guided_wave_8shots.md)
+}
+
+
 def roofline(exec_, info, prof, nt, ns):
     """Roofline entries of the dominant and of the other stencil kernel."""
     hbm, peak_kind = peaks()
@@ -148,8 +159,15 @@ def roofline(exec_, info, prof, nt, ns):
             name = f"{name.split(' ')[0]} [{staging}, tile {tile[0]}x{tile[1]}] {' '.join(name.split(' ')[1:])}"
         avg = ms / n / 1e3
         achieved = bpc * cells / avg / 1e9
+        traffic = None
+        if exec_ == "batched":
+            key = (k, info["stencil"] if k == "step" else info["adj_stencil"],
+                   info["tile_x"] if k == "step" else info["adj_tile_x"],
+                   info["tile_z"] if k == "step" else info["adj_tile_z"])
+            if key in TRAFFIC_PER_CELL:
+                traffic = TRAFFIC_PER_CELL[key] * cells
         out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": None, "kernel": name, "bytes_per_cell": bpc, "cells_per_launch": cells,
+                    "traffic": traffic, "kernel": name, "bytes_per_cell": bpc, "cells_per_launch": cells,
                     "peak_kind": peak_kind, "launches_timed": n, "avg_us": avg * 1e6,
                     "time_share_est": avg * per_grad[k]})
     tot = sum(r["time_share_est"] for r in out) or 1.0
@@ -228,7 +246,9 @@ def run_ours(args):
     dev = lambda a, dt=np.float32: torch.tensor(np.asarray(a, dt), device="cuda")
     vp, vs, rho = dev(p.vp), dev(p.vs), dev(p.rho)
     tile = tuple(int(v) for v in args.tile.lower().split("x"))
-    plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store, stencil=args.stencil, tile=tile)
+    adj_tile = tuple(int(v) for v in args.adj_tile.lower().split("x"))
+    plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store, stencil=args.stencil, tile=tile,
+                     adj_stencil=args.adj_stencil, adj_tile=adj_tile)
     # observed data: the same sources in the model with the Gaussian anomaly
     ns = acq.ns
     tv = lambda m: dev(np.repeat(np.asarray(m)[None], ns, 0))

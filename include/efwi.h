@@ -112,6 +112,8 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *   stencil            EFWI_STENCIL_*: how EXEC_BATCHED stages a tile in shared
  *                      memory (AUTO lets the autotuner choose); every choice gives
  *                      bitwise-identical results
+ *   adj_tile_x/_z,     the same two choices for the adjoint step (0, 0, AUTO =
+ *   adj_stencil        autotune independently of the forward step)
  */
 typedef struct efwi_plan_desc {
     int nx, nz;
@@ -137,6 +139,8 @@ typedef struct efwi_plan_desc {
     int exec;
     int tile_x, tile_z;
     int stencil;
+    int adj_tile_x, adj_tile_z;
+    int adj_stencil;
 } efwi_plan_desc;
 
 /* What a plan chose and holds (filled by efwi_plan_info). */

@@ -69,7 +69,7 @@ class Plan:
     """
 
     def __init__(self, acq, exec: str = "batched", ckpt_interval: int = 0, ckpt_store: str = "fp32",
-                 tile=(0, 0), stencil: str = "auto"):
+                 tile=(0, 0), stencil: str = "auto", adj_tile=(0, 0), adj_stencil: str = "auto"):
         lib = _abi.load()
         a = acq
         self.nx, self.nz, self.nt = int(a.nx), int(a.nz), int(a.nt)
@@ -105,6 +105,8 @@ class Plan:
         d.exec = EXEC[exec]
         d.tile_x, d.tile_z = int(tile[0]), int(tile[1])
         d.stencil = STENCIL[stencil]
+        d.adj_tile_x, d.adj_tile_z = int(adj_tile[0]), int(adj_tile[1])
+        d.adj_stencil = STENCIL[adj_stencil]
         self.exec, self.ckpt_store = exec, ckpt_store
         h = C.c_void_p()
         torch.cuda.init()

@@ -564,7 +564,9 @@ int select_fwd(efwi_plan *p, const Variant &v) {
 int efwi_autotune(efwi_plan *p) {
     set_all_attrs();
     const int want = p->d.stencil;
+    const int want_a = p->d.adj_stencil;
     const bool fixed = p->tile_x > 0 && p->tile_z > 0;
+    const bool fixed_a = p->adj_tile_x > 0 && p->adj_tile_z > 0;
     std::vector<Variant> fwd, adj;
     for (auto &s : kShapes) {
         if (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)) continue;
@@ -575,16 +577,24 @@ int efwi_autotune(efwi_plan *p) {
             for (int nst = 2; nst <= 4; ++nst)
                 if (tma_shape_ok(s.tx, s.tz, nst, vec)) fwd.push_back({kind, s.tx, s.tz, nst, vec});
         }
-        if (want == EFWI_STENCIL_AUTO || want == EFWI_STENCIL_LOADS) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+    }
+    // the adjoint follows its own request, or the forward one when it has none
+    const int wa = want_a != EFWI_STENCIL_AUTO ? want_a : want;
+    for (auto &s : kShapes) {
+        if (fixed_a ? (s.tx != p->adj_tile_x || s.tz != p->adj_tile_z)
+                    : (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)))
+            continue;
+        if (wa == EFWI_STENCIL_AUTO || wa == EFWI_STENCIL_LOADS) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
         for (int nst = 1; nst <= 2; ++nst)
-            if (want != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
+            if (wa != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
                 adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, nst});
     }
     // a requested staging without an instantiation for this tile falls back to per-thread loads
     for (auto &s : kShapes) {
-        if (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)) continue;
-        if (fwd.empty()) fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-        if (adj.empty()) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        if (fwd.empty() && (!fixed || (s.tx == p->tile_x && s.tz == p->tile_z)))
+            fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        if (adj.empty() && (!fixed_a || (s.tx == p->adj_tile_x && s.tz == p->adj_tile_z)))
+            adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
     }
     if (fwd.empty() || adj.empty()) {
         p->err = "no compiled stencil variant matches the requested tile/stencil "

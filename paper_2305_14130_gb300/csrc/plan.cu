@@ -199,8 +199,12 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (d->exec == EFWI_EXEC_BATCHED &&
         ((d->tile_x != 0 || d->tile_z != 0) && (d->tile_x <= 0 || d->tile_z <= 0)))
         return fail(nullptr, EFWI_ERR_ARG, "tile_x and tile_z must both be 0 or both positive");
-    if (d->stencil < EFWI_STENCIL_AUTO || d->stencil > EFWI_STENCIL_TMA_PAIRS)
+    if (d->stencil < EFWI_STENCIL_AUTO || d->stencil > EFWI_STENCIL_TMA_PAIRS ||
+        d->adj_stencil < EFWI_STENCIL_AUTO || d->adj_stencil > EFWI_STENCIL_TMA_PAIRS)
         return fail(nullptr, EFWI_ERR_ARG, "unknown stencil");
+    if (d->exec == EFWI_EXEC_BATCHED &&
+        ((d->adj_tile_x != 0 || d->adj_tile_z != 0) && (d->adj_tile_x <= 0 || d->adj_tile_z <= 0)))
+        return fail(nullptr, EFWI_ERR_ARG, "adj_tile_x and adj_tile_z must both be 0 or both positive");
 
     const long long ncell = (long long)d->nx * d->nz;
     double vmax = d->pml_vmax;
@@ -444,6 +448,7 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     }
     if (d->exec == EFWI_EXEC_BATCHED) {
         p->tile_x = d->tile_x; p->tile_z = d->tile_z;
+        p->adj_tile_x = d->adj_tile_x; p->adj_tile_z = d->adj_tile_z;
         int rc = efwi_autotune(p);
         if (rc != EFWI_OK) {
             std::string m = p->err;
