@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--tile", default="0x0", help="forward tile, e.g. 32x16 (0x0 = autotune)")
     ap.add_argument("--adj-stencil", default="auto", choices=["auto", "loads", "tma"])
     ap.add_argument("--adj-tile", default="0x0", help="adjoint tile (0x0 = autotune)")
+    ap.add_argument("--overlap", default="auto", choices=["auto", "off", "on"])
     ap.add_argument("--ns", type=int, default=32)
     ap.add_argument("--nt", type=int, default=4000)
     return ap.parse_args()
@@ -248,7 +249,7 @@ def run_ours(args):
     tile = tuple(int(v) for v in args.tile.lower().split("x"))
     adj_tile = tuple(int(v) for v in args.adj_tile.lower().split("x"))
     plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store, stencil=args.stencil, tile=tile,
-                     adj_stencil=args.adj_stencil, adj_tile=adj_tile)
+                     adj_stencil=args.adj_stencil, adj_tile=adj_tile, overlap=args.overlap)
     # observed data: the same sources in the model with the Gaussian anomaly
     ns = acq.ns
     tv = lambda m: dev(np.repeat(np.asarray(m)[None], ns, 0))
@@ -368,6 +369,7 @@ def run_ours(args):
                            "stencil": {1: "loads", 2: "tma", 3: "tma_pairs"}.get(info["stencil"], "?"), "stages": info["stages"],
                            "adj_stencil": {1: "loads", 2: "tma"}.get(info["adj_stencil"], "?"),
                            "adj_stages": info["adj_stages"],
+                           "overlap_blocks_per_sm": [info["overlap_fwd_blocks"], info["overlap_adj_blocks"]],
                            "l2": "working set > L2 (wavefields, checkpoints, data >> 129 MB)",
                            "parallelism": f"replicas x{world} (independent extended problems)"},
                 "s_per_gradient": s_per_grad,

@@ -75,6 +75,7 @@ enum efwi_store { EFWI_STORE_FP32 = 0, EFWI_STORE_FP16 = 1, EFWI_STORE_BF16 = 2 
 enum efwi_exec { EFWI_EXEC_PLAIN = 0, EFWI_EXEC_BATCHED = 1 };
 /* tile staging of the batched forward and adjoint steps: per-thread loads, or
  * TMA bulk tensor copies into pipelined shared memory (persistent CTAs)     */
+enum efwi_overlap { EFWI_OVERLAP_AUTO = 0, EFWI_OVERLAP_OFF = 1, EFWI_OVERLAP_ON = 2 };
 enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_TMA = 2,
                     EFWI_STENCIL_TMA_PAIRS = 3 /* TMA, two adjacent cells per thread (forward step) */ };
 
@@ -114,6 +115,9 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *                      bitwise-identical results
  *   adj_tile_x/_z,     the same two choices for the adjoint step (0, 0, AUTO =
  *   adj_stencil        autotune independently of the forward step)
+ *   overlap            EFWI_OVERLAP_*: whether the checkpoint recompute of one
+ *                      segment runs concurrently with the adjoint of the next
+ *                      (EXEC_BATCHED with ckpt_interval < nt); results are the same
  */
 typedef struct efwi_plan_desc {
     int nx, nz;
@@ -141,6 +145,7 @@ typedef struct efwi_plan_desc {
     int stencil;
     int adj_tile_x, adj_tile_z;
     int adj_stencil;
+    int overlap;
 } efwi_plan_desc;
 
 /* What a plan chose and holds (filled by efwi_plan_info). */
@@ -153,6 +158,9 @@ typedef struct efwi_plan_info_t {
     int stages;                 /* shared-memory pipeline depth of the TMA forward step */
     int adj_stencil;            /* EFWI_STENCIL_* used by the adjoint step */
     int adj_stages;             /* pipeline depth of the TMA adjoint step */
+    int overlap_fwd_blocks;     /* persistent blocks per SM of the recompute step when it
+                                   overlaps the adjoint (0: no overlap) */
+    int overlap_adj_blocks;     /* and of the adjoint step */
     size_t workspace_bytes;     /* device bytes owned by the plan */
     long long padded_cells;     /* sum over shots of padded (nx_w + 2P)(nz + 2P) */
     long long physical_cells;   /* sum over shots of window width * nz */

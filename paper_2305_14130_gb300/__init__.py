@@ -23,7 +23,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import EfwiError, STORE, EXEC, STENCIL
+from ._abi import EfwiError, STORE, EXEC, STENCIL, OVERLAP
 
 __all__ = ["Plan", "zoi_weights", "EfwiError", "load_library", "DataMisfit", "Consistency", "extended_objective"]
 
@@ -69,7 +69,8 @@ class Plan:
     """
 
     def __init__(self, acq, exec: str = "batched", ckpt_interval: int = 0, ckpt_store: str = "fp32",
-                 tile=(0, 0), stencil: str = "auto", adj_tile=(0, 0), adj_stencil: str = "auto"):
+                 tile=(0, 0), stencil: str = "auto", adj_tile=(0, 0), adj_stencil: str = "auto",
+                 overlap: str = "auto"):
         lib = _abi.load()
         a = acq
         self.nx, self.nz, self.nt = int(a.nx), int(a.nz), int(a.nt)
@@ -107,6 +108,7 @@ class Plan:
         d.stencil = STENCIL[stencil]
         d.adj_tile_x, d.adj_tile_z = int(adj_tile[0]), int(adj_tile[1])
         d.adj_stencil = STENCIL[adj_stencil]
+        d.overlap = OVERLAP[overlap]
         self.exec, self.ckpt_store = exec, ckpt_store
         h = C.c_void_p()
         torch.cuda.init()

@@ -13,6 +13,7 @@ DAS_STRAIN, DAS_STRAIN_RATE = 0, 1
 STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXEC = {"plain": 0, "batched": 1}
 STENCIL = {"auto": 0, "loads": 1, "tma": 2, "tma_pairs": 3}
+OVERLAP = {"auto": 0, "off": 1, "on": 2}
 
 PD = C.POINTER(C.c_double)
 PF = C.POINTER(C.c_float)
@@ -27,13 +28,15 @@ class PlanDesc(C.Structure):
                 ("ch_xz", PD), ("ch_t", PD), ("gauge", C.c_double), ("das_mode", C.c_int), ("win", PI),
                 ("ref_vp", PF), ("ref_vs", PF), ("ref_rho", PF), ("ckpt_interval", C.c_int),
                 ("ckpt_store", C.c_int), ("exec", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
-                ("stencil", C.c_int), ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("adj_stencil", C.c_int)]
+                ("stencil", C.c_int), ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("adj_stencil", C.c_int),
+                ("overlap", C.c_int)]
 
 
 class PlanInfo(C.Structure):
     _fields_ = [("ckpt_interval", C.c_int), ("n_ckpt", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
                 ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("stencil", C.c_int),
                 ("stages", C.c_int), ("adj_stencil", C.c_int), ("adj_stages", C.c_int),
+                ("overlap_fwd_blocks", C.c_int), ("overlap_adj_blocks", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong)]
 

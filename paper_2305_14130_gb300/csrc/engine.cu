@@ -49,6 +49,8 @@ void reset_forward_state(efwi_plan *p, cudaStream_t st) {
 
 float *seg_x(efwi_plan *p, int slot) { return p->seg + (size_t)slot * 2 * p->fsz_total; }
 float *seg_z(efwi_plan *p, int slot) { return p->seg + (size_t)slot * 2 * p->fsz_total + p->fsz_total; }
+// slot of the segment buffer half used by segment sgi in the overlapped schedule
+int seg_slot(efwi_plan *p, int sgi, int k) { return (p->seg_double ? (sgi & 1) * p->K : 0) + k; }
 
 // One forward step of every shot; d == nullptr skips the DAS sampling.
 void forward_step(efwi_plan *p, int n, float *d, float *sx, float *sz, cudaStream_t st) {
@@ -113,6 +115,40 @@ void adjoint_loop(efwi_plan *p, cudaStream_t st) {
     const int nt = p->d.nt, K = p->K;
     const bool full = K >= nt;
     const int nseg = (nt + K - 1) / K;
+    if (!full && p->ov_fwd > 0 && p->seg_double) {
+        // recompute of segment s-1 (stream sr) runs concurrently with the adjoint of
+        // segment s (stream st); the two alternate between the segment-buffer halves
+        cudaStream_t sr = p->cap2;
+        cudaEvent_t *evR = &p->ovev[0], *evA = &p->ovev[nseg];
+        cudaEvent_t fork = p->ovev[2 * nseg], join = p->ovev[2 * nseg + 1];
+        cudaEventRecord(fork, st);
+        cudaStreamWaitEvent(sr, fork);
+        auto recompute = [&](int s) {
+            if (s + 2 < nseg) cudaStreamWaitEvent(sr, evA[s + 2]);
+            const int n0 = s * K, n1 = std::min(n0 + K, nt);
+            launch_ckpt_load(p, s, sr);
+            p->grid_fwd_override = p->ov_fwd * p->n_sms;
+            for (int n = n0; n < n1; ++n)
+                forward_step(p, n, nullptr, seg_x(p, seg_slot(p, s, n - n0)), seg_z(p, seg_slot(p, s, n - n0)), sr);
+            p->grid_fwd_override = 0;
+            cudaEventRecord(evR[s], sr);
+        };
+        recompute(nseg - 1);
+        for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+            if (sgi > 0) recompute(sgi - 1);
+            cudaStreamWaitEvent(st, evR[sgi]);
+            const int n0 = sgi * K, n1 = std::min(n0 + K, nt);
+            p->grid_adj_override = p->ov_adj * p->n_sms;
+            for (int n = n1 - 1; n >= n0; --n)
+                adjoint_step(p, n, seg_x(p, seg_slot(p, sgi, n - n0)), seg_z(p, seg_slot(p, sgi, n - n0)), st);
+            p->grid_adj_override = 0;
+            if (p->Gtot) launch_kahan_fold(p, st);
+            cudaEventRecord(evA[sgi], st);
+        }
+        cudaEventRecord(join, sr);
+        cudaStreamWaitEvent(st, join);
+        return;
+    }
     for (int sgi = nseg - 1; sgi >= 0; --sgi) {
         const int n0 = sgi * K, n1 = std::min(n0 + K, nt);
         if (!full) {

@@ -559,7 +559,8 @@ void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaSt
         launch_step_tma(p, n, vseg_x, vseg_z, st);
     } else {
         FwdArgs a = fwd_args(p, n, vseg_x, vseg_z);
-        EFWI_DISPATCH(p->tiles.tx, p->tiles.tz, fwd_launch, a, a.ntiles, st);
+        const int grid = p->grid_fwd_override > 0 ? std::min(p->grid_fwd_override, a.ntiles) : a.ntiles;
+        EFWI_DISPATCH(p->tiles.tx, p->tiles.tz, fwd_launch, a, grid, st);
     }
     prof_end(p, st, slot);
     p->launches++;
@@ -575,7 +576,8 @@ void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, c
         launch_adj_tma(p, vfx, st);
     } else {
         AdjArgsF a = adj_args_f(p, vfx, vfz);
-        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, a.ntiles, st);
+        const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles) : a.ntiles;
+        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
     }
     prof_end(p, st, slot);
     p->launches++;
@@ -699,6 +701,84 @@ int efwi_autotune(efwi_plan *p) {
         cudaEventDestroy(e1);
         cudaStreamDestroy(st);
     }
+    // overlap of recompute and adjoint: time both chains on two streams for a few
+    // splits of the SMs' blocks, against running them one after the other
+    rc = select_fwd(p, bf);
+    if (!rc) rc = select_adj(p, ba);
+    p->ov_fwd = p->ov_adj = 0;
+    const long long segbytes = sizeof(float) * (long long)p->K * 2 * p->fsz_total;
+    float *seg2 = nullptr;
+    if (!rc && p->K < p->d.nt && p->d.overlap != EFWI_OVERLAP_OFF &&
+        cudaMalloc((void **)&seg2, segbytes) != cudaSuccess) {
+        cudaGetLastError();
+        seg2 = nullptr;
+        if (p->d.overlap == EFWI_OVERLAP_ON) {
+            p->err = "autotune: no memory for the second segment buffer of the overlapped schedule";
+            return EFWI_ERR_OOM;
+        }
+    }
+    if (seg2) {
+        cudaStream_t sa, sr;
+        cudaStreamCreateWithFlags(&sa, cudaStreamNonBlocking);
+        cudaStreamCreateWithFlags(&sr, cudaStreamNonBlocking);
+        cudaEvent_t e0, e1, ej;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventCreateWithFlags(&ej, cudaEventDisableTiming);
+        float *sx0 = p->seg, *sz0 = p->seg + p->fsz_total;
+        float *sx1 = seg2, *sz1 = seg2 + p->fsz_total;
+        const int reps = 4;
+        const bool tma_adj = p->adj_stencil == EFWI_STENCIL_TMA;
+        auto run = [&](int of, int oa) {
+            float t = 0;
+            for (int w = 0; w < 2; ++w) {
+                cudaEventRecord(e0, sa);
+                cudaStreamWaitEvent(sr, e0);
+                p->grid_fwd_override = of * p->n_sms;
+                for (int r = 0; r < reps; ++r) launch_step_fused(p, 0, sx1, sz1, of ? sr : sa);
+                p->grid_fwd_override = 0;
+                p->grid_adj_override = oa * p->n_sms;
+                for (int r = 0; r < reps; ++r) launch_adj_fused(p, 0, sx0, sz0, sa);
+                p->grid_adj_override = 0;
+                cudaEventRecord(ej, sr);
+                cudaStreamWaitEvent(sa, ej);
+                cudaEventRecord(e1, sa);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&t, e0, e1);
+            }
+            return cudaGetLastError() == cudaSuccess ? t : 1e30f;
+        };
+        (void)tma_adj;
+        const bool force = p->d.overlap == EFWI_OVERLAP_ON;
+        float best = force ? 1e30f : run(0, 0);
+        const int splits[][2] = {{1, 1}, {1, 2}, {2, 1}, {2, 2}, {1, 3}, {3, 1}};
+        for (auto &sp : splits) {
+            const float t = run(sp[0], sp[1]);
+            if (t < (force ? 1.f : 0.97f) * best) { best = t; p->ov_fwd = sp[0]; p->ov_adj = sp[1]; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaEventDestroy(ej);
+        cudaStreamDestroy(sa);
+        cudaStreamDestroy(sr);
+        cudaDeviceSynchronize();
+        cudaFree(seg2);
+        if (p->ov_fwd > 0) {
+            // keep the schedule: one contiguous two-half segment buffer (the TMA adjoint
+            // map covers both halves), maps re-encoded for it
+            float *both = nullptr;
+            if (cudaMalloc((void **)&both, 2 * segbytes) != cudaSuccess) {
+                cudaGetLastError();
+                p->ov_fwd = p->ov_adj = 0;
+            } else {
+                cudaFree(p->seg);
+                p->seg = both;
+                p->bytes += segbytes;
+                p->seg_double = true;
+                rc = select_adj(p, ba);
+            }
+        }
+    }
     // the timing runs touched workspace only; clear what the next call expects zeroed
     cudaDeviceSynchronize();
     for (int k = 0; k < 2; ++k)
@@ -708,14 +788,12 @@ int efwi_autotune(efwi_plan *p) {
     cudaMemset(p->psi, 0, sizeof(float) * 4 * p->H);
     cudaMemset(p->apsi, 0, sizeof(float) * 4 * p->H);
     cudaMemset(p->G, 0, sizeof(float) * 5 * p->fsz_total);
-    cudaMemset(p->seg, 0, sizeof(float) * 2 * p->fsz_total);
+    cudaMemset(p->seg, 0, sizeof(float) * (p->seg_double ? 2 : 1) * p->K * 2 * p->fsz_total);
     cudaMemset(p->dev_err, 0, sizeof(int));
     p->scur = p->acur = p->psi_v = p->psi_s = p->apsi_v = p->apsi_s = 0;
     p->launches = 0;
     p->prof_counter[0] = p->prof_counter[1] = 0;
     p->ev_used = 0;
-    rc = select_fwd(p, bf);
-    if (!rc) rc = select_adj(p, ba);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         p->err = std::string("autotune: ") + cudaGetErrorString(e);

@@ -487,7 +487,7 @@ void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t
     a.rdx = (float)(1.0 / p->d.dx);
     a.rdz = (float)(1.0 / p->d.dz);
     a.err = p->dev_err;
-    const int grid = std::min(p->tma_grid, a.ntiles);
+    const int grid = std::min(p->grid_fwd_override > 0 ? p->grid_fwd_override : p->tma_grid, a.ntiles);
     const int tx = p->tiles.tx, tz = p->tiles.tz, nst = p->tma_stages, vec = p->tma_vec;
 #define EFWI_LAUNCH_X(a_, b_, c_, d_) \
     if (tx == a_ && tz == b_ && nst == c_ && vec == d_) launch_tma<a_, b_, c_, d_>(a, grid, st);
@@ -789,7 +789,7 @@ int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst) {
         const ShotDev &sh = p->shots[s];
         int rc = encode_map(&h[s].ad, p->adj[0], sh, F, 10, tx + 8, tz + 8, 5);
         if (!rc) rc = encode_map(&h[s].m5, p->mat, sh, F, 5, tx + 8, tz + 8, 5);
-        if (!rc) rc = encode_map(&h[s].sg, p->seg, sh, F, 2 * p->K, tx + 8, tz + 8, 2);
+        if (!rc) rc = encode_map(&h[s].sg, p->seg, sh, F, (p->seg_double ? 4 : 2) * p->K, tx + 8, tz + 8, 2);
         if (rc) {
             p->err = "cuTensorMapEncodeTiled failed for the adjoint maps";
             return rc;
@@ -830,7 +830,7 @@ void launch_adj_tma(efwi_plan *p, const float *vfx, cudaStream_t st) {
     a.rdx = (float)(1.0 / p->d.dx);
     a.rdz = (float)(1.0 / p->d.dz);
     a.err = p->dev_err;
-    const int grid = std::min(p->tma_adj_grid, a.ntiles);
+    const int grid = std::min(p->grid_adj_override > 0 ? p->grid_adj_override : p->tma_adj_grid, a.ntiles);
     const int tx = p->adj_tiles.tx, tz = p->adj_tiles.tz, nst = p->tma_adj_stages;
 #define EFWI_LAUNCH_X(a_, b_, c_) if (tx == a_ && tz == b_ && nst == c_) launch_adj_tma_t<a_, b_, c_>(a, grid, st);
     EFWI_TMA_ADJ_VARIANTS(EFWI_LAUNCH_X)

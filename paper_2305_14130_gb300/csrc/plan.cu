@@ -167,6 +167,8 @@ static void free_plan(efwi_plan *p) {
     for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj})
         if (g->exec) cudaGraphExecDestroy(g->exec);
     if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->cap2) cudaStreamDestroy(p->cap2);
+    for (auto &e : p->ovev) cudaEventDestroy(e);
     for (auto &e : p->ev) cudaEventDestroy(e);
     delete p;
 }
@@ -205,6 +207,8 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (d->exec == EFWI_EXEC_BATCHED &&
         ((d->adj_tile_x != 0 || d->adj_tile_z != 0) && (d->adj_tile_x <= 0 || d->adj_tile_z <= 0)))
         return fail(nullptr, EFWI_ERR_ARG, "adj_tile_x and adj_tile_z must both be 0 or both positive");
+    if (d->overlap < EFWI_OVERLAP_AUTO || d->overlap > EFWI_OVERLAP_ON)
+        return fail(nullptr, EFWI_ERR_ARG, "unknown overlap");
 
     const long long ncell = (long long)d->nx * d->nz;
     double vmax = d->pml_vmax;
@@ -396,6 +400,9 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     A(&p->resid, (size_t)std::max(ntr, 1) * nt, "residual");
     A(&p->dbuf, (size_t)std::max(ntr, 1) * nt, "data buffer");
     A(&p->partial, (size_t)kPartials + 8, "reduction scratch");
+    // the second half of the segment buffer exists only if the autotuner keeps the
+    // overlapped recompute/adjoint schedule (or the caller forces it)
+    p->seg_double = false;
     A(&p->seg, (size_t)K * 2 * F, "segment buffer");
     const size_t nck_el = (size_t)p->ck.n * 5 * F;
     if (p->ck.store == EFWI_STORE_FP32) A((float **)&p->ck.fields, nck_el, "checkpoints");
@@ -439,6 +446,14 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     p->ev.resize(8192);
     p->ev_kind.assign(4096, 0);
     cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&p->cap2, cudaStreamNonBlocking);
+    p->ovev.resize(2 * p->ck.n + 2);   // events of the overlapped schedule (dependency only)
+    for (auto &e : p->ovev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&p->n_sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     for (auto &e : p->ev) cudaEventCreate(&e);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -484,6 +499,8 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->stages = p->stencil >= EFWI_STENCIL_TMA ? p->tma_stages : 0;
     info->adj_stencil = p->adj_stencil;
     info->adj_stages = p->adj_stencil == EFWI_STENCIL_TMA ? p->tma_adj_stages : 0;
+    info->overlap_fwd_blocks = p->ov_fwd;
+    info->overlap_adj_blocks = p->ov_adj;
     info->workspace_bytes = p->bytes;
     info->padded_cells = p->padded_cells;
     info->physical_cells = p->physical_cells;

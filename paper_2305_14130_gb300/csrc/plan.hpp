@@ -94,7 +94,7 @@ struct efwi_plan {
     float *resid = nullptr;                // [ntr][nt]
     float *dbuf = nullptr;                 // [ntr][nt]
     double *partial = nullptr;             // reduction scratch
-    float *seg = nullptr;                  // segment buffer: K x 2 x fsz_total
+    float *seg = nullptr;                  // segment buffer: (1 or 2) x K x 2 x fsz_total
     efwi::CkptStore ck;
     int K = 0;                             // checkpoint interval
     int tile_x = 0, tile_z = 0;            // forward tile
@@ -113,6 +113,14 @@ struct efwi_plan {
 
     // batched path: time loops captured once and replayed
     cudaStream_t cap = nullptr;            // capture stream (never executes work)
+    cudaStream_t cap2 = nullptr;           // second capture stream (recompute branch)
+    std::vector<cudaEvent_t> ovev;         // dependency events of the overlapped schedule
+    int n_sms = 0;
+    // recompute of segment k-1 overlapped with the adjoint of segment k: persistent
+    // blocks per SM of the forward and adjoint step kernels (0: run one after the other)
+    int ov_fwd = 0, ov_adj = 0;
+    int grid_fwd_override = 0, grid_adj_override = 0;   // launch grids in effect (0 = default)
+    bool seg_double = false;               // segment buffer holds two halves (overlap)
     efwi::GraphCache g_fwd, g_fwd_ck, g_adj;
     bool use_graphs = true;
 
