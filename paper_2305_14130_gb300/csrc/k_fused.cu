@@ -20,6 +20,7 @@
 // Every per-cell expression matches the plain kernels term by term.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "plan.hpp"
@@ -685,16 +686,23 @@ int efwi_autotune(efwi_plan *p) {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
+        // EFWI_AUTOTUNE_LOG=1 reports every timed variant on stderr
+        const char *lg = getenv("EFWI_AUTOTUNE_LOG");
+        const bool log = lg && lg[0] == '1';
         float best = 1e30f;
         for (auto &v : fwd) {
             if (select_fwd(p, v)) continue;
             const float t = time_steps(p, false, st, e0, e1);
+            if (log) fprintf(stderr, "efwi autotune fwd kind %d tile %dx%d param %d vec %d: %.1f us\n", v.kind, v.tx,
+                             v.tz, v.nst, v.vec, t * 1e3f / 3);
             if (t < best) { best = t; bf = v; }
         }
         best = 1e30f;
         for (auto &v : adj) {
             if (select_adj(p, v)) continue;
             const float t = time_steps(p, true, st, e0, e1);
+            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d: %.1f us\n", v.kind, v.tx, v.tz,
+                             v.nst, t * 1e3f / 3);
             if (t < best) { best = t; ba = v; }
         }
         cudaEventDestroy(e0);
