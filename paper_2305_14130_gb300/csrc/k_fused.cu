@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <type_traits>
 #include <vector>
 
 #include "plan.hpp"
@@ -197,7 +198,7 @@ struct AdjArgsF {
 };
 
 template <int TX, int TZ>
-__global__ void __launch_bounds__(kThreads) k_adj_fused(AdjArgsF a) {
+__global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(AdjArgsF a) {
     constexpr int SX = TX + 8, SZ = TZ + 8;
     constexpr int VX = TX + 4, VZ = TZ + 4;
     extern __shared__ float4 smem4[];
@@ -208,210 +209,216 @@ __global__ void __launch_bounds__(kThreads) k_adj_fused(AdjArgsF a) {
 
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = a.tiles[t];
-        const ShotDev *sp = a.shots + tl.x;
-        const int NX = sp->NX, NZ = sp->NZ, PP = sp->P, profx = sp->profx, pitch = sp->pitch, w = sp->w;
-        const long long off = sp->off, psx = sp->psx, psz = sp->psz;
-        const bool edge = (tl.w & 4) != 0;      // 4-cell halo touches a strip or the grid edge
-        const int i0 = tl.y, j0 = tl.z;
-        const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
+        // interior tiles (no CPML strip or grid edge within the 4-cell halo) run a
+        // copy of the body without any of the edge tests
+        auto tile = [&](auto edge_c) {
+            const ShotDev *sp = a.shots + tl.x;
+            const int NX = sp->NX, NZ = sp->NZ, PP = sp->P, profx = sp->profx, pitch = sp->pitch, w = sp->w;
+            const long long off = sp->off, psx = sp->psx, psz = sp->psz;
+            constexpr bool edge = decltype(edge_c)::value;   // 4-cell halo touches a strip or the grid edge
+            const int i0 = tl.y, j0 = tl.z;
+            const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
 
-        // Each phase first issues every global load of the thread's cells into
-        // registers (no store in between, so all are in flight together), then
-        // computes; each cell's arithmetic is unchanged.
-        // 1. f^ on the tile + 4-cell halo; the tile's stress-sub-step PML memory advances
-        constexpr int N1 = (SX * SZ + kThreads - 1) / kThreads;
-        float lxx[N1], lzz[N1], lxz[N1], llam[N1], lmu[N1], lmxz[N1];
+            // Each phase first issues every global load of the thread's cells into
+            // registers (no store in between, so all are in flight together), then
+            // computes; each cell's arithmetic is unchanged.
+            // 1. f^ on the tile + 4-cell halo; the tile's stress-sub-step PML memory advances
+            constexpr int N1 = (SX * SZ + kThreads - 1) / kThreads;
+            float lxx[N1], lzz[N1], lxz[N1], llam[N1], lmu[N1], lmxz[N1];
 #pragma unroll
-        for (int r = 0; r < N1; ++r) {
-            const int q = tid + r * kThreads;
-            lxx[r] = lzz[r] = lxz[r] = llam[r] = lmu[r] = lmxz[r] = 0.f;
-            const int y = q / SX, x = q - y * SX;
-            const int i = i0 - 4 + x, j = j0 - 4 + y;
-            if (q < SX * SZ && (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ))) {
-                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                lxx[r] = __ldg(a.in.sxx + c); lzz[r] = __ldg(a.in.szz + c); lxz[r] = __ldg(a.in.sxz + c);
-                llam[r] = __ldg(a.M.lam + c); lmu[r] = __ldg(a.M.mu + c); lmxz[r] = __ldg(a.M.muxz + c);
+            for (int r = 0; r < N1; ++r) {
+                const int q = tid + r * kThreads;
+                lxx[r] = lzz[r] = lxz[r] = llam[r] = lmu[r] = lmxz[r] = 0.f;
+                const int y = q / SX, x = q - y * SX;
+                const int i = i0 - 4 + x, j = j0 - 4 + y;
+                if (q < SX * SZ && (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ))) {
+                    const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    lxx[r] = __ldg(a.in.sxx + c); lzz[r] = __ldg(a.in.szz + c); lxz[r] = __ldg(a.in.sxz + c);
+                    llam[r] = __ldg(a.M.lam + c); lmu[r] = __ldg(a.M.mu + c); lmxz[r] = __ldg(a.M.muxz + c);
+                }
             }
-        }
 #pragma unroll
-        for (int r = 0; r < N1; ++r) {
-            const int q = tid + r * kThreads;
-            if (q >= SX * SZ) break;
-            const int y = q / SX, x = q - y * SX;
-            const int i = i0 - 4 + x, j = j0 - 4 + y;
-            float g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f;
-            if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
-                const float hxx = lxx[r], hzz = lzz[r], hxz = lxz[r];
-                const float lam = llam[r], l2m = lam + 2.f * lmu[r];
-                const float Ex = dt * (l2m * hxx + lam * hzz);
-                const float Ez = dt * (lam * hxx + l2m * hzz);
-                const float Exz = dt * lmxz[r] * hxz;
-                g1 = Ex; g2 = Ez; g3 = Exz; g4 = Exz;
-                if (edge) {
-                    const bool own = x >= 4 && x < TX + 4 && y >= 4 && y < TZ + 4;
-                    const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
-                    const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
-                    if (xs >= 0) {
-                        const long long k = psx + (long long)j * 2 * PP + xs;
-                        const int pq = profx + i;
-                        const float P5 = a.pml.x[2][k], P8 = a.pml.x[3][k];
-                        g1 += a.pml.ax_i[pq] * (P5 + Ex);
-                        g4 += a.pml.ax_h[pq] * (P8 + Exz);
-                        if (own) {
-                            a.n5[k] = a.pml.bx_i[pq] * (P5 + Ex);
-                            a.n8[k] = a.pml.bx_h[pq] * (P8 + Exz);
+            for (int r = 0; r < N1; ++r) {
+                const int q = tid + r * kThreads;
+                if (q >= SX * SZ) break;
+                const int y = q / SX, x = q - y * SX;
+                const int i = i0 - 4 + x, j = j0 - 4 + y;
+                float g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f;
+                if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
+                    const float hxx = lxx[r], hzz = lzz[r], hxz = lxz[r];
+                    const float lam = llam[r], l2m = lam + 2.f * lmu[r];
+                    const float Ex = dt * (l2m * hxx + lam * hzz);
+                    const float Ez = dt * (lam * hxx + l2m * hzz);
+                    const float Exz = dt * lmxz[r] * hxz;
+                    g1 = Ex; g2 = Ez; g3 = Exz; g4 = Exz;
+                    if (edge) {
+                        const bool own = x >= 4 && x < TX + 4 && y >= 4 && y < TZ + 4;
+                        const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                        const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                        if (xs >= 0) {
+                            const long long k = psx + (long long)j * 2 * PP + xs;
+                            const int pq = profx + i;
+                            const float P5 = a.pml.x[2][k], P8 = a.pml.x[3][k];
+                            g1 += a.pml.ax_i[pq] * (P5 + Ex);
+                            g4 += a.pml.ax_h[pq] * (P8 + Exz);
+                            if (own) {
+                                a.n5[k] = a.pml.bx_i[pq] * (P5 + Ex);
+                                a.n8[k] = a.pml.bx_h[pq] * (P8 + Exz);
+                            }
                         }
-                    }
-                    if (zs >= 0) {
-                        const long long k = psz + (long long)zs * NX + i;
-                        const float P6 = a.pml.z[2][k], P7 = a.pml.z[3][k];
-                        g2 += a.pml.az_i[j] * (P6 + Ez);
-                        g3 += a.pml.az_h[j] * (P7 + Exz);
-                        if (own) {
-                            a.n6[k] = a.pml.bz_i[j] * (P6 + Ez);
-                            a.n7[k] = a.pml.bz_h[j] * (P7 + Exz);
+                        if (zs >= 0) {
+                            const long long k = psz + (long long)zs * NX + i;
+                            const float P6 = a.pml.z[2][k], P7 = a.pml.z[3][k];
+                            g2 += a.pml.az_i[j] * (P6 + Ez);
+                            g3 += a.pml.az_h[j] * (P7 + Exz);
+                            if (own) {
+                                a.n6[k] = a.pml.bz_i[j] * (P6 + Ez);
+                                a.n7[k] = a.pml.bz_h[j] * (P7 + Exz);
+                            }
                         }
                     }
                 }
+                f1s[q] = g1; f2s[q] = g2; f3s[q] = g3; f4s[q] = g4;
             }
-            f1s[q] = g1; f2s[q] = g2; f3s[q] = g3; f4s[q] = g4;
-        }
-        __syncthreads();
+            __syncthreads();
 
-        // 2. v^ += D^T f^ on the tile + 2-cell halo; e^ in shared memory
-        constexpr int N2 = (VX * VZ + kThreads - 1) / kThreads;
-        float lvx[N2], lvz[N2], lbx[N2], lbz[N2], lfx[N2], lfz[N2], lgx[N2], lgz[N2];
+            // 2. v^ += D^T f^ on the tile + 2-cell halo; e^ in shared memory
+            constexpr int N2 = (VX * VZ + kThreads - 1) / kThreads;
+            float lvx[N2], lvz[N2], lbx[N2], lbz[N2], lfx[N2], lfz[N2], lgx[N2], lgz[N2];
 #pragma unroll
-        for (int r = 0; r < N2; ++r) {
-            const int q = tid + r * kThreads;
-            lvx[r] = lvz[r] = lbx[r] = lbz[r] = lfx[r] = lfz[r] = lgx[r] = lgz[r] = 0.f;
-            const int y = q / VX, x = q - y * VX;
-            const int i = i0 - 2 + x, j = j0 - 2 + y;
-            if (q < VX * VZ && (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ))) {
-                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                lvx[r] = __ldg(a.in.vx + c); lvz[r] = __ldg(a.in.vz + c);
-                lbx[r] = __ldg(a.M.bx + c); lbz[r] = __ldg(a.M.bz + c);
-                const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
-                if (own && (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP))) {
-                    lfx[r] = __ldg(a.vfx + c); lfz[r] = __ldg(a.vfz + c);
-                    lgx[r] = a.Gbx[c]; lgz[r] = a.Gbz[c];
-                }
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < N2; ++r) {
-            const int q = tid + r * kThreads;
-            if (q >= VX * VZ) break;
-            const int y = q / VX, x = q - y * VX;
-            const int i = i0 - 2 + x, j = j0 - 2 + y;
-            float h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f;
-            if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
-                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                const int o = (y + 2) * SX + (x + 2);
-                const float inc_x = -(C1 * (f1s[o + 1] - f1s[o]) + C2 * (f1s[o + 2] - f1s[o - 1])) * rdx
-                                    - (C1 * (f3s[o] - f3s[o - SX]) + C2 * (f3s[o + SX] - f3s[o - 2 * SX])) * rdz;
-                const float inc_z = -(C1 * (f2s[o + SX] - f2s[o]) + C2 * (f2s[o + 2 * SX] - f2s[o - SX])) * rdz
-                                    - (C1 * (f4s[o] - f4s[o - 1]) + C2 * (f4s[o + 1] - f4s[o - 2])) * rdx;
-                const float vx = lvx[r] + inc_x;
-                const float vz = lvz[r] + inc_z;
-                const float qx = dt * lbx[r] * vx, qz = dt * lbz[r] * vz;
-                h1 = qx; h2 = qx; h3 = qz; h4 = qz;
-                const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
-                if (edge) {
-                    const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
-                    const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
-                    if (xs >= 0) {
-                        const long long k = psx + (long long)j * 2 * PP + xs;
-                        const int pq = profx + i;
-                        const float P1 = a.pml.x[0][k], P3 = a.pml.x[1][k];
-                        h1 += a.pml.ax_h[pq] * (P1 + qx);
-                        h3 += a.pml.ax_i[pq] * (P3 + qz);
-                        if (own) {
-                            a.n1[k] = a.pml.bx_h[pq] * (P1 + qx);
-                            a.n3[k] = a.pml.bx_i[pq] * (P3 + qz);
-                        }
-                    }
-                    if (zs >= 0) {
-                        const long long k = psz + (long long)zs * NX + i;
-                        const float P2 = a.pml.z[0][k], P4 = a.pml.z[1][k];
-                        h2 += a.pml.az_i[j] * (P2 + qx);
-                        h4 += a.pml.az_h[j] * (P4 + qz);
-                        if (own) {
-                            a.n2[k] = a.pml.bz_i[j] * (P2 + qx);
-                            a.n4[k] = a.pml.bz_h[j] * (P4 + qz);
-                        }
-                    }
-                }
-                if (own) {
-                    a.out.vx[c] = vx;
-                    a.out.vz[c] = vz;
-                    if (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP)) {
-                        a.Gbx[c] = lgx[r] + lfx[r] * inc_x;
-                        a.Gbz[c] = lgz[r] + lfz[r] * inc_z;
+            for (int r = 0; r < N2; ++r) {
+                const int q = tid + r * kThreads;
+                lvx[r] = lvz[r] = lbx[r] = lbz[r] = lfx[r] = lfz[r] = lgx[r] = lgz[r] = 0.f;
+                const int y = q / VX, x = q - y * VX;
+                const int i = i0 - 2 + x, j = j0 - 2 + y;
+                if (q < VX * VZ && (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ))) {
+                    const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    lvx[r] = __ldg(a.in.vx + c); lvz[r] = __ldg(a.in.vz + c);
+                    lbx[r] = __ldg(a.M.bx + c); lbz[r] = __ldg(a.M.bz + c);
+                    const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
+                    if (own && (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP))) {
+                        lfx[r] = __ldg(a.vfx + c); lfz[r] = __ldg(a.vfz + c);
+                        lgx[r] = a.Gbx[c]; lgz[r] = a.Gbz[c];
                     }
                 }
             }
-            e1s[q] = h1; e2s[q] = h2; e3s[q] = h3; e4s[q] = h4;
-        }
-        __syncthreads();
+#pragma unroll
+            for (int r = 0; r < N2; ++r) {
+                const int q = tid + r * kThreads;
+                if (q >= VX * VZ) break;
+                const int y = q / VX, x = q - y * VX;
+                const int i = i0 - 2 + x, j = j0 - 2 + y;
+                float h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f;
+                if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
+                    const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    const int o = (y + 2) * SX + (x + 2);
+                    const float inc_x = -(C1 * (f1s[o + 1] - f1s[o]) + C2 * (f1s[o + 2] - f1s[o - 1])) * rdx
+                                        - (C1 * (f3s[o] - f3s[o - SX]) + C2 * (f3s[o + SX] - f3s[o - 2 * SX])) * rdz;
+                    const float inc_z = -(C1 * (f2s[o + SX] - f2s[o]) + C2 * (f2s[o + 2 * SX] - f2s[o - SX])) * rdz
+                                        - (C1 * (f4s[o] - f4s[o - 1]) + C2 * (f4s[o + 1] - f4s[o - 2])) * rdx;
+                    const float vx = lvx[r] + inc_x;
+                    const float vz = lvz[r] + inc_z;
+                    const float qx = dt * lbx[r] * vx, qz = dt * lbz[r] * vz;
+                    h1 = qx; h2 = qx; h3 = qz; h4 = qz;
+                    const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
+                    if (edge) {
+                        const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                        const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                        if (xs >= 0) {
+                            const long long k = psx + (long long)j * 2 * PP + xs;
+                            const int pq = profx + i;
+                            const float P1 = a.pml.x[0][k], P3 = a.pml.x[1][k];
+                            h1 += a.pml.ax_h[pq] * (P1 + qx);
+                            h3 += a.pml.ax_i[pq] * (P3 + qz);
+                            if (own) {
+                                a.n1[k] = a.pml.bx_h[pq] * (P1 + qx);
+                                a.n3[k] = a.pml.bx_i[pq] * (P3 + qz);
+                            }
+                        }
+                        if (zs >= 0) {
+                            const long long k = psz + (long long)zs * NX + i;
+                            const float P2 = a.pml.z[0][k], P4 = a.pml.z[1][k];
+                            h2 += a.pml.az_i[j] * (P2 + qx);
+                            h4 += a.pml.az_h[j] * (P4 + qz);
+                            if (own) {
+                                a.n2[k] = a.pml.bz_i[j] * (P2 + qx);
+                                a.n4[k] = a.pml.bz_h[j] * (P4 + qz);
+                            }
+                        }
+                    }
+                    if (own) {
+                        a.out.vx[c] = vx;
+                        a.out.vz[c] = vz;
+                        if (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP)) {
+                            a.Gbx[c] = lgx[r] + lfx[r] * inc_x;
+                            a.Gbz[c] = lgz[r] + lfz[r] * inc_z;
+                        }
+                    }
+                }
+                e1s[q] = h1; e2s[q] = h2; e3s[q] = h3; e4s[q] = h4;
+            }
+            __syncthreads();
 
-        // 3. sigma^ += D^T e^ on the tile, with the C-imaging
-        constexpr int N3 = (TX * TZ + kThreads - 1) / kThreads;
-        float sxx_r[N3], szz_r[N3], sxz_r[N3], fxm2[N3], fxm1[N3], fx0[N3], fxp1[N3], fzm2[N3], fzm1[N3], fz0[N3],
-            fzp1[N3], fxzm[N3], fxz1[N3], fxz2[N3], vzx1[N3], vzx2[N3], vzm1[N3], g0[N3], g1v[N3], g2v[N3];
+            // 3. sigma^ += D^T e^ on the tile, with the C-imaging
+            constexpr int N3 = (TX * TZ + kThreads - 1) / kThreads;
+            float sxx_r[N3], szz_r[N3], sxz_r[N3], fxm2[N3], fxm1[N3], fx0[N3], fxp1[N3], fzm2[N3], fzm1[N3], fz0[N3],
+                fzp1[N3], fxzm[N3], fxz1[N3], fxz2[N3], vzx1[N3], vzx2[N3], vzm1[N3], g0[N3], g1v[N3], g2v[N3];
 #pragma unroll
-        for (int r = 0; r < N3; ++r) {
-            const int q = tid + r * kThreads;
-            const int y = q / TX, x = q - y * TX;
-            const int i = i0 + x, j = j0 + y;
-            sxx_r[r] = szz_r[r] = sxz_r[r] = 0.f;
-            fxm2[r] = fxm1[r] = fx0[r] = fxp1[r] = fzm2[r] = fzm1[r] = fz0[r] = fzp1[r] = 0.f;
-            fxzm[r] = fxz1[r] = fxz2[r] = vzx1[r] = vzx2[r] = vzm1[r] = g0[r] = g1v[r] = g2v[r] = 0.f;
-            if (q < TX * TZ && !(edge && (i >= NX || j >= NZ))) {
-                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                sxx_r[r] = __ldg(a.in.sxx + c); szz_r[r] = __ldg(a.in.szz + c); sxz_r[r] = __ldg(a.in.sxz + c);
-                const bool node = !edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP);
-                const bool half = !edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP);
-                if (node || half) {
-                    fxm2[r] = __ldg(a.vfx + c - 2); fxm1[r] = __ldg(a.vfx + c - 1); fx0[r] = __ldg(a.vfx + c);
-                    fxp1[r] = __ldg(a.vfx + c + 1);
-                    fzm2[r] = __ldg(a.vfz + c - 2 * pitch); fzm1[r] = __ldg(a.vfz + c - pitch);
-                    fz0[r] = __ldg(a.vfz + c); fzp1[r] = __ldg(a.vfz + c + pitch);
-                    fxzm[r] = __ldg(a.vfx + c - pitch); fxz1[r] = __ldg(a.vfx + c + pitch);
-                    fxz2[r] = __ldg(a.vfx + c + 2 * pitch);
-                    vzm1[r] = __ldg(a.vfz + c - 1); vzx1[r] = __ldg(a.vfz + c + 1); vzx2[r] = __ldg(a.vfz + c + 2);
+            for (int r = 0; r < N3; ++r) {
+                const int q = tid + r * kThreads;
+                const int y = q / TX, x = q - y * TX;
+                const int i = i0 + x, j = j0 + y;
+                sxx_r[r] = szz_r[r] = sxz_r[r] = 0.f;
+                fxm2[r] = fxm1[r] = fx0[r] = fxp1[r] = fzm2[r] = fzm1[r] = fz0[r] = fzp1[r] = 0.f;
+                fxzm[r] = fxz1[r] = fxz2[r] = vzx1[r] = vzx2[r] = vzm1[r] = g0[r] = g1v[r] = g2v[r] = 0.f;
+                if (q < TX * TZ && !(edge && (i >= NX || j >= NZ))) {
+                    const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    sxx_r[r] = __ldg(a.in.sxx + c); szz_r[r] = __ldg(a.in.szz + c); sxz_r[r] = __ldg(a.in.sxz + c);
+                    const bool node = !edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP);
+                    const bool half = !edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP);
+                    if (node || half) {
+                        fxm2[r] = __ldg(a.vfx + c - 2); fxm1[r] = __ldg(a.vfx + c - 1); fx0[r] = __ldg(a.vfx + c);
+                        fxp1[r] = __ldg(a.vfx + c + 1);
+                        fzm2[r] = __ldg(a.vfz + c - 2 * pitch); fzm1[r] = __ldg(a.vfz + c - pitch);
+                        fz0[r] = __ldg(a.vfz + c); fzp1[r] = __ldg(a.vfz + c + pitch);
+                        fxzm[r] = __ldg(a.vfx + c - pitch); fxz1[r] = __ldg(a.vfx + c + pitch);
+                        fxz2[r] = __ldg(a.vfx + c + 2 * pitch);
+                        vzm1[r] = __ldg(a.vfz + c - 1); vzx1[r] = __ldg(a.vfz + c + 1); vzx2[r] = __ldg(a.vfz + c + 2);
+                    }
+                    if (node) { g0[r] = a.Glam[c]; g1v[r] = a.Gmu[c]; }
+                    if (half) g2v[r] = a.Gmuxz[c];
                 }
-                if (node) { g0[r] = a.Glam[c]; g1v[r] = a.Gmu[c]; }
-                if (half) g2v[r] = a.Gmuxz[c];
             }
-        }
 #pragma unroll
-        for (int r = 0; r < N3; ++r) {
-            const int q = tid + r * kThreads;
-            if (q >= TX * TZ) break;
-            const int y = q / TX, x = q - y * TX;
-            const int i = i0 + x, j = j0 + y;
-            if (edge && (i >= NX || j >= NZ)) continue;
-            const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-            const float hxx = sxx_r[r], hzz = szz_r[r], hxz = sxz_r[r];
-            if (!edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP)) {
-                const float fx = (C1 * (fx0[r] - fxm1[r]) + C2 * (fxp1[r] - fxm2[r])) * rdx;
-                const float fz = (C1 * (fz0[r] - fzm1[r]) + C2 * (fzp1[r] - fzm2[r])) * rdz;
-                a.Glam[c] = g0[r] + dt * (hxx + hzz) * (fx + fz);
-                a.Gmu[c] = g1v[r] + 2.f * dt * (hxx * fx + hzz * fz);
+            for (int r = 0; r < N3; ++r) {
+                const int q = tid + r * kThreads;
+                if (q >= TX * TZ) break;
+                const int y = q / TX, x = q - y * TX;
+                const int i = i0 + x, j = j0 + y;
+                if (edge && (i >= NX || j >= NZ)) continue;
+                const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                const float hxx = sxx_r[r], hzz = szz_r[r], hxz = sxz_r[r];
+                if (!edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP)) {
+                    const float fx = (C1 * (fx0[r] - fxm1[r]) + C2 * (fxp1[r] - fxm2[r])) * rdx;
+                    const float fz = (C1 * (fz0[r] - fzm1[r]) + C2 * (fzp1[r] - fzm2[r])) * rdz;
+                    a.Glam[c] = g0[r] + dt * (hxx + hzz) * (fx + fz);
+                    a.Gmu[c] = g1v[r] + 2.f * dt * (hxx * fx + hzz * fz);
+                }
+                if (!edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP)) {
+                    const float fxz = (C1 * (fxz1[r] - fx0[r]) + C2 * (fxz2[r] - fxzm[r])) * rdz +
+                                      (C1 * (vzx1[r] - fz0[r]) + C2 * (vzx2[r] - vzm1[r])) * rdx;
+                    a.Gmuxz[c] = g2v[r] + dt * hxz * fxz;
+                }
+                const int o = (y + 2) * VX + (x + 2);
+                a.out.sxx[c] = hxx - (C1 * (e1s[o] - e1s[o - 1]) + C2 * (e1s[o + 1] - e1s[o - 2])) * rdx;
+                a.out.szz[c] = hzz - (C1 * (e4s[o] - e4s[o - VX]) + C2 * (e4s[o + VX] - e4s[o - 2 * VX])) * rdz;
+                a.out.sxz[c] = hxz - (C1 * (e2s[o + VX] - e2s[o]) + C2 * (e2s[o + 2 * VX] - e2s[o - VX])) * rdz
+                                   - (C1 * (e3s[o + 1] - e3s[o]) + C2 * (e3s[o + 2] - e3s[o - 1])) * rdx;
             }
-            if (!edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP)) {
-                const float fxz = (C1 * (fxz1[r] - fx0[r]) + C2 * (fxz2[r] - fxzm[r])) * rdz +
-                                  (C1 * (vzx1[r] - fz0[r]) + C2 * (vzx2[r] - vzm1[r])) * rdx;
-                a.Gmuxz[c] = g2v[r] + dt * hxz * fxz;
-            }
-            const int o = (y + 2) * VX + (x + 2);
-            a.out.sxx[c] = hxx - (C1 * (e1s[o] - e1s[o - 1]) + C2 * (e1s[o + 1] - e1s[o - 2])) * rdx;
-            a.out.szz[c] = hzz - (C1 * (e4s[o] - e4s[o - VX]) + C2 * (e4s[o + VX] - e4s[o - 2 * VX])) * rdz;
-            a.out.sxz[c] = hxz - (C1 * (e2s[o + VX] - e2s[o]) + C2 * (e2s[o + 2 * VX] - e2s[o - VX])) * rdz
-                               - (C1 * (e3s[o + 1] - e3s[o]) + C2 * (e3s[o + 2] - e3s[o - 1])) * rdx;
-        }
-        __syncthreads();
+            __syncthreads();
+        };
+        if (tl.w & 4) tile(std::true_type{});
+        else tile(std::false_type{});
     }
 }
 

@@ -13,6 +13,7 @@
 // by the copy engine, matching the zero ghosts of the layout.  Every mbarrier
 // wait is bounded (about 1 s of clock cycles); on expiry the CTA records the
 // error in the plan's device flag and returns.
+#include <type_traits>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -66,7 +67,7 @@ __device__ __forceinline__ void issue_fwd(const TmaFwdArgs &a, int t, float *buf
 }
 
 template <int TX, int TZ, int NST, int VEC>
-__global__ void __launch_bounds__(kThreads) k_step_tma(TmaFwdArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
     using L = FwdLayout<TX, TZ, NST, VEC>;
     constexpr int SX = L::SX;
     extern __shared__ float4 smem_raw[];
@@ -104,279 +105,285 @@ __global__ void __launch_bounds__(kThreads) k_step_tma(TmaFwdArgs a) {
         phase ^= 1u << b;
 
         const int4 tl = a.tiles[t];
-        const ShotDev *sp = a.shots + tl.x;
-        // shot scalars in registers (loaded once per tile, not after every store)
-        const int NX = sp->NX, NZ = sp->NZ, P = sp->P, profx = sp->profx, pitch = sp->pitch;
-        const long long off = sp->off, psx = sp->psx, psz = sp->psz;
-        const bool edge = (tl.w & 2) != 0;
-        const int i0 = tl.y, j0 = tl.z;
-        float *svx = buf, *svz = buf + L::NS, *sxx = buf + 2 * L::NS, *szz = buf + 3 * L::NS, *sxz = buf + 4 * L::NS;
-        const float *sbx = buf + 5 * L::NS, *sbz = buf + 6 * L::NS;
-        const float *slam = buf + 7 * L::NS, *smu = slam + L::NC, *smxz = smu + L::NC;
-        float *__restrict__ ovx = a.out.vx + off;
-        float *__restrict__ ovz = a.out.vz + off;
-        const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
+        // interior tiles (no CPML strip or grid edge within the halo) run a copy of
+        // the body without any of the edge tests
+        auto tile = [&](auto edge_c) {
+            const ShotDev *sp = a.shots + tl.x;
+            // shot scalars in registers (loaded once per tile, not after every store)
+            const int NX = sp->NX, NZ = sp->NZ, P = sp->P, profx = sp->profx, pitch = sp->pitch;
+            const long long off = sp->off, psx = sp->psx, psz = sp->psz;
+            constexpr bool edge = decltype(edge_c)::value;
+            const int i0 = tl.y, j0 = tl.z;
+            float *svx = buf, *svz = buf + L::NS, *sxx = buf + 2 * L::NS, *szz = buf + 3 * L::NS, *sxz = buf + 4 * L::NS;
+            const float *sbx = buf + 5 * L::NS, *sbz = buf + 6 * L::NS;
+            const float *slam = buf + 7 * L::NS, *smu = slam + L::NC, *smxz = smu + L::NC;
+            float *__restrict__ ovx = a.out.vx + off;
+            float *__restrict__ ovz = a.out.vz + off;
+            const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
 
-        if constexpr (VEC == 2) {
-            // Cell pairs (x, x+1) in halo-4 coordinates, x even: adjacent x-stencils share
-            // their inputs and every shared-memory access moves two cells.  Each cell's
-            // arithmetic is the scalar expression, term by term.
-            constexpr int NPX = (TX + 4) / 2;           // pairs per row of the velocity region
-            for (int q = tid; q < NPX * (TZ + 4); q += kThreads) {
-                const int yy = q / NPX;
-                const int x = 2 + 2 * (q - yy * NPX), y = 2 + yy;
-                const int i = i0 - 4 + x, j = j0 - 4 + y;
-                const int o = y * SX + x;
-                const float2 xa = ld2(sxx + o - 2), xb = ld2(sxx + o), xc = ld2(sxx + o + 2);
-                const float2 za = ld2(sxz + o - 2), zb = ld2(sxz + o), zc = ld2(sxz + o + 2);
-                const float2 zm2 = ld2(sxz + o - 2 * SX), zm1 = ld2(sxz + o - SX), zp1 = ld2(sxz + o + SX);
-                const float2 cm1 = ld2(szz + o - SX), c0 = ld2(szz + o), cp1 = ld2(szz + o + SX),
-                             cp2 = ld2(szz + o + 2 * SX);
-                float e1[2], e2[2], e3[2], e4[2];
-                e1[0] = (C1 * (xb.y - xb.x) + C2 * (xc.x - xa.y)) * rdx;
-                e1[1] = (C1 * (xc.x - xb.y) + C2 * (xc.y - xb.x)) * rdx;
-                e2[0] = (C1 * (zb.x - zm1.x) + C2 * (zp1.x - zm2.x)) * rdz;
-                e2[1] = (C1 * (zb.y - zm1.y) + C2 * (zp1.y - zm2.y)) * rdz;
-                e3[0] = (C1 * (zb.x - za.y) + C2 * (zb.y - za.x)) * rdx;
-                e3[1] = (C1 * (zb.y - zb.x) + C2 * (zc.x - za.y)) * rdx;
-                e4[0] = (C1 * (cp1.x - c0.x) + C2 * (cp2.x - cm1.x)) * rdz;
-                e4[1] = (C1 * (cp1.y - c0.y) + C2 * (cp2.y - cm1.y)) * rdz;
-                const bool own = x >= 4 && x < TX + 4 && y >= 4 && y < TZ + 4;
-                bool in[2] = {true, true};
-                if (edge) {
+            if constexpr (VEC == 2) {
+                // Cell pairs (x, x+1) in halo-4 coordinates, x even: adjacent x-stencils share
+                // their inputs and every shared-memory access moves two cells.  Each cell's
+                // arithmetic is the scalar expression, term by term.
+                constexpr int NPX = (TX + 4) / 2;           // pairs per row of the velocity region
+                for (int q = tid; q < NPX * (TZ + 4); q += kThreads) {
+                    const int yy = q / NPX;
+                    const int x = 2 + 2 * (q - yy * NPX), y = 2 + yy;
+                    const int i = i0 - 4 + x, j = j0 - 4 + y;
+                    const int o = y * SX + x;
+                    const float2 xa = ld2(sxx + o - 2), xb = ld2(sxx + o), xc = ld2(sxx + o + 2);
+                    const float2 za = ld2(sxz + o - 2), zb = ld2(sxz + o), zc = ld2(sxz + o + 2);
+                    const float2 zm2 = ld2(sxz + o - 2 * SX), zm1 = ld2(sxz + o - SX), zp1 = ld2(sxz + o + SX);
+                    const float2 cm1 = ld2(szz + o - SX), c0 = ld2(szz + o), cp1 = ld2(szz + o + SX),
+                                 cp2 = ld2(szz + o + 2 * SX);
+                    float e1[2], e2[2], e3[2], e4[2];
+                    e1[0] = (C1 * (xb.y - xb.x) + C2 * (xc.x - xa.y)) * rdx;
+                    e1[1] = (C1 * (xc.x - xb.y) + C2 * (xc.y - xb.x)) * rdx;
+                    e2[0] = (C1 * (zb.x - zm1.x) + C2 * (zp1.x - zm2.x)) * rdz;
+                    e2[1] = (C1 * (zb.y - zm1.y) + C2 * (zp1.y - zm2.y)) * rdz;
+                    e3[0] = (C1 * (zb.x - za.y) + C2 * (zb.y - za.x)) * rdx;
+                    e3[1] = (C1 * (zb.y - zb.x) + C2 * (zc.x - za.y)) * rdx;
+                    e4[0] = (C1 * (cp1.x - c0.x) + C2 * (cp2.x - cm1.x)) * rdz;
+                    e4[1] = (C1 * (cp1.y - c0.y) + C2 * (cp2.y - cm1.y)) * rdz;
+                    const bool own = x >= 4 && x < TX + 4 && y >= 4 && y < TZ + 4;
+                    bool in[2] = {true, true};
+                    if (edge) {
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int ih = i + h;
-                        in[h] = ih >= 0 && ih < NX && j >= 0 && j < NZ;
-                        if (!in[h]) continue;
-                        const int xs = ih < P ? ih : (ih >= NX - P ? ih - NX + 2 * P : -1);
-                        const int zs = j < P ? j : (j >= NZ - P ? j - NZ + 2 * P : -1);
-                        if (xs >= 0) {
-                            const long long kk = psx + (long long)j * 2 * P + xs;
-                            const int pq = profx + ih;
-                            const float p1 = a.pml.bx_h[pq] * a.pml.x[0][kk] + a.pml.ax_h[pq] * e1[h];
-                            const float p3 = a.pml.bx_i[pq] * a.pml.x[1][kk] + a.pml.ax_i[pq] * e3[h];
-                            if (own) { a.n1[kk] = p1; a.n3[kk] = p3; }
-                            e1[h] += p1; e3[h] += p3;
-                        }
-                        if (zs >= 0) {
-                            const long long kk = psz + (long long)zs * NX + ih;
-                            const float p2 = a.pml.bz_i[j] * a.pml.z[0][kk] + a.pml.az_i[j] * e2[h];
-                            const float p4 = a.pml.bz_h[j] * a.pml.z[1][kk] + a.pml.az_h[j] * e4[h];
-                            if (own) { a.n2[kk] = p2; a.n4[kk] = p4; }
-                            e2[h] += p2; e4[h] += p4;
-                        }
-                    }
-                }
-                const float2 vxo = ld2(svx + o), vzo = ld2(svz + o), bxo = ld2(sbx + o), bzo = ld2(sbz + o);
-                float2 vx, vz;
-                vx.x = in[0] ? vxo.x + dt * bxo.x * (e1[0] + e2[0]) : 0.f;
-                vx.y = in[1] ? vxo.y + dt * bxo.y * (e1[1] + e2[1]) : 0.f;
-                vz.x = in[0] ? vzo.x + dt * bzo.x * (e3[0] + e4[0]) : 0.f;
-                vz.y = in[1] ? vzo.y + dt * bzo.y * (e3[1] + e4[1]) : 0.f;
-                st2(svx + o, vx);
-                st2(svz + o, vz);
-                if (own) {
-                    const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                    if (!edge || (i + 1 < NX && j < NZ)) {
-                        st2g(ovx + c, vx);
-                        st2g(ovz + c, vz);
-                        if (a.segx) { st2g(a.segx + off + c, vx); st2g(a.segz + off + c, vz); }
-                    } else if (i < NX && j < NZ) {
-                        ovx[c] = vx.x; ovz[c] = vz.x;
-                        if (a.segx) { a.segx[off + c] = vx.x; a.segz[off + c] = vz.x; }
-                    }
-                }
-            }
-            __syncthreads();
-
-            float *__restrict__ oxx = a.out.sxx + off;
-            float *__restrict__ ozz = a.out.szz + off;
-            float *__restrict__ oxz = a.out.sxz + off;
-            const bool inj = (tl.w & 1) != 0;
-            const float dwn = inj ? a.dw[(long long)tl.x * a.nt + a.n] : 0.f;
-            constexpr int NPT = TX / 2;
-            for (int q = tid; q < NPT * TZ; q += kThreads) {
-                const int yy = q / NPT;
-                const int xx = 2 * (q - yy * NPT);
-                const int x = 4 + xx, y = 4 + yy;
-                const int i = i0 + xx, j = j0 + yy;
-                if (edge && (i >= NX || j >= NZ)) continue;
-                const int o = y * SX + x;
-                const float2 va = ld2(svx + o - 2), vb = ld2(svx + o), vc = ld2(svx + o + 2);
-                const float2 wa = ld2(svz + o - 2), wb = ld2(svz + o), wc = ld2(svz + o + 2);
-                const float2 wm2 = ld2(svz + o - 2 * SX), wm1 = ld2(svz + o - SX), wp1 = ld2(svz + o + SX);
-                const float2 um1 = ld2(svx + o - SX), up1 = ld2(svx + o + SX), up2 = ld2(svx + o + 2 * SX);
-                float f1[2], f2[2], f3[2], f4[2];
-                f1[0] = (C1 * (vb.x - va.y) + C2 * (vb.y - va.x)) * rdx;
-                f1[1] = (C1 * (vb.y - vb.x) + C2 * (vc.x - va.y)) * rdx;
-                f2[0] = (C1 * (wb.x - wm1.x) + C2 * (wp1.x - wm2.x)) * rdz;
-                f2[1] = (C1 * (wb.y - wm1.y) + C2 * (wp1.y - wm2.y)) * rdz;
-                f3[0] = (C1 * (up1.x - vb.x) + C2 * (up2.x - um1.x)) * rdz;
-                f3[1] = (C1 * (up1.y - vb.y) + C2 * (up2.y - um1.y)) * rdz;
-                f4[0] = (C1 * (wb.y - wb.x) + C2 * (wc.x - wa.y)) * rdx;
-                f4[1] = (C1 * (wc.x - wb.y) + C2 * (wc.y - wb.x)) * rdx;
-                if (edge) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int ih = i + h;
-                        if (ih >= NX) continue;
-                        const int xs = ih < P ? ih : (ih >= NX - P ? ih - NX + 2 * P : -1);
-                        const int zs = j < P ? j : (j >= NZ - P ? j - NZ + 2 * P : -1);
-                        if (xs >= 0) {
-                            const long long kk = psx + (long long)j * 2 * P + xs;
-                            const int pq = profx + ih;
-                            const float p5 = a.pml.bx_i[pq] * a.pml.x[2][kk] + a.pml.ax_i[pq] * f1[h];
-                            const float p8 = a.pml.bx_h[pq] * a.pml.x[3][kk] + a.pml.ax_h[pq] * f4[h];
-                            a.pml.x[2][kk] = p5; a.pml.x[3][kk] = p8;
-                            f1[h] += p5; f4[h] += p8;
-                        }
-                        if (zs >= 0) {
-                            const long long kk = psz + (long long)zs * NX + ih;
-                            const float p6 = a.pml.bz_i[j] * a.pml.z[2][kk] + a.pml.az_i[j] * f2[h];
-                            const float p7 = a.pml.bz_h[j] * a.pml.z[3][kk] + a.pml.az_h[j] * f3[h];
-                            a.pml.z[2][kk] = p6; a.pml.z[3][kk] = p7;
-                            f2[h] += p6; f3[h] += p7;
-                        }
-                    }
-                }
-                const int oc = yy * TX + xx;
-                const float2 lam = ld2(slam + oc), mu = ld2(smu + oc), mxz = ld2(smxz + oc);
-                const float2 oxxv = ld2(sxx + o), ozzv = ld2(szz + o), oxzv = ld2(sxz + o);
-                float nxx[2], nzz[2], nxz[2];
-                const float lm[2] = {lam.x, lam.y}, m2[2] = {2.f * mu.x, 2.f * mu.y}, mx[2] = {mxz.x, mxz.y};
-                const float sx0[2] = {oxxv.x, oxxv.y}, sz0[2] = {ozzv.x, ozzv.y}, sc0[2] = {oxzv.x, oxzv.y};
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float tr = lm[h] * (f1[h] + f2[h]);
-                    nxx[h] = sx0[h] + dt * (tr + m2[h] * f1[h]);
-                    nzz[h] = sz0[h] + dt * (tr + m2[h] * f2[h]);
-                    nxz[h] = sc0[h] + dt * mx[h] * (f3[h] + f4[h]);
-                }
-                const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                if (inj) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            if (c + h == sp->inj_n[kk]) {
-                                nxx[h] -= sp->mxx * dwn * sp->inj_nw[kk];
-                                nzz[h] -= sp->mzz * dwn * sp->inj_nw[kk];
+                        for (int h = 0; h < 2; ++h) {
+                            const int ih = i + h;
+                            in[h] = ih >= 0 && ih < NX && j >= 0 && j < NZ;
+                            if (!in[h]) continue;
+                            const int xs = ih < P ? ih : (ih >= NX - P ? ih - NX + 2 * P : -1);
+                            const int zs = j < P ? j : (j >= NZ - P ? j - NZ + 2 * P : -1);
+                            if (xs >= 0) {
+                                const long long kk = psx + (long long)j * 2 * P + xs;
+                                const int pq = profx + ih;
+                                const float p1 = a.pml.bx_h[pq] * a.pml.x[0][kk] + a.pml.ax_h[pq] * e1[h];
+                                const float p3 = a.pml.bx_i[pq] * a.pml.x[1][kk] + a.pml.ax_i[pq] * e3[h];
+                                if (own) { a.n1[kk] = p1; a.n3[kk] = p3; }
+                                e1[h] += p1; e3[h] += p3;
                             }
-                            if (c + h == sp->inj_x[kk]) nxz[h] -= sp->mxz * dwn * sp->inj_xw[kk];
+                            if (zs >= 0) {
+                                const long long kk = psz + (long long)zs * NX + ih;
+                                const float p2 = a.pml.bz_i[j] * a.pml.z[0][kk] + a.pml.az_i[j] * e2[h];
+                                const float p4 = a.pml.bz_h[j] * a.pml.z[1][kk] + a.pml.az_h[j] * e4[h];
+                                if (own) { a.n2[kk] = p2; a.n4[kk] = p4; }
+                                e2[h] += p2; e4[h] += p4;
+                            }
                         }
+                    }
+                    const float2 vxo = ld2(svx + o), vzo = ld2(svz + o), bxo = ld2(sbx + o), bzo = ld2(sbz + o);
+                    float2 vx, vz;
+                    vx.x = in[0] ? vxo.x + dt * bxo.x * (e1[0] + e2[0]) : 0.f;
+                    vx.y = in[1] ? vxo.y + dt * bxo.y * (e1[1] + e2[1]) : 0.f;
+                    vz.x = in[0] ? vzo.x + dt * bzo.x * (e3[0] + e4[0]) : 0.f;
+                    vz.y = in[1] ? vzo.y + dt * bzo.y * (e3[1] + e4[1]) : 0.f;
+                    st2(svx + o, vx);
+                    st2(svz + o, vz);
+                    if (own) {
+                        const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                        if (!edge || (i + 1 < NX && j < NZ)) {
+                            st2g(ovx + c, vx);
+                            st2g(ovz + c, vz);
+                            if (a.segx) { st2g(a.segx + off + c, vx); st2g(a.segz + off + c, vz); }
+                        } else if (i < NX && j < NZ) {
+                            ovx[c] = vx.x; ovz[c] = vz.x;
+                            if (a.segx) { a.segx[off + c] = vx.x; a.segz[off + c] = vz.x; }
+                        }
+                    }
                 }
-                if (!edge || i + 1 < NX) {
-                    st2g(oxx + c, make_float2(nxx[0], nxx[1]));
-                    st2g(ozz + c, make_float2(nzz[0], nzz[1]));
-                    st2g(oxz + c, make_float2(nxz[0], nxz[1]));
-                } else {
-                    oxx[c] = nxx[0]; ozz[c] = nzz[0]; oxz[c] = nxz[0];
+                __syncthreads();
+
+                float *__restrict__ oxx = a.out.sxx + off;
+                float *__restrict__ ozz = a.out.szz + off;
+                float *__restrict__ oxz = a.out.sxz + off;
+                const bool inj = (tl.w & 1) != 0;
+                const float dwn = inj ? a.dw[(long long)tl.x * a.nt + a.n] : 0.f;
+                constexpr int NPT = TX / 2;
+                for (int q = tid; q < NPT * TZ; q += kThreads) {
+                    const int yy = q / NPT;
+                    const int xx = 2 * (q - yy * NPT);
+                    const int x = 4 + xx, y = 4 + yy;
+                    const int i = i0 + xx, j = j0 + yy;
+                    if (edge && (i >= NX || j >= NZ)) continue;
+                    const int o = y * SX + x;
+                    const float2 va = ld2(svx + o - 2), vb = ld2(svx + o), vc = ld2(svx + o + 2);
+                    const float2 wa = ld2(svz + o - 2), wb = ld2(svz + o), wc = ld2(svz + o + 2);
+                    const float2 wm2 = ld2(svz + o - 2 * SX), wm1 = ld2(svz + o - SX), wp1 = ld2(svz + o + SX);
+                    const float2 um1 = ld2(svx + o - SX), up1 = ld2(svx + o + SX), up2 = ld2(svx + o + 2 * SX);
+                    float f1[2], f2[2], f3[2], f4[2];
+                    f1[0] = (C1 * (vb.x - va.y) + C2 * (vb.y - va.x)) * rdx;
+                    f1[1] = (C1 * (vb.y - vb.x) + C2 * (vc.x - va.y)) * rdx;
+                    f2[0] = (C1 * (wb.x - wm1.x) + C2 * (wp1.x - wm2.x)) * rdz;
+                    f2[1] = (C1 * (wb.y - wm1.y) + C2 * (wp1.y - wm2.y)) * rdz;
+                    f3[0] = (C1 * (up1.x - vb.x) + C2 * (up2.x - um1.x)) * rdz;
+                    f3[1] = (C1 * (up1.y - vb.y) + C2 * (up2.y - um1.y)) * rdz;
+                    f4[0] = (C1 * (wb.y - wb.x) + C2 * (wc.x - wa.y)) * rdx;
+                    f4[1] = (C1 * (wc.x - wb.y) + C2 * (wc.y - wb.x)) * rdx;
+                    if (edge) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int ih = i + h;
+                            if (ih >= NX) continue;
+                            const int xs = ih < P ? ih : (ih >= NX - P ? ih - NX + 2 * P : -1);
+                            const int zs = j < P ? j : (j >= NZ - P ? j - NZ + 2 * P : -1);
+                            if (xs >= 0) {
+                                const long long kk = psx + (long long)j * 2 * P + xs;
+                                const int pq = profx + ih;
+                                const float p5 = a.pml.bx_i[pq] * a.pml.x[2][kk] + a.pml.ax_i[pq] * f1[h];
+                                const float p8 = a.pml.bx_h[pq] * a.pml.x[3][kk] + a.pml.ax_h[pq] * f4[h];
+                                a.pml.x[2][kk] = p5; a.pml.x[3][kk] = p8;
+                                f1[h] += p5; f4[h] += p8;
+                            }
+                            if (zs >= 0) {
+                                const long long kk = psz + (long long)zs * NX + ih;
+                                const float p6 = a.pml.bz_i[j] * a.pml.z[2][kk] + a.pml.az_i[j] * f2[h];
+                                const float p7 = a.pml.bz_h[j] * a.pml.z[3][kk] + a.pml.az_h[j] * f3[h];
+                                a.pml.z[2][kk] = p6; a.pml.z[3][kk] = p7;
+                                f2[h] += p6; f3[h] += p7;
+                            }
+                        }
+                    }
+                    const int oc = yy * TX + xx;
+                    const float2 lam = ld2(slam + oc), mu = ld2(smu + oc), mxz = ld2(smxz + oc);
+                    const float2 oxxv = ld2(sxx + o), ozzv = ld2(szz + o), oxzv = ld2(sxz + o);
+                    float nxx[2], nzz[2], nxz[2];
+                    const float lm[2] = {lam.x, lam.y}, m2[2] = {2.f * mu.x, 2.f * mu.y}, mx[2] = {mxz.x, mxz.y};
+                    const float sx0[2] = {oxxv.x, oxxv.y}, sz0[2] = {ozzv.x, ozzv.y}, sc0[2] = {oxzv.x, oxzv.y};
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float tr = lm[h] * (f1[h] + f2[h]);
+                        nxx[h] = sx0[h] + dt * (tr + m2[h] * f1[h]);
+                        nzz[h] = sz0[h] + dt * (tr + m2[h] * f2[h]);
+                        nxz[h] = sc0[h] + dt * mx[h] * (f3[h] + f4[h]);
+                    }
+                    const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    if (inj) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                if (c + h == sp->inj_n[kk]) {
+                                    nxx[h] -= sp->mxx * dwn * sp->inj_nw[kk];
+                                    nzz[h] -= sp->mzz * dwn * sp->inj_nw[kk];
+                                }
+                                if (c + h == sp->inj_x[kk]) nxz[h] -= sp->mxz * dwn * sp->inj_xw[kk];
+                            }
+                    }
+                    if (!edge || i + 1 < NX) {
+                        st2g(oxx + c, make_float2(nxx[0], nxx[1]));
+                        st2g(ozz + c, make_float2(nzz[0], nzz[1]));
+                        st2g(oxz + c, make_float2(nxz[0], nxz[1]));
+                    } else {
+                        oxx[c] = nxx[0]; ozz[c] = nzz[0]; oxz[c] = nxz[0];
+                    }
                 }
-            }
-        } else {
-        // v^{n+1/2} on the tile + 2-cell halo, in place over v^{n-1/2}
-            constexpr int VX = TX + 4, VZ = TZ + 4;
-            for (int q = tid; q < VX * VZ; q += kThreads) {
-                const int y = q / VX, x = q - y * VX;
-                const int i = i0 - 2 + x, j = j0 - 2 + y;
-                const int o = (y + 2) * SX + (x + 2);
-                float vx = 0.f, vz = 0.f;
-                if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
-                    float e1 = (C1 * (sxx[o + 1] - sxx[o]) + C2 * (sxx[o + 2] - sxx[o - 1])) * rdx;
-                    float e2 = (C1 * (sxz[o] - sxz[o - SX]) + C2 * (sxz[o + SX] - sxz[o - 2 * SX])) * rdz;
-                    float e3 = (C1 * (sxz[o] - sxz[o - 1]) + C2 * (sxz[o + 1] - sxz[o - 2])) * rdx;
-                    float e4 = (C1 * (szz[o + SX] - szz[o]) + C2 * (szz[o + 2 * SX] - szz[o - SX])) * rdz;
-                    const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2;
+            } else {
+            // v^{n+1/2} on the tile + 2-cell halo, in place over v^{n-1/2}
+                constexpr int VX = TX + 4, VZ = TZ + 4;
+                for (int q = tid; q < VX * VZ; q += kThreads) {
+                    const int y = q / VX, x = q - y * VX;
+                    const int i = i0 - 2 + x, j = j0 - 2 + y;
+                    const int o = (y + 2) * SX + (x + 2);
+                    float vx = 0.f, vz = 0.f;
+                    if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
+                        float e1 = (C1 * (sxx[o + 1] - sxx[o]) + C2 * (sxx[o + 2] - sxx[o - 1])) * rdx;
+                        float e2 = (C1 * (sxz[o] - sxz[o - SX]) + C2 * (sxz[o + SX] - sxz[o - 2 * SX])) * rdz;
+                        float e3 = (C1 * (sxz[o] - sxz[o - 1]) + C2 * (sxz[o + 1] - sxz[o - 2])) * rdx;
+                        float e4 = (C1 * (szz[o + SX] - szz[o]) + C2 * (szz[o + 2 * SX] - szz[o - SX])) * rdz;
+                        const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2;
+                        if (edge) {
+                            const int xs = i < P ? i : (i >= NX - P ? i - NX + 2 * P : -1);
+                            const int zs = j < P ? j : (j >= NZ - P ? j - NZ + 2 * P : -1);
+                            if (xs >= 0) {
+                                const long long kk = psx + (long long)j * 2 * P + xs;
+                                const int pq = profx + i;
+                                const float p1 = a.pml.bx_h[pq] * a.pml.x[0][kk] + a.pml.ax_h[pq] * e1;
+                                const float p3 = a.pml.bx_i[pq] * a.pml.x[1][kk] + a.pml.ax_i[pq] * e3;
+                                if (own) { a.n1[kk] = p1; a.n3[kk] = p3; }
+                                e1 += p1; e3 += p3;
+                            }
+                            if (zs >= 0) {
+                                const long long kk = psz + (long long)zs * NX + i;
+                                const float p2 = a.pml.bz_i[j] * a.pml.z[0][kk] + a.pml.az_i[j] * e2;
+                                const float p4 = a.pml.bz_h[j] * a.pml.z[1][kk] + a.pml.az_h[j] * e4;
+                                if (own) { a.n2[kk] = p2; a.n4[kk] = p4; }
+                                e2 += p2; e4 += p4;
+                            }
+                        }
+                        vx = svx[o] + dt * sbx[o] * (e1 + e2);
+                        vz = svz[o] + dt * sbz[o] * (e3 + e4);
+                        if (own && (!edge || (i < NX && j < NZ))) {
+                            const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                            ovx[c] = vx;
+                            ovz[c] = vz;
+                            if (a.segx) { a.segx[off + c] = vx; a.segz[off + c] = vz; }
+                        }
+                    }
+                    svx[o] = vx;
+                    svz[o] = vz;
+                }
+                __syncthreads();
+    
+                // sigma^{n+1} on the tile, then the moment-tensor source
+                float *__restrict__ oxx = a.out.sxx + off;
+                float *__restrict__ ozz = a.out.szz + off;
+                float *__restrict__ oxz = a.out.sxz + off;
+                const bool inj = (tl.w & 1) != 0;
+                const float dwn = inj ? a.dw[(long long)tl.x * a.nt + a.n] : 0.f;
+                for (int q = tid; q < TX * TZ; q += kThreads) {
+                    const int y = q / TX, x = q - y * TX;
+                    const int i = i0 + x, j = j0 + y;
+                    if (edge && (i >= NX || j >= NZ)) continue;
+                    const int o = (y + 4) * SX + (x + 4);
+                    float f1 = (C1 * (svx[o] - svx[o - 1]) + C2 * (svx[o + 1] - svx[o - 2])) * rdx;
+                    float f2 = (C1 * (svz[o] - svz[o - SX]) + C2 * (svz[o + SX] - svz[o - 2 * SX])) * rdz;
+                    float f3 = (C1 * (svx[o + SX] - svx[o]) + C2 * (svx[o + 2 * SX] - svx[o - SX])) * rdz;
+                    float f4 = (C1 * (svz[o + 1] - svz[o]) + C2 * (svz[o + 2] - svz[o - 1])) * rdx;
                     if (edge) {
                         const int xs = i < P ? i : (i >= NX - P ? i - NX + 2 * P : -1);
                         const int zs = j < P ? j : (j >= NZ - P ? j - NZ + 2 * P : -1);
                         if (xs >= 0) {
                             const long long kk = psx + (long long)j * 2 * P + xs;
                             const int pq = profx + i;
-                            const float p1 = a.pml.bx_h[pq] * a.pml.x[0][kk] + a.pml.ax_h[pq] * e1;
-                            const float p3 = a.pml.bx_i[pq] * a.pml.x[1][kk] + a.pml.ax_i[pq] * e3;
-                            if (own) { a.n1[kk] = p1; a.n3[kk] = p3; }
-                            e1 += p1; e3 += p3;
+                            const float p5 = a.pml.bx_i[pq] * a.pml.x[2][kk] + a.pml.ax_i[pq] * f1;
+                            const float p8 = a.pml.bx_h[pq] * a.pml.x[3][kk] + a.pml.ax_h[pq] * f4;
+                            a.pml.x[2][kk] = p5; a.pml.x[3][kk] = p8;
+                            f1 += p5; f4 += p8;
                         }
                         if (zs >= 0) {
                             const long long kk = psz + (long long)zs * NX + i;
-                            const float p2 = a.pml.bz_i[j] * a.pml.z[0][kk] + a.pml.az_i[j] * e2;
-                            const float p4 = a.pml.bz_h[j] * a.pml.z[1][kk] + a.pml.az_h[j] * e4;
-                            if (own) { a.n2[kk] = p2; a.n4[kk] = p4; }
-                            e2 += p2; e4 += p4;
+                            const float p6 = a.pml.bz_i[j] * a.pml.z[2][kk] + a.pml.az_i[j] * f2;
+                            const float p7 = a.pml.bz_h[j] * a.pml.z[3][kk] + a.pml.az_h[j] * f3;
+                            a.pml.z[2][kk] = p6; a.pml.z[3][kk] = p7;
+                            f2 += p6; f3 += p7;
                         }
                     }
-                    vx = svx[o] + dt * sbx[o] * (e1 + e2);
-                    vz = svz[o] + dt * sbz[o] * (e3 + e4);
-                    if (own && (!edge || (i < NX && j < NZ))) {
-                        const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                        ovx[c] = vx;
-                        ovz[c] = vz;
-                        if (a.segx) { a.segx[off + c] = vx; a.segz[off + c] = vz; }
-                    }
-                }
-                svx[o] = vx;
-                svz[o] = vz;
-            }
-            __syncthreads();
-    
-            // sigma^{n+1} on the tile, then the moment-tensor source
-            float *__restrict__ oxx = a.out.sxx + off;
-            float *__restrict__ ozz = a.out.szz + off;
-            float *__restrict__ oxz = a.out.sxz + off;
-            const bool inj = (tl.w & 1) != 0;
-            const float dwn = inj ? a.dw[(long long)tl.x * a.nt + a.n] : 0.f;
-            for (int q = tid; q < TX * TZ; q += kThreads) {
-                const int y = q / TX, x = q - y * TX;
-                const int i = i0 + x, j = j0 + y;
-                if (edge && (i >= NX || j >= NZ)) continue;
-                const int o = (y + 4) * SX + (x + 4);
-                float f1 = (C1 * (svx[o] - svx[o - 1]) + C2 * (svx[o + 1] - svx[o - 2])) * rdx;
-                float f2 = (C1 * (svz[o] - svz[o - SX]) + C2 * (svz[o + SX] - svz[o - 2 * SX])) * rdz;
-                float f3 = (C1 * (svx[o + SX] - svx[o]) + C2 * (svx[o + 2 * SX] - svx[o - SX])) * rdz;
-                float f4 = (C1 * (svz[o + 1] - svz[o]) + C2 * (svz[o + 2] - svz[o - 1])) * rdx;
-                if (edge) {
-                    const int xs = i < P ? i : (i >= NX - P ? i - NX + 2 * P : -1);
-                    const int zs = j < P ? j : (j >= NZ - P ? j - NZ + 2 * P : -1);
-                    if (xs >= 0) {
-                        const long long kk = psx + (long long)j * 2 * P + xs;
-                        const int pq = profx + i;
-                        const float p5 = a.pml.bx_i[pq] * a.pml.x[2][kk] + a.pml.ax_i[pq] * f1;
-                        const float p8 = a.pml.bx_h[pq] * a.pml.x[3][kk] + a.pml.ax_h[pq] * f4;
-                        a.pml.x[2][kk] = p5; a.pml.x[3][kk] = p8;
-                        f1 += p5; f4 += p8;
-                    }
-                    if (zs >= 0) {
-                        const long long kk = psz + (long long)zs * NX + i;
-                        const float p6 = a.pml.bz_i[j] * a.pml.z[2][kk] + a.pml.az_i[j] * f2;
-                        const float p7 = a.pml.bz_h[j] * a.pml.z[3][kk] + a.pml.az_h[j] * f3;
-                        a.pml.z[2][kk] = p6; a.pml.z[3][kk] = p7;
-                        f2 += p6; f3 += p7;
-                    }
-                }
-                const int oc = y * TX + x;
-                const float lam = slam[oc], mu2 = 2.f * smu[oc];
-                const float tr = lam * (f1 + f2);
-                float nxx = sxx[o] + dt * (tr + mu2 * f1);
-                float nzz = szz[o] + dt * (tr + mu2 * f2);
-                float nxz = sxz[o] + dt * smxz[oc] * (f3 + f4);
-                const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                if (inj) {
-    #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        if (c == sp->inj_n[kk]) {
-                            nxx -= sp->mxx * dwn * sp->inj_nw[kk];
-                            nzz -= sp->mzz * dwn * sp->inj_nw[kk];
+                    const int oc = y * TX + x;
+                    const float lam = slam[oc], mu2 = 2.f * smu[oc];
+                    const float tr = lam * (f1 + f2);
+                    float nxx = sxx[o] + dt * (tr + mu2 * f1);
+                    float nzz = szz[o] + dt * (tr + mu2 * f2);
+                    float nxz = sxz[o] + dt * smxz[oc] * (f3 + f4);
+                    const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    if (inj) {
+        #pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            if (c == sp->inj_n[kk]) {
+                                nxx -= sp->mxx * dwn * sp->inj_nw[kk];
+                                nzz -= sp->mzz * dwn * sp->inj_nw[kk];
+                            }
+                            if (c == sp->inj_x[kk]) nxz -= sp->mxz * dwn * sp->inj_xw[kk];
                         }
-                        if (c == sp->inj_x[kk]) nxz -= sp->mxz * dwn * sp->inj_xw[kk];
                     }
+                    oxx[c] = nxx;
+                    ozz[c] = nzz;
+                    oxz[c] = nxz;
                 }
-                oxx[c] = nxx;
-                ozz[c] = nzz;
-                oxz[c] = nxz;
             }
-        }
+        };
+        if (tl.w & 2) tile(std::true_type{});
+        else tile(std::false_type{});
         __syncthreads();   // this buffer is refilled by the next iteration's prefetch
     }
 }
