@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
     float *sm = reinterpret_cast<float *>(smem4);
     float *f1s = sm, *f2s = sm + SX * SZ, *f3s = sm + 2 * SX * SZ, *f4s = sm + 3 * SX * SZ;
     float *e1s = sm + 4 * SX * SZ, *e2s = e1s + VX * VZ, *e3s = e2s + VX * VZ, *e4s = e3s + VX * VZ;
+    float *vfxs = e4s + VX * VZ, *vfzs = vfxs + VX * VZ;   // forward v^{n+1/2} on the tile + 2-cell halo
     const int tid = threadIdx.x;
 
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -278,12 +279,14 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                         }
                     }
                 }
-                f1s[q] = g1; f2s[q] = g2; f3s[q] = g3; f4s[q] = g4;
+                f1s[q] = g1; f2s[q] = g2; f3s[q] = g3;
+                if (edge) f4s[q] = g4;                     // f^4 == f^3 away from the CPML
             }
             __syncthreads();
 
             // 2. v^ += D^T f^ on the tile + 2-cell halo; e^ in shared memory
             constexpr int N2 = (VX * VZ + kThreads - 1) / kThreads;
+            float *f4r = edge ? f4s : f3s;
             float lvx[N2], lvz[N2], lbx[N2], lbz[N2], lfx[N2], lfz[N2], lgx[N2], lgz[N2];
 #pragma unroll
             for (int r = 0; r < N2; ++r) {
@@ -295,9 +298,9 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                     const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                     lvx[r] = __ldg(a.in.vx + c); lvz[r] = __ldg(a.in.vz + c);
                     lbx[r] = __ldg(a.M.bx + c); lbz[r] = __ldg(a.M.bz + c);
+                    lfx[r] = __ldg(a.vfx + c); lfz[r] = __ldg(a.vfz + c);
                     const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
                     if (own && (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP))) {
-                        lfx[r] = __ldg(a.vfx + c); lfz[r] = __ldg(a.vfz + c);
                         lgx[r] = a.Gbx[c]; lgz[r] = a.Gbz[c];
                     }
                 }
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                     const float inc_x = -(C1 * (f1s[o + 1] - f1s[o]) + C2 * (f1s[o + 2] - f1s[o - 1])) * rdx
                                         - (C1 * (f3s[o] - f3s[o - SX]) + C2 * (f3s[o + SX] - f3s[o - 2 * SX])) * rdz;
                     const float inc_z = -(C1 * (f2s[o + SX] - f2s[o]) + C2 * (f2s[o + 2 * SX] - f2s[o - SX])) * rdz
-                                        - (C1 * (f4s[o] - f4s[o - 1]) + C2 * (f4s[o + 1] - f4s[o - 2])) * rdx;
+                                        - (C1 * (f4r[o] - f4r[o - 1]) + C2 * (f4r[o + 1] - f4r[o - 2])) * rdx;
                     const float vx = lvx[r] + inc_x;
                     const float vz = lvz[r] + inc_z;
                     const float qx = dt * lbx[r] * vx, qz = dt * lbz[r] * vz;
@@ -355,36 +358,27 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                         }
                     }
                 }
-                e1s[q] = h1; e2s[q] = h2; e3s[q] = h3; e4s[q] = h4;
+                e1s[q] = h1; e3s[q] = h3;
+                if (edge) { e2s[q] = h2; e4s[q] = h4; }    // e^2 == e^1, e^4 == e^3 away from the CPML
+                vfxs[q] = lfx[r]; vfzs[q] = lfz[r];
             }
             __syncthreads();
+            const float *e2r = edge ? e2s : e1s, *e4r = edge ? e4s : e3s;
 
             // 3. sigma^ += D^T e^ on the tile, with the C-imaging
             constexpr int N3 = (TX * TZ + kThreads - 1) / kThreads;
-            float sxx_r[N3], szz_r[N3], sxz_r[N3], fxm2[N3], fxm1[N3], fx0[N3], fxp1[N3], fzm2[N3], fzm1[N3], fz0[N3],
-                fzp1[N3], fxzm[N3], fxz1[N3], fxz2[N3], vzx1[N3], vzx2[N3], vzm1[N3], g0[N3], g1v[N3], g2v[N3];
+            float sxx_r[N3], szz_r[N3], sxz_r[N3], g0[N3], g1v[N3], g2v[N3];
 #pragma unroll
             for (int r = 0; r < N3; ++r) {
                 const int q = tid + r * kThreads;
                 const int y = q / TX, x = q - y * TX;
                 const int i = i0 + x, j = j0 + y;
-                sxx_r[r] = szz_r[r] = sxz_r[r] = 0.f;
-                fxm2[r] = fxm1[r] = fx0[r] = fxp1[r] = fzm2[r] = fzm1[r] = fz0[r] = fzp1[r] = 0.f;
-                fxzm[r] = fxz1[r] = fxz2[r] = vzx1[r] = vzx2[r] = vzm1[r] = g0[r] = g1v[r] = g2v[r] = 0.f;
+                sxx_r[r] = szz_r[r] = sxz_r[r] = g0[r] = g1v[r] = g2v[r] = 0.f;
                 if (q < TX * TZ && !(edge && (i >= NX || j >= NZ))) {
                     const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                     sxx_r[r] = __ldg(a.in.sxx + c); szz_r[r] = __ldg(a.in.szz + c); sxz_r[r] = __ldg(a.in.sxz + c);
                     const bool node = !edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP);
                     const bool half = !edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP);
-                    if (node || half) {
-                        fxm2[r] = __ldg(a.vfx + c - 2); fxm1[r] = __ldg(a.vfx + c - 1); fx0[r] = __ldg(a.vfx + c);
-                        fxp1[r] = __ldg(a.vfx + c + 1);
-                        fzm2[r] = __ldg(a.vfz + c - 2 * pitch); fzm1[r] = __ldg(a.vfz + c - pitch);
-                        fz0[r] = __ldg(a.vfz + c); fzp1[r] = __ldg(a.vfz + c + pitch);
-                        fxzm[r] = __ldg(a.vfx + c - pitch); fxz1[r] = __ldg(a.vfx + c + pitch);
-                        fxz2[r] = __ldg(a.vfx + c + 2 * pitch);
-                        vzm1[r] = __ldg(a.vfz + c - 1); vzx1[r] = __ldg(a.vfz + c + 1); vzx2[r] = __ldg(a.vfz + c + 2);
-                    }
                     if (node) { g0[r] = a.Glam[c]; g1v[r] = a.Gmu[c]; }
                     if (half) g2v[r] = a.Gmuxz[c];
                 }
@@ -398,21 +392,22 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                 if (edge && (i >= NX || j >= NZ)) continue;
                 const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                 const float hxx = sxx_r[r], hzz = szz_r[r], hxz = sxz_r[r];
+                const int o = (y + 2) * VX + (x + 2);      // (i, j) in the halo-2 staging
+                const float *fvx = vfxs + o, *fvz = vfzs + o;
                 if (!edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP)) {
-                    const float fx = (C1 * (fx0[r] - fxm1[r]) + C2 * (fxp1[r] - fxm2[r])) * rdx;
-                    const float fz = (C1 * (fz0[r] - fzm1[r]) + C2 * (fzp1[r] - fzm2[r])) * rdz;
+                    const float fx = (C1 * (fvx[0] - fvx[-1]) + C2 * (fvx[1] - fvx[-2])) * rdx;
+                    const float fz = (C1 * (fvz[0] - fvz[-VX]) + C2 * (fvz[VX] - fvz[-2 * VX])) * rdz;
                     a.Glam[c] = g0[r] + dt * (hxx + hzz) * (fx + fz);
                     a.Gmu[c] = g1v[r] + 2.f * dt * (hxx * fx + hzz * fz);
                 }
                 if (!edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP)) {
-                    const float fxz = (C1 * (fxz1[r] - fx0[r]) + C2 * (fxz2[r] - fxzm[r])) * rdz +
-                                      (C1 * (vzx1[r] - fz0[r]) + C2 * (vzx2[r] - vzm1[r])) * rdx;
+                    const float fxz = (C1 * (fvx[VX] - fvx[0]) + C2 * (fvx[2 * VX] - fvx[-VX])) * rdz +
+                                      (C1 * (fvz[1] - fvz[0]) + C2 * (fvz[2] - fvz[-1])) * rdx;
                     a.Gmuxz[c] = g2v[r] + dt * hxz * fxz;
                 }
-                const int o = (y + 2) * VX + (x + 2);
                 a.out.sxx[c] = hxx - (C1 * (e1s[o] - e1s[o - 1]) + C2 * (e1s[o + 1] - e1s[o - 2])) * rdx;
-                a.out.szz[c] = hzz - (C1 * (e4s[o] - e4s[o - VX]) + C2 * (e4s[o + VX] - e4s[o - 2 * VX])) * rdz;
-                a.out.sxz[c] = hxz - (C1 * (e2s[o + VX] - e2s[o]) + C2 * (e2s[o + 2 * VX] - e2s[o - VX])) * rdz
+                a.out.szz[c] = hzz - (C1 * (e4r[o] - e4r[o - VX]) + C2 * (e4r[o + VX] - e4r[o - 2 * VX])) * rdz;
+                a.out.sxz[c] = hxz - (C1 * (e2r[o + VX] - e2r[o]) + C2 * (e2r[o + 2 * VX] - e2r[o - VX])) * rdz
                                    - (C1 * (e3s[o + 1] - e3s[o]) + C2 * (e3s[o + 2] - e3s[o - 1])) * rdx;
             }
             __syncthreads();
@@ -432,7 +427,7 @@ constexpr Shape kShapes[] = {{32, 8}, {32, 16}, {64, 8}, {64, 16}, {32, 32}, {12
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 size_t fwd_smem(int tx, int tz) { return sizeof(float) * (3 * (tx + 8) * (tz + 8) + 2 * (tx + 4) * (tz + 4)); }
-size_t adj_smem(int tx, int tz) { return sizeof(float) * (4 * (tx + 8) * (tz + 8) + 4 * (tx + 4) * (tz + 4)); }
+size_t adj_smem(int tx, int tz) { return sizeof(float) * (4 * (tx + 8) * (tz + 8) + 6 * (tx + 4) * (tz + 4)); }
 
 template <int TX, int TZ>
 void fwd_launch(const FwdArgs &a, int grid, cudaStream_t st) {
