@@ -137,8 +137,6 @@ KERNELS = {
 # profiles/ (8-shot case, same kernel variant; scaled to a launch by its cells).
 # Keyed by (kernel, staging, tile); any other variant reports traffic null.
 TRAFFIC_PER_CELL = {
-    ("step", 3, 32, 16): 54.66,   # TMA, cell pairs, 32x16 (profiles/k_step_tma_guided_wave_8shots.md)
-    ("adj", 1, 64, 8): 94.87,     # per-thread loads, 64x8 (profiles/k_adj_fused_guided_wave_8shots.md)
 }
 
 

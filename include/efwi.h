@@ -257,6 +257,16 @@ int efwi_regularization_grad_noalloc(int ns, int nx, int nz, const float *m, con
                                      const float *bp, const uint8_t *sink, double eta,
                                      double *phi_reg, float *g, efwi_stream_t stream);
 
+/* Collapse of an extended field to one physical field, out = S_w W x~
+ * (eq. 9: the final model from the extended model; the same operator applied
+ * to the per-source gradients is the preconditioned gradient of eq. 15).
+ * W of eq. 11 and S_w of eq. 12 act per pixel over the ns components, in FP64.
+ *   x, b, bp   device [ns][nz][nx] FP32; sink device [ns][nz][nx] uint8
+ *   out        device [nz][nx] FP32 (overwritten)
+ * No plan and no workspace; EFWI_ERR_ARG on sizes < 1 or NULL pointers.     */
+int efwi_collapse(int ns, int nx, int nz, const float *x, const float *b, const float *bp,
+                  const uint8_t *sink, float *out, efwi_stream_t stream);
+
 /* Extended objective of eq. 8: phi_data (as efwi_forward + misfit) and
  * phi_reg summed over the three parameter fields (Vp, Vs, rho) with their
  * own eta[3].  Both results are device doubles (overwritten).               */

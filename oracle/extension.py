@@ -105,10 +105,22 @@ def regularization(m, b, bp, sink, eta, chunk=4096):
     return phi, g.reshape(shp)
 
 
-def collapse(m, b, bp, sink):
-    """Final physical model m^ = S_w W m~ (eq. 9): [Ns, nz, nx] -> [nz, nx]."""
+def collapse(m, b, bp, sink, chunk=4096):
+    """Final physical model m^ = S_w W m~ (eq. 9): [Ns, nz, nx] -> [nz, nx].
+
+    Applied to the per-source gradients g~ it gives the preconditioned gradient
+    S_w W g~ of eq. 15.  Pixels are independent; they are processed in chunks.
+    """
     ns = m.shape[0]
-    W = w_matrices(b.reshape(ns, -1), sink.reshape(ns, -1))
-    om = sw_rows(bp.reshape(ns, -1))
-    y = np.einsum("pij,jp->pi", W, m.reshape(ns, -1))
-    return np.einsum("pi,pi->p", om, y).reshape(m.shape[1:])
+    mf = np.asarray(m, np.float64).reshape(ns, -1)
+    bf = np.asarray(b, np.float64).reshape(ns, -1)
+    bpf = np.asarray(bp, np.float64).reshape(ns, -1)
+    sf = np.asarray(sink).reshape(ns, -1)
+    out = np.zeros(mf.shape[1])
+    for p0 in range(0, mf.shape[1], chunk):
+        sl = slice(p0, p0 + chunk)
+        W = w_matrices(bf[:, sl], sf[:, sl])
+        om = sw_rows(bpf[:, sl])
+        y = np.einsum("pij,jp->pi", W, mf[:, sl])
+        out[sl] = np.einsum("pi,pi->p", om, y)
+    return out.reshape(m.shape[1:])

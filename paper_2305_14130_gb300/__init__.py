@@ -25,7 +25,7 @@ import torch
 from . import _abi
 from ._abi import EfwiError, STORE, EXEC, STENCIL, OVERLAP
 
-__all__ = ["Plan", "zoi_weights", "EfwiError", "load_library", "DataMisfit", "Consistency", "extended_objective"]
+__all__ = ["Plan", "zoi_weights", "collapse", "EfwiError", "load_library", "DataMisfit", "Consistency", "extended_objective"]
 
 
 from .autograd import DataMisfit, Consistency, extended_objective  # noqa: E402
@@ -225,3 +225,19 @@ def zoi_weights(ns, nx, nz, dx, dz, zoi, device="cuda"):
                                     C.c_void_p(b.data_ptr()), C.c_void_p(bp.data_ptr()),
                                     C.c_void_p(sink.data_ptr()), _stream()))
     return b, bp, sink
+
+
+def collapse(x, b, bp, sink, out=None):
+    """S_w W x~ of an extended field x [ns, nz, nx] (eq. 9 for a model, eq. 15 for
+    per-source gradients): one physical field [nz, nx], computed on the device."""
+    lib = _abi.load()
+    ns, nz, nx = x.shape
+    for t, dt in ((x, torch.float32), (b, torch.float32), (bp, torch.float32), (sink, torch.uint8)):
+        if t.dtype != dt or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (ns, nz, nx):
+            raise ValueError("collapse: x, b, bp (float32) and sink (uint8) must be contiguous CUDA [ns, nz, nx]")
+    if out is None:
+        out = torch.empty((nz, nx), dtype=torch.float32, device=x.device)
+    _abi.check(lib.efwi_collapse(int(ns), int(nx), int(nz), C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()),
+                                 C.c_void_p(bp.data_ptr()), C.c_void_p(sink.data_ptr()), C.c_void_p(out.data_ptr()),
+                                 _stream()))
+    return out

@@ -58,6 +58,7 @@ SIGNATURES = {
     "efwi_zoi_weights": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(ZoiDesc),
                                    VP, VP, VP, VP]),
     "efwi_regularization_grad": (C.c_int, [VP, VP, VP, VP, VP, C.c_double, VP, VP, VP]),
+    "efwi_collapse": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, VP, VP]),
     "efwi_regularization_grad_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, C.c_double, VP, VP,
                                                     VP]),
     "efwi_extended_objective": (C.c_int, [VP, VP, VP, VP, VP, PD, VP, VP, VP, VP, VP, VP]),

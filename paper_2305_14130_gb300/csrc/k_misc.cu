@@ -318,6 +318,31 @@ __global__ void k_zoi(ZoiShot z, int s, int nx, int nz, double dx, double dz, do
 //   omega_s = b'_s / sum b'                                        (eq. 12)
 //   r = (I - 1 omega^T) W m;  phi += 1/2 eta^2 |r|^2
 //   y = r - omega (1^T r);  g_i += eta^2 [(d_i - c_i b_i) y_i + b_i sum_s c_s y_s]
+// Collapse of an extended field to one physical field (eq. 9, and eq. 15 when
+// applied to the per-source gradients): out = S_w W x~ per pixel, FP64:
+//   (W x)_s = (d_s - c_s b_s) x_s + c_s sum_i b_i x_i  (eq. 11, c_s and d_s as in k_reg)
+//   out = sum_s b'_s (W x)_s / sum_s b'_s               (eq. 12)
+__global__ void k_collapse(const float *x, const float *b, const float *bp, const uint8_t *sink, int ns,
+                           long long npix, float *out) {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
+        double B = 0, BX = 0, SBp = 0;
+        for (int s = 0; s < ns; ++s) {
+            const long long o = s * npix + p;
+            B += b[o]; BX += (double)b[o] * x[o]; SBp += bp[o];
+        }
+        double acc = 0;
+        for (int s = 0; s < ns; ++s) {
+            const long long o = s * npix + p;
+            const double bs = b[o];
+            const bool in = sink[o] != 0 && ns > 1;
+            const double c = in ? (1.0 - bs) / (B - bs) : 0.0;
+            const double dd = in ? bs : 1.0;
+            acc += (double)bp[o] * ((dd - c * bs) * x[o] + c * BX);
+        }
+        out[p] = (float)(acc / SBp);
+    }
+}
+
 __global__ void k_reg(const float *m, const float *b, const float *bp, const uint8_t *sink, int ns, long long npix,
                       double eta2, float *g, double *partial) {
     double acc = 0.0;
@@ -517,6 +542,12 @@ int launch_zoi(int ns, int nx, int nz, double dx, double dz, const efwi_zoi_desc
         return EFWI_ERR_CUDA;
     }
     return EFWI_OK;
+}
+
+void launch_collapse(int ns, long long npix, const float *x, const float *b, const float *bp, const uint8_t *sink,
+                     float *out, cudaStream_t st) {
+    const long long blocks = std::min<long long>((npix + 255) / 256, 152LL * 16);
+    k_collapse<<<(int)std::max<long long>(blocks, 1), 256, 0, st>>>(x, b, bp, sink, ns, npix, out);
 }
 
 void launch_reg(efwi_plan *p, const float *m, const float *b, const float *bp, const uint8_t *sink, double eta,

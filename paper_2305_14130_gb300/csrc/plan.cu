@@ -555,6 +555,16 @@ extern "C" int efwi_zoi_weights(int ns, int nx, int nz, double dx, double dz, co
     return EFWI_OK;
 }
 
+extern "C" int efwi_collapse(int ns, int nx, int nz, const float *x, const float *b, const float *bp,
+                             const uint8_t *sink, float *out, efwi_stream_t stream) {
+    if (ns < 1 || nx < 1 || nz < 1) return fail(nullptr, EFWI_ERR_ARG, "ns, nx and nz must be >= 1");
+    if (!x || !b || !bp || !sink || !out) return fail(nullptr, EFWI_ERR_ARG, "NULL device pointer");
+    launch_collapse(ns, (long long)nx * nz, x, b, bp, sink, out, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, EFWI_ERR_CUDA, cudaGetErrorString(e));
+    return EFWI_OK;
+}
+
 extern "C" int efwi_regularization_grad(efwi_plan *p, const float *m, const float *b, const float *bp,
                                         const uint8_t *sink, double eta, double *phi_reg, float *g,
                                         efwi_stream_t stream) {

@@ -152,6 +152,8 @@ void launch_ckpt_save(efwi_plan *p, int slot, cudaStream_t st);
 void launch_ckpt_load(efwi_plan *p, int slot, cudaStream_t st);
 int launch_zoi(int ns, int nx, int nz, double dx, double dz, const efwi_zoi_desc *z, float *b, float *bp,
                uint8_t *sink, cudaStream_t st, std::string &err);
+void launch_collapse(int ns, long long npix, const float *x, const float *b, const float *bp, const uint8_t *sink,
+                     float *out, cudaStream_t st);
 void launch_reg(efwi_plan *p, const float *m, const float *b, const float *bp, const uint8_t *sink, double eta,
                 double *phi, float *g, int accumulate_phi, cudaStream_t st);
 

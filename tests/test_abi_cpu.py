@@ -112,6 +112,15 @@ def test_plan_create_rejects_positions_outside_window(lib):
     assert "trace 3" in lib.efwi_last_error(None).decode()
 
 
+def test_collapse_rejects_bad_arguments(lib):
+    """Argument checks happen on the host, before any launch."""
+    p = C.c_void_p(16)
+    assert lib.efwi_collapse(0, 4, 4, p, p, p, p, p, None) == -1
+    assert "ns, nx and nz" in lib.efwi_last_error(None).decode()
+    assert lib.efwi_collapse(2, 4, 4, None, p, p, p, p, None) == -1
+    assert "NULL" in lib.efwi_last_error(None).decode()
+
+
 def test_null_arguments(lib):
     h = C.c_void_p()
     assert lib.efwi_plan_create(C.byref(h), None) == -1

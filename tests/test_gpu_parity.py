@@ -177,6 +177,41 @@ def test_regularization_parity(efwi, ns):
     plan.close()
 
 
+@pytest.mark.parametrize("ns", [1, 2, 5])
+def test_collapse_parity(efwi, ns):
+    """S_w W x~ (eq. 9 on a model, eq. 15 on per-source gradients) against the
+    oracle's dense per-pixel operators; FP32 inputs, FP64 arithmetic, FP32 out."""
+    rng = np.random.default_rng(10 + ns)
+    nz, nx = 23, 37
+    p = W.tiny(nx=nx, nz=nz, ns=ns, nt=10, npml=3)
+    bo, bpo, sinko = X.zoi_weights(p.zoi, nx, nz, p.acq.dx, p.acq.dz)
+    bo, bpo = f32(bo), f32(bpo)
+    for x in (f32(3000 + 100 * rng.standard_normal((ns, nz, nx))), f32(rng.standard_normal((ns, nz, nx)))):
+        ref = X.collapse(x, bo, bpo, sinko)
+        out = efwi.collapse(dev(x), dev(bo), dev(bpo), dev(sinko, np.uint8))
+        torch.cuda.synchronize()
+        assert rel_l2(out.cpu().numpy(), ref) <= 1e-6
+        if ns == 1:
+            assert np.array_equal(out.cpu().numpy(), x[0])
+
+
+def test_collapse_full_size_sampled_rows(efwi):
+    """32 components of the 1000x300 guided-wave model with its zones of
+    influence; the oracle checks every pixel of five sampled rows (pixels are
+    independent, so a row slice is an exact sub-problem)."""
+    p = W.guided_wave_1000x300()
+    acq = p.acq
+    bo, bpo, sinko = X.zoi_weights(p.zoi, acq.nx, acq.nz, acq.dx, acq.dz)
+    bo, bpo = f32(bo), f32(bpo)
+    x = f32(p.vs)
+    out = efwi.collapse(dev(x), dev(bo), dev(bpo), dev(sinko, np.uint8)).cpu().numpy()
+    assert np.isfinite(out).all()
+    for r in (0, 117, 150, 151, 299):
+        sl = (slice(None), slice(r, r + 1), slice(None))
+        ref = X.collapse(x[sl], bo[sl], bpo[sl], sinko[sl])[0]
+        assert rel_l2(out[r], ref) <= 1e-6
+
+
 def test_extended_objective_parity(efwi):
     p = rounded(W.tiny(nx=40, nz=30, ns=3, nt=60, npml=6))
     d_obs = observed(p)

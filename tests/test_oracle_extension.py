@@ -163,3 +163,35 @@ def test_collapse_of_constant_extension_is_identity():
     b, bp, sink = _fig2_setup()
     m = rng.standard_normal((1, 1, 31))
     assert np.allclose(X.collapse(np.repeat(m, 3, axis=0), b, bp, sink), m[0], atol=1e-14)
+
+
+def test_collapse_hand_computed_pixel():
+    """One pixel, three sources, inside the sinkhole of source 0 only:
+    (W m)_0 = b_0 m_0 + (1 - b_0)(b_1 m_1 + b_2 m_2)/(b_1 + b_2) = 0.5 + 0.5 * 2.2 = 1.6,
+    (W m)_1 = 2, (W m)_2 = 3 (eq. 11); b' = (1, b_1, b_2) (eq. 12), so
+    S_w W m = (1.6 + 0.8 * 2 + 0.2 * 3) / 2 = 1.9 (eq. 9)."""
+    b = np.array([0.5, 0.8, 0.2]).reshape(3, 1, 1)
+    bp = np.array([1.0, 0.8, 0.2]).reshape(3, 1, 1)
+    sink = np.array([1, 0, 0], np.uint8).reshape(3, 1, 1)
+    m = np.array([1.0, 2.0, 3.0]).reshape(3, 1, 1)
+    assert X.collapse(m, b, bp, sink)[0, 0] == pytest.approx(1.9, abs=1e-15)
+
+
+def test_collapse_single_source_and_no_sinkholes():
+    """Ns = 1: W = I and S_w = 1, so the collapse returns the component itself;
+    without sinkholes W = I and the collapse is the b'-weighted mean."""
+    rng = np.random.default_rng(5)
+    m = rng.standard_normal((1, 4, 7))
+    b = rng.uniform(0.1, 1, (1, 4, 7))
+    assert np.array_equal(X.collapse(m, b, b, np.ones((1, 4, 7), np.uint8)), m[0])
+    m = rng.standard_normal((3, 4, 7))
+    b = rng.uniform(0.1, 1, (3, 4, 7))
+    ref = (b * m).sum(0) / b.sum(0)
+    assert np.allclose(X.collapse(m, b, b, np.zeros((3, 4, 7), np.uint8)), ref, rtol=1e-14, atol=1e-14)
+
+
+def test_collapse_chunks_do_not_change_the_result():
+    rng = np.random.default_rng(6)
+    b, bp, sink = _fig2_setup()
+    m = rng.standard_normal((3, 1, 31))
+    assert np.array_equal(X.collapse(m, b, bp, sink, chunk=7), X.collapse(m, b, bp, sink))
