@@ -267,6 +267,67 @@ int efwi_regularization_grad_noalloc(int ns, int nx, int nz, const float *m, con
 int efwi_collapse(int ns, int nx, int nz, const float *x, const float *b, const float *bp,
                   const uint8_t *sink, float *out, efwi_stream_t stream);
 
+/* ---- Optimizer: limited-memory BFGS with a strong-Wolfe line search -------
+ * The paper's inversions run l-BFGS with a step length satisfying the Wolfe
+ * conditions and stop when the convergence rate of eq. 13,
+ *   rate_{k+1} = (Phi_k - Phi_{k+1}) / Phi_k,
+ * drops below a threshold (0.1 %) or when no suitable step is found.
+ * A handle owns m pairs (s_i, y_i) of n-element FP32 device vectors plus
+ * scratch (about (2m + 5) n floats).  Directions come from the two-loop
+ * recursion with H_0 = (s^T y / y^T y) I of the newest pair (I without pairs);
+ * inner products are FP64 reductions in a fixed order.  The line search
+ * (bracketing, then zoom with safeguarded quadratic interpolation) starts at
+ * step 1 (1 / ||g|| on the first iteration) and evaluates the objective
+ * through the caller's callback:
+ *   fn(ctx, x, phi, g, stream): x device [n] (read only), phi HOST double
+ *   (written), g device [n] (written); returns 0, or nonzero to abort (a
+ *   negative value is passed on as the status).
+ * A pair is stored only when s^T y > 0.                                     */
+typedef struct efwi_lbfgs efwi_lbfgs;
+typedef int (*efwi_objective_fn)(void *ctx, const float *x, double *phi, float *g, efwi_stream_t stream);
+
+enum efwi_lbfgs_stop {
+    EFWI_LBFGS_STOP_MAX_ITER = 0,  /* max_iter iterations done */
+    EFWI_LBFGS_STOP_RATE = 1,      /* rate of eq. 13 below min_rate */
+    EFWI_LBFGS_STOP_NO_STEP = 2    /* the line search found no step within max_ls evaluations */
+};
+
+typedef struct efwi_lbfgs_info_t {
+    double phi;          /* objective after the iteration(s) */
+    double phi_prev;     /* objective before the last iteration */
+    double rate;         /* eq. 13 of the last iteration */
+    double alpha;        /* accepted step length of the last iteration */
+    int evals;           /* objective evaluations */
+    int iters;           /* iterations done (efwi_lbfgs_run) */
+    int pairs;           /* stored (s, y) pairs */
+    int ls_failed;       /* 1: no step found (x, g and phi unchanged) */
+    int stop;            /* EFWI_LBFGS_STOP_* (efwi_lbfgs_run) */
+} efwi_lbfgs_info_t;
+
+/* n vector length, m stored pairs (1..64), 0 < c1 < c2 < 1 (sufficient
+ * decrease and curvature constants, e.g. 1e-4 and 0.9), max_ls objective
+ * evaluations per line search.  Errors: EFWI_ERR_ARG, EFWI_ERR_OOM.         */
+int efwi_lbfgs_create(efwi_lbfgs **out, long long n, int m, double c1, double c2, int max_ls);
+int efwi_lbfgs_destroy(efwi_lbfgs *h);
+/* Forgets the stored pairs. */
+int efwi_lbfgs_reset(efwi_lbfgs *h);
+/* Stores the pair (s, y) (device [n] each, copied) if s^T y > 0; *accepted
+ * (may be NULL) tells whether it was.  Synchronises the stream.             */
+int efwi_lbfgs_push(efwi_lbfgs *h, const float *s, const float *y, int *accepted, efwi_stream_t stream);
+/* d = -H g (device [n] each) from the stored pairs, asynchronous.          */
+int efwi_lbfgs_direction(efwi_lbfgs *h, const float *g, float *d, efwi_stream_t stream);
+/* One iteration from x (device [n], updated), *phi (host, updated) and its
+ * gradient g (device [n], updated): direction, line search, new pair.  The
+ * history restarts from -g when d is not a descent direction.  When no step
+ * is found info->ls_failed = 1 and x, phi, g are unchanged.                */
+int efwi_lbfgs_iterate(efwi_lbfgs *h, float *x, double *phi, float *g, efwi_objective_fn fn, void *ctx,
+                       efwi_lbfgs_info_t *info, efwi_stream_t stream);
+/* Evaluates fn at x, then iterates until max_iter iterations, a rate of
+ * eq. 13 below min_rate (0.001 in the paper) or a failed line search.
+ * x and g (device [n]) hold the final model and its gradient.              */
+int efwi_lbfgs_run(efwi_lbfgs *h, float *x, float *g, efwi_objective_fn fn, void *ctx, int max_iter,
+                   double min_rate, efwi_lbfgs_info_t *info, efwi_stream_t stream);
+
 /* Extended objective of eq. 8: phi_data (as efwi_forward + misfit) and
  * phi_reg summed over the three parameter fields (Vp, Vs, rho) with their
  * own eta[3].  Both results are device doubles (overwritten).               */

@@ -46,7 +46,14 @@ class ZoiDesc(C.Structure):
                 ("n", C.c_double), ("nu", C.c_double)]
 
 
+class LbfgsInfo(C.Structure):
+    _fields_ = [("phi", C.c_double), ("phi_prev", C.c_double), ("rate", C.c_double), ("alpha", C.c_double),
+                ("evals", C.c_int), ("iters", C.c_int), ("pairs", C.c_int), ("ls_failed", C.c_int), ("stop", C.c_int)]
+
+
 VP = C.c_void_p
+# int fn(void *ctx, const float *x, double *phi, float *g, cudaStream_t stream)
+OBJECTIVE_FN = C.CFUNCTYPE(C.c_int, VP, VP, C.POINTER(C.c_double), VP, VP)
 SIGNATURES = {
     "efwi_plan_create": (C.c_int, [C.POINTER(VP), C.POINTER(PlanDesc)]),
     "efwi_plan_destroy": (C.c_int, [VP]),
@@ -59,6 +66,13 @@ SIGNATURES = {
                                    VP, VP, VP, VP]),
     "efwi_regularization_grad": (C.c_int, [VP, VP, VP, VP, VP, C.c_double, VP, VP, VP]),
     "efwi_collapse": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, VP, VP]),
+    "efwi_lbfgs_create": (C.c_int, [C.POINTER(VP), C.c_longlong, C.c_int, C.c_double, C.c_double, C.c_int]),
+    "efwi_lbfgs_destroy": (C.c_int, [VP]),
+    "efwi_lbfgs_reset": (C.c_int, [VP]),
+    "efwi_lbfgs_push": (C.c_int, [VP, VP, VP, C.POINTER(C.c_int), VP]),
+    "efwi_lbfgs_direction": (C.c_int, [VP, VP, VP, VP]),
+    "efwi_lbfgs_iterate": (C.c_int, [VP, VP, C.POINTER(C.c_double), VP, OBJECTIVE_FN, VP, C.POINTER(LbfgsInfo), VP]),
+    "efwi_lbfgs_run": (C.c_int, [VP, VP, VP, OBJECTIVE_FN, VP, C.c_int, C.c_double, C.POINTER(LbfgsInfo), VP]),
     "efwi_regularization_grad_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, C.c_double, VP, VP,
                                                     VP]),
     "efwi_extended_objective": (C.c_int, [VP, VP, VP, VP, VP, PD, VP, VP, VP, VP, VP, VP]),

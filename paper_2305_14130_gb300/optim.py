@@ -1,0 +1,151 @@
+"""l-BFGS with a strong-Wolfe line search on the device (the paper's solver),
+stopping on the convergence rate of eq. 13.
+
+Thin binding of the ``efwi_lbfgs_*`` C-ABI: every vector operation runs in the
+library's CUDA kernels; this module only marshals pointers and wraps the
+objective as the C callback.  The objective is a Python callable
+
+    phi = objective(x, g)
+
+that receives the trial point ``x`` (float32 CUDA vector of n elements, read
+only) and writes its gradient into ``g`` (same shape), returning phi as a
+Python float.  Both are views of device memory owned by the caller or by the
+l-BFGS handle, valid only during the call.
+
+``extended_fwi_objective`` builds that callable for the extended misfit of
+eq. 8 over the packed model (Vp, Vs, rho), each [ns, nz, nx].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _abi
+
+STOP = {0: "max_iter", 1: "rate", 2: "no_step"}
+
+
+class _DevView:
+    """__cuda_array_interface__ of a raw float32 device pointer (no copy)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def _as_tensor(ptr, n):
+    return torch.as_tensor(_DevView(ptr, n), device="cuda")
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _vec(t, n, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+            and t.numel() == n):
+        raise ValueError(f"{name}: contiguous float32 CUDA tensor of {n} elements expected")
+    return C.c_void_p(t.data_ptr())
+
+
+def _info(i):
+    return {"phi": i.phi, "phi_prev": i.phi_prev, "rate": i.rate, "alpha": i.alpha, "evals": i.evals,
+            "iters": i.iters, "pairs": i.pairs, "ls_failed": bool(i.ls_failed), "stop": STOP.get(i.stop, i.stop)}
+
+
+class LBFGS:
+    """Device l-BFGS over n-element float32 vectors with m stored pairs."""
+
+    def __init__(self, n: int, m: int = 5, c1: float = 1e-4, c2: float = 0.9, max_ls: int = 20):
+        self._lib = _abi.load()
+        self.n = int(n)
+        h = C.c_void_p()
+        _abi.check(self._lib.efwi_lbfgs_create(C.byref(h), self.n, int(m), float(c1), float(c2), int(max_ls)))
+        self._h = h
+        self._err = None
+
+    def close(self):
+        if self._h:
+            self._lib.efwi_lbfgs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        _abi.check(self._lib.efwi_lbfgs_reset(self._h))
+
+    def push(self, s, y) -> bool:
+        """Stores the pair (s, y) when s^T y > 0; returns whether it was stored."""
+        acc = C.c_int()
+        _abi.check(self._lib.efwi_lbfgs_push(self._h, _vec(s, self.n, "s"), _vec(y, self.n, "y"), C.byref(acc),
+                                             _stream()))
+        return bool(acc.value)
+
+    def direction(self, g, d=None):
+        """d = -H g from the stored pairs (two-loop recursion)."""
+        if d is None:
+            d = torch.empty_like(g)
+        _abi.check(self._lib.efwi_lbfgs_direction(self._h, _vec(g, self.n, "g"), _vec(d, self.n, "d"), _stream()))
+        return d
+
+    def _callback(self, objective):
+        n = self.n
+
+        def fn(ctx, xp, phip, gp, stream):
+            try:
+                phip[0] = float(objective(_as_tensor(xp, n), _as_tensor(gp, n)))
+                return 0
+            except Exception as e:          # reported after the C call returns
+                self._err = e
+                return 1
+        return _abi.OBJECTIVE_FN(fn)
+
+    def _raise(self, code):
+        if self._err is not None:
+            e, self._err = self._err, None
+            raise e
+        _abi.check(code)
+
+    def iterate(self, x, phi: float, g, objective):
+        """One iteration from (x, phi, g), all updated in place; returns (phi, info)."""
+        cb = self._callback(objective)
+        p = C.c_double(phi)
+        info = _abi.LbfgsInfo()
+        rc = self._lib.efwi_lbfgs_iterate(self._h, _vec(x, self.n, "x"), C.byref(p), _vec(g, self.n, "g"), cb, None,
+                                          C.byref(info), _stream())
+        self._raise(rc)
+        return p.value, _info(info)
+
+    def run(self, x, objective, max_iter: int = 100, min_rate: float = 1e-3, g=None):
+        """Iterates from x (updated in place) until max_iter, a rate of eq. 13
+        below min_rate or a failed line search; returns (g, info)."""
+        if g is None:
+            g = torch.empty_like(x)
+        cb = self._callback(objective)
+        info = _abi.LbfgsInfo()
+        rc = self._lib.efwi_lbfgs_run(self._h, _vec(x, self.n, "x"), _vec(g, self.n, "g"), cb, None, int(max_iter),
+                                      float(min_rate), C.byref(info), _stream())
+        self._raise(rc)
+        return g, _info(info)
+
+
+def extended_fwi_objective(plan, d_obs, b, bp, sink, eta, mask=None):
+    """phi = phi_data + sum_p phi_reg,p (eq. 8) over the packed model x = (Vp, Vs, rho)
+    [3 * ns * nz * nx]; writes the packed gradient into g."""
+    shape = (3, plan.ns, plan.nz, plan.nx)
+
+    def objective(x, g):
+        m = x.view(shape)
+        gg = g.view(shape)
+        phi_d, *_ = plan.gradient(m[0], m[1], m[2], d_obs, mask=mask, out=(gg[0], gg[1], gg[2]))
+        phi = phi_d
+        for k in range(3):
+            phi_r, _ = plan.regularization_grad(m[k], b, bp, sink, eta[k], g=gg[k])
+            phi = phi + phi_r
+        return float(phi.item())
+    return objective

@@ -45,6 +45,8 @@ def test_struct_layouts_match_binding(tmp_path):
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "efwi.h"', 'int main(void) {',
              'printf("%zu\\n", sizeof(efwi_plan_desc));']
     lines += [f'printf("%zu\\n", offsetof(efwi_plan_desc, {f}));' for f in fields]
+    lines += ['printf("%zu\\n", sizeof(efwi_lbfgs_info_t));']
+    lines += [f'printf("%zu\\n", offsetof(efwi_lbfgs_info_t, {f}));' for f, _ in _abi.LbfgsInfo._fields_]
     lines += ['printf("%zu\\n", sizeof(efwi_plan_info_t));', 'printf("%zu\\n", sizeof(efwi_zoi_desc));',
               'return 0; }']
     prog.write_text("\n".join(lines))
@@ -54,6 +56,10 @@ def test_struct_layouts_match_binding(tmp_path):
     assert vals[0] == C.sizeof(_abi.PlanDesc)
     for f, off in zip(fields, vals[1:1 + len(fields)]):
         assert getattr(_abi.PlanDesc, f).offset == off, f
+    lb = vals[1 + len(fields):1 + len(fields) + 1 + len(_abi.LbfgsInfo._fields_)]
+    assert lb[0] == C.sizeof(_abi.LbfgsInfo)
+    for (f, _), off in zip(_abi.LbfgsInfo._fields_, lb[1:]):
+        assert getattr(_abi.LbfgsInfo, f).offset == off, f
     assert vals[-2] == C.sizeof(_abi.PlanInfo)
     assert vals[-1] == C.sizeof(_abi.ZoiDesc)
 
@@ -119,6 +125,19 @@ def test_collapse_rejects_bad_arguments(lib):
     assert "ns, nx and nz" in lib.efwi_last_error(None).decode()
     assert lib.efwi_collapse(2, 4, 4, None, p, p, p, p, None) == -1
     assert "NULL" in lib.efwi_last_error(None).decode()
+
+
+def test_lbfgs_rejects_bad_arguments(lib):
+    """Argument checks of the l-BFGS handle happen before any allocation."""
+    h = C.c_void_p()
+    assert lib.efwi_lbfgs_create(C.byref(h), 0, 5, 1e-4, 0.9, 20) == -1
+    assert lib.efwi_lbfgs_create(C.byref(h), 100, 0, 1e-4, 0.9, 20) == -1
+    assert lib.efwi_lbfgs_create(C.byref(h), 100, 5, 0.9, 1e-4, 20) == -1
+    assert "c1 < c2" in lib.efwi_last_error(None).decode()
+    assert lib.efwi_lbfgs_create(C.byref(h), 100, 5, 1e-4, 0.9, 0) == -1
+    assert not h.value
+    assert lib.efwi_lbfgs_destroy(None) == 0
+    assert lib.efwi_lbfgs_reset(None) == -1
 
 
 def test_null_arguments(lib):

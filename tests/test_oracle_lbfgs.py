@@ -1,0 +1,121 @@
+"""Pins of the optimizer oracle (l-BFGS, strong-Wolfe line search, eq. 13) to
+facts independent of its code: the dense BFGS inverse-Hessian formula, the
+secant equation, closed-form line minimisers of quadratics, the Wolfe
+conditions themselves, and finite termination on convex quadratics."""
+import numpy as np
+import pytest
+
+from oracle import lbfgs as L
+
+
+def _pairs(n, k, seed):
+    """k pairs with y = A s for an SPD A (so s^T y > 0), rows oldest first."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(rng.uniform(0.5, 5.0, n)) @ Q.T
+    S = rng.standard_normal((k, n))
+    return S, S @ A.T, A
+
+
+@pytest.mark.parametrize("k", [0, 1, 3, 5])
+def test_two_loop_equals_dense_bfgs_matrix(k):
+    S, Y, _ = _pairs(12, k, 1)
+    g = np.random.default_rng(2).standard_normal(12)
+    H = L.bfgs_inverse_hessian(S, Y)
+    assert np.allclose(L.two_loop(g, S, Y), H @ g, rtol=1e-12, atol=1e-12)
+
+
+def test_dense_matrix_satisfies_secant_equation_and_symmetry():
+    S, Y, _ = _pairs(9, 4, 3)
+    H = L.bfgs_inverse_hessian(S, Y)
+    assert np.allclose(H @ Y[-1], S[-1], rtol=1e-12, atol=1e-12)
+    assert np.allclose(H, H.T, atol=1e-12)
+    assert np.all(np.linalg.eigvalsh(H) > 0)
+
+
+def test_n_pairs_of_a_quadratic_reproduce_its_inverse_hessian():
+    """n A-conjugate pairs y_i = A s_i of a quadratic: BFGS keeps H y_j = s_j
+    for every earlier pair (hereditary property), so after the n-th update
+    H = A^{-1} exactly, whatever H_0."""
+    n = 6
+    rng = np.random.default_rng(4)
+    A = np.diag(rng.uniform(1.0, 3.0, n))
+    S = np.eye(n)                       # A-conjugate for a diagonal A
+    Y = S @ A.T
+    H = L.bfgs_inverse_hessian(S, Y)
+    assert np.allclose(H, np.linalg.inv(A), rtol=1e-12, atol=1e-12)
+
+
+def test_zoom_hits_the_minimiser_of_a_one_dimensional_quadratic():
+    """phi(a) = phi0 + phi'(0) a + c a^2 / 2 (here a* = 1/4): a first step
+    a0 = 0.3 just beyond the minimiser has phi'(a0) > 0 and, with c2 = 0.1,
+    fails the curvature condition; the quadratic interpolating the bracket
+    ends is phi itself, so the first zoom trial is a* = -phi'(0)/c exactly
+    (inside the inner 80 % of [0, 0.3])."""
+    c, x0 = 4.0, np.array([3.0])
+
+    def f(x):
+        return 0.5 * c * float(x @ x), c * x
+
+    phi0, g0 = f(x0)
+    d = -g0
+    a, phi, g, evals = L.wolfe_search(f, x0, phi0, g0, d, a0=0.3, c2=0.1)
+    assert a == pytest.approx(1.0 / c, rel=1e-14)
+    assert evals == 2
+    assert abs(phi) < 1e-25
+
+
+@pytest.mark.parametrize("fun", ["quadratic", "rosenbrock"])
+def test_accepted_step_satisfies_the_strong_wolfe_conditions(fun):
+    rng = np.random.default_rng(5)
+    if fun == "quadratic":
+        A = np.diag(rng.uniform(0.1, 10.0, 8))
+
+        def f(x):
+            return 0.5 * float(x @ A @ x), A @ x
+        x0 = rng.standard_normal(8)
+    else:
+        def f(x):
+            phi = float(np.sum(100.0 * (x[1:] - x[:-1] ** 2) ** 2 + (1 - x[:-1]) ** 2))
+            g = np.zeros_like(x)
+            g[:-1] = -400.0 * x[:-1] * (x[1:] - x[:-1] ** 2) - 2.0 * (1 - x[:-1])
+            g[1:] += 200.0 * (x[1:] - x[:-1] ** 2)
+            return phi, g
+        x0 = np.full(6, -1.2)
+    c1, c2 = 1e-4, 0.9
+    for a0 in (1e-3, 1.0, 50.0):
+        phi0, g0 = f(x0)
+        d = -g0
+        a, phi, g, _ = L.wolfe_search(f, x0, phi0, g0, d, a0, c1, c2, max_ls=40)
+        assert a is not None
+        assert phi <= phi0 + c1 * a * (g0 @ d) + 1e-12 * abs(phi0)
+        assert abs(g @ d) <= -c2 * (g0 @ d)
+
+
+def test_lbfgs_minimises_a_convex_quadratic_and_reports_eq13_rates():
+    rng = np.random.default_rng(6)
+    n = 20
+    a = rng.uniform(0.5, 20.0, n)
+    c = rng.standard_normal(n)
+
+    def f(x):
+        r = x - c
+        return 0.5 * float(np.sum(a * r * r)) + 1.0, a * r
+
+    it = L.lbfgs(f, np.zeros(n), iters=60, m=5)
+    assert np.linalg.norm(it[-1]["x"] - c) < 1e-6
+    it = [r for r in it if r["rate"] is not None]     # a last failed search (at the minimum) moves nothing
+    phis = [f(np.zeros(n))[0]] + [r["phi"] for r in it]
+    for k, r in enumerate(it):
+        assert r["rate"] == pytest.approx((phis[k] - phis[k + 1]) / phis[k], rel=1e-15)
+        assert r["phi"] <= phis[k]
+
+
+def test_failed_search_keeps_the_point():
+    """A direction of ascent never satisfies the sufficient decrease."""
+    def f(x):
+        return float(x @ x), 2 * x
+    x0 = np.array([1.0, -2.0])
+    phi0, g0 = f(x0)
+    a, phi, g, evals = L.wolfe_search(f, x0, phi0, g0, g0, 1.0, max_ls=5)
+    assert a is None and evals == 5
