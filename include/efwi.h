@@ -20,7 +20,8 @@
  * Physics (the paper fixes no scheme): 2D isotropic elastic velocity-stress
  * equations on a Virieux staggered grid, 4th order in space, 2nd order in
  * time, convolutional PML (Komatitsch & Martin 2007), moment-tensor sources,
- * DAS gauge-averaged axial strain (or strain rate).  The gradient is the exact
+ * DAS gauge-averaged axial strain (or strain rate) or 2-C particle-velocity
+ * receivers.  The gradient is the exact
  * discrete adjoint of the forward time stepping.
  *
  * Conventions shared by every call
@@ -65,7 +66,13 @@ enum efwi_status {
     EFWI_ERR_NOT_IMPLEMENTED = -7
 };
 
-enum efwi_das_mode { EFWI_DAS_STRAIN = 0, EFWI_DAS_STRAIN_RATE = 1 };
+/* receiver kind of every trace:
+ *  STRAIN       DAS gauge-averaged axial strain t.(u(p+) - u(p-))/L, u the running
+ *               time integral of the particle velocity at the gauge ends p+- = c +- (L/2) t
+ *  STRAIN_RATE  the same with v instead of u
+ *  VELOCITY     particle-velocity receiver (2-C geophones: one trace per component):
+ *               t.v(c) at the channel point c; the gauge is not used                */
+enum efwi_das_mode { EFWI_DAS_STRAIN = 0, EFWI_DAS_STRAIN_RATE = 1, EFWI_DAS_VELOCITY = 2 };
 /* storage precision of the wavefield checkpoints (the time stepping is FP32) */
 enum efwi_store { EFWI_STORE_FP32 = 0, EFWI_STORE_FP16 = 1, EFWI_STORE_BF16 = 2 };
 /* execution strategy:
@@ -94,11 +101,13 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *   src_xz [ns][2]     source positions (m), inside the shot's window
  *   mt [ns][3]         moment tensor (Mxx, Mzz, Mxz) per source (eq. 2)
  *   wavelet [ns][nt+1] source time function w(t_n), t_n = n dt
- *   ntr, tr_ptr[ns+1]  DAS traces, CSR over sources (the set N_r^s of eq. 4)
- *   ch_xz [ntr][2]     gauge centres (m); ch_t [ntr][2] unit tangents
+ *   ntr, tr_ptr[ns+1]  traces, CSR over sources (the set N_r^s of eq. 4)
+ *   ch_xz [ntr][2]     gauge centres / receiver points (m); ch_t [ntr][2] unit
+ *                      tangents (DAS) or recorded components (VELOCITY)
  *   gauge              gauge length L (m): d = t.(u(p+) - u(p-)) / L,
  *                      p+- = centre +- (L/2) t, u the displacement (STRAIN)
- *                      or the particle velocity (STRAIN_RATE)
+ *                      or the particle velocity (STRAIN_RATE); unused for
+ *                      VELOCITY receivers (d = t.v(centre))
  *   win [ns][2]        optional per-shot window (x0, width) in cells: shot s
  *                      is modelled on columns x0 .. x0+width-1 only (NULL =
  *                      the full grid for every shot)

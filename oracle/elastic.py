@@ -18,7 +18,9 @@ What it follows
   for the reciprocity and Green's-function checks only.
 * Sampling operator K_r (eq. 3) as DAS gauge-averaged axial strain
   t.(u(p+) - u(p-))/L with u the running time integral of the particle
-  velocity at the gauge ends (or strain rate with v instead of u).
+  velocity at the gauge ends (or strain rate with v instead of u), or as a
+  particle-velocity receiver (the synthetic section's 2-C acquisition):
+  trace value t.v(p) at the channel point p, one trace per component t.
 * Misfit phi = 1/2 sum_s sum_r ||d_{s,r} - d_obs||^2 (eq. 4; first term of
   eq. 8 with the model m_s specific to shot s).
 * Gradient g_s = J_s^T (d_s - d_obs_s) (eq. 6) by the adjoint-state method:
@@ -52,7 +54,7 @@ import numpy as np
 
 C1 = 9.0 / 8.0
 C2 = -1.0 / 24.0
-STRAIN, STRAIN_RATE = 0, 1
+STRAIN, STRAIN_RATE, VELOCITY = 0, 1, 2
 
 
 # ---------------------------------------------------------------------------
@@ -224,8 +226,11 @@ class Shot:
         for c in range(self.ntr):
             cx, cz = acq.ch_xz[a + c]
             tx, tz = self.ch_t[c]
-            pp = (cx + 0.5 * self.gauge * tx, cz + 0.5 * self.gauge * tz)
-            pm = (cx - 0.5 * self.gauge * tx, cz - 0.5 * self.gauge * tz)
+            if acq.das_mode == VELOCITY:            # one point; the "p-" samples get zero weight
+                pp = pm = (cx, cz)
+            else:
+                pp = (cx + 0.5 * self.gauge * tx, cz + 0.5 * self.gauge * tz)
+                pm = (cx - 0.5 * self.gauge * tx, cz - 0.5 * self.gauge * tz)
             for k, (pt, ox, oz) in enumerate(((pp, 0.5, 0.0), (pp, 0.0, 0.5), (pm, 0.5, 0.0), (pm, 0.0, 0.5))):
                 for q, (j, i, wt) in enumerate(self._weights(pt[0], pt[1], ox, oz)):
                     self.das_j[c, k, q], self.das_i[c, k, q], self.das_wt[c, k, q] = j, i, wt
@@ -300,6 +305,8 @@ class Shot:
         if self.acq.das_mode == STRAIN:
             U += dt * vals
             return (tx * (U[:, 0] - U[:, 2]) + tz * (U[:, 1] - U[:, 3])) / L
+        if self.acq.das_mode == VELOCITY:
+            return tx * vals[:, 0] + tz * vals[:, 1]
         return (tx * (vals[:, 0] - vals[:, 2]) + tz * (vals[:, 1] - vals[:, 3])) / L
 
     def step(self, st, n):
@@ -378,9 +385,13 @@ class Shot:
 
         # DAS sampling transposed
         if self.ntr:
-            rc = np.asarray(r_n, np.float64) / self.gauge
             tx, tz = self.ch_t[:, 0], self.ch_t[:, 1]
-            dd = np.stack([tx * rc, tz * rc, -tx * rc, -tz * rc], axis=1)   # d d^n / d (U or v samples)
+            if self.acq.das_mode == VELOCITY:
+                rc = np.asarray(r_n, np.float64)
+                dd = np.stack([tx * rc, tz * rc, 0 * rc, 0 * rc], axis=1)
+            else:
+                rc = np.asarray(r_n, np.float64) / self.gauge
+                dd = np.stack([tx * rc, tz * rc, -tx * rc, -tz * rc], axis=1)   # d d^n / d (U or v samples)
             if self.acq.das_mode == STRAIN:
                 adj["U"] += dd
                 val = dt * adj["U"]

@@ -9,7 +9,7 @@ from .build import LIB
 EFWI_OK = 0
 STATUS = {0: "EFWI_OK", -1: "EFWI_ERR_ARG", -2: "EFWI_ERR_CFL", -3: "EFWI_ERR_OOM", -4: "EFWI_ERR_CUDA",
           -5: "EFWI_ERR_TIMEOUT", -6: "EFWI_ERR_NAN", -7: "EFWI_ERR_NOT_IMPLEMENTED"}
-DAS_STRAIN, DAS_STRAIN_RATE = 0, 1
+DAS_STRAIN, DAS_STRAIN_RATE, DAS_VELOCITY = 0, 1, 2
 STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXEC = {"plain": 0, "batched": 1}
 STENCIL = {"auto": 0, "loads": 1, "tma": 2, "tma_pairs": 3}

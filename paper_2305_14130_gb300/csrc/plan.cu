@@ -188,9 +188,10 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (!d->src_xz || !d->mt || !d->wavelet || !d->tr_ptr || !d->ref_vp || !d->ref_vs || !d->ref_rho)
         return fail(nullptr, EFWI_ERR_ARG, "a required host array is NULL");
     if (d->ntr > 0 && (!d->ch_xz || !d->ch_t)) return fail(nullptr, EFWI_ERR_ARG, "channel arrays are NULL");
-    if (d->das_mode != EFWI_DAS_STRAIN && d->das_mode != EFWI_DAS_STRAIN_RATE)
+    if (d->das_mode != EFWI_DAS_STRAIN && d->das_mode != EFWI_DAS_STRAIN_RATE && d->das_mode != EFWI_DAS_VELOCITY)
         return fail(nullptr, EFWI_ERR_ARG, "unknown das_mode");
-    if (d->ntr > 0 && !(d->gauge > 0)) return fail(nullptr, EFWI_ERR_ARG, "gauge must be > 0");
+    if (d->ntr > 0 && d->das_mode != EFWI_DAS_VELOCITY && !(d->gauge > 0))
+        return fail(nullptr, EFWI_ERR_ARG, "gauge must be > 0");
     if (d->ckpt_store < EFWI_STORE_FP32 || d->ckpt_store > EFWI_STORE_BF16)
         return fail(nullptr, EFWI_ERR_ARG, "unknown ckpt_store");
     if (d->exec != EFWI_EXEC_PLAIN && d->exec != EFWI_EXEC_BATCHED) return fail(nullptr, EFWI_ERR_ARG, "unknown exec");
@@ -301,11 +302,15 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
             p->trace_shot[c] = s;
             const double cx = d->ch_xz[2 * c], cz = d->ch_xz[2 * c + 1];
             const double tx = d->ch_t[2 * c], tz = d->ch_t[2 * c + 1];
-            const double hl = 0.5 * d->gauge;
+            // DAS: gauge ends p+- = c +- (L/2) t with weights +-t/L; particle-velocity
+            // receiver: the point c with weight t (the second "end" carries zero weight)
+            const bool point = d->das_mode == EFWI_DAS_VELOCITY;
+            const double hl = point ? 0.0 : 0.5 * d->gauge;
+            const double scale = point ? 1.0 : 1.0 / d->gauge;
             const double ends[2][2] = {{cx + hl * tx, cz + hl * tz}, {cx - hl * tx, cz - hl * tz}};
             for (int k = 0; k < 4; ++k) {
                 const int e = k >> 1, field = k & 1;
-                const double sgn = e == 0 ? 1.0 : -1.0;
+                const double sgn = e == 0 ? 1.0 : (point ? 0.0 : -1.0);
                 const double tcomp = field == 0 ? tx : tz;
                 Corner cr[4];
                 if (!bilinear(*d, sh, ends[e][0], ends[e][1], field == 0 ? 0.5 : 0.0, field == 0 ? 0.0 : 0.5, cr)) {
@@ -316,7 +321,7 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
                 }
                 for (int q = 0; q < 4; ++q) {
                     const int o = local_off(sh, cr[q].i, cr[q].j);
-                    const float wq = (float)(cr[q].w * sgn * tcomp / d->gauge);
+                    const float wq = (float)(cr[q].w * sgn * tcomp * scale);
                     h_off[(size_t)c * 16 + k * 4 + q] = o;
                     h_w[(size_t)c * 16 + k * 4 + q] = wq;
                     if (wq != 0.f) gmap[std::make_tuple(s, field, o)].push_back({c, wq});

@@ -38,6 +38,8 @@ CASES = {
     "tiny_strain": lambda: W.tiny(nx=40, nz=30, ns=3, nt=80, npml=6),
     "tiny_strain_rate": lambda: W.tiny(nx=37, nz=29, ns=2, nt=70, npml=5, das_mode=W.STRAIN_RATE),
     "tiny_windows": lambda: W.tiny(nx=48, nz=26, ns=3, nt=60, npml=4, win=[[0, 30], [9, 37], [20, 28]]),
+    "tiny_2c_velocity": lambda: W.two_component(W.tiny(nx=43, nz=31, ns=3, nt=70, npml=5,
+                                                       win=[[0, 35], [6, 37], [12, 31]])),
 }
 
 
@@ -139,6 +141,52 @@ def test_reduced_precision_checkpoints(efwi, store, bound):
     print(f"{store} checkpoint gradient rel-L2 errors (vp, vs, rho): {errs}")
     assert 0 < max(errs) <= bound
     ref.close(); red.close()
+
+
+def test_random_layered_128_parity(efwi):
+    """The differentiation case: 128x128 dx=2 m random-layered model, 4 shots,
+    nt = 600 (the oracle's finite-difference gradient check runs on it):
+    data, misfit and the three gradients of every component against the oracle."""
+    p = rounded(W.random_layered_128())
+    d_obs = observed(p)
+    phi_o, gvp_o, gvs_o, grho_o = E.gradient(p.acq, p.vp, p.vs, p.rho, d_obs)
+    d_o = E.forward(p.acq, p.vp, p.vs, p.rho)
+    plan = efwi.Plan(p.acq, exec="batched")
+    phi, gvp, gvs, grho, d = plan.gradient(dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs), return_data=True)
+    torch.cuda.synchronize()
+    assert rel_l2(d.cpu().numpy(), d_o) <= TOL
+    assert abs(phi.item() - phi_o) <= TOL * phi_o
+    for g, go in ((gvp, gvp_o), (gvs, gvs_o), (grho, grho_o)):
+        assert rel_l2(g.cpu().numpy(), go) <= TOL
+    plan.close()
+
+
+@pytest.fixture(scope="module")
+def uneven_subset():
+    p = rounded(W.uneven_windows_subset_256x128())
+    d_obs = observed(p)
+    return p, d_obs, E.gradient(p.acq, p.vp, p.vs, p.rho, d_obs), E.forward(p.acq, p.vp, p.vs, p.rho)
+
+
+@pytest.mark.parametrize("store,bound", [("fp32", TOL), ("fp16", 2e-3), ("bf16", 2e-2)])
+def test_uneven_windows_subset_against_oracle(efwi, uneven_subset, store, bound):
+    """Uneven batching with reduced-precision checkpoints, on the 256x128 subset
+    of the uneven-window configuration (6 shots on windows of 55-138 cells, one
+    launch per step): every output against the FP64 oracle.  FP32 checkpoints
+    meet the parity tolerance; the FP16 / BF16 errors are printed and bounded
+    (stored state errs by at most s 2^-12 / s 2^-9 per element)."""
+    p, d_obs, (phi_o, gvp_o, gvs_o, grho_o), d_o = uneven_subset
+    plan = efwi.Plan(p.acq, exec="batched", ckpt_store=store)
+    phi, gvp, gvs, grho, d = plan.gradient(dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs), return_data=True)
+    torch.cuda.synchronize()
+    errs = {"d": rel_l2(d.cpu().numpy(), d_o), "phi": abs(phi.item() - phi_o) / phi_o}
+    for k, g, go in (("g_vp", gvp, gvp_o), ("g_vs", gvs, gvs_o), ("g_rho", grho, grho_o)):
+        errs[k] = rel_l2(g.cpu().numpy(), go)
+    print(f"uneven windows 256x128, {store} checkpoints, errors vs FP64 oracle: {errs}")
+    assert errs["d"] <= TOL and errs["phi"] <= TOL     # data do not depend on the checkpoints
+    for k in ("g_vp", "g_vs", "g_rho"):
+        assert errs[k] <= bound, k
+    plan.close()
 
 
 def test_zoi_weights_parity(efwi):

@@ -2,7 +2,8 @@
 
 * dot-product tests <L x, y> = <x, L^T y> to 1e-12 for the whole step map
   (all wavefields, CPML memory variables, DAS accumulators) and for the
-  wavelet -> data map, in both DAS modes and with a cropped window;
+  wavelet -> data map, in both DAS modes, for particle-velocity receivers and
+  with a cropped window;
 * central finite differences of the misfit against <g, dm> for Vp, Vs and
   rho separately;
 * zero residual gives an exactly zero gradient.
@@ -29,7 +30,7 @@ def _inner(a, b):
     return s + sum(float(np.sum(a["psi"][k] * b["psi"][k])) for k in range(8))
 
 
-@pytest.mark.parametrize("mode", [W.STRAIN, W.STRAIN_RATE])
+@pytest.mark.parametrize("mode", [W.STRAIN, W.STRAIN_RATE, W.VELOCITY])
 @pytest.mark.parametrize("win", [None, [[3, 16], [5, 17]]])
 def test_dot_product_state_map(mode, win):
     p = W.tiny(das_mode=mode, win=win)
@@ -45,7 +46,7 @@ def test_dot_product_state_map(mode, win):
         assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-@pytest.mark.parametrize("mode", [W.STRAIN, W.STRAIN_RATE])
+@pytest.mark.parametrize("mode", [W.STRAIN, W.STRAIN_RATE, W.VELOCITY])
 def test_dot_product_wavelet_map(mode):
     p = W.tiny(das_mode=mode)
     rng = np.random.default_rng(2)
@@ -74,7 +75,7 @@ def _fd_check(p, d_obs, rel_h=1e-6, tol=1e-6, seed=5):
         assert abs(fd - an) <= tol * abs(an), (k, fd, an)
 
 
-@pytest.mark.parametrize("mode", [W.STRAIN, W.STRAIN_RATE])
+@pytest.mark.parametrize("mode", [W.STRAIN, W.STRAIN_RATE, W.VELOCITY])
 def test_gradient_finite_difference_tiny(mode):
     p = W.tiny(das_mode=mode, win=[[0, 24], [2, 20]])
     ns = p.acq.ns

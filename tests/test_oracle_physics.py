@@ -122,6 +122,19 @@ def test_das_strain_is_integral_of_strain_rate():
                        atol=1e-12 * np.abs(d_strain).max())
 
 
+def test_velocity_receivers_equal_geophone_recordings():
+    """2-C particle-velocity traces (VELOCITY mode, t = (1, 0) and (0, 1) at each
+    channel point) equal the oracle's separate geophone recording of (vx, vz)
+    at the same points, the path the Green's-function test pins."""
+    p = W.two_component(W.tiny(ns=1, nt=40))
+    acq = p.acq
+    pts = acq.ch_xz[::2]
+    d, g, _ = E.Shot(acq, 0, p.vp[0], p.vs[0], p.rho[0], geophones=pts).forward()
+    assert np.abs(g).max() > 0
+    assert np.allclose(d[0::2], g[:, 0], rtol=0, atol=1e-15 * np.abs(g).max())
+    assert np.allclose(d[1::2], g[:, 1], rtol=0, atol=1e-15 * np.abs(g).max())
+
+
 def test_explosion_is_mirror_symmetric():
     """Homogeneous medium, explosion on the centre node: v_x is odd about the source."""
     n, dx, dt, nt, f0 = 41, 2.0, 2e-4, 120, 60.0

@@ -22,6 +22,7 @@ import numpy as np
 
 STRAIN = 0        # gauge-averaged axial strain (running displacement)
 STRAIN_RATE = 1   # gauge-averaged axial strain rate (velocity)
+VELOCITY = 2      # particle-velocity receiver: one trace per component t, value t.v(p)
 
 
 @dataclass
@@ -285,21 +286,22 @@ def random_layered_128(ns: int = 4, nt: int = 600) -> Problem:
                    zoi=default_zoi(acq, taper_m=40.0, sink_ax=16.0, sink_az=10.0))
 
 
-def uneven_windows_3000x800(ns: int = 96, nt: int = 4000, seed: int = 0) -> Problem:
-    """3000x800 dx=0.75 m waveguide, 96 shots each on its own cropped window.
+def uneven_windows(nx: int, nz: int, dx: float, dt: float, ns: int, nt: int, wmin: int, wmax: int, z_top: float,
+                   z_src: float, z_fib: float, seed: int = 0, name: str = "uneven_windows") -> Problem:
+    """Waveguide with every shot on its own cropped window of uneven width.
 
-    Window widths uniform in [600, 1800] cells (seeded), each centred on its
-    shot; channels are the fibre channels inside the window.
+    Window widths uniform in [wmin, wmax] cells (seeded), each centred on its
+    shot (clipped to the grid); channels are the fibre channels inside the
+    window.  150 Hz Ricker.
     """
-    nx, nz, dx = 3000, 800, 0.75
-    dt, f0 = 7.5e-5, 150.0
-    vp, vs, rho = waveguide_model(nx, nz, dx, z_top=135.0 * 2, thickness=30.0, dx=dx)
+    f0 = 150.0
+    vp, vs, rho = waveguide_model(nx, nz, dx, z_top=z_top, thickness=30.0, dx=dx)
     rng = np.random.default_rng(seed)
-    widths = rng.integers(600, 1801, ns)
+    widths = rng.integers(wmin, wmax + 1, ns)
     xs = np.linspace(0.2 * nx * dx, 0.8 * nx * dx, ns)
-    src = np.stack([xs, np.full(ns, 300.0)], axis=1)
+    src = np.stack([xs, np.full(ns, z_src)], axis=1)
     mt = np.tile(np.array([[1e6, 0.75e6, 0.0]]), (ns, 1))
-    fib, ft = horizontal_fibre(dx * 2, int((nx - 4) * dx), 1.0, 340.0)
+    fib, ft = horizontal_fibre(dx * 2, int((nx - 4) * dx), 1.0, z_fib)
     win = np.zeros((ns, 2), np.int32)
     chs, tts, ptr = [], [], [0]
     for s in range(ns):
@@ -313,7 +315,28 @@ def uneven_windows_3000x800(ns: int = 96, nt: int = 4000, seed: int = 0) -> Prob
     acq = Acquisition(nx=nx, nz=nz, dx=dx, dz=dx, nt=nt, dt=dt, src_xz=src, mt=mt, wavelet=wav,
                       tr_ptr=np.array(ptr, np.int32), ch_xz=np.concatenate(chs), ch_t=np.concatenate(tts),
                       gauge=10.0, ref_vp=vp, ref_vs=vs, ref_rho=rho, win=win, pml_f0=f0)
-    return Problem("uneven_windows_3000x800", acq, extend(vp, ns), extend(vs, ns), extend(rho, ns))
+    bump = gaussian_bump(nx, nz, nx // 2, int(round((z_top + 15.0) / dx)), nx // 20 + 2, 8)
+    return Problem(name, acq, extend(vp, ns), extend(vs, ns), extend(rho, ns),
+                   true_vp=vp * (1 + 0.04 * bump), true_vs=vs * (1 + 0.06 * bump), true_rho=rho.copy())
+
+
+def uneven_windows_3000x800(ns: int = 96, nt: int = 4000, seed: int = 0) -> Problem:
+    """3000x800 dx=0.75 m waveguide, 96 shots each on its own cropped window.
+
+    Window widths uniform in [600, 1800] cells (seeded); layer at 270-300 m,
+    sources at 300 m, fibre at 340 m; dt = 0.075 ms.
+    """
+    return uneven_windows(3000, 800, 0.75, 7.5e-5, ns, nt, 600, 1800, z_top=270.0, z_src=300.0, z_fib=340.0, seed=seed,
+                          name="uneven_windows_3000x800")
+
+
+def uneven_windows_subset_256x128(ns: int = 6, nt: int = 500, seed: int = 0) -> Problem:
+    """256x128 parity subset of the uneven-window configuration: same dx, layer
+    thickness, source-fibre offset (40 m) and width distribution scaled to the
+    grid (widths uniform in [51, 153] cells); layer at 33-63 m, sources at 48 m,
+    fibre at 88 m."""
+    return uneven_windows(256, 128, 0.75, 7.5e-5, ns, nt, 51, 153, z_top=33.0, z_src=48.0, z_fib=88.0, seed=seed,
+                          name="uneven_windows_subset_256x128")
 
 
 def tiny(nx=24, nz=20, ns=2, nt=40, dx=5.0, dt=5e-4, npml=4, das_mode=STRAIN, win=None, seed=0,
@@ -355,6 +378,23 @@ def tiny(nx=24, nz=20, ns=2, nt=40, dx=5.0, dt=5e-4, npml=4, das_mode=STRAIN, wi
     ext_rho = extend(rho, ns) * (1 + 0.02 * rng2.standard_normal((ns, nz, nx)))
     return Problem("tiny", acq, ext_vp, ext_vs, ext_rho, true_vp=vp, true_vs=vs, true_rho=rho,
                    zoi=default_zoi(acq, taper_m=3 * dx, sink_ax=3 * dx, sink_az=2 * dx))
+
+
+def two_component(p: Problem) -> Problem:
+    """The same problem recorded by 2-C particle-velocity receivers at the
+    channel positions instead of DAS gauges: every channel becomes two traces,
+    horizontal (t = (1, 0)) then vertical (t = (0, 1))."""
+    a = p.acq
+    ptr, xz, t = [0], [], []
+    for s in range(a.ns):
+        lo, hi = int(a.tr_ptr[s]), int(a.tr_ptr[s + 1])
+        for c in range(lo, hi):
+            xz += [a.ch_xz[c], a.ch_xz[c]]
+            t += [(1.0, 0.0), (0.0, 1.0)]
+        ptr.append(ptr[-1] + 2 * (hi - lo))
+    acq = replace(a, tr_ptr=np.array(ptr, np.int32), ch_xz=np.array(xz, np.float64).reshape(-1, 2),
+                  ch_t=np.array(t, np.float64).reshape(-1, 2), das_mode=VELOCITY)
+    return replace(p, acq=acq)
 
 
 def with_windows(p: Problem, win) -> Problem:
