@@ -91,10 +91,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
     for (int k = 0; t < a.ntiles; t += gridDim.x, ++k) {
         const int b = k % NST;
         float *buf = smb + b * L::BUF;
-        // refill the stage consumed in the previous iteration with tile k + NST - 1
-        const int tn = t + (NST - 1) * gridDim.x;
-        const int bn = (k + NST - 1) % NST;
-        if (tid == 0 && tn < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, tn, smb + bn * L::BUF, &bar[bn]);
         if (tid == 0) ok_s = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
         __syncthreads();
         if (!ok_s) {
@@ -103,6 +99,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         }
         mbar_wait_bounded(&bar[b], (phase >> b) & 1u);   // completed: acquire for every thread
         phase ^= 1u << b;
+        // refill the stage consumed in the previous iteration with tile k + NST - 1: every
+        // thread has passed the barrier above, so none still reads that stage
+        const int tn = t + (NST - 1) * gridDim.x;
+        const int bn = (k + NST - 1) % NST;
+        if (tid == 0 && tn < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, tn, smb + bn * L::BUF, &bar[bn]);
 
         const int4 tl = a.tiles[t];
         // interior tiles (no CPML strip or grid edge within the halo) run a copy of
@@ -384,7 +385,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         };
         if (tl.w & 2) tile(std::true_type{});
         else tile(std::false_type{});
-        __syncthreads();   // this buffer is refilled by the next iteration's prefetch
     }
 }
 
