@@ -127,6 +127,10 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *   overlap            EFWI_OVERLAP_*: whether the checkpoint recompute of one
  *                      segment runs concurrently with the adjoint of the next
  *                      (EXEC_BATCHED with ckpt_interval < nt); results are the same
+ *   force [ns][2]      optional vector-force sources (Fx, Fz) (eq. 2, second
+ *                      case), replacing the moment tensors (mt is then ignored):
+ *                      v^{n+1/2} += dt b F w(t_n) delta_h on the staggered v
+ *                      grids (bilinear delta_h / (dx dz)); NULL = moment tensors
  */
 typedef struct efwi_plan_desc {
     int nx, nz;
@@ -155,6 +159,7 @@ typedef struct efwi_plan_desc {
     int adj_tile_x, adj_tile_z;
     int adj_stencil;
     int overlap;
+    const double *force;
 } efwi_plan_desc;
 
 /* What a plan chose and holds (filled by efwi_plan_info). */

@@ -14,8 +14,9 @@ What it follows
 * Moment-tensor point source -M grad(delta) w(t) (eq. 2, third case): since
   -M grad(delta) w = div(-M delta w), the stresses are driven by -M delta w;
   per step sigma^{n+1} -= M (w_{n+1} - w_n) delta_h, delta_h = bilinear
-  weight / (dx dz).  A vector-force source (eq. 2, second case) is available
-  for the reciprocity and Green's-function checks only.
+  weight / (dx dz).  A vector-force source F delta w (eq. 2, second case)
+  enters the velocity sub-step: v^{n+1/2} += dt b F w(t_n) delta_h on the
+  staggered v grids; it replaces the moment tensor of its shot.
 * Sampling operator K_r (eq. 3) as DAS gauge-averaged axial strain
   t.(u(p+) - u(p-))/L with u the running time integral of the particle
   velocity at the gauge ends (or strain rate with v instead of u), or as a
@@ -168,7 +169,7 @@ class Shot:
 
     vp, vs, rho: [nz, nx] physical model (the extended component of shot s).
     force: optional (fx, fz) replacing the moment tensor by a vector force
-    (oracle-only source, used by the physics checks).
+    (default: acq.force[s] when the acquisition has forces).
     geophones: optional [k, 2] points where (vx, vz) are also recorded.
     """
 
@@ -206,6 +207,8 @@ class Shot:
         # source
         sx, sz = acq.src_xz[s]
         self.wav = np.asarray(acq.wavelet[s], np.float64)
+        if force is None and getattr(acq, "force", None) is not None:
+            force = np.asarray(acq.force[s], np.float64)
         self.force = force
         self.inj_node = self._weights(sx, sz, 0.0, 0.0)
         self.inj_xz = self._weights(sx, sz, 0.5, 0.5)
@@ -409,6 +412,12 @@ class Shot:
             gw[n] += self.force[1] * wn * sum(wt * dt * self.bz[j, i] * vz_h[j, i] for j, i, wt in self.inj_vz)
         G["bx"] += vx_h * dt * acc_x
         G["bz"] += vz_h * dt * acc_z
+        if self.force is not None:          # the force term dt b F w_n delta_h depends on b too
+            wn = self.wav[n] / (dx * dz)
+            for j, i, wt in self.inj_vx:
+                G["bx"][j, i] += vx_h[j, i] * dt * self.force[0] * wn * wt
+            for j, i, wt in self.inj_vz:
+                G["bz"][j, i] += vz_h[j, i] * dt * self.force[1] * wn * wt
         qx = dt * self.bx * vx_h
         qz = dt * self.bz * vz_h
         eh = []

@@ -83,6 +83,10 @@ class Plan:
             rvp=_np(a.ref_vp, np.float32), rvs=_np(a.ref_vs, np.float32), rrho=_np(a.ref_rho, np.float32))
         win = getattr(a, "win", None)
         keep["win"] = None if win is None else _np(win, np.int32)
+        force = getattr(a, "force", None)
+        keep["force"] = None if force is None else _np(np.asarray(force).reshape(-1, 2), np.float64)
+        if keep["force"] is not None and keep["force"].shape != (self.ns, 2):
+            raise ValueError("force must be [ns, 2]")
         if keep["wav"].shape != (self.ns, self.nt + 1):
             raise ValueError("wavelet must be [ns, nt+1]")
         P = lambda arr, typ: arr.ctypes.data_as(C.POINTER(typ)) if arr is not None and arr.size else None
@@ -109,6 +113,7 @@ class Plan:
         d.adj_tile_x, d.adj_tile_z = int(adj_tile[0]), int(adj_tile[1])
         d.adj_stencil = STENCIL[adj_stencil]
         d.overlap = OVERLAP[overlap]
+        d.force = P(keep["force"], C.c_double)
         self.exec, self.ckpt_store = exec, ckpt_store
         h = C.c_void_p()
         torch.cuda.init()

@@ -29,7 +29,7 @@ class PlanDesc(C.Structure):
                 ("ref_vp", PF), ("ref_vs", PF), ("ref_rho", PF), ("ckpt_interval", C.c_int),
                 ("ckpt_store", C.c_int), ("exec", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
                 ("stencil", C.c_int), ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("adj_stencil", C.c_int),
-                ("overlap", C.c_int)]
+                ("overlap", C.c_int), ("force", PD)]
 
 
 class PlanInfo(C.Structure):

@@ -49,7 +49,12 @@ struct ShotDev {
     float inj_nw[4];    // bilinear weight / (dx dz)
     int inj_x[4];       // sxz-grid injection cells
     float inj_xw[4];
-    float mxx, mzz, mxz;
+    float mxx, mzz, mxz;  // zero for a force source
+    int inj_vx[4];      // vx-grid cells of a vector-force source (bilinear)
+    float inj_vxw[4];   // bilinear weight (the 1/(dx dz) sits in the wavelet copy wv)
+    int inj_vz[4];      // vz-grid cells
+    float inj_vzw[4];
+    float fx, fz;       // force components; zero for a moment-tensor source
 };
 
 // The five wavefield (or adjoint-wavefield) arrays.

@@ -58,6 +58,7 @@ void forward_step(efwi_plan *p, int n, float *d, float *sx, float *sz, cudaStrea
         Fields F = state_fields(p, 0);
         for (int s = 0; s < p->d.ns; ++s) {
             launch_vel_plain(p, s, sx, sz, st);
+            launch_force(p, F, n, s, sx, sz, st);
             if (d) launch_das_fwd(p, F, n, d, s, st);
             launch_stress_plain(p, s, st);
             launch_inject(p, F, n, s, st);

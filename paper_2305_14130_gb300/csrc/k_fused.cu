@@ -41,6 +41,7 @@ struct FwdArgs {
     float *n1, *n3, *n2, *n4;   // next V block: psi1, psi3 (x-strips), psi2, psi4 (z-strips)
     float *segx, *segz;         // optional copy of v^{n+1/2}
     const float *dw;
+    const float *wv;            // w_n / (dx dz) of force sources (null without)
     int nt, n;
     float dt, rdx, rdz;
 };
@@ -115,6 +116,15 @@ __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
                 }
                 vx = __ldg(a.in.vx + c) + dt * __ldg(a.M.bx + c) * (e1 + e2);
                 vz = __ldg(a.in.vz + c) + dt * __ldg(a.M.bz + c) * (e3 + e4);
+                if (tl.w & 8) {                      // vector force of this shot (k_force's expression)
+                    const int lc = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    const float wvn = a.wv[(long long)tl.x * a.nt + a.n];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (lc == sp->inj_vx[k]) vx = vx + dt * __ldg(a.M.bx + c) * (sp->fx * wvn * sp->inj_vxw[k]);
+                        if (lc == sp->inj_vz[k]) vz = vz + dt * __ldg(a.M.bz + c) * (sp->fz * wvn * sp->inj_vzw[k]);
+                    }
+                }
                 if (own && (!edge || (i < NX && j < NZ))) {
                     a.out.vx[c] = vx;
                     a.out.vz[c] = vz;
@@ -488,6 +498,13 @@ std::vector<int4> make_tiles(efwi_plan *p, int tx, int tz) {
                     const int xa = i0 - h, xb = i0 + tx + h, za = j0 - h, zb = j0 + tz + h;
                     if (xa < sh.P || xb > sh.NX - sh.P || za < sh.P || zb > sh.NZ - sh.P) flags |= h;
                 }
+                // bit 3: a vector-force cell lies in the tile or its 2-cell velocity halo
+                if (sh.fx != 0.f || sh.fz != 0.f)
+                    for (int q = 0; q < 4; ++q)
+                        for (int o : {sh.inj_vx[q], sh.inj_vz[q]}) {
+                            const int j = o / sh.pitch - EFWI_GZ, i = o % sh.pitch - EFWI_GX;
+                            if (i >= i0 - 2 && i < i0 + tx + 2 && j >= j0 - 2 && j < j0 + tz + 2) flags |= 8;
+                        }
                 t.push_back(make_int4(s, i0, j0, flags));
             }
     }
@@ -523,6 +540,7 @@ FwdArgs fwd_args(efwi_plan *p, int n, float *segx, float *segz) {
     a.n1 = vn; a.n3 = vn + p->psx_total; a.n2 = vn + 2 * p->psx_total; a.n4 = vn + 2 * p->psx_total + p->psz_total;
     a.segx = segx; a.segz = segz;
     a.dw = p->dw;
+    a.wv = p->wv;
     a.nt = p->d.nt;
     a.n = n;
     a.dt = (float)p->d.dt;

@@ -78,6 +78,28 @@ __global__ void k_inject(const ShotDev *shots, Fields F, const float *dw, int nt
     }
 }
 
+// Vector-force source (eq. 2, second case), after the velocity sub-step of
+// step n: v^{n+1/2} += dt b F w_n delta_h on the vx and vz grids.  The fused
+// steps add the same term, with the same expression, inside their velocity phase.
+__global__ void k_force(const ShotDev *shots, Fields F, Mat M, const float *wv, int nt, int n, int s0, int ns,
+                        float dt, float *segx, float *segz) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ns) return;
+    const int s = s0 + t;
+    const ShotDev sh = shots[s];
+    const float w = wv[(long long)s * nt + n];
+    for (int q = 0; q < 4; ++q) {
+        const long long cx = sh.off + sh.inj_vx[q], cz = sh.off + sh.inj_vz[q];
+        F.vx[cx] = F.vx[cx] + dt * M.bx[cx] * (sh.fx * w * sh.inj_vxw[q]);
+        F.vz[cz] = F.vz[cz] + dt * M.bz[cz] * (sh.fz * w * sh.inj_vzw[q]);
+    }
+    if (segx)                                   // the segment copy of v^{n+1/2} (after all four corners)
+        for (int q = 0; q < 4; ++q) {
+            segx[sh.off + sh.inj_vx[q]] = F.vx[sh.off + sh.inj_vx[q]];
+            segz[sh.off + sh.inj_vz[q]] = F.vz[sh.off + sh.inj_vz[q]];
+        }
+}
+
 // --------------------------------------------------------------------------
 // DAS sampling K_r (eq. 3): strain rate of trace t = sum of 16 weighted
 // velocity samples (weights carry +-t_k / L); strain = running time integral.
@@ -414,6 +436,14 @@ void launch_materials(efwi_plan *p, const float *vp, const float *vs, const floa
 void launch_inject(efwi_plan *p, Fields F, int n, int shot, cudaStream_t st) {
     const int s0 = shot < 0 ? 0 : shot, cnt = shot < 0 ? p->d.ns : 1;
     k_inject<<<(cnt + 127) / 128, 128, 0, st>>>(p->shots_d, F, p->dw, p->d.nt, n, s0, cnt);
+    p->launches++;
+}
+
+void launch_force(efwi_plan *p, Fields F, int n, int shot, float *segx, float *segz, cudaStream_t st) {
+    if (!p->has_force) return;
+    const int s0 = shot < 0 ? 0 : shot, cnt = shot < 0 ? p->d.ns : 1;
+    k_force<<<(cnt + 127) / 128, 128, 0, st>>>(p->shots_d, F, materials(p), p->wv, p->d.nt, n, s0, cnt,
+                                               (float)p->d.dt, segx, segz);
     p->launches++;
 }
 

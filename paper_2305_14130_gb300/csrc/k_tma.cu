@@ -39,6 +39,7 @@ struct TmaFwdArgs {
     float *n1, *n3, *n2, *n4;   // next V block
     float *segx, *segz;
     const float *dw;
+    const float *wv;            // w_n / (dx dz) of force sources (null without)
     int nt, n;
     float dt, rdx, rdz;
     int *err;
@@ -179,6 +180,17 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                     vx.y = in[1] ? vxo.y + dt * bxo.y * (e1[1] + e2[1]) : 0.f;
                     vz.x = in[0] ? vzo.x + dt * bzo.x * (e3[0] + e4[0]) : 0.f;
                     vz.y = in[1] ? vzo.y + dt * bzo.y * (e3[1] + e4[1]) : 0.f;
+                    if (tl.w & 8) {                  // vector force of this shot (k_force's expression)
+                        const int lc = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                        const float wvn = a.wv[(long long)tl.x * a.nt + a.n];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (lc == sp->inj_vx[k]) vx.x = vx.x + dt * bxo.x * (sp->fx * wvn * sp->inj_vxw[k]);
+                            if (lc + 1 == sp->inj_vx[k]) vx.y = vx.y + dt * bxo.y * (sp->fx * wvn * sp->inj_vxw[k]);
+                            if (lc == sp->inj_vz[k]) vz.x = vz.x + dt * bzo.x * (sp->fz * wvn * sp->inj_vzw[k]);
+                            if (lc + 1 == sp->inj_vz[k]) vz.y = vz.y + dt * bzo.y * (sp->fz * wvn * sp->inj_vzw[k]);
+                        }
+                    }
                     st2(svx + o, vx);
                     st2(svz + o, vz);
                     if (own) {
@@ -314,6 +326,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                         }
                         vx = svx[o] + dt * sbx[o] * (e1 + e2);
                         vz = svz[o] + dt * sbz[o] * (e3 + e4);
+                        if (tl.w & 8) {              // vector force of this shot (k_force's expression)
+                            const int lc = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                            const float wvn = a.wv[(long long)tl.x * a.nt + a.n];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                if (lc == sp->inj_vx[k]) vx = vx + dt * sbx[o] * (sp->fx * wvn * sp->inj_vxw[k]);
+                                if (lc == sp->inj_vz[k]) vz = vz + dt * sbz[o] * (sp->fz * wvn * sp->inj_vzw[k]);
+                            }
+                        }
                         if (own && (!edge || (i < NX && j < NZ))) {
                             const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                             ovx[c] = vx;
@@ -488,6 +509,7 @@ void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t
     a.n1 = vn; a.n3 = vn + p->psx_total; a.n2 = vn + 2 * p->psx_total; a.n4 = vn + 2 * p->psx_total + p->psz_total;
     a.segx = segx; a.segz = segz;
     a.dw = p->dw;
+    a.wv = p->wv;
     a.nt = p->d.nt;
     a.n = n;
     a.dt = (float)p->d.dt;

@@ -158,7 +158,7 @@ void prof_end(efwi_plan *p, cudaStream_t st, int slot) {
 static void free_plan(efwi_plan *p) {
     if (!p) return;
     void *ptrs[] = {p->shots_d, p->state[0], p->mat, p->adj[0], p->fwd_maps, p->adj_maps, p->dev_err, p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
-                    p->prof, p->dw, p->ref, p->tr_shot, p->tr_off, p->tr_w, p->tr_acc, p->tr_coef,
+                    p->prof, p->dw, p->wv, p->ref, p->tr_shot, p->tr_off, p->tr_w, p->tr_acc, p->tr_coef,
                     p->gather.tgt_shot, p->gather.tgt_field, p->gather.tgt_off, p->gather.ptr, p->gather.tr,
                     p->gather.w, p->tiles.tiles, p->adj_tiles.tiles, p->resid, p->dbuf, p->partial, p->seg, p->ck.fields, p->ck.psi,
                     p->ck.scale};
@@ -210,6 +210,9 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
         return fail(nullptr, EFWI_ERR_ARG, "adj_tile_x and adj_tile_z must both be 0 or both positive");
     if (d->overlap < EFWI_OVERLAP_AUTO || d->overlap > EFWI_OVERLAP_ON)
         return fail(nullptr, EFWI_ERR_ARG, "unknown overlap");
+    if (d->force)
+        for (int k = 0; k < 2 * d->ns; ++k)
+            if (!std::isfinite(d->force[k])) return fail(nullptr, EFWI_ERR_ARG, "force components must be finite");
 
     const long long ncell = (long long)d->nx * d->nz;
     double vmax = d->pml_vmax;
@@ -233,6 +236,7 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     p->d.src_xz = nullptr; p->d.mt = nullptr; p->d.wavelet = nullptr; p->d.tr_ptr = nullptr;
     p->d.ch_xz = nullptr; p->d.ch_t = nullptr; p->d.win = nullptr;
     p->d.ref_vp = p->d.ref_vs = p->d.ref_rho = nullptr;
+    p->d.force = nullptr;
     p->d.pml_vmax = vmax;
     const int P = d->npml + 1;
     p->P = P;
@@ -287,7 +291,23 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
             sh.inj_n[q] = local_off(sh, cn[q].i, cn[q].j); sh.inj_nw[q] = (float)(cn[q].w / cellA);
             sh.inj_x[q] = local_off(sh, cx[q].i, cx[q].j); sh.inj_xw[q] = (float)(cx[q].w / cellA);
         }
+        // vector force (eq. 2, second case) on the staggered v grids; it replaces the
+        // moment tensor (whose injection then adds zeros)
+        Corner fxc[4], fzc[4];
+        bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.5, 0.0, fxc);
+        bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.0, 0.5, fzc);
+        for (int q = 0; q < 4; ++q) {
+            sh.inj_vx[q] = local_off(sh, fxc[q].i, fxc[q].j); sh.inj_vxw[q] = (float)fxc[q].w;
+            sh.inj_vz[q] = local_off(sh, fzc[q].i, fzc[q].j); sh.inj_vzw[q] = (float)fzc[q].w;
+        }
+        sh.fx = sh.fz = 0.f;
+        if (d->force) {
+            sh.fx = (float)d->force[2 * s];
+            sh.fz = (float)d->force[2 * s + 1];
+            sh.mxx = sh.mzz = sh.mxz = 0.f;
+        }
     }
+    p->has_force = d->force != nullptr;
 
     // --- DAS gauges: 4 components x 4 corners per trace ------------------------
     const int ntr = d->ntr;
@@ -349,6 +369,11 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
         for (int n = 0; n < nt; ++n)
             h_dw[(size_t)s * nt + n] =
                 (float)((double)d->wavelet[(size_t)s * (nt + 1) + n + 1] - (double)d->wavelet[(size_t)s * (nt + 1) + n]);
+    std::vector<float> h_wv(p->has_force ? (size_t)ns * nt : 0);
+    for (size_t k = 0; k < h_wv.size(); ++k) {
+        const size_t s = k / nt, n = k % nt;
+        h_wv[k] = (float)((double)d->wavelet[s * (nt + 1) + n] / cellA);
+    }
     const int X = p->prof_x_total;
     std::vector<float> h_prof(4 * (size_t)X + 4 * (size_t)NZ);
     for (int s = 0; s < ns; ++s) {
@@ -388,6 +413,7 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     A(&p->apsi, (size_t)(4 * p->H), "adjoint psi");
     A(&p->prof, h_prof.size(), "profiles");
     A(&p->dw, h_dw.size(), "wavelet increments");
+    if (p->has_force) A(&p->wv, h_wv.size(), "wavelet");
     A(&p->ref, (size_t)(3 * ncell), "reference model");
     A(&p->tr_shot, (size_t)std::max(ntr, 1), "trace shots");
     A(&p->tr_off, h_off.size(), "trace offsets");
@@ -432,6 +458,7 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     up(p->shots_d, p->shots.data(), sizeof(ShotDev) * ns);
     up(p->prof, h_prof.data(), h_prof.size() * 4);
     up(p->dw, h_dw.data(), h_dw.size() * 4);
+    if (p->has_force) up(p->wv, h_wv.data(), h_wv.size() * 4);
     up(p->ref, d->ref_vp, ncell * 4);
     up(p->ref + ncell, d->ref_vs, ncell * 4);
     up(p->ref + 2 * ncell, d->ref_rho, ncell * 4);

@@ -81,6 +81,8 @@ struct efwi_plan {
     int apsi_v = 0, apsi_s = 0;
     float *prof = nullptr;                 // 4 * prof_x_total + 4 * nzp
     float *dw = nullptr;                   // [ns][nt] (w_{n+1} - w_n)
+    float *wv = nullptr;                   // [ns][nt] w_n / (dx dz), force sources only
+    bool has_force = false;
     float *ref = nullptr;                  // [3][nz][nx] reference model
     int *tr_shot = nullptr;                // [ntr]
     int *tr_off = nullptr;                 // [ntr][16] offsets within shot block
@@ -141,6 +143,7 @@ constexpr int kPartials = 1024;            // blocks of the FP64 reductions
 // --- k_misc.cu ---------------------------------------------------------------
 void launch_materials(efwi_plan *p, const float *vp, const float *vs, const float *rho, cudaStream_t st);
 void launch_inject(efwi_plan *p, Fields F, int n, int shot /* -1 = all */, cudaStream_t st);
+void launch_force(efwi_plan *p, Fields F, int n, int shot, float *segx, float *segz, cudaStream_t st);
 void launch_das_fwd(efwi_plan *p, Fields F, int n, float *d, int shot, cudaStream_t st);
 void launch_das_adj(efwi_plan *p, Fields A, const float *vf_x, const float *vf_z, float *Gbx, float *Gbz,
                     int n, int shot, cudaStream_t st);

@@ -40,6 +40,8 @@ CASES = {
     "tiny_windows": lambda: W.tiny(nx=48, nz=26, ns=3, nt=60, npml=4, win=[[0, 30], [9, 37], [20, 28]]),
     "tiny_2c_velocity": lambda: W.two_component(W.tiny(nx=43, nz=31, ns=3, nt=70, npml=5,
                                                        win=[[0, 35], [6, 37], [12, 31]])),
+    "tiny_force": lambda: W.with_forces(W.tiny(nx=41, nz=30, ns=3, nt=70, npml=5,
+                                               win=[[0, 34], [5, 36], [11, 30]])),
 }
 
 
@@ -308,12 +310,16 @@ TMA_SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16)]
 VARIANTS = [("loads", s) for s in SHAPES] + [(k, s) for k in ("tma", "tma_pairs") for s in TMA_SHAPES]
 
 
-def test_stencil_variants_do_not_change_results(efwi):
+@pytest.mark.parametrize("source", ["moment_tensor", "force"])
+def test_stencil_variants_do_not_change_results(efwi, source):
     """The autotuner's choice changes only the work decomposition and the
     shared-memory staging: every compiled variant (per-thread loads or TMA,
     every tile shape) gives bitwise-identical data and gradients (uneven
-    windows, ragged tiles)."""
+    windows, ragged tiles; moment-tensor or vector-force sources, whose
+    injection cells then lie in several tiles' velocity halos)."""
     p = rounded(W.tiny(nx=70, nz=41, ns=3, nt=40, npml=5, win=[[0, 45], [13, 57], [30, 40]]))
+    if source == "force":
+        p = W.with_forces(p)
     d_obs = observed(p)
     args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
     ref = None
@@ -355,8 +361,11 @@ def test_tma_full_size_matches_loads(efwi):
             assert torch.equal(a, b)
 
 
-def test_batched_matches_plain(efwi):
+@pytest.mark.parametrize("source", ["moment_tensor", "force"])
+def test_batched_matches_plain(efwi, source):
     p = rounded(W.tiny(nx=50, nz=33, ns=3, nt=60, npml=5, win=[[0, 40], [7, 43], [10, 35]]))
+    if source == "force":
+        p = W.with_forces(p)
     d_obs = observed(p)
     args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
     a = [t.cpu().numpy() for t in efwi.Plan(p.acq, exec="plain").gradient(*args, return_data=True)]

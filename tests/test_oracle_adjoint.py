@@ -46,9 +46,12 @@ def test_dot_product_state_map(mode, win):
         assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-@pytest.mark.parametrize("mode", [W.STRAIN, W.STRAIN_RATE, W.VELOCITY])
-def test_dot_product_wavelet_map(mode):
+@pytest.mark.parametrize("mode,force", [(W.STRAIN, False), (W.STRAIN_RATE, False), (W.VELOCITY, False),
+                                        (W.STRAIN, True)])
+def test_dot_product_wavelet_map(mode, force):
     p = W.tiny(das_mode=mode)
+    if force:
+        p = W.with_forces(p)
     rng = np.random.default_rng(2)
     sh = E.Shot(p.acq, 1, p.vp[1], p.vs[1], p.rho[1])
     w = rng.standard_normal(sh.wav.shape)
@@ -78,6 +81,15 @@ def _fd_check(p, d_obs, rel_h=1e-6, tol=1e-6, seed=5):
 @pytest.mark.parametrize("mode", [W.STRAIN, W.STRAIN_RATE, W.VELOCITY])
 def test_gradient_finite_difference_tiny(mode):
     p = W.tiny(das_mode=mode, win=[[0, 24], [2, 20]])
+    ns = p.acq.ns
+    d_obs = E.forward(p.acq, *(np.repeat(m[None], ns, 0) for m in (p.true_vp, p.true_vs, p.true_rho)))
+    _fd_check(p, d_obs)
+
+
+def test_gradient_finite_difference_force_sources():
+    """Vector-force sources: the injected term dt b F w delta_h depends on the
+    buoyancy, so the b part of the gradient carries an extra term."""
+    p = W.with_forces(W.tiny(win=[[0, 24], [2, 20]]))
     ns = p.acq.ns
     d_obs = E.forward(p.acq, *(np.repeat(m[None], ns, 0) for m in (p.true_vp, p.true_vs, p.true_rho)))
     _fd_check(p, d_obs)

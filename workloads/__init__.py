@@ -54,6 +54,7 @@ class Acquisition:
     pml_R: float = 1e-3
     pml_vmax: float = 0.0         # 0 -> max of reference Vp
     pml_f0: float = 0.0           # dominant frequency used for the CPML alpha profile
+    force: Optional[np.ndarray] = None  # [Ns, 2] vector force (Fx, Fz); replaces the moment tensor
 
     @property
     def ns(self) -> int:
@@ -378,6 +379,16 @@ def tiny(nx=24, nz=20, ns=2, nt=40, dx=5.0, dt=5e-4, npml=4, das_mode=STRAIN, wi
     ext_rho = extend(rho, ns) * (1 + 0.02 * rng2.standard_normal((ns, nz, nx)))
     return Problem("tiny", acq, ext_vp, ext_vs, ext_rho, true_vp=vp, true_vs=vs, true_rho=rho,
                    zoi=default_zoi(acq, taper_m=3 * dx, sink_ax=3 * dx, sink_az=2 * dx))
+
+
+def with_forces(p: Problem, angle_deg: float = 30.0, amplitude: float = 1e6) -> Problem:
+    """The same problem driven by vector-force sources (eq. 2, second case) at the
+    source positions instead of moment tensors: F_s of the given amplitude, its
+    direction rotated by angle_deg * s from vertical."""
+    a = p.acq
+    ang = np.deg2rad(angle_deg) * np.arange(a.ns)
+    f = amplitude * np.stack([np.sin(ang), np.cos(ang)], axis=1)
+    return replace(p, acq=replace(a, force=f))
 
 
 def two_component(p: Problem) -> Problem:
