@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--stencil", default="auto", choices=["auto", "loads", "tma", "tma_pairs"])
+    ap.add_argument("--stencil", default="auto", choices=["auto", "loads", "tma", "tma_pairs", "tma_staged"])
     ap.add_argument("--tile", default="0x0", help="forward tile, e.g. 32x16 (0x0 = autotune)")
     ap.add_argument("--adj-stencil", default="auto", choices=["auto", "loads", "tma"])
     ap.add_argument("--adj-tile", default="0x0", help="adjoint tile (0x0 = autotune)")
@@ -366,7 +366,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "exec": args.exec, "ckpt_store": args.ckpt_store,
                            "ckpt_interval": info["ckpt_interval"], "tile": [info["tile_x"], info["tile_z"]],
                            "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
-                           "stencil": {1: "loads", 2: "tma", 3: "tma_pairs"}.get(info["stencil"], "?"), "stages": info["stages"],
+                           "stencil": {1: "loads", 2: "tma", 3: "tma_pairs", 4: "tma_staged"}.get(info["stencil"], "?"), "stages": info["stages"],
                            "adj_stencil": {1: "loads", 2: "tma"}.get(info["adj_stencil"], "?"),
                            "adj_stages": info["adj_stages"],
                            "overlap_blocks_per_sm": [info["overlap_fwd_blocks"], info["overlap_adj_blocks"]],

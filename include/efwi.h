@@ -84,7 +84,9 @@ enum efwi_exec { EFWI_EXEC_PLAIN = 0, EFWI_EXEC_BATCHED = 1 };
  * TMA bulk tensor copies into pipelined shared memory (persistent CTAs)     */
 enum efwi_overlap { EFWI_OVERLAP_AUTO = 0, EFWI_OVERLAP_OFF = 1, EFWI_OVERLAP_ON = 2 };
 enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_TMA = 2,
-                    EFWI_STENCIL_TMA_PAIRS = 3 /* TMA, two adjacent cells per thread (forward step) */ };
+                    EFWI_STENCIL_TMA_PAIRS = 3 /* TMA, two adjacent cells per thread (forward step) */,
+                    EFWI_STENCIL_TMA_STAGED = 4 /* TMA_PAIRS with the tile's outputs staged in shared
+                                                   memory and written by bulk tensor stores (forward) */ };
 
 /*
  * Problem description (host memory; copied by efwi_plan_create).

@@ -12,7 +12,7 @@ STATUS = {0: "EFWI_OK", -1: "EFWI_ERR_ARG", -2: "EFWI_ERR_CFL", -3: "EFWI_ERR_OO
 DAS_STRAIN, DAS_STRAIN_RATE, DAS_VELOCITY = 0, 1, 2
 STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXEC = {"plain": 0, "batched": 1}
-STENCIL = {"auto": 0, "loads": 1, "tma": 2, "tma_pairs": 3}
+STENCIL = {"auto": 0, "loads": 1, "tma": 2, "tma_pairs": 3, "tma_staged": 4}
 OVERLAP = {"auto": 0, "off": 1, "on": 2}
 
 PD = C.POINTER(C.c_double)

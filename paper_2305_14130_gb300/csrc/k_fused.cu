@@ -618,7 +618,7 @@ using namespace efwi;
 namespace {
 
 struct Variant {
-    int kind, tx, tz, nst, vec = 1;
+    int kind, tx, tz, nst, vec = 1, st = 0;
 };
 
 float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
@@ -650,7 +650,7 @@ int select_adj(efwi_plan *p, const Variant &v) {
 int select_fwd(efwi_plan *p, const Variant &v) {
     p->stencil = v.kind;
     int rc = upload_tiles(p, p->tiles, v.tx, v.tz);
-    if (!rc && v.kind >= EFWI_STENCIL_TMA) rc = tma_prepare_fwd(p, v.tx, v.tz, v.nst, v.vec);
+    if (!rc && v.kind >= EFWI_STENCIL_TMA) rc = tma_prepare_fwd(p, v.tx, v.tz, v.nst, v.vec, v.st);
     p->tile_x = v.tx;
     p->tile_z = v.tz;
     return rc;
@@ -668,12 +668,13 @@ int efwi_autotune(efwi_plan *p) {
     for (auto &s : kShapes) {
         if (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)) continue;
         if (want == EFWI_STENCIL_AUTO || want == EFWI_STENCIL_LOADS) fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-        for (int vec = 1; vec <= 2; ++vec) {
-            const int kind = vec == 1 ? EFWI_STENCIL_TMA : EFWI_STENCIL_TMA_PAIRS;
-            if (want != EFWI_STENCIL_AUTO && want != kind) continue;
-            for (int nst = 2; nst <= 4; ++nst)
-                if (tma_shape_ok(s.tx, s.tz, nst, vec)) fwd.push_back({kind, s.tx, s.tz, nst, vec});
-        }
+        for (int vec = 1; vec <= 2; ++vec)
+            for (int stg = 0; stg <= 1; ++stg) {
+                const int kind = vec == 1 ? EFWI_STENCIL_TMA : stg ? EFWI_STENCIL_TMA_STAGED : EFWI_STENCIL_TMA_PAIRS;
+                if (want != EFWI_STENCIL_AUTO && want != kind) continue;
+                for (int nst = 2; nst <= 4; ++nst)
+                    if (tma_shape_ok(s.tx, s.tz, nst, vec, stg)) fwd.push_back({kind, s.tx, s.tz, nst, vec, stg});
+            }
     }
     // the adjoint follows its own request, or the forward one when it has none
     const int wa = want_a != EFWI_STENCIL_AUTO ? want_a : want;
@@ -713,8 +714,8 @@ int efwi_autotune(efwi_plan *p) {
         for (auto &v : fwd) {
             if (select_fwd(p, v)) continue;
             const float t = time_steps(p, false, st, e0, e1);
-            if (log) fprintf(stderr, "efwi autotune fwd kind %d tile %dx%d param %d vec %d: %.1f us\n", v.kind, v.tx,
-                             v.tz, v.nst, v.vec, t * 1e3f / 3);
+            if (log) fprintf(stderr, "efwi autotune fwd kind %d tile %dx%d param %d vec %d staged %d: %.1f us\n",
+                             v.kind, v.tx, v.tz, v.nst, v.vec, v.st, t * 1e3f / 3);
             if (t < best) { best = t; bf = v; }
         }
         best = 1e30f;
@@ -804,6 +805,7 @@ int efwi_autotune(efwi_plan *p) {
                 p->bytes += segbytes;
                 p->seg_double = true;
                 rc = select_adj(p, ba);
+                if (!rc) rc = select_fwd(p, bf);   // the forward segment map covers both halves
             }
         }
     }

@@ -43,6 +43,8 @@ struct TmaFwdArgs {
     int nt, n;
     float dt, rdx, rdz;
     int *err;
+    int ofield;                 // state-map field of the written buffer's vx (output staging)
+    int segf;                   // segment-map field of this step's vx, or -1 (output staging)
 };
 
 template <int TX, int TZ, int NST, int VEC = 1>
@@ -67,8 +69,27 @@ __device__ __forceinline__ void issue_fwd(const TmaFwdArgs &a, int t, float *buf
     tma_load_3d(buf + 7 * L::NS, &m->mc, bar, tl.y + 4, tl.z + 2, 0);
 }
 
-template <int TX, int TZ, int NST, int VEC>
+// Shared-memory output staging (ST = 1, cell pairs only): the new stresses of the
+// tile overwrite lambda, mu, mu_xz of the stage (each cell reads its own three
+// materials before writing), the new velocities go densely over b_x/b_z (read
+// only by the velocity sub-step), and after the tile one thread stores them with
+// bulk tensor copies.  The stores of tile k are issued once every thread has
+// passed the first barrier of tile k + 1; their shared-memory reads finish before
+// that stage is refilled.
+template <int TX, int TZ, int NST>
+__device__ __forceinline__ void store_fwd(const TmaFwdArgs &a, int4 tl, const float *buf) {
+    using L = FwdLayout<TX, TZ, NST, 2>;
+    const FwdMaps *m = a.maps + tl.x;
+    const int x = tl.y + EFWI_GX, y = tl.z + EFWI_GZ;
+    tma_store_3d(&m->o2, buf + 5 * L::NS, x, y, a.ofield);
+    tma_store_3d(&m->o3, buf + 7 * L::NS, x, y, a.ofield + 2);
+    if (a.segf >= 0) tma_store_3d(&m->sg, buf + 5 * L::NS, x, y, a.segf);
+    bulk_commit();
+}
+
+template <int TX, int TZ, int NST, int VEC, int ST = 0>
 __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
+    static_assert(ST == 0 || VEC == 2, "output staging is implemented for cell pairs");
     using L = FwdLayout<TX, TZ, NST, VEC>;
     constexpr int SX = L::SX;
     extern __shared__ float4 smem_raw[];
@@ -89,13 +110,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         }
     uint32_t phase = 0;
     int t = blockIdx.x;
-    for (int k = 0; t < a.ntiles; t += gridDim.x, ++k) {
+    // the work item of the next tile is loaded one tile ahead, and its shot scalars
+    // before the tile's barrier, so neither load's latency follows the barrier
+    int4 tl_next = t < a.ntiles ? __ldg(a.tiles + t) : make_int4(0, 0, 0, 0);
+    int4 tl_prev = tl_next;
+    int k = 0;
+    for (; t < a.ntiles; t += gridDim.x, ++k) {
         const int b = k % NST;
         float *buf = smb + b * L::BUF;
+        const int4 tl = tl_next;
+        const ShotDev *sp = a.shots + tl.x;
+        const int NX = __ldg(&sp->NX), NZ = __ldg(&sp->NZ), P = __ldg(&sp->P), profx = __ldg(&sp->profx),
+                  pitch = __ldg(&sp->pitch);
+        const long long off = __ldg(&sp->off), psx = __ldg(&sp->psx), psz = __ldg(&sp->psz);
+        if (t + gridDim.x < a.ntiles) tl_next = __ldg(a.tiles + t + gridDim.x);
         if (tid == 0) ok_s = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
         __syncthreads();
         if (!ok_s) {
-            if (tid == 0) atomicExch(a.err, 1);
+            if (tid == 0) {
+                atomicExch(a.err, 1);
+                if (ST) bulk_wait0();       // stores already issued finish before the CTA exits
+            }
             return;
         }
         mbar_wait_bounded(&bar[b], (phase >> b) & 1u);   // completed: acquire for every thread
@@ -104,21 +139,26 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         // thread has passed the barrier above, so none still reads that stage
         const int tn = t + (NST - 1) * gridDim.x;
         const int bn = (k + NST - 1) % NST;
-        if (tid == 0 && tn < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, tn, smb + bn * L::BUF, &bar[bn]);
+        if (tid == 0) {
+            if (ST && k > 0) {
+                store_fwd<TX, TZ, NST>(a, tl_prev, smb + bn * L::BUF);   // stage bn held tile k - 1
+                bulk_wait_read0();
+            }
+            if (tn < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, tn, smb + bn * L::BUF, &bar[bn]);
+        }
+        tl_prev = tl;
 
-        const int4 tl = a.tiles[t];
         // interior tiles (no CPML strip or grid edge within the halo) run a copy of
         // the body without any of the edge tests
         auto tile = [&](auto edge_c) {
-            const ShotDev *sp = a.shots + tl.x;
-            // shot scalars in registers (loaded once per tile, not after every store)
-            const int NX = sp->NX, NZ = sp->NZ, P = sp->P, profx = sp->profx, pitch = sp->pitch;
-            const long long off = sp->off, psx = sp->psx, psz = sp->psz;
             constexpr bool edge = decltype(edge_c)::value;
             const int i0 = tl.y, j0 = tl.z;
             float *svx = buf, *svz = buf + L::NS, *sxx = buf + 2 * L::NS, *szz = buf + 3 * L::NS, *sxz = buf + 4 * L::NS;
             const float *sbx = buf + 5 * L::NS, *sbz = buf + 6 * L::NS;
             const float *slam = buf + 7 * L::NS, *smu = slam + L::NC, *smxz = smu + L::NC;
+            // output staging: dense [2][TZ][TX] velocities over b_x/b_z, [3][TZ][TX] stresses over
+            // lambda, mu, mu_xz
+            float *dv = buf + 5 * L::NS, *ds = buf + 7 * L::NS;
             float *__restrict__ ovx = a.out.vx + off;
             float *__restrict__ ovz = a.out.vz + off;
             const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
@@ -193,7 +233,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                     }
                     st2(svx + o, vx);
                     st2(svz + o, vz);
-                    if (own) {
+                    if (!ST && own) {
                         const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                         if (!edge || (i + 1 < NX && j < NZ)) {
                             st2g(ovx + c, vx);
@@ -218,7 +258,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                     const int xx = 2 * (q - yy * NPT);
                     const int x = 4 + xx, y = 4 + yy;
                     const int i = i0 + xx, j = j0 + yy;
-                    if (edge && (i >= NX || j >= NZ)) continue;
+                    if (edge && (i >= NX || j >= NZ)) {
+                        if (ST) {                   // cells past the grid: the ghosts stay zero
+                            const int oc = yy * TX + xx;
+                            const float2 z2 = make_float2(0.f, 0.f);
+                            st2(dv + oc, z2); st2(dv + L::NC + oc, z2);
+                            st2(ds + oc, z2); st2(ds + L::NC + oc, z2); st2(ds + 2 * L::NC + oc, z2);
+                        }
+                        continue;
+                    }
                     const int o = y * SX + x;
                     const float2 va = ld2(svx + o - 2), vb = ld2(svx + o), vc = ld2(svx + o + 2);
                     const float2 wa = ld2(svz + o - 2), wb = ld2(svz + o), wc = ld2(svz + o + 2);
@@ -283,7 +331,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                                 if (c + h == sp->inj_x[kk]) nxz[h] -= sp->mxz * dwn * sp->inj_xw[kk];
                             }
                     }
-                    if (!edge || i + 1 < NX) {
+                    if (ST) {
+                        // lambda, mu, mu_xz of these cells were read above by this thread only
+                        const bool two = !edge || i + 1 < NX;
+                        st2(ds + oc, make_float2(nxx[0], two ? nxx[1] : 0.f));
+                        st2(ds + L::NC + oc, make_float2(nzz[0], two ? nzz[1] : 0.f));
+                        st2(ds + 2 * L::NC + oc, make_float2(nxz[0], two ? nxz[1] : 0.f));
+                        st2(dv + oc, vb);          // v^{n+1/2} of the pair (zero past the grid)
+                        st2(dv + L::NC + oc, wb);
+                    } else if (!edge || i + 1 < NX) {
                         st2g(oxx + c, make_float2(nxx[0], nxx[1]));
                         st2g(ozz + c, make_float2(nzz[0], nzz[1]));
                         st2g(oxz + c, make_float2(nxz[0], nxz[1]));
@@ -291,6 +347,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                         oxx[c] = nxx[0]; ozz[c] = nzz[0]; oxz[c] = nxz[0];
                     }
                 }
+                if (ST) fence_proxy_async_smem();   // the staged outputs are read by bulk copies
             } else {
             // v^{n+1/2} on the tile + 2-cell halo, in place over v^{n-1/2}
                 constexpr int VX = TX + 4, VZ = TZ + 4;
@@ -407,6 +464,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         if (tl.w & 2) tile(std::true_type{});
         else tile(std::false_type{});
     }
+    if (ST) {
+        __syncthreads();                    // every thread has staged the last tile's outputs
+        if (tid == 0) {
+            if (k > 0) store_fwd<TX, TZ, NST>(a, tl_prev, smb + ((k - 1) % NST) * L::BUF);
+            bulk_wait0();
+        }
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -421,26 +485,29 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int TX, int TZ, int NST, int VEC>
+template <int TX, int TZ, int NST, int VEC, int ST>
 void launch_tma(const TmaFwdArgs &a, int grid, cudaStream_t st) {
-    k_step_tma<TX, TZ, NST, VEC><<<grid, kThreads, FwdLayout<TX, TZ, NST, VEC>::smem(), st>>>(a);
+    k_step_tma<TX, TZ, NST, VEC, ST><<<grid, kThreads, FwdLayout<TX, TZ, NST, VEC>::smem(), st>>>(a);
 }
 
-template <int TX, int TZ, int NST, int VEC>
+template <int TX, int TZ, int NST, int VEC, int ST>
 int occupancy() {
-    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST, VEC, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)FwdLayout<TX, TZ, NST, VEC>::smem());
-    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST, VEC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST, VEC, ST>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<TX, TZ, NST, VEC>, kThreads,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<TX, TZ, NST, VEC, ST>, kThreads,
                                                   FwdLayout<TX, TZ, NST, VEC>::smem());
     return nb;
 }
 
-// compiled TMA variants: tile shape x pipeline stages x cells per thread (1 or 2)
+// compiled TMA variants: tile shape x pipeline stages x cells per thread (1 or 2) x
+// output staging (0: per-thread global stores, 1: shared memory + bulk tensor stores)
 #define EFWI_TMA_VARIANTS(X)                                                                             \
-    X(32, 8, 2, 1) X(32, 8, 3, 1) X(32, 16, 2, 1) X(64, 8, 2, 1) X(64, 16, 2, 1) X(32, 8, 2, 2)         \
-    X(32, 8, 3, 2) X(32, 16, 2, 2) X(32, 16, 3, 2) X(64, 8, 2, 2) X(64, 16, 2, 2)
+    X(32, 8, 2, 1, 0) X(32, 8, 3, 1, 0) X(32, 16, 2, 1, 0) X(64, 8, 2, 1, 0) X(64, 16, 2, 1, 0)          \
+    X(32, 8, 2, 2, 0) X(32, 8, 3, 2, 0) X(32, 16, 2, 2, 0) X(32, 16, 3, 2, 0) X(64, 8, 2, 2, 0)          \
+    X(64, 16, 2, 2, 0) X(32, 8, 3, 2, 1) X(32, 16, 2, 2, 1) X(32, 16, 3, 2, 1) X(64, 8, 2, 2, 1)         \
+    X(64, 16, 2, 2, 1)
 
 }  // namespace
 
@@ -459,15 +526,15 @@ int encode_map(CUtensorMap *m, float *base, const ShotDev &s, long long F, int n
     return r == CUDA_SUCCESS ? EFWI_OK : EFWI_ERR_CUDA;
 }
 
-bool tma_shape_ok(int tx, int tz, int nst, int vec) {
-#define EFWI_OK_X(a, b, c, d) if (tx == a && tz == b && nst == c && vec == d) return true;
+bool tma_shape_ok(int tx, int tz, int nst, int vec, int st) {
+#define EFWI_OK_X(a, b, c, d, e) if (tx == a && tz == b && nst == c && vec == d && st == e) return true;
     EFWI_TMA_VARIANTS(EFWI_OK_X)
 #undef EFWI_OK_X
     return false;
 }
 
 // Encode the forward maps of every shot for tile shape (tx, tz) into p->fwd_maps.
-int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec) {
+int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int stg) {
     std::vector<FwdMaps> h(p->d.ns);
     const long long F = p->fsz_total;
     for (int s = 0; s < p->d.ns; ++s) {
@@ -475,6 +542,9 @@ int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec) {
         int rc = encode_map(&h[s].st, p->state[0], sh, F, 10, tx + 8, tz + 8, 5);
         if (!rc) rc = encode_map(&h[s].mb, p->mat, sh, F, 5, tx + 8, tz + 8, 2);
         if (!rc) rc = encode_map(&h[s].mc, p->mat, sh, F, 5, tx, tz, 3);
+        if (!rc) rc = encode_map(&h[s].o2, p->state[0], sh, F, 10, tx, tz, 2);
+        if (!rc) rc = encode_map(&h[s].o3, p->state[0], sh, F, 10, tx, tz, 3);
+        if (!rc) rc = encode_map(&h[s].sg, p->seg, sh, F, (p->seg_double ? 4 : 2) * p->K, tx, tz, 2);
         if (rc) {
             p->err = "cuTensorMapEncodeTiled failed for the forward maps";
             return rc;
@@ -484,11 +554,13 @@ int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec) {
         return EFWI_ERR_OOM;
     cudaMemcpy(p->fwd_maps, h.data(), sizeof(FwdMaps) * p->d.ns, cudaMemcpyHostToDevice);
     int nb = 0;
-#define EFWI_OCC_X(a, b, c, d) if (tx == a && tz == b && nst == c && vec == d) nb = occupancy<a, b, c, d>();
+#define EFWI_OCC_X(a, b, c, d, e) \
+    if (tx == a && tz == b && nst == c && vec == d && stg == e) nb = occupancy<a, b, c, d, e>();
     EFWI_TMA_VARIANTS(EFWI_OCC_X)
 #undef EFWI_OCC_X
     p->tma_stages = nst;
     p->tma_vec = vec;
+    p->tma_store = stg;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -516,10 +588,12 @@ void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t
     a.rdx = (float)(1.0 / p->d.dx);
     a.rdz = (float)(1.0 / p->d.dz);
     a.err = p->dev_err;
+    a.ofield = 5 * (1 - p->scur);
+    a.segf = segx ? (int)((segx - p->seg) / p->fsz_total) : -1;
     const int grid = std::min(p->grid_fwd_override > 0 ? p->grid_fwd_override : p->tma_grid, a.ntiles);
-    const int tx = p->tiles.tx, tz = p->tiles.tz, nst = p->tma_stages, vec = p->tma_vec;
-#define EFWI_LAUNCH_X(a_, b_, c_, d_) \
-    if (tx == a_ && tz == b_ && nst == c_ && vec == d_) launch_tma<a_, b_, c_, d_>(a, grid, st);
+    const int tx = p->tiles.tx, tz = p->tiles.tz, nst = p->tma_stages, vec = p->tma_vec, stg = p->tma_store;
+#define EFWI_LAUNCH_X(a_, b_, c_, d_, e_) \
+    if (tx == a_ && tz == b_ && nst == c_ && vec == d_ && stg == e_) launch_tma<a_, b_, c_, d_, e_>(a, grid, st);
     EFWI_TMA_VARIANTS(EFWI_LAUNCH_X)
 #undef EFWI_LAUNCH_X
 }

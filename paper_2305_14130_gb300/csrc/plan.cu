@@ -202,8 +202,8 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (d->exec == EFWI_EXEC_BATCHED &&
         ((d->tile_x != 0 || d->tile_z != 0) && (d->tile_x <= 0 || d->tile_z <= 0)))
         return fail(nullptr, EFWI_ERR_ARG, "tile_x and tile_z must both be 0 or both positive");
-    if (d->stencil < EFWI_STENCIL_AUTO || d->stencil > EFWI_STENCIL_TMA_PAIRS ||
-        d->adj_stencil < EFWI_STENCIL_AUTO || d->adj_stencil > EFWI_STENCIL_TMA_PAIRS)
+    if (d->stencil < EFWI_STENCIL_AUTO || d->stencil > EFWI_STENCIL_TMA_STAGED ||
+        d->adj_stencil < EFWI_STENCIL_AUTO || d->adj_stencil > EFWI_STENCIL_TMA_STAGED)
         return fail(nullptr, EFWI_ERR_ARG, "unknown stencil");
     if (d->exec == EFWI_EXEC_BATCHED &&
         ((d->adj_tile_x != 0 || d->adj_tile_z != 0) && (d->adj_tile_x <= 0 || d->adj_tile_z <= 0)))

@@ -105,6 +105,7 @@ struct efwi_plan {
     int tma_grid = 0;                      // persistent CTAs of the TMA forward step
     int tma_stages = 2;                    // shared-memory pipeline depth of the TMA forward step
     int tma_vec = 1;                       // cells per thread and shared-memory access (1 or 2)
+    int tma_store = 0;                     // forward outputs staged in shared memory, bulk-stored
     int adj_stencil = EFWI_STENCIL_LOADS;  // staging of the adjoint step (after tuning)
     efwi::AdjMaps *adj_maps = nullptr;
     int tma_adj_grid = 0, tma_adj_stages = 1;
@@ -167,8 +168,8 @@ void launch_adj_vel_plain(efwi_plan *p, int shot, const float *vfx, const float 
 void launch_adj_stress_plain(efwi_plan *p, int shot, const float *vfx, const float *vfz, cudaStream_t st);
 
 // --- k_tma.cu ----------------------------------------------------------------
-bool tma_shape_ok(int tx, int tz, int nst, int vec);
-int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec);
+bool tma_shape_ok(int tx, int tz, int nst, int vec, int st);
+int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int st);
 void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t st);
 bool tma_adj_shape_ok(int tx, int tz, int nst);
 int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst);

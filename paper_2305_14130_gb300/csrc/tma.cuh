@@ -10,8 +10,11 @@ namespace efwi {
 // Tensor maps of one shot for the forward step: the state (both buffers,
 // 10 fields, box = tile + 4-cell halo over 5 fields), b_x/b_z (halo box) and
 // lambda/mu/mu_xz (tile box).
+// With shared-memory output staging, o2 / o3 store the new velocities / stresses
+// of a tile (boxes of 2 and 3 fields, tile only) and sg the segment-buffer copy
+// of the velocities.
 struct __align__(64) FwdMaps {
-    CUtensorMap st, mb, mc;
+    CUtensorMap st, mb, mc, o2, o3, sg;
 };
 
 // Tensor maps of one shot for the adjoint step: adjoint state (both buffers,
@@ -72,6 +75,29 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
         ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
         : "memory");
+}
+
+// Tile store shared -> global through the tensor map (bulk-group completion).
+// Box elements outside the tensor's extent are not written.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
+        ::"l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// every committed bulk store has finished reading its shared-memory source
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// every committed bulk store has completed
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// order this thread's generic-proxy shared-memory writes before later async-proxy
+// (bulk copy) reads of them
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 }  // namespace efwi

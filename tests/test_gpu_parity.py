@@ -307,7 +307,9 @@ def test_guided_wave_full_size_sampled(efwi):
 
 SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16), (32, 32), (128, 8), (64, 32)]
 TMA_SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16)]
-VARIANTS = [("loads", s) for s in SHAPES] + [(k, s) for k in ("tma", "tma_pairs") for s in TMA_SHAPES]
+STAGED_SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16)]
+VARIANTS = [("loads", s) for s in SHAPES] + [(k, s) for k in ("tma", "tma_pairs") for s in TMA_SHAPES] + \
+    [("tma_staged", s) for s in STAGED_SHAPES]
 
 
 @pytest.mark.parametrize("source", ["moment_tensor", "force"])
@@ -327,7 +329,7 @@ def test_stencil_variants_do_not_change_results(efwi, source):
         plan = efwi.Plan(p.acq, exec="batched", tile=(tx, tz), stencil=stencil)
         info = plan.info()
         assert (info["tile_x"], info["tile_z"]) == (tx, tz)
-        assert info["stencil"] == {"loads": 1, "tma": 2, "tma_pairs": 3}[stencil]
+        assert info["stencil"] == {"loads": 1, "tma": 2, "tma_pairs": 3, "tma_staged": 4}[stencil]
         assert info["adj_stencil"] in (1, 2)
         out = [t.clone() for t in plan.gradient(*args, return_data=True)]
         plan.sync_status()
@@ -351,7 +353,7 @@ def test_tma_full_size_matches_loads(efwi):
     m = (dev(p.vp), dev(p.vs), dev(p.rho))
     outs = []
     d_obs = torch.zeros((acq.ntr, acq.nt), device="cuda")
-    for stencil in ("loads", "tma", "tma_pairs"):
+    for stencil in ("loads", "tma", "tma_pairs", "tma_staged"):
         plan = efwi.Plan(acq, exec="batched", stencil=stencil, ckpt_interval=30)
         outs.append([t.clone() for t in plan.gradient(*m, d_obs, return_data=True)])
         plan.sync_status()
