@@ -156,7 +156,8 @@ def roofline(exec_, info, prof, nt, ns):
         if exec_ == "batched":
             kind = info["stencil"] if k == "step" else info["adj_stencil"]
             tile = (info["tile_x"], info["tile_z"]) if k == "step" else (info["adj_tile_x"], info["adj_tile_z"])
-            staging = {1: "per-thread loads", 2: "TMA", 3: "TMA, cell pairs"}.get(kind, "?")
+            staging = {1: "per-thread loads", 2: "TMA", 3: "TMA, cell pairs",
+                       4: "TMA, cell pairs, staged stores"}.get(kind, "?")
             name = f"{name.split(' ')[0]} [{staging}, tile {tile[0]}x{tile[1]}] {' '.join(name.split(' ')[1:])}"
         avg = ms / n / 1e3
         achieved = bpc * cells / avg / 1e9

@@ -696,7 +696,7 @@ int efwi_autotune(efwi_plan *p) {
     }
     if (fwd.empty() || adj.empty()) {
         p->err = "no compiled stencil variant matches the requested tile/stencil "
-                 "(loads: 32x8 32x16 64x8 64x16 32x32 128x8 64x32; tma: 32x8 32x16 64x8 64x16)";
+                 "(loads: 32x8 32x16 64x8 64x16 32x32 128x8 64x32; tma: 32x8 32x16 64x8 64x16; tma_staged: 32x16)";
         return EFWI_ERR_ARG;
     }
     int rc = EFWI_OK;

@@ -506,8 +506,7 @@ int occupancy() {
 #define EFWI_TMA_VARIANTS(X)                                                                             \
     X(32, 8, 2, 1, 0) X(32, 8, 3, 1, 0) X(32, 16, 2, 1, 0) X(64, 8, 2, 1, 0) X(64, 16, 2, 1, 0)          \
     X(32, 8, 2, 2, 0) X(32, 8, 3, 2, 0) X(32, 16, 2, 2, 0) X(32, 16, 3, 2, 0) X(64, 8, 2, 2, 0)          \
-    X(64, 16, 2, 2, 0) X(32, 8, 3, 2, 1) X(32, 16, 2, 2, 1) X(32, 16, 3, 2, 1) X(64, 8, 2, 2, 1)         \
-    X(64, 16, 2, 2, 1)
+    X(64, 16, 2, 2, 0) X(32, 16, 2, 2, 1)
 
 }  // namespace
 
