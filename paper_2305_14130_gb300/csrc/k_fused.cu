@@ -665,6 +665,9 @@ int efwi_autotune(efwi_plan *p) {
     const bool fixed = p->tile_x > 0 && p->tile_z > 0;
     const bool fixed_a = p->adj_tile_x > 0 && p->adj_tile_z > 0;
     std::vector<Variant> fwd, adj;
+    // EFWI_TMA_STAGES=n keeps only n-stage TMA forward variants (reproducible profiles)
+    const char *fs = getenv("EFWI_TMA_STAGES");
+    const int only_nst = fs ? atoi(fs) : 0;
     for (auto &s : kShapes) {
         if (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)) continue;
         if (want == EFWI_STENCIL_AUTO || want == EFWI_STENCIL_LOADS) fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
@@ -673,7 +676,8 @@ int efwi_autotune(efwi_plan *p) {
                 const int kind = vec == 1 ? EFWI_STENCIL_TMA : stg ? EFWI_STENCIL_TMA_STAGED : EFWI_STENCIL_TMA_PAIRS;
                 if (want != EFWI_STENCIL_AUTO && want != kind) continue;
                 for (int nst = 2; nst <= 4; ++nst)
-                    if (tma_shape_ok(s.tx, s.tz, nst, vec, stg)) fwd.push_back({kind, s.tx, s.tz, nst, vec, stg});
+                    if ((!only_nst || nst == only_nst) && tma_shape_ok(s.tx, s.tz, nst, vec, stg))
+                        fwd.push_back({kind, s.tx, s.tz, nst, vec, stg});
             }
     }
     // the adjoint follows its own request, or the forward one when it has none
