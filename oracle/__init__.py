@@ -12,5 +12,9 @@ elastic    forward modelling (eqs. 1-3), L2 misfit (eq. 4 / first term of
 extension  zone-of-influence weights (eq. 10), the footprint operator W
            (eq. 11), the weighted collapse S_w (eq. 12) and the
            inter-component consistency term of eq. 8 with its gradient.
+hessian    the pseudo-Hessian of the paper's illumination-compensation
+           comparison (zero-lag auto-correlation of |v| summed over shots)
+           and its clipped, scaled inverse.
+lbfgs      the optimizer (l-BFGS, strong-Wolfe line search, eq. 13 rate).
 """
-from . import elastic, extension  # noqa: F401
+from . import elastic, extension, hessian  # noqa: F401
