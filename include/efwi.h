@@ -283,6 +283,25 @@ int efwi_regularization_grad_noalloc(int ns, int nx, int nz, const float *m, con
 int efwi_collapse(int ns, int nx, int nz, const float *x, const float *b, const float *bp,
                   const uint8_t *sink, float *out, efwi_stream_t stream);
 
+/* Pseudo-Hessian of the paper's illumination-compensation comparison method
+ * (pseudo-Hessian = diagonal of the approximate Hessian, the preconditioning
+ * paragraph; built, as the comparison section describes, by auto-correlating
+ * the absolute particle velocity in time, summing over shots, clipping and
+ * scaling, and given to l-BFGS as the initial inverse Hessian):
+ *   h(x)    = sum_s sum_n |v_s(x, t_{n+1/2})|^2   (zero lag, no dt factor),
+ *   h_inv(x) = c / max(h(x), c),  c = eps * max_x h   (1 everywhere if h = 0),
+ * with |v|^2 at a node from the mean of the two staggered neighbours of each
+ * velocity component.  Shot s runs in its own component of the extended
+ * model (vp, vs, rho: device [ns][nz][nx]) and contributes inside its window.
+ *   eps     clipping level, 0 < eps <= 1 (EFWI_ERR_ARG otherwise)
+ *   h       device [nz][nx] FP32 (overwritten); accumulated in FP64
+ *   h_inv   device [nz][nx] FP32 (overwritten), or NULL
+ * Runs one forward pass of every shot (no DAS sampling); uses the plan's
+ * imaging workspace, so it must not overlap an efwi_adjoint_gradient call
+ * of the same plan on the GPU.                                              */
+int efwi_pseudo_hessian(efwi_plan *plan, const float *vp, const float *vs, const float *rho, double eps,
+                        float *h, float *h_inv, efwi_stream_t stream);
+
 /* ---- Optimizer: limited-memory BFGS with a strong-Wolfe line search -------
  * The paper's inversions run l-BFGS with a step length satisfying the Wolfe
  * conditions and stop when the convergence rate of eq. 13,

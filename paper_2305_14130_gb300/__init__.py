@@ -196,6 +196,17 @@ class Plan:
             _ptr(pr, "phi_reg", 1, torch.float64), _stream()))
         return pd, pr
 
+    def pseudo_hessian(self, vp, vs, rho, eps=1e-3, inverse=True):
+        """(h, h_inv) [nz, nx]: zero-lag auto-correlation of |v| summed over the
+        shots, and its clipped, scaled inverse (None unless inverse)."""
+        m = self._model(vp, vs, rho)
+        h = torch.empty((self.nz, self.nx), dtype=torch.float32, device=vp.device)
+        hi = torch.empty_like(h) if inverse else None
+        self._check(self._lib.efwi_pseudo_hessian(self._h, *m, float(eps), _ptr(h, "h", self.nz * self.nx),
+                                                  _ptr(hi, "h_inv", self.nz * self.nx, allow_none=True),
+                                                  _stream()))
+        return h, hi
+
     def sync_status(self):
         """Synchronise the current stream; raise on device-side failures of earlier calls."""
         self._check(self._lib.efwi_sync_status(self._h, _stream()))

@@ -251,6 +251,41 @@ extern "C" int efwi_adjoint_gradient(efwi_plan *p, const float *vp, const float 
     return cuda_status(p, "gradient epilogue");
 }
 
+extern "C" int efwi_pseudo_hessian(efwi_plan *p, const float *vp, const float *vs, const float *rho, double eps,
+                                   float *h, float *h_inv, efwi_stream_t stream) {
+    if (!p) return EFWI_ERR_ARG;
+    int rc = check_model_args(p, vp, vs, rho);
+    if (rc) return rc;
+    if (!h) {
+        p->err = "h must be a device pointer";
+        return EFWI_ERR_ARG;
+    }
+    if (!(eps > 0.0 && eps <= 1.0)) {
+        p->err = "eps must lie in (0, 1]";
+        return EFWI_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    p->launches = 0;
+    launch_materials(p, vp, vs, rho, st);
+    // FP64 accumulator with the wavefield layout, over the imaging workspace G
+    double *acc = reinterpret_cast<double *>(p->G);
+    auto body = [&](cudaStream_t cs) {
+        reset_forward_state(p, cs);
+        cudaMemsetAsync(acc, 0, sizeof(double) * p->fsz_total, cs);
+        for (int n = 0; n < p->d.nt; ++n) {
+            forward_step(p, n, nullptr, nullptr, nullptr, cs);
+            launch_vel_energy(p, state_fields(p, p->d.exec == EFWI_EXEC_PLAIN ? 0 : p->scur), acc, cs);
+        }
+    };
+    if (p->d.exec == EFWI_EXEC_BATCHED && p->use_graphs) {
+        if ((rc = replay(p, p->g_ph, st, body))) return rc;
+    } else {
+        body(st);
+    }
+    launch_ph_finish(p, acc, eps, h, h_inv, st);
+    return cuda_status(p, "pseudo-Hessian");
+}
+
 extern "C" int efwi_extended_objective(efwi_plan *p, const float *vp, const float *vs, const float *rho,
                                        const float *d_obs, const double eta[3], const float *b, const float *bp,
                                        const uint8_t *sink, double *phi_data, double *phi_reg,

@@ -164,7 +164,7 @@ static void free_plan(efwi_plan *p) {
                     p->ck.scale};
     for (void *q : ptrs)
         if (q) cudaFree(q);
-    for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj})
+    for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj, &p->g_ph})
         if (g->exec) cudaGraphExecDestroy(g->exec);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->cap2) cudaStreamDestroy(p->cap2);
@@ -556,7 +556,7 @@ extern "C" int efwi_sync_status(efwi_plan *p, efwi_stream_t stream) {
 extern "C" int efwi_prof_enable(efwi_plan *p, int every) {
     if (!p || every < 0) return fail(p, EFWI_ERR_ARG, "bad arguments to efwi_prof_enable");
     cudaDeviceSynchronize();
-    for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj})
+    for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj, &p->g_ph})
         if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
     p->prof_every = every;
     p->prof_counter[0] = p->prof_counter[1] = 0;

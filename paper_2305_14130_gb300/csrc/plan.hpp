@@ -124,7 +124,7 @@ struct efwi_plan {
     int ov_fwd = 0, ov_adj = 0;
     int grid_fwd_override = 0, grid_adj_override = 0;   // launch grids in effect (0 = default)
     bool seg_double = false;               // segment buffer holds two halves (overlap)
-    efwi::GraphCache g_fwd, g_fwd_ck, g_adj;
+    efwi::GraphCache g_fwd, g_fwd_ck, g_adj, g_ph;
     bool use_graphs = true;
 
     // timing of the dominant kernels (event pairs, tagged by kernel kind)
@@ -160,6 +160,10 @@ void launch_collapse(int ns, long long npix, const float *x, const float *b, con
                      float *out, cudaStream_t st);
 void launch_reg(efwi_plan *p, const float *m, const float *b, const float *bp, const uint8_t *sink, double eta,
                 double *phi, float *g, int accumulate_phi, cudaStream_t st);
+
+// --- k_hessian.cu --------------------------------------------------------------
+void launch_vel_energy(efwi_plan *p, Fields F, double *acc, cudaStream_t st);
+void launch_ph_finish(efwi_plan *p, const double *acc, double eps, float *h, float *hinv, cudaStream_t st);
 
 // --- k_plain.cu (shot >= 0: that shot only; shot < 0: all shots in one launch) ---
 void launch_vel_plain(efwi_plan *p, int shot, float *segx, float *segz, cudaStream_t st);

@@ -146,3 +146,4 @@ def test_null_arguments(lib):
     assert lib.efwi_plan_create(None, None) == -1
     assert lib.efwi_plan_destroy(None) == 0
     assert lib.efwi_forward(None, None, None, None, None, None) == -1
+    assert lib.efwi_pseudo_hessian(None, None, None, None, 1e-3, None, None, None) == -1
