@@ -137,7 +137,7 @@ KERNELS = {
 # profiles/ (8-shot case, same kernel variant; scaled to a launch by its cells).
 # Keyed by (kernel, staging, tile); any other variant reports traffic null.
 TRAFFIC_PER_CELL = {
-    ("step", 3, 32, 16): 54.68,   # TMA, cell pairs, 32x16 (profiles/k_step_tma_guided_wave_8shots.md)
+    ("step", 3, 32, 16): 54.86,   # TMA, cell pairs, 32x16 (profiles/k_step_tma_guided_wave_8shots.md)
     ("adj", 1, 32, 16): 96.05,    # per-thread loads, 32x16 (profiles/k_adj_fused_guided_wave_8shots.md)
 }
 
