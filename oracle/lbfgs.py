@@ -8,15 +8,18 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   definition, dense: H_0 = gamma I with gamma = s^T y / y^T y of the newest
   pair, then for every stored pair, oldest first,
   H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T, rho = 1 / y^T s
-  (Nocedal & Wright, eq. 6.17 and 7.20).
+  (Nocedal & Wright, eq. 6.17 and 7.20).  With a positive diagonal D as the
+  initial guess (the paper hands l-BFGS an approximate inverse pseudo-Hessian
+  as its initial inverse Hessian), H_0 = gamma D with gamma = s^T y / y^T D y,
+  and H_0 = D without pairs.
 * ``two_loop``: the same product H g by the two-loop recursion (Nocedal &
   Wright, Alg. 7.4), for vectors too long for a dense matrix.
 * ``wolfe_search``: Nocedal & Wright Alg. 3.5 (bracketing by doubling the
   step) and Alg. 3.6 (zoom); the zoom trial is the minimiser of the quadratic
   through phi(lo), phi'(lo), phi(hi), replaced by the bracket midpoint when it
   falls outside the inner 80 % of the bracket or the quadratic is not convex.
-* ``lbfgs``: the iteration: d = -H g (restart from -g if d is not a descent
-  direction), first step 1/||g|| without stored pairs else 1, store the pair
+* ``lbfgs``: the iteration: d = -H g (restart from -H_0 g if d is not a
+  descent direction), first step 1/||d|| without stored pairs else 1, store the pair
   only when s^T y > 0, keep the newest m pairs, rate_{k+1} = (Phi_k -
   Phi_{k+1}) / Phi_k (eq. 13).
 """
@@ -25,14 +28,16 @@ from __future__ import annotations
 import numpy as np
 
 
-def bfgs_inverse_hessian(S, Y):
-    """Dense H from the pairs (rows of S and Y, oldest first)."""
+def bfgs_inverse_hessian(S, Y, D=None, n=None):
+    """Dense H from the pairs (rows of S and Y, oldest first); D: optional
+    positive diagonal of the initial guess."""
     S = np.asarray(S, np.float64)
     Y = np.asarray(Y, np.float64)
-    n = S.shape[1]
+    n = S.shape[1] if S.ndim == 2 else (len(D) if D is not None else n)
+    D0 = np.eye(n) if D is None else np.diag(np.asarray(D, np.float64))
     if S.shape[0] == 0:
-        return np.eye(n)
-    H = (S[-1] @ Y[-1]) / (Y[-1] @ Y[-1]) * np.eye(n)
+        return D0
+    H = (S[-1] @ Y[-1]) / (Y[-1] @ D0 @ Y[-1]) * D0
     for s, y in zip(S, Y):
         rho = 1.0 / (y @ s)
         V = np.eye(n) - rho * np.outer(y, s)
@@ -40,20 +45,22 @@ def bfgs_inverse_hessian(S, Y):
     return H
 
 
-def two_loop(g, S, Y):
-    """H g by the two-loop recursion (pairs as rows, oldest first)."""
+def two_loop(g, S, Y, D=None):
+    """H g by the two-loop recursion (pairs as rows, oldest first); D: optional
+    positive diagonal of the initial guess H_0."""
     S = np.asarray(S, np.float64)
     Y = np.asarray(Y, np.float64)
     q = np.array(g, np.float64)
+    Dv = np.ones_like(q) if D is None else np.asarray(D, np.float64)
     k = S.shape[0]
     if k == 0:
-        return q
+        return Dv * q
     rho = [1.0 / (Y[i] @ S[i]) for i in range(k)]
     alpha = [0.0] * k
     for i in range(k - 1, -1, -1):
         alpha[i] = rho[i] * (S[i] @ q)
         q = q - alpha[i] * Y[i]
-    r = (S[-1] @ Y[-1]) / (Y[-1] @ Y[-1]) * q
+    r = (S[-1] @ Y[-1]) / (Y[-1] @ (Dv * Y[-1])) * (Dv * q)
     for i in range(k):
         beta = rho[i] * (Y[i] @ r)
         r = r + (alpha[i] - beta) * S[i]
@@ -128,18 +135,19 @@ def wolfe_search(f, x, phi0, g0, d, a0, c1=1e-4, c2=0.9, max_ls=20):
     return t[0], t[1], g, evals
 
 
-def lbfgs(f, x0, iters, m=5, c1=1e-4, c2=0.9, max_ls=20):
-    """Iterates of l-BFGS from x0: list of dicts (x, phi, alpha, rate, evals)."""
+def lbfgs(f, x0, iters, m=5, c1=1e-4, c2=0.9, max_ls=20, D=None):
+    """Iterates of l-BFGS from x0: list of dicts (x, phi, alpha, rate, evals).
+    D: optional positive diagonal initial inverse Hessian."""
     x = np.array(x0, np.float64)
     phi, g = f(x)
     S, Y = [], []
     out = []
     for _ in range(iters):
-        d = -two_loop(g, S, Y)
+        d = -two_loop(g, S, Y, D)
         if not (g @ d < 0):
             S, Y = [], []
-            d = -g
-        a0 = min(1.0, 1.0 / np.sqrt(g @ g)) if not S else 1.0
+            d = -two_loop(g, S, Y, D)
+        a0 = min(1.0, 1.0 / np.sqrt(d @ d)) if not S else 1.0
         a, phi1, g1, evals = wolfe_search(f, x, phi, g, d, a0, c1, c2, max_ls)
         if a is None:
             out.append({"x": x.copy(), "phi": phi, "alpha": None, "rate": None, "evals": evals})

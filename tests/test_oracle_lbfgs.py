@@ -119,3 +119,59 @@ def test_failed_search_keeps_the_point():
     phi0, g0 = f(x0)
     a, phi, g, evals = L.wolfe_search(f, x0, phi0, g0, g0, 1.0, max_ls=5)
     assert a is None and evals == 5
+
+
+# --- diagonal initial inverse Hessian (the pseudo-Hessian preconditioner) ----------
+
+@pytest.mark.parametrize("k", [0, 1, 3, 5])
+def test_two_loop_with_diagonal_equals_dense_bfgs_matrix(k):
+    """The recursion with H_0 = gamma D equals the dense update from H_0 = gamma D
+    (gamma = s^T y / y^T D y of the newest pair; D itself without pairs)."""
+    S, Y, _ = _pairs(10, k, 11)
+    D = np.random.default_rng(12).uniform(0.1, 3.0, 10)
+    g = np.random.default_rng(13).standard_normal(10)
+    H = L.bfgs_inverse_hessian(S, Y, D)
+    assert np.allclose(L.two_loop(g, S, Y, D), H @ g, rtol=1e-12, atol=1e-12)
+    if k == 0:
+        assert np.allclose(H, np.diag(D), rtol=0, atol=0)
+
+
+def test_constant_diagonal_is_the_identity_guess():
+    """D = c 1 changes nothing once a pair is stored (gamma absorbs c)."""
+    S, Y, _ = _pairs(8, 3, 14)
+    g = np.random.default_rng(15).standard_normal(8)
+    assert np.allclose(L.two_loop(g, S, Y, np.full(8, 7.5)), L.two_loop(g, S, Y), rtol=1e-13, atol=1e-13)
+
+
+def test_diagonal_guess_keeps_secant_equation_and_hereditary_property():
+    S, Y, _ = _pairs(9, 4, 16)
+    D = np.random.default_rng(17).uniform(0.2, 2.0, 9)
+    H = L.bfgs_inverse_hessian(S, Y, D)
+    assert np.allclose(H @ Y[-1], S[-1], rtol=1e-12, atol=1e-12)
+    assert np.allclose(H, H.T, atol=1e-12) and np.all(np.linalg.eigvalsh(H) > 0)
+    n = 6
+    A = np.diag(np.random.default_rng(18).uniform(1.0, 3.0, n))
+    Hn = L.bfgs_inverse_hessian(np.eye(n), A, np.random.default_rng(19).uniform(0.1, 5.0, n))
+    assert np.allclose(Hn, np.linalg.inv(A), rtol=1e-12, atol=1e-12)
+
+
+def test_exact_diagonal_preconditioner_points_at_the_minimiser():
+    """phi = 1/2 (x - c)^T A (x - c) with A diagonal and D = A^{-1}: the first
+    direction is c - x0 exactly, the first trial step 1/||d|| along it."""
+    rng = np.random.default_rng(20)
+    a = rng.uniform(0.5, 40.0, 30)
+    c = rng.standard_normal(30)
+
+    def f(x):
+        return 0.5 * float(np.sum(a * (x - c) ** 2)), a * (x - c)
+
+    x0 = np.zeros(30)
+    _, g0 = f(x0)
+    assert np.allclose(-L.two_loop(g0, [], [], 1.0 / a), c - x0, rtol=1e-14, atol=0)
+    out = L.lbfgs(f, x0, iters=1, D=1.0 / a)
+    # along the Newton direction phi(t) = (1 - t)^2 phi(x0): the first trial t0 = 1/||c||
+    # (here in [0.1, 1]) meets both strong Wolfe conditions and is accepted as it is
+    t0 = 1.0 / np.linalg.norm(c)
+    assert 0.1 < t0 < 1.0
+    assert out[0]["alpha"] == pytest.approx(t0, rel=1e-14) and out[0]["evals"] == 1
+    assert out[0]["phi"] == pytest.approx((1.0 - t0) ** 2 * f(x0)[0], rel=1e-12)
