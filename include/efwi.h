@@ -309,10 +309,11 @@ int efwi_pseudo_hessian(efwi_plan *plan, const float *vp, const float *vs, const
  * drops below a threshold (0.1 %) or when no suitable step is found.
  * A handle owns m pairs (s_i, y_i) of n-element FP32 device vectors plus
  * scratch (about (2m + 5) n floats).  Directions come from the two-loop
- * recursion with H_0 = (s^T y / y^T y) I of the newest pair (I without pairs);
- * inner products are FP64 reductions in a fixed order.  The line search
- * (bracketing, then zoom with safeguarded quadratic interpolation) starts at
- * step 1 (1 / ||g|| on the first iteration) and evaluates the objective
+ * recursion with H_0 = (s^T y / y^T y) I of the newest pair (I without pairs),
+ * or a caller's diagonal guess (efwi_lbfgs_set_h0); inner products are FP64
+ * reductions in a fixed order.  The line search (bracketing, then zoom with
+ * safeguarded quadratic interpolation) starts at step 1 (1 / ||d|| on the
+ * first iteration, d = -H_0 g) and evaluates the objective
  * through the caller's callback:
  *   fn(ctx, x, phi, g, stream): x device [n] (read only), phi HOST double
  *   (written), g device [n] (written); returns 0, or nonzero to abort (a
@@ -349,6 +350,12 @@ int efwi_lbfgs_reset(efwi_lbfgs *h);
 /* Stores the pair (s, y) (device [n] each, copied) if s^T y > 0; *accepted
  * (may be NULL) tells whether it was.  Synchronises the stream.             */
 int efwi_lbfgs_push(efwi_lbfgs *h, const float *s, const float *y, int *accepted, efwi_stream_t stream);
+/* Positive diagonal D (device [n], copied) as the initial inverse Hessian:
+ * H_0 = gamma D with gamma = s^T y / y^T D y of the newest pair, H_0 = D
+ * without pairs (the paper gives l-BFGS the clipped, scaled inverse
+ * pseudo-Hessian of efwi_pseudo_hessian this way).  NULL returns to
+ * H_0 = gamma I.  Forgets the stored pairs.                                 */
+int efwi_lbfgs_set_h0(efwi_lbfgs *h, const float *diag, efwi_stream_t stream);
 /* d = -H g (device [n] each) from the stored pairs, asynchronous.          */
 int efwi_lbfgs_direction(efwi_lbfgs *h, const float *g, float *d, efwi_stream_t stream);
 /* One iteration from x (device [n], updated), *phi (host, updated) and its

@@ -6,7 +6,10 @@
 // y_i = g_{i+1} - g_i) are FP32 device arrays of n elements; every inner
 // product is an FP64 reduction with a fixed summation order (deterministic).
 // The search direction is the two-loop recursion (Nocedal & Wright, Alg. 7.4)
-// with H_0 = gamma I, gamma = s^T y / y^T y of the newest pair; its scalars
+// with H_0 = gamma I, gamma = s^T y / y^T y of the newest pair, or, when the
+// caller sets a positive diagonal D as the initial guess (the paper hands its
+// l-BFGS an approximate inverse pseudo-Hessian), H_0 = gamma D with
+// gamma = s^T y / y^T D y (H_0 = D without pairs); its scalars
 // (alpha_i, beta) stay on the device, so the recursion is a fixed sequence of
 // launches.  The line search (Nocedal & Wright, Alg. 3.5 with the zoom of
 // Alg. 3.6, quadratic interpolation safeguarded to the inner 80 % of the
@@ -55,6 +58,21 @@ __global__ void k_dot_final(const double *partial, int nb, double scale, const d
     if (threadIdx.x == 0) *out = scale * v * (mul ? *mul : 1.0);
 }
 
+// partial[b] = sum over block b's grid-stride share of x_i w_i y_i
+__global__ void k_dot3(const float *x, const float *w, const float *y, long long n, double *partial) {
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (double)x[i] * ((double)w[i] * (double)y[i]);
+    acc = lb_block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// y = w * y elementwise
+__global__ void k_mul(float *y, const float *w, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = w[i] * y[i];
+}
+
 // y += (a0 - a1) * x, with a0, a1 device scalars (a1 may be NULL)
 __global__ void k_axpy_dev(float *y, const float *x, long long n, const double *a0, const double *a1, double sign) {
     const double a = sign * (*a0 - (a1 ? *a1 : 0.0));
@@ -96,6 +114,8 @@ struct efwi_lbfgs {
     std::vector<int> order;           // slots of the stored pairs, oldest first (at most m)
     float *S = nullptr, *Y = nullptr; // (m + 1) x n: the stored pairs and one candidate slot
     float *d = nullptr, *xt = nullptr, *gt = nullptr;
+    float *D = nullptr;               // diagonal initial inverse Hessian (efwi_lbfgs_set_h0)
+    bool has_d = false;
     double *dev = nullptr;            // device scalars, see the offsets below
     double *partial = nullptr;
     double c1 = 1e-4, c2 = 0.9;
@@ -149,7 +169,7 @@ int read_scalar(const double *p, double *v, cudaStream_t st) {
 float *slot_s(efwi_lbfgs *h, int k) { return h->S + (long long)k * h->n; }
 float *slot_y(efwi_lbfgs *h, int k) { return h->Y + (long long)k * h->n; }
 
-// d = -H g by the two-loop recursion; H = I without stored pairs
+// d = -H g by the two-loop recursion; H = H_0 (I or D) without stored pairs
 void lb_direction(efwi_lbfgs *h, const float *g, cudaStream_t st) {
     const long long n = h->n;
     const int G = lb_grid(n);
@@ -162,6 +182,7 @@ void lb_direction(efwi_lbfgs *h, const float *g, cudaStream_t st) {
         k_axpy_dev<<<G, kLbThreads, 0, st>>>(h->d, slot_y(h, k), n, alpha + k, nullptr, -1.0);
     }
     if (np > 0) k_scale_dev<<<G, kLbThreads, 0, st>>>(h->d, h->d, n, h->dev + h->o_gamma(), 1.0);
+    if (h->has_d) k_mul<<<G, kLbThreads, 0, st>>>(h->d, h->D, n);
     for (int j = 0; j < np; ++j) {                               // oldest to newest
         const int k = h->order[j];
         dot_dev(h, slot_y(h, k), h->d, beta, 1.0, rho + k, st);
@@ -281,7 +302,12 @@ int lb_check(const char *what) {
 int lb_accept_pair(efwi_lbfgs *h, int k, cudaStream_t st, int *accepted) {
     double *sy = h->dev + h->o_sy(), *yy = h->dev + h->o_yy();
     dot_dev(h, slot_s(h, k), slot_y(h, k), sy, 1.0, nullptr, st);
-    dot_dev(h, slot_y(h, k), slot_y(h, k), yy, 1.0, nullptr, st);
+    if (h->has_d) {                                  // y^T D y for gamma of H_0 = gamma D
+        k_dot3<<<kLbBlocks, kLbThreads, 0, st>>>(slot_y(h, k), h->D, slot_y(h, k), h->n, h->partial);
+        k_dot_final<<<1, 1024, 0, st>>>(h->partial, kLbBlocks, 1.0, nullptr, yy);
+    } else {
+        dot_dev(h, slot_y(h, k), slot_y(h, k), yy, 1.0, nullptr, st);
+    }
     double v = 0, w = 0;
     if (read_scalar(sy, &v, st) != EFWI_OK || read_scalar(yy, &w, st) != EFWI_OK)
         return lb_fail(EFWI_ERR_CUDA, "l-BFGS: reading s^T y failed");
@@ -328,7 +354,7 @@ extern "C" int efwi_lbfgs_create(efwi_lbfgs **out, long long n, int m, double c1
 extern "C" int efwi_lbfgs_destroy(efwi_lbfgs *h) {
     if (!h) return EFWI_OK;
     for (void *p : {(void *)h->S, (void *)h->Y, (void *)h->d, (void *)h->xt, (void *)h->gt, (void *)h->dev,
-                    (void *)h->partial})
+                    (void *)h->partial, (void *)h->D})
         if (p) cudaFree(p);
     delete h;
     return EFWI_OK;
@@ -338,6 +364,23 @@ extern "C" int efwi_lbfgs_reset(efwi_lbfgs *h) {
     if (!h) return lb_fail(EFWI_ERR_ARG, "handle is NULL");
     h->order.clear();
     return EFWI_OK;
+}
+
+extern "C" int efwi_lbfgs_set_h0(efwi_lbfgs *h, const float *diag, efwi_stream_t stream) {
+    if (!h) return lb_fail(EFWI_ERR_ARG, "handle is NULL");
+    h->order.clear();                           // gamma of the stored pairs depends on H_0
+    if (!diag) {
+        h->has_d = false;
+        return EFWI_OK;
+    }
+    if (!h->D && cudaMalloc((void **)&h->D, sizeof(float) * h->n) != cudaSuccess) {
+        cudaGetLastError();
+        h->D = nullptr;
+        return lb_fail(EFWI_ERR_OOM, "l-BFGS: device allocation of the diagonal failed");
+    }
+    cudaMemcpyAsync(h->D, diag, sizeof(float) * h->n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    h->has_d = true;
+    return lb_check("l-BFGS initial inverse Hessian");
 }
 
 extern "C" int efwi_lbfgs_push(efwi_lbfgs *h, const float *s, const float *y, int *accepted, efwi_stream_t stream) {
@@ -385,11 +428,11 @@ extern "C" int efwi_lbfgs_iterate(efwi_lbfgs *h, float *x, double *phi, float *g
         return lb_check("l-BFGS");
     }
     double a0 = 1.0;
-    if (h->order.empty()) {                     // first step (or restart): unit length along -g
-        dot_dev(h, g, g, tmp, 1.0, nullptr, st);
-        double gg = 0;
-        if (read_scalar(tmp, &gg, st) != EFWI_OK) return lb_fail(EFWI_ERR_CUDA, "l-BFGS: reading g^T g failed");
-        a0 = std::fmin(1.0, 1.0 / std::sqrt(gg));
+    if (h->order.empty()) {                     // first step (or restart): unit length along d = -H_0 g
+        dot_dev(h, h->d, h->d, tmp, 1.0, nullptr, st);
+        double dd = 0;
+        if (read_scalar(tmp, &dd, st) != EFWI_OK) return lb_fail(EFWI_ERR_CUDA, "l-BFGS: reading d^T d failed");
+        a0 = std::fmin(1.0, 1.0 / std::sqrt(dd));
     }
     Trial t;
     const bool found = ls.run(a0, t);

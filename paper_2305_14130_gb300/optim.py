@@ -86,6 +86,13 @@ class LBFGS:
                                              _stream()))
         return bool(acc.value)
 
+    def set_h0(self, diag=None):
+        """Positive diagonal initial inverse Hessian (e.g. the clipped, scaled inverse
+        pseudo-Hessian, flattened like the model vector); None returns to gamma I.
+        Forgets the stored pairs."""
+        p = None if diag is None else _vec(diag, self.n, "diag")
+        _abi.check(self._lib.efwi_lbfgs_set_h0(self._h, p, _stream()))
+
     def direction(self, g, d=None):
         """d = -H g from the stored pairs (two-loop recursion)."""
         if d is None:

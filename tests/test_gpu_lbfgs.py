@@ -170,3 +170,59 @@ def test_extended_fwi_inversion_decreases_the_objective(efwi):
     assert len(phis) >= 3
     opt.close()
     plan.close()
+
+
+@pytest.mark.parametrize("n,k", [(7, 0), (300_001, 0), (300_001, 5)])
+def test_direction_with_diagonal_guess_matches_two_loop(efwi, n, k):
+    """H_0 = gamma D (D without pairs) set through efwi_lbfgs_set_h0."""
+    from paper_2305_14130_gb300.optim import LBFGS
+    S, Y = _spd_pairs(n, k, 21)
+    D = np.random.default_rng(22).uniform(0.05, 4.0, n).astype(np.float32)
+    g = np.random.default_rng(23).standard_normal(n).astype(np.float32)
+    opt = LBFGS(n, m=5)
+    opt.set_h0(torch.tensor(D, device="cuda"))
+    for s, y in zip(S, Y):
+        assert opt.push(torch.tensor(s, device="cuda"), torch.tensor(y, device="cuda"))
+    d = opt.direction(torch.tensor(g, device="cuda")).cpu().numpy()
+    ref = -L.two_loop(g.astype(np.float64), S.astype(np.float64), Y.astype(np.float64), D.astype(np.float64))
+    assert rel_l2(d, ref) <= (1e-7 if k == 0 else 1e-5)
+    opt.set_h0(None)                          # back to gamma I (pairs forgotten): d = -g
+    assert np.array_equal(opt.direction(torch.tensor(g, device="cuda")).cpu().numpy(), -g)
+    opt.close()
+
+
+def test_iterations_with_diagonal_guess_match_oracle(efwi):
+    """The quadratic of the test above with D = 1/a (its exact inverse Hessian,
+    the role the inverse pseudo-Hessian plays for the wave-equation problem):
+    steps, objective values and evaluation counts agree with the oracle."""
+    from paper_2305_14130_gb300.optim import LBFGS
+    n = 200_003
+    a, c = _quadratic(n, 9)
+    D = (1.0 / a).astype(np.float32)
+    at, ct = torch.tensor(a, device="cuda"), torch.tensor(c, device="cuda")
+
+    def obj(x, g):
+        r = x - ct
+        g.copy_(at * r)
+        return 0.5 * float(torch.sum(at.double() * r.double() * r.double())) + 1.0
+
+    def f(x):
+        r = x - c.astype(np.float64)
+        return 0.5 * float(np.sum(a * r * r)) + 1.0, a * r
+
+    iters = 2                                 # a doubling search along the Newton direction, then the exact step
+    ref = L.lbfgs(f, np.zeros(n), iters=iters, m=5, D=D.astype(np.float64))
+    opt = LBFGS(n, m=5)
+    opt.set_h0(torch.tensor(D, device="cuda"))
+    x = torch.zeros(n, device="cuda")
+    g = torch.empty(n, device="cuda")
+    phi = obj(x, g)
+    for k in range(iters):
+        if ref[k]["alpha"] is None:
+            break
+        phi, info = opt.iterate(x, phi, g, obj)
+        assert not info["ls_failed"]
+        assert info["alpha"] == pytest.approx(ref[k]["alpha"], rel=1e-4)
+        assert phi == pytest.approx(ref[k]["phi"], rel=1e-5)
+        assert info["evals"] == ref[k]["evals"]
+    opt.close()
