@@ -156,3 +156,14 @@ def extended_fwi_objective(plan, d_obs, b, bp, sink, eta, mask=None):
             phi = phi + phi_r
         return float(phi.item())
     return objective
+
+
+def pseudo_hessian_h0(plan, x, eps=1e-3):
+    """Diagonal initial inverse Hessian for the packed model x = (Vp, Vs, rho)
+    [3 * ns * nz * nx]: the clipped, scaled inverse pseudo-Hessian of the model
+    x (efwi_pseudo_hessian), the same [nz, nx] map for every parameter and
+    component.  Pass it to LBFGS.set_h0."""
+    shape = (3, plan.ns, plan.nz, plan.nx)
+    m = x.view(shape)
+    _, hinv = plan.pseudo_hessian(m[0], m[1], m[2], eps=eps)
+    return hinv.expand(shape).contiguous().view(-1)
