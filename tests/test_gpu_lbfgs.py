@@ -230,21 +230,17 @@ def test_iterations_with_diagonal_guess_match_oracle(efwi):
 
 def test_pseudo_hessian_preconditioned_inversion_decreases_the_objective(efwi):
     """The paper's first comparison method on a tiny problem: l-BFGS with the
-    clipped, scaled inverse pseudo-Hessian as initial inverse Hessian on the
-    data term; every iteration lowers the objective, eq. 13 rates."""
-    from paper_2305_14130_gb300.optim import LBFGS, pseudo_hessian_h0
+    clipped, scaled inverse pseudo-Hessian as initial inverse Hessian, on the
+    extended objective (eq. 8); every iteration lowers it, eq. 13 rates."""
+    from paper_2305_14130_gb300.optim import LBFGS, extended_fwi_objective, pseudo_hessian_h0
     p = rounded(W.tiny(nx=40, nz=30, ns=3, nt=60, npml=6))
-    plan = efwi.Plan(p.acq, exec="batched")
-    dev = lambda v: torch.tensor(np.asarray(v, np.float32), device="cuda")
+    acq = p.acq
+    plan = efwi.Plan(acq, exec="batched")
+    dev = lambda v, dt=np.float32: torch.tensor(np.asarray(v, dt), device="cuda")
     true = [np.broadcast_to(v, p.vp.shape).copy() for v in (p.true_vp, p.true_vs, p.true_rho)]
     d_obs = plan.forward(*[dev(v) for v in true]).clone()
-    shape = (3, plan.ns, plan.nz, plan.nx)
-
-    def obj(x, g):
-        m, gg = x.view(shape), g.view(shape)
-        phi, *_ = plan.gradient(m[0], m[1], m[2], d_obs, out=(gg[0], gg[1], gg[2]))
-        return float(phi.item())
-
+    bo, bpo, sinko = X.zoi_weights(p.zoi, acq.nx, acq.nz, acq.dx, acq.dz)
+    obj = extended_fwi_objective(plan, d_obs, dev(bo), dev(bpo), dev(sinko, np.uint8), (1e-3, 1e-3, 1e-3))
     x = torch.cat([dev(v).reshape(-1) for v in (p.vp, p.vs, p.rho)])
     D = pseudo_hessian_h0(plan, x, eps=0.05)
     assert D.shape == x.shape and float(D.min()) >= 0.05 * (1 - 1e-6) and float(D.max()) == 1.0
@@ -253,7 +249,7 @@ def test_pseudo_hessian_preconditioned_inversion_decreases_the_objective(efwi):
     opt.set_h0(D)
     phi = obj(x, g)
     phis = [phi]
-    for _ in range(3):
+    for _ in range(4):
         phi, info = opt.iterate(x, phi, g, obj)
         if info["ls_failed"]:
             break

@@ -186,6 +186,13 @@ def extend(m: np.ndarray, ns: int) -> np.ndarray:
     return np.repeat(np.asarray(m, np.float64)[None], ns, axis=0).copy()
 
 
+def extend_view(m: np.ndarray, ns: int) -> np.ndarray:
+    """[ns, nz, nx] read-only view of one model (no copy): the starting extended
+    model of the large workloads, where a copy per component would take GBs."""
+    m = np.asarray(m, np.float64)
+    return np.broadcast_to(m[None], (ns,) + m.shape)
+
+
 def horizontal_fibre(x_first, n, spacing, z):
     ch = np.stack([x_first + spacing * np.arange(n), np.full(n, float(z))], axis=1)
     t = np.tile(np.array([[1.0, 0.0]]), (n, 1))
@@ -317,7 +324,7 @@ def uneven_windows(nx: int, nz: int, dx: float, dt: float, ns: int, nt: int, wmi
                       tr_ptr=np.array(ptr, np.int32), ch_xz=np.concatenate(chs), ch_t=np.concatenate(tts),
                       gauge=10.0, ref_vp=vp, ref_vs=vs, ref_rho=rho, win=win, pml_f0=f0)
     bump = gaussian_bump(nx, nz, nx // 2, int(round((z_top + 15.0) / dx)), nx // 20 + 2, 8)
-    return Problem(name, acq, extend(vp, ns), extend(vs, ns), extend(rho, ns),
+    return Problem(name, acq, extend_view(vp, ns), extend_view(vs, ns), extend_view(rho, ns),
                    true_vp=vp * (1 + 0.04 * bump), true_vs=vs * (1 + 0.06 * bump), true_rho=rho.copy())
 
 
@@ -416,3 +423,115 @@ def seeded_data(shape, seed, scale=1.0):
     """Seeded synthetic 'observed' traces for parity cases that need any d_obs."""
     rng = np.random.default_rng(seed)
     return scale * rng.standard_normal(shape)
+
+
+def differentiation_2000x600(ns: int = 64, nt: int = 6000, nch: int = 500) -> Problem:
+    """Differentiation-path workload at scale: 2000x600 grid, dx=1 m, the
+    random-layered model (seed 0, Vp 3000-5000 m/s, Vs = Vp/1.8, 4-8 layers),
+    64 moment-tensor sources at z=300 m spread over x = 200-1800 m, 500 DAS
+    channels at z=340 m (1 m spacing, 10 m gauge, centred), 150 Hz Ricker,
+    nt=6000, dt=0.1 ms.  Observed data: a +3 % Vp / +5 % Vs / +2 % rho Gaussian
+    anomaly between the source line and the fibre."""
+    nx, nz, dx = 2000, 600, 1.0
+    dt, f0 = 1e-4, 150.0
+    vp, vs, rho = random_layered_model(nx, nz, seed=0)
+    xs = np.linspace(200.0, 1800.0, ns) + 0.37
+    src = np.stack([xs, np.full(ns, 300.0)], axis=1)
+    mt = np.tile(np.array([[1e6, 0.75e6, 2e5]]), (ns, 1))
+    ch, t = horizontal_fibre(1000.0 - nch / 2, nch, 1.0, 340.0)
+    tr_ptr, chs, ts = same_traces_per_shot(ns, ch, t)
+    wav = np.tile(ricker(f0, nt, dt)[None], (ns, 1))
+    acq = Acquisition(nx=nx, nz=nz, dx=dx, dz=dx, nt=nt, dt=dt, src_xz=src, mt=mt, wavelet=wav,
+                      tr_ptr=tr_ptr, ch_xz=chs, ch_t=ts, gauge=10.0,
+                      ref_vp=vp, ref_vs=vs, ref_rho=rho, pml_f0=f0)
+    bump = gaussian_bump(nx, nz, 1000, 320, 60, 12)
+    return Problem("differentiation_2000x600", acq, extend_view(vp, ns), extend_view(vs, ns), extend_view(rho, ns),
+                   true_vp=vp * (1 + 0.03 * bump), true_vs=vs * (1 + 0.05 * bump), true_rho=rho * (1 + 0.02 * bump),
+                   zoi=default_zoi(acq, taper_m=50.0, sink_ax=12.0, sink_az=6.0), eta=(1e-3, 1e-3, 1e-3))
+
+
+def full_iteration_4000x1200(ns: int = 128, nt: int = 8000, nch: int = 1500, seed: int = 0) -> Problem:
+    """Full extended-FWI iteration at scale: 4000x1200 grid, dx=0.5 m, the
+    waveguide (30 m shale layer at 285-315 m, +-3 % random fields with a 20 m
+    correlation length), 128 perforation-like moment-tensor sources on a
+    horizontal well in the layer (z=300 m, x = 200-1800 m), 1500 DAS channels at
+    z=340 m (0.5 m spacing, 10 m gauge, centred), 150 Hz Ricker, nt=8000,
+    dt=0.05 ms.
+
+    The acquisition carries the modelled sources, with seeded source errors
+    (rng(seed)): amplitude x U(0.9, 1.1), time shift U(-0.2, 0.2) ms and a
+    mechanism rotation U(-15, 15) degrees (R M R^T).  The error-free sources
+    that generate the observed data are in meta["true_mt"] and
+    meta["true_wavelet"]; the observed data also see a +4 % Vp / +6 % Vs
+    Gaussian anomaly in the layer.
+    """
+    nx, nz, dx = 4000, 1200, 0.5
+    dt, f0 = 5e-5, 150.0
+    vp, vs, rho = waveguide_model(nx, nz, dx, z_top=285.0, thickness=30.0, dx=dx)
+    xs = np.linspace(200.0, 1800.0, ns) + 0.13
+    src = np.stack([xs, np.full(ns, 300.0)], axis=1)
+    mt_true = np.tile(np.array([[1e6, 0.75e6, 0.0]]), (ns, 1))
+    wav_true = np.tile(ricker(f0, nt, dt)[None], (ns, 1))
+    rng = np.random.default_rng(seed)
+    amp = rng.uniform(0.9, 1.1, ns)
+    shift = rng.uniform(-2e-4, 2e-4, ns)
+    theta = np.deg2rad(rng.uniform(-15.0, 15.0, ns))
+    mt = np.array([rotate_mt(*(amp[s] * mt_true[s]), theta[s]) for s in range(ns)])
+    wav = np.stack([ricker(f0, nt, dt, shift=shift[s]) for s in range(ns)])
+    ch, t = horizontal_fibre(1000.0 - 0.25 * nch, nch, 0.5, 340.0)
+    tr_ptr, chs, ts = same_traces_per_shot(ns, ch, t)
+    acq = Acquisition(nx=nx, nz=nz, dx=dx, dz=dx, nt=nt, dt=dt, src_xz=src, mt=mt, wavelet=wav,
+                      tr_ptr=tr_ptr, ch_xz=chs, ch_t=ts, gauge=10.0,
+                      ref_vp=vp, ref_vs=vs, ref_rho=rho, pml_f0=f0)
+    bump = gaussian_bump(nx, nz, 2000, 600, 80, 20)
+    return Problem("full_iteration_4000x1200", acq, extend_view(vp, ns), extend_view(vs, ns), extend_view(rho, ns),
+                   true_vp=vp * (1 + 0.04 * bump), true_vs=vs * (1 + 0.06 * bump), true_rho=rho.copy(),
+                   zoi=default_zoi(acq, taper_m=50.0, sink_ax=12.0, sink_az=6.0), eta=(1e-3, 1e-3, 1e-3),
+                   meta={"true_mt": mt_true, "true_wavelet": wav_true, "amplitude": amp, "shift_s": shift,
+                         "rotation_rad": theta})
+
+
+def shot_subset(p: Problem, shots) -> Problem:
+    """The problem restricted to the given shots (their traces, windows and
+    extended-model components)."""
+    a = p.acq
+    shots = [int(s) for s in shots]
+    ptr, idx = [0], []
+    for s in shots:
+        lo, hi = int(a.tr_ptr[s]), int(a.tr_ptr[s + 1])
+        idx.extend(range(lo, hi))
+        ptr.append(ptr[-1] + hi - lo)
+    idx = np.asarray(idx, np.int64)
+    sel = lambda v: None if v is None else np.asarray(v)[shots]
+    acq = replace(a, src_xz=a.src_xz[shots], mt=a.mt[shots], wavelet=np.asarray(a.wavelet)[shots],
+                  tr_ptr=np.asarray(ptr, np.int32), ch_xz=a.ch_xz[idx].reshape(-1, 2), ch_t=a.ch_t[idx].reshape(-1, 2),
+                  win=sel(a.win), force=sel(a.force))
+    meta = dict(p.meta)
+    meta["shots"] = shots
+    meta["traces"] = idx
+    for k in ("true_mt", "true_wavelet"):
+        if k in meta:
+            meta[k] = np.asarray(meta[k])[shots]
+    zoi = None
+    if p.zoi is not None:
+        z = p.zoi
+        zoi = replace(z, active_x=z.active_x[shots], taper=z.taper[shots], sink_xz=z.sink_xz[shots],
+                      sink_ax=z.sink_ax[shots], sink_az=z.sink_az[shots])
+    return replace(p, acq=acq, vp=p.vp[shots], vs=p.vs[shots], rho=p.rho[shots], zoi=zoi, meta=meta)
+
+
+def oracle_window(p: Problem, shot: int, x0: int, w: int) -> Problem:
+    """One shot of p on the cropped window [x0, x0 + w) of its grid, keeping
+    only the traces whose gauge ends lie inside it: an early-time stand-in for
+    the full grid (identical until waves reach the window's edge)."""
+    q = shot_subset(p, [shot])
+    a = q.acq
+    half = 0.5 * a.gauge * a.ch_t
+    ends = np.concatenate([a.ch_xz - half, a.ch_xz + half])[:, 0] / a.dx
+    ok = np.all(((ends >= x0 + 1) & (ends <= x0 + w - 2)).reshape(2, -1), axis=0)
+    idx = np.nonzero(ok)[0]
+    acq = replace(a, tr_ptr=np.array([0, len(idx)], np.int32), ch_xz=a.ch_xz[idx], ch_t=a.ch_t[idx],
+                  win=np.array([[x0, w]], np.int32))
+    meta = dict(q.meta)
+    meta["traces"] = np.asarray(q.meta["traces"])[idx]
+    return replace(q, acq=acq, meta=meta)
