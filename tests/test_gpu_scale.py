@@ -44,16 +44,18 @@ def true_model(p):
             for m in (p.true_vp, p.true_vs, p.true_rho)]
 
 
-def early_oracle_check(p, d_gpu, shot, x0, w, nsteps):
+def early_oracle_check(p, d_gpu, shot, x0, w, nsteps, own_window=False):
     """Data of shot `shot` (d_gpu: device [ntr, nt]) over its first nsteps against
-    the oracle on the window [x0, x0 + w); asserts that the waves stay inside the
-    window meanwhile and that the compared traces carry signal."""
+    the oracle on the window [x0, x0 + w); unless that window is the shot's own
+    (the GPU ran it on the same domain), asserts that the waves stay inside it
+    meanwhile.  The compared traces must carry signal."""
     o = rounded(W.oracle_window(p, shot, x0, w))
     a = o.acq
-    sx = a.src_xz[0, 0] / a.dx
-    dist = min(sx - x0, x0 + w - 1 - sx) * a.dx
-    vmax = float(np.max(o.vp[0]))
-    assert vmax * nsteps * a.dt < 0.9 * dist, "window too narrow for the compared steps"
+    if not own_window:
+        sx = a.src_xz[0, 0] / a.dx
+        dist = min(sx - x0, x0 + w - 1 - sx) * a.dx
+        vmax = float(np.max(o.vp[0]))
+        assert vmax * nsteps * a.dt < 0.9 * dist, "window too narrow for the compared steps"
     short = dataclasses.replace(a, nt=nsteps, wavelet=np.asarray(a.wavelet)[:, :nsteps + 1])
     ref = E.forward(short, o.vp, o.vs, o.rho)
     idx = torch.as_tensor(np.asarray(o.meta["traces"]), device=d_gpu.device)
@@ -79,7 +81,7 @@ def grad_outside_windows_is_zero(acq, gs):
 
 def test_uneven_windows_3000x800_full(efwi):
     """96 shots on windows 600-1800 cells wide, nt=4000, one persistent launch per
-    step: FP32 and scaled-FP16 checkpoints; the narrowest shot's first 600 steps
+    step: FP32 and scaled-FP16 checkpoints; the narrowest shot's first 500 steps
     against the oracle on the same window."""
     p = W.uneven_windows_3000x800()
     acq = p.acq
@@ -107,7 +109,7 @@ def test_uneven_windows_3000x800_full(efwi):
         assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= 2e-3
     win = acq.windows()
     s = int(np.argmin(win[:, 1]))
-    early_oracle_check(p, d, s, int(win[s, 0]), int(win[s, 1]), 600)
+    early_oracle_check(p, d, s, int(win[s, 0]), int(win[s, 1]), 500, own_window=True)
 
 
 def test_differentiation_2000x600_full(efwi):
