@@ -665,18 +665,20 @@ int efwi_autotune(efwi_plan *p) {
     const bool fixed = p->tile_x > 0 && p->tile_z > 0;
     const bool fixed_a = p->adj_tile_x > 0 && p->adj_tile_z > 0;
     std::vector<Variant> fwd, adj;
-    // EFWI_TMA_STAGES=n keeps only n-stage TMA forward variants (reproducible profiles)
-    const char *fs = getenv("EFWI_TMA_STAGES");
-    const int only_nst = fs ? atoi(fs) : 0;
+    // EFWI_TMA_STAGES=n / EFWI_TMA_VEC=v keep only n-stage / v-layout TMA forward variants
+    // (reproducible profiles, tests of one layout)
+    const char *fs = getenv("EFWI_TMA_STAGES"), *fv = getenv("EFWI_TMA_VEC");
+    const int only_nst = fs ? atoi(fs) : 0, only_vec = fv ? atoi(fv) : 0;
     for (auto &s : kShapes) {
         if (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)) continue;
         if (want == EFWI_STENCIL_AUTO || want == EFWI_STENCIL_LOADS) fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-        for (int vec = 1; vec <= 2; ++vec)
+        for (int vec = 1; vec <= 3; ++vec)
             for (int stg = 0; stg <= 1; ++stg) {
                 const int kind = vec == 1 ? EFWI_STENCIL_TMA : stg ? EFWI_STENCIL_TMA_STAGED : EFWI_STENCIL_TMA_PAIRS;
                 if (want != EFWI_STENCIL_AUTO && want != kind) continue;
                 for (int nst = 2; nst <= 4; ++nst)
-                    if ((!only_nst || nst == only_nst) && tma_shape_ok(s.tx, s.tz, nst, vec, stg))
+                    if ((!only_nst || nst == only_nst) && (!only_vec || vec == only_vec || vec == 1) &&
+                        tma_shape_ok(s.tx, s.tz, nst, vec, stg))
                         fwd.push_back({kind, s.tx, s.tz, nst, vec, stg});
             }
     }

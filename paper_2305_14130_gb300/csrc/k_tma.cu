@@ -89,7 +89,7 @@ __device__ __forceinline__ void store_fwd(const TmaFwdArgs &a, int4 tl, const fl
 
 template <int TX, int TZ, int NST, int VEC, int ST = 0>
 __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
-    static_assert(ST == 0 || VEC == 2, "output staging is implemented for cell pairs");
+    static_assert(ST == 0 || VEC >= 2, "output staging is implemented for cell pairs");
     using L = FwdLayout<TX, TZ, NST, VEC>;
     constexpr int SX = L::SX;
     extern __shared__ float4 smem_raw[];
@@ -163,14 +163,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
             float *__restrict__ ovz = a.out.vz + off;
             const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
 
-            if constexpr (VEC == 2) {
+            if constexpr (VEC >= 2) {
                 // Cell pairs (x, x+1) in halo-4 coordinates, x even: adjacent x-stencils share
                 // their inputs and every shared-memory access moves two cells.  Each cell's
                 // arithmetic is the scalar expression, term by term.
                 constexpr int NPX = (TX + 4) / 2;           // pairs per row of the velocity region
-                for (int q = tid; q < NPX * (TZ + 4); q += kThreads) {
-                    const int yy = q / NPX;
-                    const int x = 2 + 2 * (q - yy * NPX), y = 2 + yy;
+                auto vpair = [&](const int x, const int y) {
                     const int i = i0 - 4 + x, j = j0 - 4 + y;
                     const int o = y * SX + x;
                     const float2 xa = ld2(sxx + o - 2), xb = ld2(sxx + o), xc = ld2(sxx + o + 2);
@@ -243,6 +241,75 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                             ovx[c] = vx.x; ovz[c] = vz.x;
                             if (a.segx) { a.segx[off + c] = vx.x; a.segz[off + c] = vz.x; }
                         }
+                    }
+                };
+                if constexpr (VEC == 3) {
+                    // Split velocity region: every thread takes one cell pair of the tile and
+                    // at most one single cell of the 2-cell halo ring (rows 2, 3, TZ+4, TZ+5
+                    // over the full width, columns 2, 3, TX+4, TX+5 in between), so no thread
+                    // waits at the barrier below for a second round of pairs.  A ring cell is
+                    // never owned: its velocity is only staged for the stress sub-step.
+                    auto vcell = [&](const int x, const int y) {
+                        const int i = i0 - 4 + x, j = j0 - 4 + y;
+                        const int o = y * SX + x;
+                        float vx = 0.f, vz = 0.f;
+                        if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
+                            float e1 = (C1 * (sxx[o + 1] - sxx[o]) + C2 * (sxx[o + 2] - sxx[o - 1])) * rdx;
+                            float e2 = (C1 * (sxz[o] - sxz[o - SX]) + C2 * (sxz[o + SX] - sxz[o - 2 * SX])) * rdz;
+                            float e3 = (C1 * (sxz[o] - sxz[o - 1]) + C2 * (sxz[o + 1] - sxz[o - 2])) * rdx;
+                            float e4 = (C1 * (szz[o + SX] - szz[o]) + C2 * (szz[o + 2 * SX] - szz[o - SX])) * rdz;
+                            if (edge) {
+                                const int xs = i < P ? i : (i >= NX - P ? i - NX + 2 * P : -1);
+                                const int zs = j < P ? j : (j >= NZ - P ? j - NZ + 2 * P : -1);
+                                if (xs >= 0) {
+                                    const long long kk = psx + (long long)j * 2 * P + xs;
+                                    const int pq = profx + i;
+                                    e1 += a.pml.bx_h[pq] * a.pml.x[0][kk] + a.pml.ax_h[pq] * e1;
+                                    e3 += a.pml.bx_i[pq] * a.pml.x[1][kk] + a.pml.ax_i[pq] * e3;
+                                }
+                                if (zs >= 0) {
+                                    const long long kk = psz + (long long)zs * NX + i;
+                                    e2 += a.pml.bz_i[j] * a.pml.z[0][kk] + a.pml.az_i[j] * e2;
+                                    e4 += a.pml.bz_h[j] * a.pml.z[1][kk] + a.pml.az_h[j] * e4;
+                                }
+                            }
+                            vx = svx[o] + dt * sbx[o] * (e1 + e2);
+                            vz = svz[o] + dt * sbz[o] * (e3 + e4);
+                            if (tl.w & 8) {          // vector force of this shot (k_force's expression)
+                                const int lc = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                                const float wvn = a.wv[(long long)tl.x * a.nt + a.n];
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    if (lc == sp->inj_vx[k]) vx = vx + dt * sbx[o] * (sp->fx * wvn * sp->inj_vxw[k]);
+                                    if (lc == sp->inj_vz[k]) vz = vz + dt * sbz[o] * (sp->fz * wvn * sp->inj_vzw[k]);
+                                }
+                            }
+                        }
+                        svx[o] = vx;
+                        svz[o] = vz;
+                    };
+                    constexpr int RW = TX + 4, NRING = 4 * RW + 4 * TZ;
+                    for (int q = tid; q < NRING; q += kThreads) {
+                        int x, y;
+                        if (q < 4 * RW) {
+                            const int r = q / RW;                   // ring rows 2, 3, TZ+4, TZ+5
+                            x = 2 + (q - r * RW);
+                            y = r < 2 ? 2 + r : TZ + 2 + r;
+                        } else {
+                            const int r = q - 4 * RW, c = r & 3;   // columns 2, 3, TX+4, TX+5
+                            y = 4 + (r >> 2);
+                            x = c < 2 ? 2 + c : TX + 2 + c;
+                        }
+                        vcell(x, y);
+                    }
+                    for (int q = tid; q < (TX / 2) * TZ; q += kThreads) {
+                        const int yy = q / (TX / 2);
+                        vpair(4 + 2 * (q - yy * (TX / 2)), 4 + yy);
+                    }
+                } else {
+                    for (int q = tid; q < NPX * (TZ + 4); q += kThreads) {
+                        const int yy = q / NPX;
+                        vpair(2 + 2 * (q - yy * NPX), 2 + yy);
                     }
                 }
                 __syncthreads();
@@ -501,12 +568,13 @@ int occupancy() {
     return nb;
 }
 
-// compiled TMA variants: tile shape x pipeline stages x cells per thread (1 or 2) x
+// compiled TMA variants: tile shape x pipeline stages x cells per thread (1, 2, or 3 = cell
+// pairs with the velocity halo ring split into single cells) x
 // output staging (0: per-thread global stores, 1: shared memory + bulk tensor stores)
 #define EFWI_TMA_VARIANTS(X)                                                                             \
     X(32, 8, 2, 1, 0) X(32, 8, 3, 1, 0) X(32, 16, 2, 1, 0) X(64, 8, 2, 1, 0) X(64, 16, 2, 1, 0)          \
     X(32, 8, 2, 2, 0) X(32, 8, 3, 2, 0) X(32, 16, 2, 2, 0) X(32, 16, 3, 2, 0) X(64, 8, 2, 2, 0)          \
-    X(64, 16, 2, 2, 0) X(32, 16, 2, 2, 1)
+    X(64, 16, 2, 2, 0) X(32, 16, 2, 2, 1) X(32, 16, 2, 3, 0) X(32, 16, 2, 3, 1)
 
 }  // namespace
 

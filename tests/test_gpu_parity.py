@@ -309,11 +309,11 @@ SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16), (32, 32), (128, 8), (64, 32)]
 TMA_SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16)]
 STAGED_SHAPES = [(32, 16)]
 VARIANTS = [("loads", s) for s in SHAPES] + [(k, s) for k in ("tma", "tma_pairs") for s in TMA_SHAPES] + \
-    [("tma_staged", s) for s in STAGED_SHAPES]
+    [("tma_staged", s) for s in STAGED_SHAPES] + [("tma_pairs:split", (32, 16)), ("tma_staged:split", (32, 16))]
 
 
 @pytest.mark.parametrize("source", ["moment_tensor", "force"])
-def test_stencil_variants_do_not_change_results(efwi, source):
+def test_stencil_variants_do_not_change_results(efwi, source, monkeypatch):
     """The autotuner's choice changes only the work decomposition and the
     shared-memory staging: every compiled variant (per-thread loads or TMA,
     every tile shape) gives bitwise-identical data and gradients (uneven
@@ -326,6 +326,12 @@ def test_stencil_variants_do_not_change_results(efwi, source):
     args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
     ref = None
     for stencil, (tx, tz) in VARIANTS:
+        # ":split": cell pairs on the tile, the velocity halo ring as single cells
+        stencil, _, layout = stencil.partition(":")
+        if layout == "split":
+            monkeypatch.setenv("EFWI_TMA_VEC", "3")
+        else:
+            monkeypatch.delenv("EFWI_TMA_VEC", raising=False)
         plan = efwi.Plan(p.acq, exec="batched", tile=(tx, tz), stencil=stencil)
         info = plan.info()
         assert (info["tile_x"], info["tile_z"]) == (tx, tz)
@@ -341,7 +347,7 @@ def test_stencil_variants_do_not_change_results(efwi, source):
                 assert torch.equal(a, b), (stencil, tx, tz)
 
 
-def test_tma_full_size_matches_loads(efwi):
+def test_tma_full_size_matches_loads(efwi, monkeypatch):
     """1000x300 grid, 32 shots, 300 steps: the TMA-staged forward and adjoint
     steps and the per-thread-load ones give bitwise-identical data, misfit and
     gradients (checkpoint recompute included)."""
@@ -353,7 +359,10 @@ def test_tma_full_size_matches_loads(efwi):
     m = (dev(p.vp), dev(p.vs), dev(p.rho))
     outs = []
     d_obs = torch.zeros((acq.ntr, acq.nt), device="cuda")
-    for stencil in ("loads", "tma", "tma_pairs", "tma_staged"):
+    for stencil in ("loads", "tma", "tma_pairs", "tma_staged", "tma_pairs:split"):
+        stencil, _, layout = stencil.partition(":")
+        if layout == "split":
+            monkeypatch.setenv("EFWI_TMA_VEC", "3")
         plan = efwi.Plan(acq, exec="batched", stencil=stencil, ckpt_interval=30)
         outs.append([t.clone() for t in plan.gradient(*m, d_obs, return_data=True)])
         plan.sync_status()
