@@ -136,9 +136,10 @@ KERNELS = {
 # DRAM traffic per padded cell of one launch, from the ncu captures summarised in
 # profiles/ (8-shot case, same kernel variant; scaled to a launch by its cells).
 # Keyed by (kernel, staging, tile); any other variant reports traffic null.
+# Forward keys carry the TMA layout (cells per thread, halo ring split) and the store mode.
 TRAFFIC_PER_CELL = {
-    ("step", 3, 32, 16): 54.86,   # TMA, cell pairs, 32x16 (profiles/k_step_tma_guided_wave_8shots.md)
-    ("adj", 1, 32, 16): 96.05,    # per-thread loads, 32x16 (profiles/k_adj_fused_guided_wave_8shots.md)
+    ("step", 3, 32, 16, 2, 0): 54.86,   # TMA, cell pairs, 32x16 (earlier capture of the pair layout)
+    ("adj", 1, 32, 16): 96.05,          # per-thread loads, 32x16 (profiles/k_adj_fused_guided_wave_8shots.md)
 }
 
 
@@ -158,6 +159,8 @@ def roofline(exec_, info, prof, nt, ns):
             tile = (info["tile_x"], info["tile_z"]) if k == "step" else (info["adj_tile_x"], info["adj_tile_z"])
             staging = {1: "per-thread loads", 2: "TMA", 3: "TMA, cell pairs",
                        4: "TMA, cell pairs, staged stores"}.get(kind, "?")
+            if k == "step" and kind >= 2 and info["layout"] == 3:
+                staging += ", halo ring as single cells"
             name = f"{name.split(' ')[0]} [{staging}, tile {tile[0]}x{tile[1]}] {' '.join(name.split(' ')[1:])}"
         avg = ms / n / 1e3
         achieved = bpc * cells / avg / 1e9
@@ -166,6 +169,8 @@ def roofline(exec_, info, prof, nt, ns):
             key = (k, info["stencil"] if k == "step" else info["adj_stencil"],
                    info["tile_x"] if k == "step" else info["adj_tile_x"],
                    info["tile_z"] if k == "step" else info["adj_tile_z"])
+            if k == "step" and info["stencil"] >= 2:
+                key = key + (info["layout"], info["staged_stores"])
             if key in TRAFFIC_PER_CELL:
                 traffic = TRAFFIC_PER_CELL[key] * cells
         out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -367,7 +372,7 @@ def run_ours(args):
                 "config": {"workload": WORKLOAD, "exec": args.exec, "ckpt_store": args.ckpt_store,
                            "ckpt_interval": info["ckpt_interval"], "tile": [info["tile_x"], info["tile_z"]],
                            "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
-                           "stencil": {1: "loads", 2: "tma", 3: "tma_pairs", 4: "tma_staged"}.get(info["stencil"], "?"), "stages": info["stages"],
+                           "stencil": {1: "loads", 2: "tma", 3: "tma_pairs", 4: "tma_staged"}.get(info["stencil"], "?"), "stages": info["stages"], "layout": info["layout"],
                            "adj_stencil": {1: "loads", 2: "tma"}.get(info["adj_stencil"], "?"),
                            "adj_stages": info["adj_stages"],
                            "overlap_blocks_per_sm": [info["overlap_fwd_blocks"], info["overlap_adj_blocks"]],

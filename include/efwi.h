@@ -181,6 +181,10 @@ typedef struct efwi_plan_info_t {
     long long padded_cells;     /* sum over shots of padded (nx_w + 2P)(nz + 2P) */
     long long physical_cells;   /* sum over shots of window width * nz */
     long long launches;         /* kernels launched by the last forward/gradient call */
+    int layout;                 /* TMA forward step: cells per thread and shared-memory access
+                                   (1, 2 = cell pairs, 3 = pairs on the tile and single cells
+                                   on the velocity halo ring); 0 otherwise */
+    int staged_stores;          /* TMA forward step writes its outputs by bulk tensor stores */
 } efwi_plan_info_t;
 
 /* Zone-of-influence description (eq. 10), host memory.  Per source s:

@@ -537,6 +537,8 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->padded_cells = p->padded_cells;
     info->physical_cells = p->physical_cells;
     info->launches = p->launches;
+    info->layout = p->stencil >= EFWI_STENCIL_TMA ? p->tma_vec : 0;
+    info->staged_stores = p->stencil >= EFWI_STENCIL_TMA ? p->tma_store : 0;
     return EFWI_OK;
 }
 
