@@ -139,6 +139,7 @@ KERNELS = {
 # Forward keys carry the TMA layout (cells per thread, halo ring split) and the store mode.
 TRAFFIC_PER_CELL = {
     ("step", 3, 32, 16, 2, 0): 54.86,   # TMA, cell pairs, 32x16 (earlier capture of the pair layout)
+    ("step", 3, 32, 16, 3, 0): 55.05,   # TMA, split layout, 32x16 (profiles/k_step_tma_guided_wave_8shots.md)
     ("adj", 1, 32, 16): 96.05,          # per-thread loads, 32x16 (profiles/k_adj_fused_guided_wave_8shots.md)
 }
 
