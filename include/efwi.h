@@ -260,6 +260,16 @@ int efwi_regularization_grad(efwi_plan *plan, const float *m, const float *b, co
                              const uint8_t *sink, double eta, double *phi_reg, float *g,
                              efwi_stream_t stream);
 
+/* efwi_regularization_grad over ns components instead of the plan's shots
+ * (m, b, bp, sink: device [ns][nz][nx] on the plan's grid).  The plan lends
+ * only its grid and reduction scratch, so a plan made for one group of shots
+ * evaluates the consistency term (eqs. 8, 11, 12) of every component when the
+ * extended problem runs in shot groups that do not fit one plan together.
+ * EFWI_ERR_ARG for ns < 1; the rest as efwi_regularization_grad.            */
+int efwi_regularization_grad_n(efwi_plan *plan, int ns, const float *m, const float *b, const float *bp,
+                               const uint8_t *sink, double eta, double *phi_reg, float *g,
+                               efwi_stream_t stream);
+
 /* Allocation-free variant of efwi_regularization_grad (no counterpart in the
  * paper; it exists for callers that cannot let a library allocate device
  * memory, e.g. applications that own all device memory through their own

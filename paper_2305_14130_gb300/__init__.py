@@ -173,7 +173,22 @@ class Plan:
         return (phi, *out, dmod) if return_data else (phi, *out)
 
     def regularization_grad(self, m, b, bp, sink, eta, g=None):
-        """phi_reg (device float64) and g += eta^2 A^T A m for one parameter field."""
+        """phi_reg (device float64) and g += eta^2 A^T A m for one parameter field.
+
+        m may hold any number of components [ns', nz, nx] on the plan's grid (for
+        shot groups: every component of the extended problem, evaluated with the
+        plan of one group)."""
+        ns = m.shape[0] if m.dim() == 3 else self.ns
+        if ns != self.ns:
+            n = ns * self.nz * self.nx
+            if g is None:
+                g = torch.zeros_like(m)
+            phi = torch.empty((), dtype=torch.float64, device=m.device)
+            self._check(self._lib.efwi_regularization_grad_n(
+                self._h, int(ns), _ptr(m, "m", n), _ptr(b, "b", n), _ptr(bp, "bp", n),
+                _ptr(sink, "sink", n, torch.uint8), float(eta), _ptr(phi, "phi", 1, torch.float64),
+                _ptr(g, "g", n), _stream()))
+            return phi, g
         n = self.model_numel
         if g is None:
             g = torch.zeros_like(m)

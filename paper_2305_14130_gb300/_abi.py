@@ -66,6 +66,7 @@ SIGNATURES = {
     "efwi_zoi_weights": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.POINTER(ZoiDesc),
                                    VP, VP, VP, VP]),
     "efwi_regularization_grad": (C.c_int, [VP, VP, VP, VP, VP, C.c_double, VP, VP, VP]),
+    "efwi_regularization_grad_n": (C.c_int, [VP, C.c_int, VP, VP, VP, VP, C.c_double, VP, VP, VP]),
     "efwi_collapse": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, VP, VP]),
     "efwi_lbfgs_create": (C.c_int, [C.POINTER(VP), C.c_longlong, C.c_int, C.c_double, C.c_double, C.c_int]),
     "efwi_lbfgs_destroy": (C.c_int, [VP]),

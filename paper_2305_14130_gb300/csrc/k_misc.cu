@@ -581,9 +581,9 @@ void launch_collapse(int ns, long long npix, const float *x, const float *b, con
 }
 
 void launch_reg(efwi_plan *p, const float *m, const float *b, const float *bp, const uint8_t *sink, double eta,
-                double *phi, float *g, int accumulate_phi, cudaStream_t st) {
+                double *phi, float *g, int accumulate_phi, cudaStream_t st, int ns) {
     const long long npix = (long long)p->d.nz * p->d.nx;
-    k_reg<<<kPartials, kRedThreads, 0, st>>>(m, b, bp, sink, p->d.ns, npix, eta * eta, g, p->partial);
+    k_reg<<<kPartials, kRedThreads, 0, st>>>(m, b, bp, sink, ns > 0 ? ns : p->d.ns, npix, eta * eta, g, p->partial);
     k_final_sum<<<1, 1024, 0, st>>>(p->partial, kPartials, 0.5 * eta * eta, phi, accumulate_phi);
     p->launches += 2;
 }

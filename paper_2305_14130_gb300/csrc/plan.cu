@@ -599,6 +599,19 @@ extern "C" int efwi_collapse(int ns, int nx, int nz, const float *x, const float
     return EFWI_OK;
 }
 
+extern "C" int efwi_regularization_grad_n(efwi_plan *p, int ns, const float *m, const float *b, const float *bp,
+                                          const uint8_t *sink, double eta, double *phi_reg, float *g,
+                                          efwi_stream_t stream) {
+    if (!p) return fail(nullptr, EFWI_ERR_ARG, "plan is NULL");
+    if (ns < 1) return fail(p, EFWI_ERR_ARG, "ns must be >= 1");
+    if (!m || !b || !bp || !sink || !phi_reg || !g) return fail(p, EFWI_ERR_ARG, "NULL device pointer");
+    if (!std::isfinite(eta)) return fail(p, EFWI_ERR_ARG, "eta must be finite");
+    launch_reg(p, m, b, bp, sink, eta, phi_reg, g, 0, (cudaStream_t)stream, ns);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(p, EFWI_ERR_CUDA, cudaGetErrorString(e));
+    return EFWI_OK;
+}
+
 extern "C" int efwi_regularization_grad(efwi_plan *p, const float *m, const float *b, const float *bp,
                                         const uint8_t *sink, double eta, double *phi_reg, float *g,
                                         efwi_stream_t stream) {

@@ -158,8 +158,9 @@ int launch_zoi(int ns, int nx, int nz, double dx, double dz, const efwi_zoi_desc
                uint8_t *sink, cudaStream_t st, std::string &err);
 void launch_collapse(int ns, long long npix, const float *x, const float *b, const float *bp, const uint8_t *sink,
                      float *out, cudaStream_t st);
+// ns > 0: the arrays hold ns components (default: the plan's shots)
 void launch_reg(efwi_plan *p, const float *m, const float *b, const float *bp, const uint8_t *sink, double eta,
-                double *phi, float *g, int accumulate_phi, cudaStream_t st);
+                double *phi, float *g, int accumulate_phi, cudaStream_t st, int ns = 0);
 
 // --- k_hessian.cu --------------------------------------------------------------
 void launch_vel_energy(efwi_plan *p, Fields F, double *acc, cudaStream_t st);

@@ -227,6 +227,25 @@ def test_regularization_parity(efwi, ns):
     plan.close()
 
 
+def test_regularization_of_more_components_than_the_plan_has(efwi):
+    """efwi_regularization_grad_n: a 2-shot plan evaluates the consistency term of
+    7 components on its grid (the shot-group case) against the oracle."""
+    rng = np.random.default_rng(17)
+    nz, nx, nc = 23, 37, 7
+    plan = efwi.Plan(rounded(W.tiny(nx=nx, nz=nz, ns=2, nt=10, npml=3)).acq, exec="batched")
+    p7 = W.tiny(nx=nx, nz=nz, ns=nc, nt=10, npml=3)
+    bo, bpo, sinko = X.zoi_weights(p7.zoi, nx, nz, p7.acq.dx, p7.acq.dz)
+    bo, bpo = f32(bo), f32(bpo)
+    m = f32(3000 + 100 * rng.standard_normal((nc, nz, nx)))
+    eta = 0.21
+    phi_o, g_o = X.regularization(m, bo, bpo, sinko, eta)
+    phi, g = plan.regularization_grad(dev(m), dev(bo), dev(bpo), dev(sinko, np.uint8), eta)
+    torch.cuda.synchronize()
+    assert abs(phi.item() - phi_o) <= 1e-10 * phi_o
+    assert rel_l2(g.cpu().numpy(), g_o) <= 1e-5
+    plan.close()
+
+
 @pytest.mark.parametrize("ns", [1, 2, 5])
 def test_collapse_parity(efwi, ns):
     """S_w W x~ (eq. 9 on a model, eq. 15 on per-source gradients) against the

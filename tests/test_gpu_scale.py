@@ -169,9 +169,10 @@ def test_full_iteration_4000x1200_group(efwi):
     4000x1200 full-iteration workload, nt=8000, FP16 checkpoints: observed data
     from the true model and the error-free sources, modelled with the seeded
     source errors.  Data-term gradient (sampled oracle check of one shot), the
-    consistency-term gradient of the group's components (sampled pixels against
-    the oracle, phi_reg = 1/2 <g_reg, m~>), and an l-BFGS update at the full
-    vector length (3 x 8 x 4.8 M) against the oracle's two-loop recursion."""
+    consistency-term gradient of all 128 components evaluated with the group's
+    plan (sampled pixels against the oracle, phi_reg = 1/2 <g_reg, m~>), and an
+    l-BFGS update at the group's full vector length (3 x 8 x 4.8 M) against the
+    oracle's two-loop recursion."""
     from oracle import extension as X
     from oracle import lbfgs as L
     from paper_2305_14130_gb300.optim import LBFGS
@@ -197,25 +198,28 @@ def test_full_iteration_4000x1200_group(efwi):
     early_oracle_check(g, d, 4, 1700, 600, 500)
     del d
 
-    # consistency term on a perturbed extension (1 % seeded noise per component)
-    ns, nz, nx = g.acq.ns, g.acq.nz, g.acq.nx
-    rng = np.random.default_rng(5)
-    mvp = (np.asarray(g.vp, np.float32) * (1 + 0.01 * rng.standard_normal((ns, nz, nx)))).astype(np.float32)
-    b, bp, sink = efwi.zoi_weights(ns, nx, nz, g.acq.dx, g.acq.dz, g.zoi)
+    # consistency term of all 128 components of the extended problem (1 % seeded noise per
+    # component), evaluated with this group's plan on the full grid
+    nsall, nz, nx = p.acq.ns, p.acq.nz, p.acq.nx
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    base = dev(p.vp[0])
+    mall = base[None] * (1 + 0.01 * torch.randn((nsall, nz, nx), device="cuda", generator=gen))
+    b, bp, sink = efwi.zoi_weights(nsall, nx, nz, p.acq.dx, p.acq.dz, p.zoi)
     eta = 1e-3
-    phi_r, g_r = plan.regularization_grad(dev(mvp), b, bp, sink, eta)
+    phi_r, g_r = plan.regularization_grad(mall, b, bp, sink, eta)
     phi_r = float(phi_r.item())
-    half_dot = 0.5 * float(torch.sum(g_r.double() * dev(mvp).double()))
+    half_dot = 0.5 * float(torch.sum(g_r.double() * mall.double()))
     assert phi_r > 0 and half_dot == pytest.approx(phi_r, rel=1e-4)
-    src = np.rint(g.acq.src_xz / g.acq.dx).astype(int)
-    pix = [(int(src[s, 1]) + dz, int(src[s, 0]) + dx) for s in range(ns) for dz in (-3, 0, 2) for dx in (-5, 0, 7)]
+    rng = np.random.default_rng(5)
+    src = np.rint(p.acq.src_xz / p.acq.dx).astype(int)
+    pix = [(int(src[s, 1]) + dz, int(src[s, 0]) + dx) for s in range(0, nsall, 9) for dz in (-3, 0, 2)
+           for dx in (-5, 0, 7)]
     pix += [(int(v), int(u)) for v, u in zip(rng.integers(0, nz, 40), rng.integers(0, nx, 40))]
-    jj, ii = np.array(pix).T
-    bo, bpo, sinko = X.zoi_weights(g.zoi, nx, nz, g.acq.dx, g.acq.dz)
-    sub = lambda a: np.asarray(a)[:, jj, ii][:, None, :]
-    _, g_ref = X.regularization(sub(mvp).astype(np.float64), sub(bo), sub(bpo), sub(sinko), eta)
-    assert rel_l2(g_r[:, jj, ii].double().cpu().numpy(), g_ref[:, 0, :]) <= TOL
-    del g_r
+    jj, ii = (torch.as_tensor(a, device="cuda") for a in np.array(pix).T)
+    sub = lambda t, dt=np.float64: t[:, jj, ii].cpu().numpy().astype(dt)[:, None, :]
+    _, g_ref = X.regularization(sub(mall), sub(b), sub(bp), sub(sink, np.uint8), eta)
+    assert rel_l2(sub(g_r)[:, 0, :], g_ref[:, 0, :]) <= TOL
+    del mall, b, bp, sink, g_r
 
     # l-BFGS update at the full vector length: a short steepest-descent step of the
     # data term (largest model change 0.05 m/s), the pair it gives, the new direction
