@@ -207,8 +207,10 @@ struct AdjArgsF {
     float dt, rdx, rdz;
 };
 
-template <int TX, int TZ>
-__global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(AdjArgsF a) {
+// MINB > 0 caps the registers for MINB resident CTAs per SM (the default keeps 4 for
+// tiles up to 512 cells)
+template <int TX, int TZ, int MINB = 0>
+__global__ void __launch_bounds__(kThreads, MINB ? MINB : (TX * TZ <= 512 ? 4 : 2)) k_adj_fused(AdjArgsF a) {
     constexpr int SX = TX + 8, SZ = TZ + 8;
     constexpr int VX = TX + 4, VZ = TZ + 4;
     extern __shared__ float4 smem4[];
@@ -459,6 +461,7 @@ void set_all_attrs() {
     if (done) return;
     done = true;
     set_attrs<32, 8>(); set_attrs<32, 16>(); set_attrs<64, 8>(); set_attrs<64, 16>();
+    cudaFuncSetAttribute(k_adj_fused<32, 16, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem(32, 16));
     set_attrs<32, 32>(); set_attrs<128, 8>(); set_attrs<64, 32>();
 }
 
@@ -598,7 +601,10 @@ void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, c
     } else {
         AdjArgsF a = adj_args_f(p, vfx, vfz);
         const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles) : a.ntiles;
-        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
+        if (p->adj_minb == 5 && p->adj_tiles.tx == 32 && p->adj_tiles.tz == 16)
+            k_adj_fused<32, 16, 5><<<grid, kThreads, adj_smem(32, 16), st>>>(a);
+        else
+            EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
     }
     prof_end(p, st, slot);
     p->launches++;
@@ -640,6 +646,7 @@ float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEv
 
 int select_adj(efwi_plan *p, const Variant &v) {
     p->adj_stencil = v.kind;
+    p->adj_minb = v.kind == EFWI_STENCIL_LOADS ? v.nst : 0;   // loads: nst holds the CTA-per-SM cap (0 = 4)
     int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
     if (!rc && v.kind == EFWI_STENCIL_TMA) rc = tma_prepare_adj(p, v.tx, v.tz, v.nst);
     p->adj_tile_x = v.tx;
@@ -688,7 +695,14 @@ int efwi_autotune(efwi_plan *p) {
         if (fixed_a ? (s.tx != p->adj_tile_x || s.tz != p->adj_tile_z)
                     : (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)))
             continue;
-        if (wa == EFWI_STENCIL_AUTO || wa == EFWI_STENCIL_LOADS) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        if (wa == EFWI_STENCIL_AUTO || wa == EFWI_STENCIL_LOADS) {
+            // EFWI_ADJ_MINB=0 or 5 keeps only that register cap (tests of one variant)
+            const char *fm = getenv("EFWI_ADJ_MINB");
+            const int only_minb = fm ? atoi(fm) : -1;
+            if (only_minb <= 0) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+            if (s.tx == 32 && s.tz == 16 && (only_minb < 0 || only_minb == 5))
+                adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 5});   // 5 CTAs/SM
+        }
         for (int nst = 1; nst <= 2; ++nst)
             if (wa != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
                 adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, nst});
