@@ -231,7 +231,7 @@ def test_full_iteration_4000x1200_group(efwi):
     assert torch.equal(d0, -g0)
     a = 0.05 / float(d0.abs().max())
     x1 = x + a * d0
-    shape = (3, ns, nz, nx)
+    shape = (3, g.acq.ns, nz, nx)
     xv = x1.view(shape)
     g1 = torch.empty_like(x)
     gv = g1.view(shape)
