@@ -220,14 +220,27 @@ __global__ void __launch_bounds__(kThreads, MINB ? MINB : (TX * TZ <= 512 ? 4 : 
     float *vfxs = e4s + VX * VZ, *vfzs = vfxs + VX * VZ;   // forward v^{n+1/2} on the tile + 2-cell halo
     const int tid = threadIdx.x;
 
+    // With a persistent grid (fewer CTAs than tiles) the next tile's work item, and
+    // the block offset and row pitch of its shot, are loaded one tile ahead, so an
+    // interior tile issues its first global loads without a dependent load in front.
+    int4 tl_next = blockIdx.x < a.ntiles ? __ldg(a.tiles + blockIdx.x) : make_int4(0, 0, 0, 0);
+    long long off_next = __ldg(&a.shots[tl_next.x].off);
+    int pitch_next = __ldg(&a.shots[tl_next.x].pitch);
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        const int4 tl = a.tiles[t];
+        const int4 tl = tl_next;
+        const long long off = off_next;
+        const int pitch = pitch_next;
+        if (t + gridDim.x < a.ntiles) {
+            tl_next = __ldg(a.tiles + t + gridDim.x);
+            off_next = __ldg(&a.shots[tl_next.x].off);
+            pitch_next = __ldg(&a.shots[tl_next.x].pitch);
+        }
         // interior tiles (no CPML strip or grid edge within the 4-cell halo) run a
         // copy of the body without any of the edge tests
         auto tile = [&](auto edge_c) {
             const ShotDev *sp = a.shots + tl.x;
-            const int NX = sp->NX, NZ = sp->NZ, PP = sp->P, profx = sp->profx, pitch = sp->pitch, w = sp->w;
-            const long long off = sp->off, psx = sp->psx, psz = sp->psz;
+            const int NX = sp->NX, NZ = sp->NZ, PP = sp->P, profx = sp->profx, w = sp->w;
+            const long long psx = sp->psx, psz = sp->psz;
             constexpr bool edge = decltype(edge_c)::value;   // 4-cell halo touches a strip or the grid edge
             const int i0 = tl.y, j0 = tl.z;
             const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
@@ -600,7 +613,9 @@ void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, c
         launch_adj_tma(p, vfx, st);
     } else {
         AdjArgsF a = adj_args_f(p, vfx, vfz);
-        const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles) : a.ntiles;
+        const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles)
+                         : p->adj_grid > 0        ? std::min(p->adj_grid, a.ntiles)
+                                                  : a.ntiles;
         if (p->adj_minb == 5 && p->adj_tiles.tx == 32 && p->adj_tiles.tz == 16)
             k_adj_fused<32, 16, 5><<<grid, kThreads, adj_smem(32, 16), st>>>(a);
         else
@@ -647,6 +662,15 @@ float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEv
 int select_adj(efwi_plan *p, const Variant &v) {
     p->adj_stencil = v.kind;
     p->adj_minb = v.kind == EFWI_STENCIL_LOADS ? v.nst : 0;   // loads: nst holds the CTA-per-SM cap (0 = 4)
+    p->adj_grid = 0;
+    if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2) {         // loads: vec 2 = persistent grid
+        int nb = 0;
+        if (p->adj_minb == 5)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16, 5>, kThreads, adj_smem(32, 16));
+        else if (v.tx == 32 && v.tz == 16)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
+        p->adj_grid = std::max(1, nb) * p->n_sms;
+    }
     int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
     if (!rc && v.kind == EFWI_STENCIL_TMA) rc = tma_prepare_adj(p, v.tx, v.tz, v.nst);
     p->adj_tile_x = v.tx;
@@ -696,12 +720,20 @@ int efwi_autotune(efwi_plan *p) {
                     : (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)))
             continue;
         if (wa == EFWI_STENCIL_AUTO || wa == EFWI_STENCIL_LOADS) {
-            // EFWI_ADJ_MINB=0 or 5 keeps only that register cap (tests of one variant)
-            const char *fm = getenv("EFWI_ADJ_MINB");
-            const int only_minb = fm ? atoi(fm) : -1;
-            if (only_minb <= 0) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-            if (s.tx == 32 && s.tz == 16 && (only_minb < 0 || only_minb == 5))
-                adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 5});   // 5 CTAs/SM
+            // 32x16 also as a persistent grid (next tile's descriptor loaded ahead) and with
+            // registers capped for 5 CTAs/SM; EFWI_ADJ_MINB=0|5 and EFWI_ADJ_PERSIST=0|1 keep
+            // only those (tests of one variant)
+            const char *fm = getenv("EFWI_ADJ_MINB"), *fp = getenv("EFWI_ADJ_PERSIST");
+            const int only_minb = fm ? atoi(fm) : -1, only_p = fp ? atoi(fp) : -1;
+            auto want = [&](int minb, int pers) {
+                return (only_minb < 0 || only_minb == minb) && (only_p < 0 || only_p == pers);
+            };
+            if (want(0, 0)) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+            if (s.tx == 32 && s.tz == 16) {
+                if (want(0, 1)) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
+                if (want(5, 0)) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 5});
+                if (want(5, 1)) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 5, 2});
+            }
         }
         for (int nst = 1; nst <= 2; ++nst)
             if (wa != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
@@ -742,8 +774,8 @@ int efwi_autotune(efwi_plan *p) {
         for (auto &v : adj) {
             if (select_adj(p, v)) continue;
             const float t = time_steps(p, true, st, e0, e1);
-            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d: %.1f us\n", v.kind, v.tx, v.tz,
-                             v.nst, t * 1e3f / 3);
+            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d persistent %d: %.1f us\n", v.kind,
+                             v.tx, v.tz, v.nst, v.vec == 2, t * 1e3f / 3);
             if (t < best) { best = t; ba = v; }
         }
         cudaEventDestroy(e0);
