@@ -140,7 +140,7 @@ KERNELS = {
 TRAFFIC_PER_CELL = {
     ("step", 3, 32, 16, 2, 0): 54.86,   # TMA, cell pairs, 32x16 (earlier capture of the pair layout)
     ("step", 3, 32, 16, 3, 0): 55.05,   # TMA, split layout, 32x16 (profiles/k_step_tma_guided_wave_8shots.md)
-    ("adj", 1, 32, 16): 96.05,          # per-thread loads, 32x16 (profiles/k_adj_fused_guided_wave_8shots.md)
+    ("adj", 1, 32, 16, 0): 96.05,       # per-thread loads, 32x16, one CTA per tile (profiles/k_adj_fused_guided_wave_8shots.md)
 }
 
 
@@ -162,6 +162,8 @@ def roofline(exec_, info, prof, nt, ns):
                        4: "TMA, cell pairs, staged stores"}.get(kind, "?")
             if k == "step" and kind >= 2 and info["layout"] == 3:
                 staging += ", halo ring as single cells"
+            if k == "adj" and kind == 1 and info["adj_persistent"]:
+                staging += ", persistent grid"
             name = f"{name.split(' ')[0]} [{staging}, tile {tile[0]}x{tile[1]}] {' '.join(name.split(' ')[1:])}"
         avg = ms / n / 1e3
         achieved = bpc * cells / avg / 1e9
@@ -172,6 +174,8 @@ def roofline(exec_, info, prof, nt, ns):
                    info["tile_z"] if k == "step" else info["adj_tile_z"])
             if k == "step" and info["stencil"] >= 2:
                 key = key + (info["layout"], info["staged_stores"])
+            if k == "adj" and info["adj_stencil"] == 1:
+                key = key + (info["adj_persistent"],)
             if key in TRAFFIC_PER_CELL:
                 traffic = TRAFFIC_PER_CELL[key] * cells
         out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

@@ -185,6 +185,7 @@ typedef struct efwi_plan_info_t {
                                    (1, 2 = cell pairs, 3 = pairs on the tile and single cells
                                    on the velocity halo ring); 0 otherwise */
     int staged_stores;          /* TMA forward step writes its outputs by bulk tensor stores */
+    int adj_persistent;         /* per-thread-load adjoint step runs on a persistent grid */
 } efwi_plan_info_t;
 
 /* Zone-of-influence description (eq. 10), host memory.  Per source s:

@@ -207,10 +207,8 @@ struct AdjArgsF {
     float dt, rdx, rdz;
 };
 
-// MINB > 0 caps the registers for MINB resident CTAs per SM (the default keeps 4 for
-// tiles up to 512 cells)
-template <int TX, int TZ, int MINB = 0>
-__global__ void __launch_bounds__(kThreads, MINB ? MINB : (TX * TZ <= 512 ? 4 : 2)) k_adj_fused(AdjArgsF a) {
+template <int TX, int TZ>
+__global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(AdjArgsF a) {
     constexpr int SX = TX + 8, SZ = TZ + 8;
     constexpr int VX = TX + 4, VZ = TZ + 4;
     extern __shared__ float4 smem4[];
@@ -474,7 +472,6 @@ void set_all_attrs() {
     if (done) return;
     done = true;
     set_attrs<32, 8>(); set_attrs<32, 16>(); set_attrs<64, 8>(); set_attrs<64, 16>();
-    cudaFuncSetAttribute(k_adj_fused<32, 16, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem(32, 16));
     set_attrs<32, 32>(); set_attrs<128, 8>(); set_attrs<64, 32>();
 }
 
@@ -616,10 +613,7 @@ void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, c
         const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles)
                          : p->adj_grid > 0        ? std::min(p->adj_grid, a.ntiles)
                                                   : a.ntiles;
-        if (p->adj_minb == 5 && p->adj_tiles.tx == 32 && p->adj_tiles.tz == 16)
-            k_adj_fused<32, 16, 5><<<grid, kThreads, adj_smem(32, 16), st>>>(a);
-        else
-            EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
+        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
     }
     prof_end(p, st, slot);
     p->launches++;
@@ -661,14 +655,10 @@ float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEv
 
 int select_adj(efwi_plan *p, const Variant &v) {
     p->adj_stencil = v.kind;
-    p->adj_minb = v.kind == EFWI_STENCIL_LOADS ? v.nst : 0;   // loads: nst holds the CTA-per-SM cap (0 = 4)
     p->adj_grid = 0;
-    if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2) {         // loads: vec 2 = persistent grid
+    if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2 && v.tx == 32 && v.tz == 16) {   // loads: vec 2 = persistent
         int nb = 0;
-        if (p->adj_minb == 5)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16, 5>, kThreads, adj_smem(32, 16));
-        else if (v.tx == 32 && v.tz == 16)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
         p->adj_grid = std::max(1, nb) * p->n_sms;
     }
     int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
@@ -720,20 +710,12 @@ int efwi_autotune(efwi_plan *p) {
                     : (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)))
             continue;
         if (wa == EFWI_STENCIL_AUTO || wa == EFWI_STENCIL_LOADS) {
-            // 32x16 also as a persistent grid (next tile's descriptor loaded ahead) and with
-            // registers capped for 5 CTAs/SM; EFWI_ADJ_MINB=0|5 and EFWI_ADJ_PERSIST=0|1 keep
-            // only those (tests of one variant)
-            const char *fm = getenv("EFWI_ADJ_MINB"), *fp = getenv("EFWI_ADJ_PERSIST");
-            const int only_minb = fm ? atoi(fm) : -1, only_p = fp ? atoi(fp) : -1;
-            auto want = [&](int minb, int pers) {
-                return (only_minb < 0 || only_minb == minb) && (only_p < 0 || only_p == pers);
-            };
-            if (want(0, 0)) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-            if (s.tx == 32 && s.tz == 16) {
-                if (want(0, 1)) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
-                if (want(5, 0)) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 5});
-                if (want(5, 1)) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 5, 2});
-            }
+            // 32x16 also on a persistent grid (the next tile's descriptor loaded ahead);
+            // EFWI_ADJ_PERSIST=0|1 keeps only one of the two (tests of one variant)
+            const char *fp = getenv("EFWI_ADJ_PERSIST");
+            const int only_p = fp ? atoi(fp) : -1;
+            if (only_p <= 0) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+            if (s.tx == 32 && s.tz == 16 && only_p != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
         }
         for (int nst = 1; nst <= 2; ++nst)
             if (wa != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))

@@ -539,6 +539,7 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->launches = p->launches;
     info->layout = p->stencil >= EFWI_STENCIL_TMA ? p->tma_vec : 0;
     info->staged_stores = p->stencil >= EFWI_STENCIL_TMA ? p->tma_store : 0;
+    info->adj_persistent = p->adj_stencil == EFWI_STENCIL_LOADS && p->adj_grid > 0;
     return EFWI_OK;
 }
 

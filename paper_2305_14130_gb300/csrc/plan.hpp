@@ -109,7 +109,6 @@ struct efwi_plan {
     int adj_stencil = EFWI_STENCIL_LOADS;  // staging of the adjoint step (after tuning)
     efwi::AdjMaps *adj_maps = nullptr;
     int tma_adj_grid = 0, tma_adj_stages = 1;
-    int adj_minb = 0;                      // per-thread-load adjoint: CTAs per SM of its register cap (0 = 4)
     int adj_grid = 0;                      // per-thread-load adjoint: persistent grid (0 = one CTA per tile)
     int *dev_err = nullptr;                // device flag: a bounded wait expired
     int adj_tile_x = 0, adj_tile_z = 0;    // adjoint tile
