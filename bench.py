@@ -133,14 +133,13 @@ KERNELS = {
 }
 
 
-# DRAM traffic per padded cell of one launch, from the ncu captures summarised in
-# profiles/ (8-shot case, same kernel variant; scaled to a launch by its cells).
-# Keyed by (kernel, staging, tile); any other variant reports traffic null.
-# Forward keys carry the TMA layout (cells per thread, halo ring split) and the store mode.
+# DRAM traffic per padded cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
+# captures of the 8-shot case of this workload with the same kernel variant, scaled to a launch by its
+# cells.  Keyed by (kernel, staging, tile, variant details); any other variant, or a kernel changed
+# since its capture, reports traffic null.
 TRAFFIC_PER_CELL = {
-    ("step", 3, 32, 16, 2, 0): 54.86,   # TMA, cell pairs, 32x16 (earlier capture of the pair layout)
-    ("step", 3, 32, 16, 3, 0): 55.05,   # TMA, split layout, 32x16 (profiles/k_step_tma_guided_wave_8shots.md)
-    ("adj", 1, 32, 16, 0): 96.05,       # per-thread loads, 32x16, one CTA per tile (profiles/k_adj_fused_guided_wave_8shots.md)
+    ("step", 3, 32, 16, 3, 0): 55.05,   # TMA, split layout, per-thread stores, 32x16
+    ("adj", 1, 32, 16, 1): 94.64,       # per-thread loads, persistent grid, 32x16
 }
 
 
