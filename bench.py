@@ -236,6 +236,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(ms, cells_per_rank, steps, world, device="cuda"):
+    """Whole-job figures from this rank's timed milliseconds: the time is the
+    maximum over ranks (every rank waits at the barrier for the slowest), and
+    the value counts the cell-updates of all ranks (weak scaling: each rank
+    runs its own copy of the workload).  Returns (ms, s per gradient, G/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    s = ms / 1e3 / steps
+    return ms, s, cells_per_rank * world / s / 1e9
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -302,13 +317,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     prof = {k: plan.prof_read(k) for k in ("step", "adj")}
     plan.prof_enable(0)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    s_per_grad = ms / 1e3 / args.steps
     cells = ns * acq.nx * acq.nz * acq.nt
-    value = cells * world / s_per_grad / 1e9
+    ms, s_per_grad, value = aggregate(ms, cells, args.steps, world)
     info = plan.info()
     roofs = roofline(args.exec, info, prof, acq.nt, ns)
 
