@@ -5,8 +5,9 @@ import numpy as np
 
 
 def f32(a):
-    """Round to float32 and back: the values the CUDA path actually sees."""
-    return np.asarray(a, np.float32).astype(np.float64)
+    """Round to float32 and back: the values the CUDA path actually sees (C-contiguous,
+    also for broadcast views)."""
+    return np.array(a, dtype=np.float32, order="C").astype(np.float64, order="C")
 
 
 def rounded(problem):

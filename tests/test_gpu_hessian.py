@@ -24,7 +24,7 @@ def efwi():
 
 
 def dev(a):
-    return torch.tensor(np.asarray(a, np.float32), device="cuda")
+    return torch.tensor(np.ascontiguousarray(np.asarray(a, np.float32)), device="cuda")
 
 
 CASES = {

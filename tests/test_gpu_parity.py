@@ -26,7 +26,7 @@ def efwi():
 
 
 def dev(a, dtype=np.float32):
-    return torch.tensor(np.asarray(a, dtype), device="cuda")
+    return torch.tensor(np.ascontiguousarray(np.asarray(a, dtype)), device="cuda")
 
 
 def observed(p):
