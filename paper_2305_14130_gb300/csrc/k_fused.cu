@@ -207,29 +207,15 @@ struct AdjArgsF {
     float dt, rdx, rdz;
 };
 
-// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero instead
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// PF: the stress sub-step's inputs of the tile (adjoint stresses and the three C-imaging
-// sums) are copied into shared memory with cp.async at the start of the tile, so they
-// arrive while the first two phases compute and the last phase issues no global load.
-template <int TX, int TZ, bool PF = false>
+template <int TX, int TZ>
 __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(AdjArgsF a) {
     constexpr int SX = TX + 8, SZ = TZ + 8;
     constexpr int VX = TX + 4, VZ = TZ + 4;
-    constexpr int NC = TX * TZ;
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     float *f1s = sm, *f2s = sm + SX * SZ, *f3s = sm + 2 * SX * SZ, *f4s = sm + 3 * SX * SZ;
     float *e1s = sm + 4 * SX * SZ, *e2s = e1s + VX * VZ, *e3s = e2s + VX * VZ, *e4s = e3s + VX * VZ;
     float *vfxs = e4s + VX * VZ, *vfzs = vfxs + VX * VZ;   // forward v^{n+1/2} on the tile + 2-cell halo
-    float *pfs = vfzs + VX * VZ;                          // PF: [6][TZ][TX] sxx szz sxz Glam Gmu Gmuxz
     const int tid = threadIdx.x;
 
     // With a persistent grid (fewer CTAs than tiles) the next tile's work item, and
@@ -256,30 +242,6 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
             constexpr bool edge = decltype(edge_c)::value;   // 4-cell halo touches a strip or the grid edge
             const int i0 = tl.y, j0 = tl.z;
             const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
-
-            constexpr int N3 = (TX * TZ + kThreads - 1) / kThreads;
-            if constexpr (PF) {
-                // the last phase's inputs, copied while the first two phases run (cells past
-                // the grid and imaging sums outside the physical domain are zero-filled)
-#pragma unroll
-                for (int r = 0; r < N3; ++r) {
-                    const int q = tid + r * kThreads;
-                    if (q >= NC) break;
-                    const int y = q / TX, x = q - y * TX;
-                    const int i = i0 + x, j = j0 + y;
-                    const bool in = !(edge && (i >= NX || j >= NZ));
-                    const long long c = in ? off + (j + EFWI_GZ) * pitch + (i + EFWI_GX) : off;
-                    const bool node = in && (!edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP));
-                    const bool half = in && (!edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP));
-                    cp_async4(pfs + q, a.in.sxx + c, in ? 4 : 0);
-                    cp_async4(pfs + NC + q, a.in.szz + c, in ? 4 : 0);
-                    cp_async4(pfs + 2 * NC + q, a.in.sxz + c, in ? 4 : 0);
-                    cp_async4(pfs + 3 * NC + q, a.Glam + c, node ? 4 : 0);
-                    cp_async4(pfs + 4 * NC + q, a.Gmu + c, node ? 4 : 0);
-                    cp_async4(pfs + 5 * NC + q, a.Gmuxz + c, half ? 4 : 0);
-                }
-                cp_async_commit();
-            }
 
             // Each phase first issues every global load of the thread's cells into
             // registers (no store in between, so all are in flight together), then
@@ -423,11 +385,11 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                 if (edge) { e2s[q] = h2; e4s[q] = h4; }    // e^2 == e^1, e^4 == e^3 away from the CPML
                 vfxs[q] = lfx[r]; vfzs[q] = lfz[r];
             }
-            if constexpr (PF) cp_async_wait_all();
             __syncthreads();
             const float *e2r = edge ? e2s : e1s, *e4r = edge ? e4s : e3s;
 
             // 3. sigma^ += D^T e^ on the tile, with the C-imaging
+            constexpr int N3 = (TX * TZ + kThreads - 1) / kThreads;
             float sxx_r[N3], szz_r[N3], sxz_r[N3], g0[N3], g1v[N3], g2v[N3];
 #pragma unroll
             for (int r = 0; r < N3; ++r) {
@@ -435,12 +397,7 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                 const int y = q / TX, x = q - y * TX;
                 const int i = i0 + x, j = j0 + y;
                 sxx_r[r] = szz_r[r] = sxz_r[r] = g0[r] = g1v[r] = g2v[r] = 0.f;
-                if (PF) {
-                    if (q < NC) {
-                        sxx_r[r] = pfs[q]; szz_r[r] = pfs[NC + q]; sxz_r[r] = pfs[2 * NC + q];
-                        g0[r] = pfs[3 * NC + q]; g1v[r] = pfs[4 * NC + q]; g2v[r] = pfs[5 * NC + q];
-                    }
-                } else if (q < TX * TZ && !(edge && (i >= NX || j >= NZ))) {
+                if (q < TX * TZ && !(edge && (i >= NX || j >= NZ))) {
                     const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                     sxx_r[r] = __ldg(a.in.sxx + c); szz_r[r] = __ldg(a.in.szz + c); sxz_r[r] = __ldg(a.in.sxz + c);
                     const bool node = !edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP);
@@ -493,9 +450,7 @@ constexpr Shape kShapes[] = {{32, 8}, {32, 16}, {64, 8}, {64, 16}, {32, 32}, {12
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 size_t fwd_smem(int tx, int tz) { return sizeof(float) * (3 * (tx + 8) * (tz + 8) + 2 * (tx + 4) * (tz + 4)); }
-size_t adj_smem(int tx, int tz, bool pf = false) {
-    return sizeof(float) * (4 * (tx + 8) * (tz + 8) + 6 * (tx + 4) * (tz + 4) + (pf ? 6 * tx * tz : 0));
-}
+size_t adj_smem(int tx, int tz) { return sizeof(float) * (4 * (tx + 8) * (tz + 8) + 6 * (tx + 4) * (tz + 4)); }
 
 template <int TX, int TZ>
 void fwd_launch(const FwdArgs &a, int grid, cudaStream_t st) {
@@ -517,8 +472,6 @@ void set_all_attrs() {
     if (done) return;
     done = true;
     set_attrs<32, 8>(); set_attrs<32, 16>(); set_attrs<64, 8>(); set_attrs<64, 16>();
-    cudaFuncSetAttribute(k_adj_fused<32, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)adj_smem(32, 16, true));
     set_attrs<32, 32>(); set_attrs<128, 8>(); set_attrs<64, 32>();
 }
 
@@ -660,10 +613,7 @@ void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, c
         const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles)
                          : p->adj_grid > 0        ? std::min(p->adj_grid, a.ntiles)
                                                   : a.ntiles;
-        if (p->adj_pf && p->adj_tiles.tx == 32 && p->adj_tiles.tz == 16)
-            k_adj_fused<32, 16, true><<<grid, kThreads, adj_smem(32, 16, true), st>>>(a);
-        else
-            EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
+        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
     }
     prof_end(p, st, slot);
     p->launches++;
@@ -705,17 +655,10 @@ float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEv
 
 int select_adj(efwi_plan *p, const Variant &v) {
     p->adj_stencil = v.kind;
-    // per-thread loads, 32x16: vec bit 1 = persistent grid, bit 2 = last phase's inputs prefetched
-    const bool l32 = v.kind == EFWI_STENCIL_LOADS && v.tx == 32 && v.tz == 16;
-    p->adj_pf = l32 && (v.vec & 4);
     p->adj_grid = 0;
-    if (l32 && (v.vec & 2)) {
+    if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2 && v.tx == 32 && v.tz == 16) {   // loads: vec 2 = persistent
         int nb = 0;
-        if (p->adj_pf)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16, true>, kThreads,
-                                                          adj_smem(32, 16, true));
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
         p->adj_grid = std::max(1, nb) * p->n_sms;
     }
     int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
@@ -767,18 +710,12 @@ int efwi_autotune(efwi_plan *p) {
                     : (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)))
             continue;
         if (wa == EFWI_STENCIL_AUTO || wa == EFWI_STENCIL_LOADS) {
-            // 32x16 also on a persistent grid (the next tile's descriptor loaded ahead) and with
-            // the last phase's inputs prefetched; EFWI_ADJ_PERSIST=0|1 and EFWI_ADJ_PF=0|1 keep
-            // only those (tests of one variant)
-            const char *fp = getenv("EFWI_ADJ_PERSIST"), *ff = getenv("EFWI_ADJ_PF");
-            const int only_p = fp ? atoi(fp) : -1, only_f = ff ? atoi(ff) : -1;
-            for (int pers = 0; pers <= 1; ++pers)
-                for (int pf = 0; pf <= 1; ++pf) {
-                    if ((only_p >= 0 && only_p != pers) || (only_f >= 0 && only_f != pf)) continue;
-                    if (!pers && !pf) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-                    else if (s.tx == 32 && s.tz == 16)
-                        adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, (pers ? 2 : 0) | (pf ? 4 : 0)});
-                }
+            // 32x16 also on a persistent grid (the next tile's descriptor loaded ahead);
+            // EFWI_ADJ_PERSIST=0|1 keeps only one of the two (tests of one variant)
+            const char *fp = getenv("EFWI_ADJ_PERSIST");
+            const int only_p = fp ? atoi(fp) : -1;
+            if (only_p <= 0) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+            if (s.tx == 32 && s.tz == 16 && only_p != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
         }
         for (int nst = 1; nst <= 2; ++nst)
             if (wa != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
@@ -819,8 +756,8 @@ int efwi_autotune(efwi_plan *p) {
         for (auto &v : adj) {
             if (select_adj(p, v)) continue;
             const float t = time_steps(p, true, st, e0, e1);
-            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d persistent %d prefetch %d: %.1f us\n",
-                             v.kind, v.tx, v.tz, v.nst, (v.vec & 2) != 0, (v.vec & 4) != 0, t * 1e3f / 3);
+            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d persistent %d: %.1f us\n", v.kind,
+                             v.tx, v.tz, v.nst, v.vec == 2, t * 1e3f / 3);
             if (t < best) { best = t; ba = v; }
         }
         cudaEventDestroy(e0);
