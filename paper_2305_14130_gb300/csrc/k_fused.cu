@@ -207,6 +207,14 @@ struct AdjArgsF {
     float dt, rdx, rdz;
 };
 
+// Read-only load that asks L2 to fetch the 256-byte block around the address: the
+// adjacent 128 bytes of a row belong to the neighbouring tile, read soon after.
+__device__ __forceinline__ float ldg256(const float *p) {
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 template <int TX, int TZ>
 __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(AdjArgsF a) {
     constexpr int SX = TX + 8, SZ = TZ + 8;
@@ -257,8 +265,8 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                 const int i = i0 - 4 + x, j = j0 - 4 + y;
                 if (q < SX * SZ && (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ))) {
                     const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                    lxx[r] = __ldg(a.in.sxx + c); lzz[r] = __ldg(a.in.szz + c); lxz[r] = __ldg(a.in.sxz + c);
-                    llam[r] = __ldg(a.M.lam + c); lmu[r] = __ldg(a.M.mu + c); lmxz[r] = __ldg(a.M.muxz + c);
+                    lxx[r] = ldg256(a.in.sxx + c); lzz[r] = ldg256(a.in.szz + c); lxz[r] = ldg256(a.in.sxz + c);
+                    llam[r] = ldg256(a.M.lam + c); lmu[r] = ldg256(a.M.mu + c); lmxz[r] = ldg256(a.M.muxz + c);
                 }
             }
 #pragma unroll
@@ -319,9 +327,9 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                 const int i = i0 - 2 + x, j = j0 - 2 + y;
                 if (q < VX * VZ && (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ))) {
                     const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                    lvx[r] = __ldg(a.in.vx + c); lvz[r] = __ldg(a.in.vz + c);
-                    lbx[r] = __ldg(a.M.bx + c); lbz[r] = __ldg(a.M.bz + c);
-                    lfx[r] = __ldg(a.vfx + c); lfz[r] = __ldg(a.vfz + c);
+                    lvx[r] = ldg256(a.in.vx + c); lvz[r] = ldg256(a.in.vz + c);
+                    lbx[r] = ldg256(a.M.bx + c); lbz[r] = ldg256(a.M.bz + c);
+                    lfx[r] = ldg256(a.vfx + c); lfz[r] = ldg256(a.vfz + c);
                     const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
                     if (own && (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP))) {
                         lgx[r] = a.Gbx[c]; lgz[r] = a.Gbz[c];
@@ -399,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                 sxx_r[r] = szz_r[r] = sxz_r[r] = g0[r] = g1v[r] = g2v[r] = 0.f;
                 if (q < TX * TZ && !(edge && (i >= NX || j >= NZ))) {
                     const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
-                    sxx_r[r] = __ldg(a.in.sxx + c); szz_r[r] = __ldg(a.in.szz + c); sxz_r[r] = __ldg(a.in.sxz + c);
+                    sxx_r[r] = ldg256(a.in.sxx + c); szz_r[r] = ldg256(a.in.szz + c); sxz_r[r] = ldg256(a.in.sxz + c);
                     const bool node = !edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP);
                     const bool half = !edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP);
                     if (node) { g0[r] = a.Glam[c]; g1v[r] = a.Gmu[c]; }
