@@ -209,6 +209,14 @@ struct AdjArgsF {
 
 // Read-only load that asks L2 to fetch the 256-byte block around the address: the
 // adjacent 128 bytes of a row belong to the neighbouring tile, read soon after.
+// Coherent load (the imaging sums are read, then written by the same thread) with the
+// same 256-byte L2 fetch.
+__device__ __forceinline__ float ld256(const float *p) {
+    float v;
+    asm("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ float ldg256(const float *p) {
     float v;
     asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
@@ -332,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                     lfx[r] = ldg256(a.vfx + c); lfz[r] = ldg256(a.vfz + c);
                     const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
                     if (own && (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP))) {
-                        lgx[r] = a.Gbx[c]; lgz[r] = a.Gbz[c];
+                        lgx[r] = ld256(a.Gbx + c); lgz[r] = ld256(a.Gbz + c);
                     }
                 }
             }
@@ -410,8 +418,8 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                     sxx_r[r] = ldg256(a.in.sxx + c); szz_r[r] = ldg256(a.in.szz + c); sxz_r[r] = ldg256(a.in.sxz + c);
                     const bool node = !edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP);
                     const bool half = !edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP);
-                    if (node) { g0[r] = a.Glam[c]; g1v[r] = a.Gmu[c]; }
-                    if (half) g2v[r] = a.Gmuxz[c];
+                    if (node) { g0[r] = ld256(a.Glam + c); g1v[r] = ld256(a.Gmu + c); }
+                    if (half) g2v[r] = ld256(a.Gmuxz + c);
                 }
             }
 #pragma unroll
