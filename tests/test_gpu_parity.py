@@ -451,3 +451,21 @@ def test_overlapped_recompute_matches_sequential(efwi):
         plan.close()
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("group", [2, 3])
+def test_grouped_gradient_equals_one_plan(efwi, group):
+    """Shots run in groups, one plan per group (extended problems too large for
+    one plan): every component's gradient equals that of a single plan holding
+    all shots (windows, uneven trace counts), the misfit its sum."""
+    from paper_2305_14130_gb300.groups import grouped_gradient
+    p = rounded(W.tiny(nx=48, nz=26, ns=5, nt=50, npml=4, win=[[0, 30], [9, 37], [20, 28], [4, 40], [12, 30]]))
+    d_obs = dev(observed(p))
+    m = (dev(p.vp), dev(p.vs), dev(p.rho))
+    plan = efwi.Plan(p.acq, exec="batched")
+    phi, *g = plan.gradient(*m, d_obs)
+    plan.close()
+    phi_g, gg = grouped_gradient(p.acq, *m, d_obs, group, exec="batched")
+    assert phi_g == pytest.approx(float(phi.item()), rel=1e-12)
+    for a, b in zip(g, gg):
+        assert torch.equal(a, b)
