@@ -219,8 +219,10 @@ int efwi_plan_info(const efwi_plan *plan, efwi_plan_info_t *info);
 
 /* Synchronise the stream and report device-side failures of earlier calls on
  * this plan: EFWI_ERR_TIMEOUT if a kernel gave up a bounded wait (its results
- * are then invalid), EFWI_ERR_CUDA for an asynchronous CUDA error.  The device
- * flag is cleared.                                                           */
+ * are then invalid), EFWI_ERR_NAN if a model passed to a call held a
+ * non-finite velocity or density or a non-positive density (checked on every
+ * cell the call's materials read), EFWI_ERR_CUDA for an asynchronous CUDA
+ * error.  The device flag is cleared.                                        */
 int efwi_sync_status(efwi_plan *plan, efwi_stream_t stream);
 
 /* Forward modelling of every shot with its own component (eqs. 1-3; first
@@ -392,6 +394,14 @@ int efwi_extended_objective(efwi_plan *plan, const float *vp, const float *vs, c
                             const float *d_obs, const double eta[3], const float *b,
                             const float *bp, const uint8_t *sink, double *phi_data,
                             double *phi_reg, efwi_stream_t stream);
+
+/* Self-test of the failure path of bounded device waits (no counterpart in
+ * the paper): launches one thread that waits, with the same bounded wait as
+ * the TMA kernels, on a barrier that never completes, and gives up after
+ * budget_cycles clock cycles (1 .. 2^32; 2^21 is about a millisecond).  The
+ * next efwi_sync_status on the plan then returns EFWI_ERR_TIMEOUT and clears
+ * the flag.  Nothing faults, traps or hangs.                                */
+int efwi_selftest_timeout(efwi_plan *plan, long long budget_cycles, efwi_stream_t stream);
 
 /* Kernel timing for measurements.  When every > 0 the plan brackets every
  * every-th launch of its two dominant stencil kernels with CUDA events on the

@@ -81,6 +81,7 @@ SIGNATURES = {
     "efwi_extended_objective": (C.c_int, [VP, VP, VP, VP, VP, PD, VP, VP, VP, VP, VP, VP]),
     "efwi_pseudo_hessian": (C.c_int, [VP, VP, VP, VP, C.c_double, VP, VP, VP]),
     "efwi_prof_enable": (C.c_int, [VP, C.c_int]),
+    "efwi_selftest_timeout": (C.c_int, [VP, C.c_longlong, VP]),
     "efwi_prof_read": (C.c_int, [VP, C.c_int, PD, C.POINTER(C.c_longlong)]),
 }
 

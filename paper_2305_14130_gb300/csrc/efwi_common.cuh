@@ -28,6 +28,10 @@
 
 #include "efwi.h"
 
+// bits of a plan's device error flag (read and cleared by efwi_sync_status)
+#define EFWI_FLAG_TIMEOUT 1      // a kernel gave up a bounded wait
+#define EFWI_FLAG_BAD_MODEL 2    // a model value was not finite, or a density not positive
+
 #define EFWI_GX 4
 #define EFWI_GZ 2
 

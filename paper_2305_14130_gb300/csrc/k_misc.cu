@@ -19,6 +19,7 @@ struct MatArgs {
     const float *vp, *vs, *rho, *ref;   // model [ns][nz][nx]; ref [3][nz][nx]
     Mat M;                              // outputs (const-cast inside)
     int nx, nz, shot;
+    int *err;                           // device flag: bit 2 set for a non-finite or invalid model value
 };
 
 __device__ void model_at(const MatArgs &a, const ShotDev &s, int shot, int i, int j, double &vp, double &vs,
@@ -53,6 +54,8 @@ __global__ void k_materials(MatArgs a) {
         r[k] = rho;
     }
     model_at(a, s, shot, i, j, vp, vs, rho);
+    // a non-finite velocity or density, or a non-positive density, makes the call's results invalid
+    if (!(isfinite(vp) && isfinite(vs) && isfinite(rho) && rho > 0.0)) atomicOr(a.err, EFWI_FLAG_BAD_MODEL);
     const long long c = cell_of(s, i, j);
     const bool zero = mu[0] == 0 || mu[1] == 0 || mu[2] == 0 || mu[3] == 0;
     ((float *)a.M.lam)[c] = (float)(rho * (vp * vp - 2.0 * vs * vs));
@@ -426,7 +429,7 @@ __global__ void k_reg(const float *m, const float *b, const float *bp, const uin
 // ==========================================================================
 
 void launch_materials(efwi_plan *p, const float *vp, const float *vs, const float *rho, cudaStream_t st) {
-    MatArgs a{p->shots_d, vp, vs, rho, p->ref, materials(p), p->d.nx, p->d.nz, -1};
+    MatArgs a{p->shots_d, vp, vs, rho, p->ref, materials(p), p->d.nx, p->d.nz, -1, p->dev_err};
     dim3 b(32, 8);
     dim3 g((p->max_nx + 31) / 32, (p->nzp + 7) / 8, p->d.ns);
     k_materials<<<g, b, 0, st>>>(a);

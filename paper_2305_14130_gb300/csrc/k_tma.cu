@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         __syncthreads();
         if (!ok_s) {
             if (tid == 0) {
-                atomicExch(a.err, 1);
+                atomicOr(a.err, EFWI_FLAG_TIMEOUT);
                 if (ST) bulk_wait0();       // stores already issued finish before the CTA exits
             }
             return;
@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(256) k_adj_tma(TmaAdjArgs a) {
         if (tid == 0) ok_s = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
         __syncthreads();
         if (!ok_s) {
-            if (tid == 0) atomicExch(a.err, 1);
+            if (tid == 0) atomicOr(a.err, EFWI_FLAG_TIMEOUT);
             return;
         }
         mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
@@ -1008,3 +1008,37 @@ void launch_adj_tma(efwi_plan *p, const float *vfx, cudaStream_t st) {
 }
 
 }  // namespace efwi
+
+// ===========================================================================
+// Self-test of the timeout path: one thread waits, with the bounded wait of the
+// TMA kernels, on an mbarrier that expects two arrivals and receives one, so
+// the phase never completes; after `budget` clock cycles the wait gives up and
+// the plan's device flag records it, exactly as a stalled copy would.  Nothing
+// else is issued (no copy, no trap), so the kernel always ends.
+// ===========================================================================
+namespace {
+
+__global__ void k_selftest_timeout(long long budget, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    efwi::mbar_init(&bar, 2);
+    efwi::fence_mbar_init();
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(efwi::smem_u32(&bar)) : "memory");
+    if (!efwi::mbar_wait_bounded(&bar, 0u, budget)) atomicOr(err, EFWI_FLAG_TIMEOUT);
+}
+
+}  // namespace
+
+extern "C" int efwi_selftest_timeout(efwi_plan *p, long long budget_cycles, efwi_stream_t stream) {
+    if (!p || budget_cycles < 1 || budget_cycles > (1LL << 32)) {
+        efwi::set_thread_error("efwi_selftest_timeout: plan NULL or budget outside [1, 2^32] cycles");
+        if (p) p->err = "budget outside [1, 2^32] cycles";
+        return EFWI_ERR_ARG;
+    }
+    k_selftest_timeout<<<1, 1, 0, (cudaStream_t)stream>>>(budget_cycles, p->dev_err);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        p->err = std::string("efwi_selftest_timeout: ") + cudaGetErrorString(e);
+        return EFWI_ERR_CUDA;
+    }
+    return EFWI_OK;
+}

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -26,14 +27,27 @@ static int fail(efwi_plan *p, int code, const std::string &msg) {
 
 namespace {
 
+// Workspace allocation of a plan.  EFWI_TEST_FAIL_ALLOC=k makes the k-th allocation
+// (1-based) fail without calling cudaMalloc, to test the out-of-memory path.
 struct Alloc {
     efwi_plan *p;
     bool ok = true;
     std::string what;
+    int count_ = 0;
+    int fail_at = [] {
+        const char *e = getenv("EFWI_TEST_FAIL_ALLOC");
+        return e ? atoi(e) : 0;
+    }();
     template <class T>
     void operator()(T **ptr, size_t count, const char *name) {
         if (!ok || count == 0) return;
         size_t bytes = count * sizeof(T);
+        if (++count_ == fail_at) {
+            ok = false;
+            what = std::string("allocation of ") + name + " failed (EFWI_TEST_FAIL_ALLOC)";
+            *ptr = nullptr;
+            return;
+        }
         cudaError_t e = cudaMalloc((void **)ptr, bytes);
         if (e != cudaSuccess) {
             ok = false;
@@ -551,7 +565,10 @@ extern "C" int efwi_sync_status(efwi_plan *p, efwi_stream_t stream) {
     cudaMemcpy(&flag, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (flag) {
         cudaMemset(p->dev_err, 0, sizeof(int));
-        return fail(p, EFWI_ERR_TIMEOUT, "a kernel gave up a bounded wait; results of that call are invalid");
+        if (flag & EFWI_FLAG_TIMEOUT)
+            return fail(p, EFWI_ERR_TIMEOUT, "a kernel gave up a bounded wait; results of that call are invalid");
+        return fail(p, EFWI_ERR_NAN, "the model holds a non-finite value or a non-positive density; results of "
+                                     "that call are invalid");
     }
     return EFWI_OK;
 }

@@ -61,12 +61,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase with the given parity, giving up after ~2^31 clock cycles
-// (about one second): returns false on expiry.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// Wait for the phase with the given parity, giving up after `budget` clock cycles
+// (default 2^31, about one second): returns false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long budget = 1LL << 31) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > budget) return false;
     return true;
 }
 
