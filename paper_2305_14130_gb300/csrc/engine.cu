@@ -14,11 +14,22 @@
 #include <cmath>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "plan.hpp"
 
 using namespace efwi;
 
 namespace {
+
+// NVTX range over a phase of a call (host timeline; no-ops without a profiler).
+// Inside CUDA graphs the ranges mark the replay call, not each replayed kernel.
+struct Phase {
+    explicit Phase(const char *name) { nvtxRangePushA(name); }
+    ~Phase() { nvtxRangePop(); }
+    Phase(const Phase &) = delete;
+    Phase &operator=(const Phase &) = delete;
+};
 
 int cuda_status(efwi_plan *p, const char *where) {
     cudaError_t e = cudaGetLastError();
@@ -186,6 +197,7 @@ int replay(efwi_plan *p, GraphCache &gc, cudaStream_t st, Body body) {
 }
 
 int run_forward(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
+    Phase ph(ck ? "efwi forward with checkpoints" : "efwi forward");
     if (p->d.exec == EFWI_EXEC_BATCHED && p->use_graphs) {
         int rc = replay(p, ck ? p->g_fwd_ck : p->g_fwd, st,
                         [&](cudaStream_t cs) { forward_loop(p, p->dbuf, ck, cs); });
@@ -199,6 +211,7 @@ int run_forward(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
 }
 
 int run_adjoint(efwi_plan *p, cudaStream_t st) {
+    Phase ph("efwi adjoint (checkpoint recompute, adjoint steps, imaging)");
     if (p->d.exec == EFWI_EXEC_BATCHED && p->use_graphs) {
         int rc = replay(p, p->g_adj, st, [&](cudaStream_t cs) { adjoint_loop(p, cs); });
         if (rc) return rc;
@@ -241,9 +254,13 @@ extern "C" int efwi_adjoint_gradient(efwi_plan *p, const float *vp, const float 
     float *d = d_out ? d_out : p->dbuf;
     launch_materials(p, vp, vs, rho, st);
     if ((rc = run_forward(p, d, true, st))) return rc;
-    if (p->d.ntr > 0) launch_residual(p, d, d_obs, phi_data, st);
-    else cudaMemsetAsync(phi_data, 0, sizeof(double), st);
+    {
+        Phase ph("efwi residual and misfit");
+        if (p->d.ntr > 0) launch_residual(p, d, d_obs, phi_data, st);
+        else cudaMemsetAsync(phi_data, 0, sizeof(double), st);
+    }
     if ((rc = run_adjoint(p, st))) return rc;
+    Phase ph("efwi chain rule");
     float *src = p->Gtot ? p->Gtot : p->G;
     const float *G[5];
     for (int k = 0; k < 5; ++k) G[k] = src + k * p->fsz_total;
@@ -269,6 +286,7 @@ extern "C" int efwi_pseudo_hessian(efwi_plan *p, const float *vp, const float *v
     launch_materials(p, vp, vs, rho, st);
     // FP64 accumulator with the wavefield layout, over the imaging workspace G
     double *acc = reinterpret_cast<double *>(p->G);
+    Phase ph("efwi pseudo-Hessian");
     auto body = [&](cudaStream_t cs) {
         reset_forward_state(p, cs);
         cudaMemsetAsync(acc, 0, sizeof(double) * p->fsz_total, cs);

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <nvtx3/nvToolsExt.h>
 #include <cstring>
 #include <map>
 #include <tuple>
@@ -624,7 +625,9 @@ extern "C" int efwi_regularization_grad_n(efwi_plan *p, int ns, const float *m, 
     if (ns < 1) return fail(p, EFWI_ERR_ARG, "ns must be >= 1");
     if (!m || !b || !bp || !sink || !phi_reg || !g) return fail(p, EFWI_ERR_ARG, "NULL device pointer");
     if (!std::isfinite(eta)) return fail(p, EFWI_ERR_ARG, "eta must be finite");
+    nvtxRangePushA("efwi consistency term");
     launch_reg(p, m, b, bp, sink, eta, phi_reg, g, 0, (cudaStream_t)stream, ns);
+    nvtxRangePop();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(p, EFWI_ERR_CUDA, cudaGetErrorString(e));
     return EFWI_OK;
@@ -636,7 +639,9 @@ extern "C" int efwi_regularization_grad(efwi_plan *p, const float *m, const floa
     if (!p) return fail(nullptr, EFWI_ERR_ARG, "plan is NULL");
     if (!m || !b || !bp || !sink || !phi_reg || !g) return fail(p, EFWI_ERR_ARG, "NULL device pointer");
     if (!std::isfinite(eta)) return fail(p, EFWI_ERR_ARG, "eta must be finite");
+    nvtxRangePushA("efwi consistency term");
     launch_reg(p, m, b, bp, sink, eta, phi_reg, g, 0, (cudaStream_t)stream);
+    nvtxRangePop();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(p, EFWI_ERR_CUDA, cudaGetErrorString(e));
     return EFWI_OK;
