@@ -47,14 +47,25 @@ struct TmaFwdArgs {
     int segf;                   // segment-map field of this step's vx, or -1 (output staging)
 };
 
+// Shared-memory stage of one tile.  Fields are staged on the tile + 4-cell halo in x
+// (SX columns) and, in z, only on the rows their readers use (halo-4 row coordinates,
+// rows 0 .. TZ+7): vx, vz, sigma_xx, b_x, b_z on rows 2 .. TZ+5 (R2 rows), sigma_zz on
+// rows 1 .. TZ+7 and sigma_xz on rows 0 .. TZ+6 (R3 rows each); lambda, mu, mu_xz on the
+// tile.  Every array starts 128-byte aligned; vx|vz and b_x|b_z are 2-field boxes.
 template <int TX, int TZ, int NST, int VEC = 1>
 struct FwdLayout {
     static constexpr int SX = TX + 8, SZ = TZ + 8;
-    static constexpr int NS = SX * SZ;              // one halo field
-    static constexpr int NC = TX * TZ;              // one tile field
-    static constexpr int BUF = 7 * NS + 3 * NC;     // floats per buffer
-    static constexpr unsigned BYTES = BUF * 4u;
-    static constexpr size_t smem() { return NST * (size_t)BYTES + 128; }
+    static constexpr int R2 = TZ + 4, R3 = TZ + 7;
+    static constexpr int A2 = SX * R2;                              // floats of an R2 field
+    static constexpr int A3 = SX * R3, A3P = (A3 + 31) & ~31;       // R3 field, padded to 128 B
+    static constexpr int NC = TX * TZ;                              // one tile field
+    static constexpr int OVX = 0, OVZ = A2, OSXX = 2 * A2, OSZZ = 3 * A2, OSXZ = OSZZ + A3P,
+                         OBX = OSXZ + A3P, OBZ = OBX + A2, OLAM = OBZ + A2;
+    static constexpr int BUF = (OLAM + 3 * NC + 31) & ~31;          // floats per stage
+    static constexpr unsigned LOADED = (5u * A2 + 2u * A3 + 3u * NC) * 4u;   // bytes the copies bring
+    static constexpr size_t smem() { return NST * (size_t)BUF * 4 + 128; }
+    static_assert(A2 % 32 == 0, "R2 fields must keep 128-byte alignment");
+    static_assert(2 * NC <= 2 * A2, "staged velocities must fit over b_x, b_z");
 };
 
 template <int TX, int TZ, int NST, int VEC>
@@ -62,11 +73,16 @@ __device__ __forceinline__ void issue_fwd(const TmaFwdArgs &a, int t, float *buf
     using L = FwdLayout<TX, TZ, NST, VEC>;
     const int4 tl = a.tiles[t];
     const FwdMaps *m = a.maps + tl.x;
-    mbar_expect_tx(bar, L::BYTES);
-    // element x = cell i + GX, row y = cell j + GZ
-    tma_load_3d(buf, &m->st, bar, tl.y, tl.z - 2, 5 * a.scur);
-    tma_load_3d(buf + 5 * L::NS, &m->mb, bar, tl.y, tl.z - 2, 3);
-    tma_load_3d(buf + 7 * L::NS, &m->mc, bar, tl.y + 4, tl.z + 2, 0);
+    mbar_expect_tx(bar, L::LOADED);
+    // element x = cell i + GX (halo-4 column 0 = cell i0 - 4), row y = cell j + GZ: halo-4 row r
+    // of the tile is map row j0 - 4 + r + GZ = tl.z - 2 + r
+    const int f = 5 * a.scur;
+    tma_load_3d(buf + L::OVX, &m->s2, bar, tl.y, tl.z, f);          // vx, vz: rows 2..
+    tma_load_3d(buf + L::OSXX, &m->s1, bar, tl.y, tl.z, f + 2);     // sigma_xx: rows 2..
+    tma_load_3d(buf + L::OSZZ, &m->s3, bar, tl.y, tl.z - 1, f + 3); // sigma_zz: rows 1..
+    tma_load_3d(buf + L::OSXZ, &m->s3, bar, tl.y, tl.z - 2, f + 4); // sigma_xz: rows 0..
+    tma_load_3d(buf + L::OBX, &m->mb, bar, tl.y, tl.z, 3);          // b_x, b_z: rows 2..
+    tma_load_3d(buf + L::OLAM, &m->mc, bar, tl.y + 4, tl.z + 2, 0); // lambda, mu, mu_xz: tile
 }
 
 // Shared-memory output staging (ST = 1, cell pairs only): the new stresses of the
@@ -81,9 +97,9 @@ __device__ __forceinline__ void store_fwd(const TmaFwdArgs &a, int4 tl, const fl
     using L = FwdLayout<TX, TZ, NST, 2>;
     const FwdMaps *m = a.maps + tl.x;
     const int x = tl.y + EFWI_GX, y = tl.z + EFWI_GZ;
-    tma_store_3d(&m->o2, buf + 5 * L::NS, x, y, a.ofield);
-    tma_store_3d(&m->o3, buf + 7 * L::NS, x, y, a.ofield + 2);
-    if (a.segf >= 0) tma_store_3d(&m->sg, buf + 5 * L::NS, x, y, a.segf);
+    tma_store_3d(&m->o2, buf + L::OBX, x, y, a.ofield);
+    tma_store_3d(&m->o3, buf + L::OLAM, x, y, a.ofield + 2);
+    if (a.segf >= 0) tma_store_3d(&m->sg, buf + L::OBX, x, y, a.segf);
     bulk_commit();
 }
 
@@ -153,12 +169,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         auto tile = [&](auto edge_c) {
             constexpr bool edge = decltype(edge_c)::value;
             const int i0 = tl.y, j0 = tl.z;
-            float *svx = buf, *svz = buf + L::NS, *sxx = buf + 2 * L::NS, *szz = buf + 3 * L::NS, *sxz = buf + 4 * L::NS;
-            const float *sbx = buf + 5 * L::NS, *sbz = buf + 6 * L::NS;
-            const float *slam = buf + 7 * L::NS, *smu = slam + L::NC, *smxz = smu + L::NC;
+            // base pointers in halo-4 coordinates (element y * SX + x), offset by each array's first row
+            float *svx = buf + L::OVX - 2 * SX, *svz = buf + L::OVZ - 2 * SX, *sxx = buf + L::OSXX - 2 * SX,
+                  *szz = buf + L::OSZZ - SX, *sxz = buf + L::OSXZ;
+            const float *sbx = buf + L::OBX - 2 * SX, *sbz = buf + L::OBZ - 2 * SX;
+            const float *slam = buf + L::OLAM, *smu = slam + L::NC, *smxz = smu + L::NC;
             // output staging: dense [2][TZ][TX] velocities over b_x/b_z, [3][TZ][TX] stresses over
             // lambda, mu, mu_xz
-            float *dv = buf + 5 * L::NS, *ds = buf + 7 * L::NS;
+            float *dv = buf + L::OBX, *ds = buf + L::OLAM;
             float *__restrict__ ovx = a.out.vx + off;
             float *__restrict__ ovz = a.out.vz + off;
             const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
@@ -606,8 +624,10 @@ int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int stg) {
     const long long F = p->fsz_total;
     for (int s = 0; s < p->d.ns; ++s) {
         const ShotDev &sh = p->shots[s];
-        int rc = encode_map(&h[s].st, p->state[0], sh, F, 10, tx + 8, tz + 8, 5);
-        if (!rc) rc = encode_map(&h[s].mb, p->mat, sh, F, 5, tx + 8, tz + 8, 2);
+        int rc = encode_map(&h[s].s2, p->state[0], sh, F, 10, tx + 8, tz + 4, 2);
+        if (!rc) rc = encode_map(&h[s].s1, p->state[0], sh, F, 10, tx + 8, tz + 4, 1);
+        if (!rc) rc = encode_map(&h[s].s3, p->state[0], sh, F, 10, tx + 8, tz + 7, 1);
+        if (!rc) rc = encode_map(&h[s].mb, p->mat, sh, F, 5, tx + 8, tz + 4, 2);
         if (!rc) rc = encode_map(&h[s].mc, p->mat, sh, F, 5, tx, tz, 3);
         if (!rc) rc = encode_map(&h[s].o2, p->state[0], sh, F, 10, tx, tz, 2);
         if (!rc) rc = encode_map(&h[s].o3, p->state[0], sh, F, 10, tx, tz, 3);

@@ -7,14 +7,16 @@
 
 namespace efwi {
 
-// Tensor maps of one shot for the forward step: the state (both buffers,
-// 10 fields, box = tile + 4-cell halo over 5 fields), b_x/b_z (halo box) and
-// lambda/mu/mu_xz (tile box).
-// With shared-memory output staging, o2 / o3 store the new velocities / stresses
-// of a tile (boxes of 2 and 3 fields, tile only) and sg the segment-buffer copy
-// of the velocities.
+// Tensor maps of one shot for the forward step, over the state (both buffers, 10
+// fields) and the materials: boxes of the tile + 4-cell halo in x and, in z, the
+// rows each field's readers use -- s2: vx, vz (2 fields, tile + 2 rows each side),
+// s1: sigma_xx (1 field, the same rows), s3: sigma_zz or sigma_xz (1 field, tile +
+// 3 rows on one side and 4 on the other), mb: b_x, b_z (2 fields, tile + 2 rows);
+// mc: lambda/mu/mu_xz on the tile.  With shared-memory output staging, o2 / o3
+// store the new velocities / stresses of a tile (boxes of 2 and 3 fields, tile
+// only) and sg the segment-buffer copy of the velocities.
 struct __align__(64) FwdMaps {
-    CUtensorMap st, mb, mc, o2, o3, sg;
+    CUtensorMap s2, s1, s3, mb, mc, o2, o3, sg;
 };
 
 // Tensor maps of one shot for the adjoint step: adjoint state (both buffers,
