@@ -133,3 +133,27 @@ def test_gradient_zero_outside_window():
         for g in (gvp, gvs, grho):
             assert not g[s, :, :x0].any() and not g[s, :, x0 + w:].any()
             assert g[s, :, x0:x0 + w].any()
+
+
+def test_summed_component_gradients_are_the_conventional_gradient():
+    """With every component equal to one model m (conventional FWI, eq. 6), the
+    extended objective's data term (eq. 8) is the conventional misfit of m, so
+    sum_s g_s must be its gradient: checked by central finite differences of the
+    conventional misfit along a perturbation of m shared by all shots, per
+    parameter (windows make the shots see different parts of m)."""
+    p = W.tiny(nx=26, nz=20, ns=3, nt=40, win=[[0, 26], [3, 18], [8, 16]])
+    acq = p.acq
+    ns = acq.ns
+    d_obs = E.forward(acq, *(np.repeat(m[None], ns, 0) for m in (p.true_vp, p.true_vs, p.true_rho)))
+    m0 = [np.asarray(v, np.float64) for v in (p.true_vp * 1.01, p.true_vs * 0.99, p.true_rho * 1.02)]
+    ext = lambda ms: [np.repeat(m[None], ns, 0) for m in ms]
+    _, *g = E.gradient(acq, *ext(m0), d_obs)
+    rng = np.random.default_rng(11)
+    for k in range(3):
+        dm = rng.standard_normal(m0[k].shape)
+        h = 1e-6 * np.abs(m0[k]).max()
+        mp = list(m0); mp[k] = m0[k] + h * dm
+        mm = list(m0); mm[k] = m0[k] - h * dm
+        fd = (E.misfit(E.forward(acq, *ext(mp)), d_obs) - E.misfit(E.forward(acq, *ext(mm)), d_obs)) / (2 * h)
+        an = float(np.sum(g[k].sum(axis=0) * dm))
+        assert abs(fd - an) <= 1e-6 * abs(an), (k, fd, an)
