@@ -15,13 +15,17 @@
  * iteration: modelled DAS data (eqs. 1-3), the data misfit (eq. 4 / first
  * term of eq. 8) and its gradient with respect to every extended component
  * (eq. 6 applied to each m_s), the zone-of-influence weights (eq. 10) and the
- * consistency term with its gradient (eqs. 8, 11, 12).
+ * consistency term with its gradient (eqs. 8, 11, 12); the collapse of the
+ * extended model to the final model (eq. 9, and eq. 15 on gradients); the
+ * pseudo-Hessian preconditioner of the paper's comparison method; and the
+ * optimizer, l-BFGS with a strong-Wolfe line search and the convergence rate
+ * of eq. 13.
  *
  * Physics (the paper fixes no scheme): 2D isotropic elastic velocity-stress
  * equations on a Virieux staggered grid, 4th order in space, 2nd order in
- * time, convolutional PML (Komatitsch & Martin 2007), moment-tensor sources,
- * DAS gauge-averaged axial strain (or strain rate) or 2-C particle-velocity
- * receivers.  The gradient is the exact
+ * time, convolutional PML (Komatitsch & Martin 2007), moment-tensor or
+ * vector-force sources, DAS gauge-averaged axial strain (or strain rate) or
+ * 2-C particle-velocity receivers.  The gradient is the exact
  * discrete adjoint of the forward time stepping.
  *
  * Conventions shared by every call
@@ -62,7 +66,8 @@ enum efwi_status {
     EFWI_ERR_OOM = -3,              /* device allocation failed at plan creation */
     EFWI_ERR_CUDA = -4,             /* a CUDA runtime call or kernel launch failed */
     EFWI_ERR_TIMEOUT = -5,          /* a bounded device-side wait expired */
-    EFWI_ERR_NAN = -6,              /* non-finite values detected */
+    EFWI_ERR_NAN = -6,              /* a model held a non-finite value or a non-positive density
+                                       (reported by efwi_sync_status) */
     EFWI_ERR_NOT_IMPLEMENTED = -7
 };
 
