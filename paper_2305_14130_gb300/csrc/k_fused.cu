@@ -223,23 +223,7 @@ __device__ __forceinline__ float ldg256(const float *p) {
     return v;
 }
 
-// 16-byte asynchronous global -> shared copy with a 256-byte L2 fetch; src_bytes = 0
-// writes zeros instead
-__device__ __forceinline__ void cp_async16(float *dst, const float *src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global.L2::256B [%0], [%1], 16, %2;"
-                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// PF1 (persistent grids): the first phase's inputs of the CTA's next tile (adjoint
-// stresses and lambda, mu, mu_xz on the tile + 4-cell halo) are copied into shared
-// memory with 16-byte cp.async while the current tile runs its last two phases, so
-// the first phase issues no global load.  Rows outside the shot's grid and chunks
-// past the row pitch are zero-filled; the remaining cells the first phase skips are
-// ghost columns, which hold zeros, so the staged values are those the loads give.
-template <int TX, int TZ, bool PF1 = false>
+template <int TX, int TZ>
 __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(AdjArgsF a) {
     constexpr int SX = TX + 8, SZ = TZ + 8;
     constexpr int VX = TX + 4, VZ = TZ + 4;
@@ -248,24 +232,7 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
     float *f1s = sm, *f2s = sm + SX * SZ, *f3s = sm + 2 * SX * SZ, *f4s = sm + 3 * SX * SZ;
     float *e1s = sm + 4 * SX * SZ, *e2s = e1s + VX * VZ, *e3s = e2s + VX * VZ, *e4s = e3s + VX * VZ;
     float *vfxs = e4s + VX * VZ, *vfzs = vfxs + VX * VZ;   // forward v^{n+1/2} on the tile + 2-cell halo
-    float *pf1 = vfzs + VX * VZ;                          // PF1: [6][SZ][SX] sxx szz sxz lam mu mu_xz
     const int tid = threadIdx.x;
-
-    auto prefetch1 = [&](int4 tln, long long offn, int pitchn, int nzn) {
-        constexpr int C4 = SX / 4, NCH = C4 * SZ;          // 16-byte chunks per field
-        for (int q = tid; q < 6 * NCH; q += kThreads) {
-            const int f = q / NCH, r = q - f * NCH;
-            const int y = r / C4, c4 = r - y * C4;
-            const int j = tln.z - 4 + y;
-            const int col = tln.y + 4 * c4;                 // pitch column of cell i0 - 4 + 4 c4
-            const bool ok = j >= 0 && j < nzn && col < pitchn;
-            const float *base = f == 0 ? a.in.sxx : f == 1 ? a.in.szz : f == 2 ? a.in.sxz
-                              : f == 3 ? a.M.lam : f == 4 ? a.M.mu : a.M.muxz;
-            const long long c = ok ? offn + (long long)(j + EFWI_GZ) * pitchn + col : 0;
-            cp_async16(pf1 + f * (SX * SZ) + y * SX + 4 * c4, base + c, ok ? 16 : 0);
-        }
-        cp_async_commit();
-    };
 
     // With a persistent grid (fewer CTAs than tiles) the next tile's work item, and
     // the block offset and row pitch of its shot, are loaded one tile ahead, so an
@@ -273,18 +240,14 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
     int4 tl_next = blockIdx.x < a.ntiles ? __ldg(a.tiles + blockIdx.x) : make_int4(0, 0, 0, 0);
     long long off_next = __ldg(&a.shots[tl_next.x].off);
     int pitch_next = __ldg(&a.shots[tl_next.x].pitch);
-    int nz_next = PF1 ? __ldg(&a.shots[tl_next.x].NZ) : 0;
-    if (PF1 && blockIdx.x < a.ntiles) prefetch1(tl_next, off_next, pitch_next, nz_next);
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const int4 tl = tl_next;
         const long long off = off_next;
         const int pitch = pitch_next;
-        const bool more = t + gridDim.x < a.ntiles;
-        if (more) {
+        if (t + gridDim.x < a.ntiles) {
             tl_next = __ldg(a.tiles + t + gridDim.x);
             off_next = __ldg(&a.shots[tl_next.x].off);
             pitch_next = __ldg(&a.shots[tl_next.x].pitch);
-            if (PF1) nz_next = __ldg(&a.shots[tl_next.x].NZ);
         }
         // interior tiles (no CPML strip or grid edge within the 4-cell halo) run a
         // copy of the body without any of the edge tests
@@ -302,23 +265,13 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
             // 1. f^ on the tile + 4-cell halo; the tile's stress-sub-step PML memory advances
             constexpr int N1 = (SX * SZ + kThreads - 1) / kThreads;
             float lxx[N1], lzz[N1], lxz[N1], llam[N1], lmu[N1], lmxz[N1];
-            if constexpr (PF1) {
-                cp_async_wait_all();                        // this tile's staged inputs
-                __syncthreads();
-            }
 #pragma unroll
             for (int r = 0; r < N1; ++r) {
                 const int q = tid + r * kThreads;
                 lxx[r] = lzz[r] = lxz[r] = llam[r] = lmu[r] = lmxz[r] = 0.f;
                 const int y = q / SX, x = q - y * SX;
                 const int i = i0 - 4 + x, j = j0 - 4 + y;
-                if (PF1) {
-                    if (q < SX * SZ) {
-                        constexpr int NS1 = SX * SZ;
-                        lxx[r] = pf1[q]; lzz[r] = pf1[NS1 + q]; lxz[r] = pf1[2 * NS1 + q];
-                        llam[r] = pf1[3 * NS1 + q]; lmu[r] = pf1[4 * NS1 + q]; lmxz[r] = pf1[5 * NS1 + q];
-                    }
-                } else if (q < SX * SZ && (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ))) {
+                if (q < SX * SZ && (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ))) {
                     const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                     lxx[r] = ldg256(a.in.sxx + c); lzz[r] = ldg256(a.in.szz + c); lxz[r] = ldg256(a.in.sxz + c);
                     llam[r] = ldg256(a.M.lam + c); lmu[r] = ldg256(a.M.mu + c); lmxz[r] = ldg256(a.M.muxz + c);
@@ -369,8 +322,6 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                 if (edge) f4s[q] = g4;                     // f^4 == f^3 away from the CPML
             }
             __syncthreads();
-            // every thread has read the staged inputs: stage the next tile's while this one finishes
-            if (PF1 && more) prefetch1(tl_next, off_next, pitch_next, nz_next);
 
             // 2. v^ += D^T f^ on the tile + 2-cell halo; e^ in shared memory
             constexpr int N2 = (VX * VZ + kThreads - 1) / kThreads;
@@ -515,9 +466,7 @@ constexpr Shape kShapes[] = {{32, 8}, {32, 16}, {64, 8}, {64, 16}, {32, 32}, {12
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 size_t fwd_smem(int tx, int tz) { return sizeof(float) * (3 * (tx + 8) * (tz + 8) + 2 * (tx + 4) * (tz + 4)); }
-size_t adj_smem(int tx, int tz, bool pf1 = false) {
-    return sizeof(float) * (4 * (tx + 8) * (tz + 8) + 6 * (tx + 4) * (tz + 4) + (pf1 ? 6 * (tx + 8) * (tz + 8) : 0));
-}
+size_t adj_smem(int tx, int tz) { return sizeof(float) * (4 * (tx + 8) * (tz + 8) + 6 * (tx + 4) * (tz + 4)); }
 
 template <int TX, int TZ>
 void fwd_launch(const FwdArgs &a, int grid, cudaStream_t st) {
@@ -539,8 +488,6 @@ void set_all_attrs() {
     if (done) return;
     done = true;
     set_attrs<32, 8>(); set_attrs<32, 16>(); set_attrs<64, 8>(); set_attrs<64, 16>();
-    cudaFuncSetAttribute(k_adj_fused<32, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)adj_smem(32, 16, true));
     set_attrs<32, 32>(); set_attrs<128, 8>(); set_attrs<64, 32>();
 }
 
@@ -682,10 +629,7 @@ void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, c
         const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles)
                          : p->adj_grid > 0        ? std::min(p->adj_grid, a.ntiles)
                                                   : a.ntiles;
-        if (p->adj_pf1 && p->adj_tiles.tx == 32 && p->adj_tiles.tz == 16)
-            k_adj_fused<32, 16, true><<<grid, kThreads, adj_smem(32, 16, true), st>>>(a);
-        else
-            EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
+        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
     }
     prof_end(p, st, slot);
     p->launches++;
@@ -727,17 +671,10 @@ float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEv
 
 int select_adj(efwi_plan *p, const Variant &v) {
     p->adj_stencil = v.kind;
-    // per-thread loads, 32x16: vec bit 1 = persistent grid, bit 3 = first phase staged ahead (persistent)
-    const bool l32 = v.kind == EFWI_STENCIL_LOADS && v.tx == 32 && v.tz == 16;
-    p->adj_pf1 = l32 && (v.vec & 8);
     p->adj_grid = 0;
-    if (l32 && (v.vec & 2)) {
+    if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2 && v.tx == 32 && v.tz == 16) {   // loads: vec 2 = persistent
         int nb = 0;
-        if (p->adj_pf1)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16, true>, kThreads,
-                                                          adj_smem(32, 16, true));
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
         p->adj_grid = std::max(1, nb) * p->n_sms;
     }
     int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
@@ -789,16 +726,12 @@ int efwi_autotune(efwi_plan *p) {
                     : (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)))
             continue;
         if (wa == EFWI_STENCIL_AUTO || wa == EFWI_STENCIL_LOADS) {
-            // 32x16 also on a persistent grid (the next tile's descriptor loaded ahead), with or
-            // without its first phase staged ahead; EFWI_ADJ_PERSIST=0|1 and EFWI_ADJ_PF1=0|1 keep
-            // only those (tests of one variant)
-            const char *fp = getenv("EFWI_ADJ_PERSIST"), *ff = getenv("EFWI_ADJ_PF1");
-            const int only_p = fp ? atoi(fp) : -1, only_f = ff ? atoi(ff) : -1;
-            if (only_p <= 0 && only_f <= 0) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-            if (s.tx == 32 && s.tz == 16 && only_p != 0) {
-                if (only_f <= 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
-                if (only_f != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2 | 8});
-            }
+            // 32x16 also on a persistent grid (the next tile's descriptor loaded ahead);
+            // EFWI_ADJ_PERSIST=0|1 keeps only one of the two (tests of one variant)
+            const char *fp = getenv("EFWI_ADJ_PERSIST");
+            const int only_p = fp ? atoi(fp) : -1;
+            if (only_p <= 0) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+            if (s.tx == 32 && s.tz == 16 && only_p != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
         }
         for (int nst = 1; nst <= 2; ++nst)
             if (wa != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
@@ -839,8 +772,8 @@ int efwi_autotune(efwi_plan *p) {
         for (auto &v : adj) {
             if (select_adj(p, v)) continue;
             const float t = time_steps(p, true, st, e0, e1);
-            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d persistent %d staged %d: %.1f us\n",
-                             v.kind, v.tx, v.tz, v.nst, (v.vec & 2) != 0, (v.vec & 8) != 0, t * 1e3f / 3);
+            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d persistent %d: %.1f us\n", v.kind,
+                             v.tx, v.tz, v.nst, v.vec == 2, t * 1e3f / 3);
             if (t < best) { best = t; ba = v; }
         }
         cudaEventDestroy(e0);

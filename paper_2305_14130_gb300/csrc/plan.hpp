@@ -110,7 +110,6 @@ struct efwi_plan {
     efwi::AdjMaps *adj_maps = nullptr;
     int tma_adj_grid = 0, tma_adj_stages = 1;
     int adj_grid = 0;                      // per-thread-load adjoint: persistent grid (0 = one CTA per tile)
-    bool adj_pf1 = false;                  // per-thread-load adjoint: first phase staged one tile ahead
     int *dev_err = nullptr;                // device flag: a bounded wait expired
     int adj_tile_x = 0, adj_tile_z = 0;    // adjoint tile
     size_t bytes = 0;

@@ -329,7 +329,7 @@ TMA_SHAPES = [(32, 8), (32, 16), (64, 8), (64, 16)]
 STAGED_SHAPES = [(32, 16)]
 VARIANTS = [("loads", s) for s in SHAPES] + [(k, s) for k in ("tma", "tma_pairs") for s in TMA_SHAPES] + \
     [("tma_staged", s) for s in STAGED_SHAPES] + [("tma_pairs:split", (32, 16)), ("tma_staged:split", (32, 16)),
-                                                   ("loads:adjp", (32, 16)), ("loads:adjp1", (32, 16))]
+                                                   ("loads:adjp", (32, 16))]
 
 
 @pytest.mark.parametrize("source", ["moment_tensor", "force"])
@@ -348,14 +348,12 @@ def test_stencil_variants_do_not_change_results(efwi, source, monkeypatch):
     for stencil, (tx, tz) in VARIANTS:
         # ":split": cell pairs on the tile, the velocity halo ring as single cells
         stencil, _, layout = stencil.partition(":")
-        # ":adjp": the per-thread-load adjoint on a persistent grid; ":adjp1" the same with its first
-        # phase's inputs staged in shared memory one tile ahead
+        # ":adjp": the per-thread-load adjoint on a persistent grid
         if layout == "split":
             monkeypatch.setenv("EFWI_TMA_VEC", "3")
         else:
             monkeypatch.delenv("EFWI_TMA_VEC", raising=False)
-        monkeypatch.setenv("EFWI_ADJ_PERSIST", "1" if layout in ("adjp", "adjp1") else "0")
-        monkeypatch.setenv("EFWI_ADJ_PF1", "1" if layout == "adjp1" else "0")
+        monkeypatch.setenv("EFWI_ADJ_PERSIST", "1" if layout == "adjp" else "0")
         plan = efwi.Plan(p.acq, exec="batched", tile=(tx, tz), stencil=stencil)
         info = plan.info()
         assert (info["tile_x"], info["tile_z"]) == (tx, tz)
