@@ -378,6 +378,14 @@ int efwi_lbfgs_push(efwi_lbfgs *h, const float *s, const float *y, int *accepted
  * pseudo-Hessian of efwi_pseudo_hessian this way).  NULL returns to
  * H_0 = gamma I.  Forgets the stored pairs.                                 */
 int efwi_lbfgs_set_h0(efwi_lbfgs *h, const float *diag, efwi_stream_t stream);
+/* Saves the history (to resume an inversion later; the paper has no
+ * counterpart): *pairs receives the number of stored pairs; when S_out and
+ * Y_out (device [pairs][n] each) are given, the pairs are copied there,
+ * oldest first (asynchronous).  Restoring is efwi_lbfgs_reset followed by
+ * efwi_lbfgs_push of each pair in the same order, which recomputes their
+ * scalars with the same reductions, so directions are bit-identical; a
+ * diagonal H_0 is set again with efwi_lbfgs_set_h0 before the pushes.       */
+int efwi_lbfgs_export(efwi_lbfgs *h, int *pairs, float *S_out, float *Y_out, efwi_stream_t stream);
 /* d = -H g (device [n] each) from the stored pairs, asynchronous.          */
 int efwi_lbfgs_direction(efwi_lbfgs *h, const float *g, float *d, efwi_stream_t stream);
 /* One iteration from x (device [n], updated), *phi (host, updated) and its

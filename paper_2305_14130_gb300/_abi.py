@@ -74,6 +74,7 @@ SIGNATURES = {
     "efwi_lbfgs_push": (C.c_int, [VP, VP, VP, C.POINTER(C.c_int), VP]),
     "efwi_lbfgs_direction": (C.c_int, [VP, VP, VP, VP]),
     "efwi_lbfgs_set_h0": (C.c_int, [VP, VP, VP]),
+    "efwi_lbfgs_export": (C.c_int, [VP, C.POINTER(C.c_int), VP, VP, VP]),
     "efwi_lbfgs_iterate": (C.c_int, [VP, VP, C.POINTER(C.c_double), VP, OBJECTIVE_FN, VP, C.POINTER(LbfgsInfo), VP]),
     "efwi_lbfgs_run": (C.c_int, [VP, VP, VP, OBJECTIVE_FN, VP, C.c_int, C.c_double, C.POINTER(LbfgsInfo), VP]),
     "efwi_regularization_grad_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, C.c_double, VP, VP,

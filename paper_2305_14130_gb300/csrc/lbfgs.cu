@@ -383,6 +383,20 @@ extern "C" int efwi_lbfgs_set_h0(efwi_lbfgs *h, const float *diag, efwi_stream_t
     return lb_check("l-BFGS initial inverse Hessian");
 }
 
+extern "C" int efwi_lbfgs_export(efwi_lbfgs *h, int *pairs, float *S_out, float *Y_out, efwi_stream_t stream) {
+    if (!h || !pairs) return lb_fail(EFWI_ERR_ARG, "NULL argument");
+    *pairs = (int)h->order.size();
+    if (!S_out && !Y_out) return EFWI_OK;                  // query the number of pairs only
+    if (!S_out || !Y_out) return lb_fail(EFWI_ERR_ARG, "S_out and Y_out must both be given");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int j = 0; j < *pairs; ++j) {                      // oldest first
+        const int k = h->order[j];
+        cudaMemcpyAsync(S_out + (long long)j * h->n, slot_s(h, k), sizeof(float) * h->n, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(Y_out + (long long)j * h->n, slot_y(h, k), sizeof(float) * h->n, cudaMemcpyDeviceToDevice, st);
+    }
+    return lb_check("l-BFGS export");
+}
+
 extern "C" int efwi_lbfgs_push(efwi_lbfgs *h, const float *s, const float *y, int *accepted, efwi_stream_t stream) {
     if (!h || !s || !y) return lb_fail(EFWI_ERR_ARG, "NULL argument");
     cudaStream_t st = (cudaStream_t)stream;

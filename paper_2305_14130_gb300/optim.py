@@ -93,6 +93,26 @@ class LBFGS:
         p = None if diag is None else _vec(diag, self.n, "diag")
         _abi.check(self._lib.efwi_lbfgs_set_h0(self._h, p, _stream()))
 
+    def state(self):
+        """The stored pairs (S, Y), device tensors [pairs, n], oldest first: save them
+        to resume the inversion with load_state."""
+        k = C.c_int()
+        _abi.check(self._lib.efwi_lbfgs_export(self._h, C.byref(k), None, None, _stream()))
+        S = torch.empty((k.value, self.n), dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(S)
+        if k.value:
+            _abi.check(self._lib.efwi_lbfgs_export(self._h, C.byref(k), C.c_void_p(S.data_ptr()),
+                                                   C.c_void_p(Y.data_ptr()), _stream()))
+        return S, Y
+
+    def load_state(self, S, Y):
+        """Replaces the history with the pairs of state() (set a diagonal H_0 first if
+        one is used); the directions then equal the saved handle's bit for bit."""
+        self.reset()
+        for s, y in zip(S, Y):
+            if not self.push(s.contiguous(), y.contiguous()):
+                raise ValueError("a saved pair has s^T y <= 0")
+
     def direction(self, g, d=None):
         """d = -H g from the stored pairs (two-loop recursion)."""
         if d is None:
