@@ -49,3 +49,29 @@ def test_aggregate_single_rank():
     import bench
     ms, s, value = bench.aggregate(50.0, cells_per_rank=1e9, steps=5, world=1)
     assert ms == 50.0 and abs(s - 0.01) < 1e-15 and abs(value - 100.0) < 1e-9
+
+
+def test_roofline_entries_from_kernel_timings():
+    """bench.roofline: achieved = algorithmic bytes x cells / mean launch time,
+    frac = achieved / measured peak, traffic only for captured variants, the
+    kernel with the larger share of the gradient first."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peak, kind = bench.peaks()
+    info = {"padded_cells": 1_000_000, "ckpt_interval": 64, "stencil": 3, "adj_stencil": 1, "tile_x": 32,
+            "tile_z": 16, "adj_tile_x": 32, "adj_tile_z": 16, "layout": 3, "staged_stores": 0, "adj_persistent": 1}
+    prof = {"step": (10.0, 100), "adj": (20.0, 50)}          # ms summed, launches timed
+    first, second = bench.roofline("batched", info, prof, nt=4000, ns=32)
+    step = first if first["kernel"].startswith("forward") else second
+    adj = second if step is first else first
+    assert abs(step["avg_us"] - 100.0) < 1e-9 and abs(adj["avg_us"] - 400.0) < 1e-9
+    assert abs(step["achieved"] - 60.0 * 1e6 / 100e-6 / 1e9) < 1e-6
+    assert abs(adj["achieved"] - 108.0 * 1e6 / 400e-6 / 1e9) < 1e-6
+    assert abs(step["frac"] - step["achieved"] / peak) < 1e-12 and step["peak_kind"] == kind
+    assert step["traffic"] == bench.TRAFFIC_PER_CELL[("step", 3, 32, 16, 3, 0)] * 1e6
+    assert adj["traffic"] == bench.TRAFFIC_PER_CELL[("adj", 1, 32, 16, 1)] * 1e6
+    # forward and recompute: 2 x 4000 x 100 us = 0.8 s against 4000 x 400 us = 1.6 s
+    assert first is adj and abs(adj["time_share_est"] - 2 / 3) < 1e-12
+    info2 = dict(info, layout=2)                             # a variant without a capture
+    s2 = [r for r in bench.roofline("batched", info2, prof, nt=4000, ns=32) if r["kernel"].startswith("forward")][0]
+    assert s2["traffic"] is None
