@@ -143,6 +143,28 @@ TRAFFIC_PER_CELL = {
 }
 
 
+# Algorithmic bytes of one whole gradient per padded cell and time step: the forward
+# pass (60 B), the recompute of every checkpoint segment, which also writes vx, vz of
+# each step to the segment buffer (60 + 8 B), and the adjoint step (108 B).  With every
+# step stored the recompute drops and the forward pass writes the velocities: 68 + 108 =
+# 176 B, the floor of the method (forward, adjoint, velocity hand-off, imaging sums).
+GRAD_FLOOR_BYTES = 176.0
+
+
+def gradient_roofline(info, nt, s_per_grad):
+    """Bandwidth of the whole gradient (one GPU's shots, every kernel of the step
+    included) at the algorithmic bytes of its schedule and at the floor of 176 B per
+    padded cell-step, both against the measured HBM peak."""
+    hbm, peak_kind = peaks()
+    sqrt_ckpt = info["ckpt_interval"] < nt
+    bpc = (60.0 + 68.0 + 108.0) if sqrt_ckpt else GRAD_FLOOR_BYTES
+    work = info["padded_cells"] * nt / s_per_grad / 1e9
+    return {"bound": "hbm", "unit": "GB/s", "peak": hbm, "peak_kind": peak_kind,
+            "schedule": "sqrt(nt) checkpoints + recompute" if sqrt_ckpt else "every step stored",
+            "bytes_per_cell_step": bpc, "achieved": bpc * work, "frac": bpc * work / hbm,
+            "floor_bytes_per_cell_step": GRAD_FLOOR_BYTES, "floor_frac": GRAD_FLOOR_BYTES * work / hbm}
+
+
 def roofline(exec_, info, prof, nt, ns):
     """Roofline entries of the dominant and of the other stencil kernel."""
     hbm, peak_kind = peaks()
@@ -431,6 +453,7 @@ def run_ours(args):
                 "padded_Gcell_updates_s": info["padded_cells"] * acq.nt * world / s_per_grad / 1e9,
                 "gpu_launches": launches_per_step * args.steps, "clocks": ck, "roofline": roofs[0],
                 "roofline_other": roofs[1],
+                "gradient_roofline": gradient_roofline(info, acq.nt, s_per_grad),
                 "e2e": e2e, "plain_fp32": plain, "cpu_baseline": cpu,
                 "workspace_GB": info["workspace_bytes"] / 1e9}
         print(json.dumps(line), flush=True)

@@ -75,3 +75,20 @@ def test_roofline_entries_from_kernel_timings():
     info2 = dict(info, layout=2)                             # a variant without a capture
     s2 = [r for r in bench.roofline("batched", info2, prof, nt=4000, ns=32) if r["kernel"].startswith("forward")][0]
     assert s2["traffic"] is None
+
+
+def test_gradient_roofline_bytes_and_fractions():
+    """bench.gradient_roofline: 236 B per padded cell-step with sqrt(nt) checkpoints
+    (forward, recompute with the velocity hand-off, adjoint), 176 B with every step
+    stored; the floor fraction always uses 176 B."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peak, _ = bench.peaks()
+    info = {"padded_cells": 2_000_000, "ckpt_interval": 64}
+    r = bench.gradient_roofline(info, nt=4000, s_per_grad=2.0)
+    work = 2e6 * 4000 / 2.0 / 1e9
+    assert r["bytes_per_cell_step"] == 236.0 and abs(r["achieved"] - 236.0 * work) < 1e-9
+    assert abs(r["frac"] - 236.0 * work / peak) < 1e-12
+    assert abs(r["floor_frac"] - 176.0 * work / peak) < 1e-12
+    full = bench.gradient_roofline(dict(info, ckpt_interval=4000), nt=4000, s_per_grad=2.0)
+    assert full["bytes_per_cell_step"] == 176.0 and full["frac"] == full["floor_frac"]
