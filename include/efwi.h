@@ -316,7 +316,8 @@ int efwi_collapse(int ns, int nx, int nz, const float *x, const float *b, const 
  * velocity component.  Shot s runs in its own component of the extended
  * model (vp, vs, rho: device [ns][nz][nx]) and contributes inside its window.
  *   eps     clipping level, 0 < eps <= 1 (EFWI_ERR_ARG otherwise)
- *   h       device [nz][nx] FP32 (overwritten); accumulated in FP64
+ *   h       device [nz][nx] FP32 (overwritten); accumulated over time in
+ *           Kahan-compensated FP32 per shot, summed over shots in FP64
  *   h_inv   device [nz][nx] FP32 (overwritten), or NULL
  * Runs one forward pass of every shot (no DAS sampling); uses the plan's
  * imaging workspace, so it must not overlap an efwi_adjoint_gradient call

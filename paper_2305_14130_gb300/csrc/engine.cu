@@ -284,15 +284,16 @@ extern "C" int efwi_pseudo_hessian(efwi_plan *p, const float *vp, const float *v
     cudaStream_t st = (cudaStream_t)stream;
     p->launches = 0;
     launch_materials(p, vp, vs, rho, st);
-    // FP64 accumulator with the wavefield layout, over the imaging workspace G
-    double *acc = reinterpret_cast<double *>(p->G);
+    // Kahan-compensated FP32 sum and its compensation with the wavefield layout,
+    // over the first two fields of the imaging workspace G
+    float *acc = p->G, *cmp = p->G + p->fsz_total;
     Phase ph("efwi pseudo-Hessian");
     auto body = [&](cudaStream_t cs) {
         reset_forward_state(p, cs);
-        cudaMemsetAsync(acc, 0, sizeof(double) * p->fsz_total, cs);
+        cudaMemsetAsync(acc, 0, sizeof(float) * 2 * p->fsz_total, cs);
         for (int n = 0; n < p->d.nt; ++n) {
             forward_step(p, n, nullptr, nullptr, nullptr, cs);
-            launch_vel_energy(p, state_fields(p, p->d.exec == EFWI_EXEC_PLAIN ? 0 : p->scur), acc, cs);
+            launch_vel_energy(p, state_fields(p, p->d.exec == EFWI_EXEC_PLAIN ? 0 : p->scur), acc, cmp, cs);
         }
     };
     if (p->d.exec == EFWI_EXEC_BATCHED && p->use_graphs) {
@@ -300,7 +301,7 @@ extern "C" int efwi_pseudo_hessian(efwi_plan *p, const float *vp, const float *v
     } else {
         body(st);
     }
-    launch_ph_finish(p, acc, eps, h, h_inv, st);
+    launch_ph_finish(p, acc, cmp, eps, h, h_inv, st);
     return cuda_status(p, "pseudo-Hessian");
 }
 

@@ -9,9 +9,11 @@
 //   P(x) = c / max(H(x), c),  c = eps * max_x H   (P = 1 everywhere if H = 0).
 //
 // k_vel_energy runs after every forward step and adds |v|^2 of every physical
-// node of every shot to an FP64 accumulator with the wavefield layout;
-// k_ph_collect sums the shots covering each physical pixel (fixed shot order)
-// and takes block maxima; k_max_final and k_ph_scale finish the inverse.
+// node of every shot, in FP32, to a Kahan-compensated FP32 sum with the
+// wavefield layout (the same precision as the imaging sums); k_ph_collect adds
+// the compensated sums of the shots covering each physical pixel in FP64
+// (fixed shot order) and takes block maxima; k_max_final and k_ph_scale finish
+// the inverse.
 #include <algorithm>
 
 #include "plan.hpp"
@@ -22,14 +24,18 @@ namespace {
 constexpr int kT = 256;
 
 // grid (ceil(wmax / kT), nz, ns): one thread per physical node of shot blockIdx.z
-__global__ void k_vel_energy(const ShotDev *shots, Fields F, double *acc) {
+__global__ void k_vel_energy(const ShotDev *shots, Fields F, float *sum, float *cmp) {
     const ShotDev &s = shots[blockIdx.z];
     const int i = blockIdx.x * kT + threadIdx.x;
     if (i >= s.w) return;
     const long long c = cell_of(s, i + s.P, (int)blockIdx.y + s.P);
-    const double vx = 0.5 * ((double)F.vx[c - 1] + (double)F.vx[c]);
-    const double vz = 0.5 * ((double)F.vz[c - s.pitch] + (double)F.vz[c]);
-    acc[c] += vx * vx + vz * vz;
+    const float vx = 0.5f * (F.vx[c - 1] + F.vx[c]);
+    const float vz = 0.5f * (F.vz[c - s.pitch] + F.vz[c]);
+    // Kahan (1965) compensated add; cmp holds the part of sum that overshoots
+    const float y = (vx * vx + vz * vz) - cmp[c];
+    const float t = sum[c] + y;
+    cmp[c] = (t - sum[c]) - y;
+    sum[c] = t;
 }
 
 __device__ double block_max(double v) {
@@ -47,8 +53,8 @@ __device__ double block_max(double v) {
     return v;
 }
 
-__global__ void k_ph_collect(const ShotDev *shots, int ns, const double *acc, int nx, long long npix, float *h,
-                             double *partial) {
+__global__ void k_ph_collect(const ShotDev *shots, int ns, const float *sum, const float *cmp, int nx,
+                             long long npix, float *h, double *partial) {
     double m = 0.0;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < npix;
          k += (long long)gridDim.x * blockDim.x) {
@@ -57,7 +63,10 @@ __global__ void k_ph_collect(const ShotDev *shots, int ns, const double *acc, in
         for (int s = 0; s < ns; ++s) {
             const ShotDev &sh = shots[s];
             const int il = i - sh.x0;
-            if (il >= 0 && il < sh.w) v += acc[cell_of(sh, il + sh.P, j + sh.P)];
+            if (il >= 0 && il < sh.w) {
+                const long long c = cell_of(sh, il + sh.P, j + sh.P);
+                v += (double)sum[c] - (double)cmp[c];
+            }
         }
         h[k] = (float)v;
         m = fmax(m, v);
@@ -82,17 +91,18 @@ __global__ void k_ph_scale(const float *h, long long npix, const double *hmax, d
 
 }  // namespace
 
-void launch_vel_energy(efwi_plan *p, Fields F, double *acc, cudaStream_t st) {
+void launch_vel_energy(efwi_plan *p, Fields F, float *sum, float *cmp, cudaStream_t st) {
     int wmax = 1;
     for (int s = 0; s < p->d.ns; ++s) wmax = std::max(wmax, p->shots[s].w);
     const dim3 grid((wmax + kT - 1) / kT, p->d.nz, p->d.ns);
-    k_vel_energy<<<grid, kT, 0, st>>>(p->shots_d, F, acc);
+    k_vel_energy<<<grid, kT, 0, st>>>(p->shots_d, F, sum, cmp);
     p->launches++;
 }
 
-void launch_ph_finish(efwi_plan *p, const double *acc, double eps, float *h, float *hinv, cudaStream_t st) {
+void launch_ph_finish(efwi_plan *p, const float *sum, const float *cmp, double eps, float *h, float *hinv,
+                      cudaStream_t st) {
     const long long npix = (long long)p->d.nx * p->d.nz;
-    k_ph_collect<<<kPartials, kT, 0, st>>>(p->shots_d, p->d.ns, acc, p->d.nx, npix, h, p->partial);
+    k_ph_collect<<<kPartials, kT, 0, st>>>(p->shots_d, p->d.ns, sum, cmp, p->d.nx, npix, h, p->partial);
     k_max_final<<<1, 1024, 0, st>>>(p->partial, kPartials, p->partial + kPartials);
     p->launches += 2;
     if (hinv) {

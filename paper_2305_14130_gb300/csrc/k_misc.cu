@@ -22,8 +22,8 @@ struct MatArgs {
     int *err;                           // device flag: bit 2 set for a non-finite or invalid model value
 };
 
-__device__ void model_at(const MatArgs &a, const ShotDev &s, int shot, int i, int j, double &vp, double &vs,
-                         double &rho) {
+__device__ void model_at(const MatArgs &a, const ShotDev &s, int shot, int i, int j, float &vp, float &vs,
+                         float &rho) {
     i = min(i, s.NX - 1);
     j = min(j, s.NZ - 1);
     int ix = i - s.P, iz = j - s.P;
@@ -40,13 +40,15 @@ __device__ void model_at(const MatArgs &a, const ShotDev &s, int shot, int i, in
     }
 }
 
+// FP32 arithmetic (each operation rounded once: the library builds without
+// multiply-add contraction); the inputs are FP32 already.
 __global__ void k_materials(MatArgs a) {
     const int shot = a.shot >= 0 ? a.shot : blockIdx.z;
     const ShotDev s = a.shots[shot];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= s.NX || j >= s.NZ) return;
-    double vp, vs, rho, mu[4], r[4];
+    float vp, vs, rho, mu[4], r[4];
     const int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
     for (int k = 0; k < 4; ++k) {
         model_at(a, s, shot, i + di[k], j + dj[k], vp, vs, rho);
@@ -55,14 +57,14 @@ __global__ void k_materials(MatArgs a) {
     }
     model_at(a, s, shot, i, j, vp, vs, rho);
     // a non-finite velocity or density, or a non-positive density, makes the call's results invalid
-    if (!(isfinite(vp) && isfinite(vs) && isfinite(rho) && rho > 0.0)) atomicOr(a.err, EFWI_FLAG_BAD_MODEL);
+    if (!(isfinite(vp) && isfinite(vs) && isfinite(rho) && rho > 0.f)) atomicOr(a.err, EFWI_FLAG_BAD_MODEL);
     const long long c = cell_of(s, i, j);
-    const bool zero = mu[0] == 0 || mu[1] == 0 || mu[2] == 0 || mu[3] == 0;
-    ((float *)a.M.lam)[c] = (float)(rho * (vp * vp - 2.0 * vs * vs));
-    ((float *)a.M.mu)[c] = (float)mu[0];
-    ((float *)a.M.muxz)[c] = zero ? 0.f : (float)(4.0 / (1.0 / mu[0] + 1.0 / mu[1] + 1.0 / mu[2] + 1.0 / mu[3]));
-    ((float *)a.M.bx)[c] = (float)(0.5 * (1.0 / r[0] + 1.0 / r[1]));
-    ((float *)a.M.bz)[c] = (float)(0.5 * (1.0 / r[0] + 1.0 / r[2]));
+    const bool zero = mu[0] == 0.f || mu[1] == 0.f || mu[2] == 0.f || mu[3] == 0.f;
+    ((float *)a.M.lam)[c] = rho * (vp * vp - 2.f * vs * vs);
+    ((float *)a.M.mu)[c] = mu[0];
+    ((float *)a.M.muxz)[c] = zero ? 0.f : 4.f / (1.f / mu[0] + 1.f / mu[1] + 1.f / mu[2] + 1.f / mu[3]);
+    ((float *)a.M.bx)[c] = 0.5f * (1.f / r[0] + 1.f / r[1]);
+    ((float *)a.M.bz)[c] = 0.5f * (1.f / r[0] + 1.f / r[2]);
 }
 
 // --------------------------------------------------------------------------
@@ -212,6 +214,8 @@ struct ChainArgs {
     int nx, nz;
 };
 
+// FP32 arithmetic; mu_xz / mu is formed before squaring so no intermediate
+// leaves the range of the moduli.
 __global__ void k_chain(ChainArgs a) {
     const int shot = blockIdx.z;
     const ShotDev s = a.shots[shot];
@@ -220,30 +224,30 @@ __global__ void k_chain(ChainArgs a) {
     if (ixw >= s.w || iz >= a.nz) return;
     const int ix = ixw + s.x0;
     const long long o = ((long long)shot * a.nz + iz) * a.nx + ix;
-    const double vp = a.vp[o], vs = a.vs[o], rho = a.rho[o];
-    const double mu = rho * vs * vs;
+    const float vp = a.vp[o], vs = a.vs[o], rho = a.rho[o];
+    const float mu = rho * vs * vs;
     const long long c = cell_of(s, ixw + s.P, iz + s.P);
     const long long P = s.pitch;
-    const double dlam = a.Glam[c];
-    double dmu = a.Gmu[c];
+    const float dlam = a.Glam[c];
+    float dmu = a.Gmu[c];
     const long long cx[4] = {c, c - 1, c - P, c - P - 1};
     for (int k = 0; k < 4; ++k) {
-        const double m = a.M.muxz[cx[k]];
-        dmu += (double)a.Gmuxz[cx[k]] * m * m / (4.0 * mu * mu);
+        const float q = a.M.muxz[cx[k]] / mu;
+        dmu += a.Gmuxz[cx[k]] * (0.25f * q * q);
     }
-    const double db = (double)a.Gbx[c] / a.M.bx[c] + (double)a.Gbx[c - 1] / a.M.bx[c - 1] +
-                      (double)a.Gbz[c] / a.M.bz[c] + (double)a.Gbz[c - P] / a.M.bz[c - P];
-    const double drho = -0.5 / (rho * rho) * db;
-    double gvp = 2.0 * rho * vp * dlam;
-    double gvs = 2.0 * rho * vs * (dmu - 2.0 * dlam);
-    double grh = dlam * (vp * vp - 2.0 * vs * vs) + dmu * vs * vs + drho;
+    const float db = a.Gbx[c] / a.M.bx[c] + a.Gbx[c - 1] / a.M.bx[c - 1] + a.Gbz[c] / a.M.bz[c] +
+                     a.Gbz[c - P] / a.M.bz[c - P];
+    const float drho = -((0.5f * db) / rho) / rho;
+    float gvp = 2.f * rho * vp * dlam;
+    float gvs = 2.f * rho * vs * (dmu - 2.f * dlam);
+    float grh = dlam * (vp * vp - 2.f * vs * vs) + dmu * (vs * vs) + drho;
     if (a.mask) {
-        const double m = a.mask[(long long)iz * a.nx + ix];
+        const float m = a.mask[(long long)iz * a.nx + ix];
         gvp *= m; gvs *= m; grh *= m;
     }
-    a.gvp[o] = (float)gvp;
-    a.gvs[o] = (float)gvs;
-    a.grho[o] = (float)grh;
+    a.gvp[o] = gvp;
+    a.gvs[o] = gvs;
+    a.grho[o] = grh;
 }
 
 // Kahan (1965) compensated add of the segment sums into the totals.

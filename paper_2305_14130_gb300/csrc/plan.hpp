@@ -164,8 +164,9 @@ void launch_reg(efwi_plan *p, const float *m, const float *b, const float *bp, c
                 double *phi, float *g, int accumulate_phi, cudaStream_t st, int ns = 0);
 
 // --- k_hessian.cu --------------------------------------------------------------
-void launch_vel_energy(efwi_plan *p, Fields F, double *acc, cudaStream_t st);
-void launch_ph_finish(efwi_plan *p, const double *acc, double eps, float *h, float *hinv, cudaStream_t st);
+void launch_vel_energy(efwi_plan *p, Fields F, float *sum, float *cmp, cudaStream_t st);
+void launch_ph_finish(efwi_plan *p, const float *sum, const float *cmp, double eps, float *h, float *hinv,
+                      cudaStream_t st);
 
 // --- k_plain.cu (shot >= 0: that shot only; shot < 0: all shots in one launch) ---
 void launch_vel_plain(efwi_plan *p, int shot, float *segx, float *segz, cudaStream_t st);

@@ -1,7 +1,8 @@
 """GPU parity of the pseudo-Hessian (efwi_pseudo_hessian) against the FP64
 oracle: the zero-lag auto-correlation of |v| summed over shots and its
 clipped, scaled inverse, through the C ABI.  Acceptance: relative L2 <= 1e-4
-(FP32 time stepping, FP64 accumulation)."""
+(FP32 time stepping, Kahan-compensated FP32 accumulation over time,
+FP64 sum over shots)."""
 import numpy as np
 import pytest
 import torch
@@ -55,7 +56,7 @@ def test_pseudo_hessian_matches_oracle(efwi, name, exec_):
 
 
 def test_repeat_calls_and_gradient_in_between_are_bitwise_identical(efwi):
-    """The FP64 accumulator reuses the imaging workspace: a gradient call in
+    """The compensated sum reuses the imaging workspace: a gradient call in
     between, and the replayed CUDA graph, leave the result unchanged."""
     p = rounded(CASES["windows"]())
     plan = efwi.Plan(p.acq, exec="batched")
