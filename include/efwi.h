@@ -211,7 +211,16 @@ typedef struct efwi_zoi_desc {
  * precomputes CPML profiles, interpolation weights and tile lists, allocates
  * the workspace and, for EXEC_BATCHED with tile 0x0, runs the tile autotuner.
  * Synchronises the device.  Errors: EFWI_ERR_ARG, EFWI_ERR_CFL, EFWI_ERR_OOM,
- * EFWI_ERR_CUDA (*out is then NULL; the message is in efwi_last_error(NULL)). */
+ * EFWI_ERR_CUDA (*out is then NULL; the message is in efwi_last_error(NULL)).
+ * Environment variables read here (all optional; no effect on results, which
+ * are bitwise the same for every variant):
+ *   EFWI_TMA_STAGES=n     the autotuner keeps only n-stage TMA forward variants
+ *   EFWI_TMA_VEC=v        only forward layout v (1 single cells, 2 cell pairs,
+ *                         3 cell pairs with the halo ring as single cells)
+ *   EFWI_ADJ_PERSIST=0|1  only the one-CTA-per-tile / persistent-grid adjoint
+ *   EFWI_AUTOTUNE_LOG=1   print every timed variant on stderr
+ *   EFWI_TEST_FAIL_ALLOC=k  make the k-th workspace allocation fail with
+ *                         EFWI_ERR_OOM (tests of the clean-up path)        */
 int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *desc);
 
 /* Free a plan and its workspace (synchronises the device).  NULL is allowed. */
