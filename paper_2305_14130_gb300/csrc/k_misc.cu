@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "plan.hpp"
+#include "reg_pixel.cuh"
 
 namespace efwi {
 namespace {
@@ -341,12 +342,7 @@ __global__ void k_zoi(ZoiShot z, int s, int nx, int nz, double dx, double dz, do
     sink[o] = inside ? 1 : 0;
 }
 
-// Per pixel over the ns components (FP64 arithmetic):
-//   B = sum b_i;  c_s = (1 - b_s)/(B - b_s) inside sink_s else 0;  d_s = b_s inside else 1
-//   (W m)_s = (d_s - c_s b_s) m_s + c_s sum_i b_i m_i              (eq. 11)
-//   omega_s = b'_s / sum b'                                        (eq. 12)
-//   r = (I - 1 omega^T) W m;  phi += 1/2 eta^2 |r|^2
-//   y = r - omega (1^T r);  g_i += eta^2 [(d_i - c_i b_i) y_i + b_i sum_s c_s y_s]
+// Consistency term per pixel: reg_pixel (reg_pixel.cuh).
 // Collapse of an extended field to one physical field (eq. 9, and eq. 15 when
 // applied to the per-source gradients): out = S_w W x~ per pixel, FP64:
 //   (W x)_s = (d_s - c_s b_s) x_s + c_s sum_i b_i x_i  (eq. 11, c_s and d_s as in k_reg)
@@ -375,53 +371,8 @@ __global__ void k_collapse(const float *x, const float *b, const float *bp, cons
 __global__ void k_reg(const float *m, const float *b, const float *bp, const uint8_t *sink, int ns, long long npix,
                       double eta2, float *g, double *partial) {
     double acc = 0.0;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
-        double B = 0, BM = 0, SBp = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            B += b[o]; BM += (double)b[o] * m[o]; SBp += bp[o];
-        }
-        auto coeffs = [&](long long o, double &c, double &dd, double &bs) {
-            bs = b[o];
-            const bool in = sink[o] != 0 && ns > 1;
-            c = in ? (1.0 - bs) / (B - bs) : 0.0;
-            dd = in ? bs : 1.0;
-        };
-        double mean = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            double c, dd, bs;
-            coeffs(o, c, dd, bs);
-            mean += (double)bp[o] * ((dd - c * bs) * m[o] + c * BM);
-        }
-        mean /= SBp;
-        double R = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            double c, dd, bs;
-            coeffs(o, c, dd, bs);
-            const double r = (dd - c * bs) * m[o] + c * BM - mean;
-            acc += r * r;
-            R += r;
-        }
-        if (!g) continue;
-        double CY = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            double c, dd, bs;
-            coeffs(o, c, dd, bs);
-            const double r = (dd - c * bs) * m[o] + c * BM - mean;
-            CY += c * (r - (double)bp[o] / SBp * R);
-        }
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            double c, dd, bs;
-            coeffs(o, c, dd, bs);
-            const double r = (dd - c * bs) * m[o] + c * BM - mean;
-            const double y = r - (double)bp[o] / SBp * R;
-            if (g) g[o] = (float)((double)g[o] + eta2 * ((dd - c * bs) * y + bs * CY));
-        }
-    }
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x)
+        acc += reg_pixel(m, b, bp, sink, ns, npix, p, eta2, g);
     acc = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }

@@ -20,6 +20,7 @@
 #include <string>
 
 #include "plan.hpp"
+#include "reg_pixel.cuh"
 
 namespace {
 
@@ -44,60 +45,13 @@ __device__ double na_block_sum(double v) {
     return v;
 }
 
-// One pixel per thread; the per-pixel arithmetic (FP64) is that of eqs. 8, 11, 12:
-//   B = sum b_i;  c_s = (1 - b_s)/(B - b_s) inside sink_s else 0;  d_s = b_s inside else 1
-//   (W m)_s = (d_s - c_s b_s) m_s + c_s sum_i b_i m_i;  omega_s = b'_s / sum b'
-//   r = (I - 1 omega^T) W m;  y = r - omega (1^T r);  g_i += eta^2 [(d_i - c_i b_i) y_i + b_i sum_s c_s y_s]
+// One pixel per thread; the per-pixel arithmetic (FP64) of eqs. 8, 11, 12 is
+// reg_pixel, the same as the plan's kernel.
 __global__ void k_reg_noalloc(const float *m, const float *b, const float *bp, const uint8_t *sink, int ns,
                               long long npix, double eta2, float *g, double *partial) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    if (p < npix) {
-        double B = 0, BM = 0, SBp = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            B += b[o]; BM += (double)b[o] * m[o]; SBp += bp[o];
-        }
-        auto coeffs = [&](long long o, double &c, double &dd, double &bs) {
-            bs = b[o];
-            const bool in = sink[o] != 0 && ns > 1;
-            c = in ? (1.0 - bs) / (B - bs) : 0.0;
-            dd = in ? bs : 1.0;
-        };
-        double mean = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            double c, dd, bs;
-            coeffs(o, c, dd, bs);
-            mean += (double)bp[o] * ((dd - c * bs) * m[o] + c * BM);
-        }
-        mean /= SBp;
-        double R = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            double c, dd, bs;
-            coeffs(o, c, dd, bs);
-            const double r = (dd - c * bs) * m[o] + c * BM - mean;
-            acc += r * r;
-            R += r;
-        }
-        double CY = 0;
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            double c, dd, bs;
-            coeffs(o, c, dd, bs);
-            const double r = (dd - c * bs) * m[o] + c * BM - mean;
-            CY += c * (r - (double)bp[o] / SBp * R);
-        }
-        for (int s = 0; s < ns; ++s) {
-            const long long o = s * npix + p;
-            double c, dd, bs;
-            coeffs(o, c, dd, bs);
-            const double r = (dd - c * bs) * m[o] + c * BM - mean;
-            const double y = r - (double)bp[o] / SBp * R;
-            g[o] = (float)((double)g[o] + eta2 * ((dd - c * bs) * y + bs * CY));
-        }
-    }
+    if (p < npix) acc = efwi::reg_pixel(m, b, bp, sink, ns, npix, p, eta2, g);
     acc = na_block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
