@@ -45,7 +45,7 @@ __device__ double na_block_sum(double v) {
     return v;
 }
 
-// One pixel per thread; the per-pixel arithmetic (FP64) of eqs. 8, 11, 12 is
+// One pixel per thread; the per-pixel arithmetic of eqs. 8, 11, 12 is
 // reg_pixel, the same as the plan's kernel.
 __global__ void k_reg_noalloc(const float *m, const float *b, const float *bp, const uint8_t *sink, int ns,
                               long long npix, double eta2, float *g, double *partial) {
