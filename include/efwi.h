@@ -269,7 +269,9 @@ int efwi_zoi_weights(int ns, int nx, int nz, double dx, double dz, const efwi_zo
 /* Consistency term of eq. 8 for one parameter field and its gradient:
  *   phi_reg = 1/2 eta^2 || (I - S^T S_w) W m~ ||^2,
  *   g      += eta^2 W^T (I - S^T S_w)^T (I - S^T S_w) W m~
- * with W of eq. 11 and S_w of eq. 12, per pixel over the ns components.
+ * with W of eq. 11 and S_w of eq. 12, per pixel over the ns components.  The
+ * residual (I - S^T S_w) W m~ and its norm are FP64; the gradient increment is
+ * FP64 at pixels where some component has its sinkhole and FP32 elsewhere.
  *   m, b, bp   device [ns][nz][nx] FP32; sink device [ns][nz][nx] uint8
  *   phi_reg    device double (overwritten; FP64 reduction)
  *   g          device [ns][nz][nx] FP32, accumulated into (+=)             */
