@@ -9,7 +9,6 @@
 * DAS strain is the running time integral of DAS strain rate.
 """
 import numpy as np
-import pytest
 
 import workloads as W
 from oracle import elastic as E
