@@ -147,3 +147,29 @@ def test_null_arguments(lib):
     assert lib.efwi_plan_destroy(None) == 0
     assert lib.efwi_forward(None, None, None, None, None, None) == -1
     assert lib.efwi_pseudo_hessian(None, None, None, None, 1e-3, None, None, None) == -1
+
+
+def test_enum_values_match_binding(tmp_path):
+    """Every status code and enum value the binding (and the workloads' DAS modes)
+    passes across the ABI equals the header's, read by compiling against it."""
+    from paper_2305_14130_gb300 import _abi
+    import workloads as W
+    names = list(_abi.STATUS.values())
+    names += [f"EFWI_STORE_{k.upper()}" for k in _abi.STORE] + [f"EFWI_EXEC_{k.upper()}" for k in _abi.EXEC]
+    names += [f"EFWI_STENCIL_{k.upper()}" for k in _abi.STENCIL] + [f"EFWI_OVERLAP_{k.upper()}" for k in _abi.OVERLAP]
+    names += ["EFWI_DAS_STRAIN", "EFWI_DAS_STRAIN_RATE", "EFWI_DAS_VELOCITY"]
+    prog = tmp_path / "enums.c"
+    prog.write_text("\n".join(['#include <stdio.h>', '#include "efwi.h"', 'int main(void) {']
+                              + [f'printf("%d\\n", (int){n});' for n in names] + ['return 0; }']))
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = dict(zip(names, (int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.split())))
+    for code, n in _abi.STATUS.items():
+        assert got[n] == code, n
+    for table, prefix in ((_abi.STORE, "STORE"), (_abi.EXEC, "EXEC"), (_abi.STENCIL, "STENCIL"),
+                          (_abi.OVERLAP, "OVERLAP")):
+        for k, v in table.items():
+            assert got[f"EFWI_{prefix}_{k.upper()}"] == v, k
+    assert (got["EFWI_DAS_STRAIN"], got["EFWI_DAS_STRAIN_RATE"], got["EFWI_DAS_VELOCITY"]) == \
+        (W.STRAIN, W.STRAIN_RATE, W.VELOCITY) == (_abi.DAS_STRAIN, _abi.DAS_STRAIN_RATE, _abi.DAS_VELOCITY)
