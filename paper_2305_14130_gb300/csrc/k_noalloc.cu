@@ -9,12 +9,17 @@
 // per thread block -- lives in a file-scope __device__ array of fixed size.
 // Every GPU that loads this library holds that array (32 KB) until the
 // process exits.  Host code cannot use the array's name as a device address,
-// so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it; that first
-// call should therefore happen before any stream capture.  All calls share the
-// array: calls that overlap on the GPU (different streams, or host threads
-// racing on one device) race on it.  Every call writes all the partials it
-// later reads, so nothing has to be cleared between calls.
+// so every call made outside a stream capture looks the address up with
+// cudaGetSymbolAddress (with the caller's device current) and remembers it for
+// that device; a call made while its stream is being captured cannot look it up
+// and uses the remembered address, so the first call on each device must come
+// before any stream capture.  A device reset (cudaDeviceReset) or the
+// destruction of the primary context unloads the module and may move the
+// array: the next uncaptured call looks it up again, but a graph captured
+// before the reset holds the old address and must not be replayed.  All calls
+// share the array: calls that overlap on the GPU (different streams, or host
+// threads racing on one device) race on it.  Every call writes all the
+// partials it later reads, so nothing has to be cleared between calls.
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -63,8 +68,10 @@ __global__ void k_sum_noalloc(const double *partial, int n, double scale, double
     if (threadIdx.x == 0) *out = scale * v;
 }
 
-// Device address of the scratch array, looked up once per device.
-int scratch_address(double **out, std::string &err) {
+// Device address of the scratch array on the current device: looked up on every
+// call outside a stream capture (so a reloaded module is found again), the last
+// address looked up on this device inside a capture.
+int scratch_address(cudaStream_t st, double **out, std::string &err) {
     static std::mutex mu;
     static double *addr[128] = {nullptr};
     int dev = 0;
@@ -73,8 +80,13 @@ int scratch_address(double **out, std::string &err) {
         err = std::string("cudaGetDevice failed: ") + cudaGetErrorString(e);
         return EFWI_ERR_CUDA;
     }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusActive;     // cannot tell: do not touch the module
+    }
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_na_partials);
         if (e != cudaSuccess || !p) {
@@ -82,6 +94,10 @@ int scratch_address(double **out, std::string &err) {
             return EFWI_ERR_CUDA;
         }
         addr[dev] = static_cast<double *>(p);
+    } else if (!addr[dev]) {
+        err = "efwi_regularization_grad_noalloc was first called on this device inside a stream capture; "
+              "call it once outside any capture first (the scratch address is looked up there)";
+        return EFWI_ERR_CUDA;
     }
     *out = addr[dev];
     return EFWI_OK;
@@ -113,14 +129,14 @@ extern "C" int efwi_regularization_grad_noalloc(int ns, int nx, int nz, const fl
                                "use efwi_regularization_grad");
         return EFWI_ERR_ARG;
     }
+    cudaStream_t st = (cudaStream_t)stream;
     double *partial = nullptr;
-    int rc = scratch_address(&partial, err);
+    int rc = scratch_address(st, &partial, err);
     if (rc != EFWI_OK) {
         efwi::set_thread_error(err);
         return rc;
     }
     const int blocks = (int)((npix + kNaThreads - 1) / kNaThreads);
-    cudaStream_t st = (cudaStream_t)stream;
     k_reg_noalloc<<<blocks, kNaThreads, 0, st>>>(m, b, bp, sink, ns, npix, eta * eta, g, partial);
     k_sum_noalloc<<<1, 1024, 0, st>>>(partial, blocks, 0.5 * eta * eta, phi_reg);
     cudaError_t e = cudaGetLastError();
