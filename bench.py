@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--exec", default="batched", choices=["batched", "plain"])
     ap.add_argument("--ckpt-store", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--snap-store", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="precision of the stored forward velocities")
+    ap.add_argument("--ckpt", default="0", help="checkpoint interval: 0 = sqrt(nt), n, or auto")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -52,6 +55,9 @@ def parse():
     ap.add_argument("--adj-stencil", default="auto", choices=["auto", "loads", "tma"])
     ap.add_argument("--adj-tile", default="0x0", help="adjoint tile (0x0 = autotune)")
     ap.add_argument("--overlap", default="auto", choices=["auto", "off", "on"])
+    ap.add_argument("--no-reduced", action="store_true", help="skip the reduced-storage record")
+    ap.add_argument("--full-iteration-groups", type=int, default=2,
+                    help="shot groups of the 4000x1200 full-iteration record to time (16 = all; 0 = skip)")
     ap.add_argument("--ns", type=int, default=32)
     ap.add_argument("--nt", type=int, default=4000)
     return ap.parse_args()
@@ -118,64 +124,88 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# Algorithmic bytes per padded cell of one launch of the two stencil kernels
-# (FP32 words each launch must move at least once):
-#   fused forward step: read vx vz sxx szz sxz + lambda mu mu_xz b_x b_z, write 5 = 15 words
-#   fused adjoint step: read 5 adjoint fields + 5 materials + forward vx vz + 5 imaging
-#                       sums, write 5 adjoint fields + 5 imaging sums = 27 words
-#   plain stress half-step: read vx vz + 3 stresses + lambda mu mu_xz, write 3 = 11 words
-#   plain adjoint stress half-step: read 2 + 2 + 3 + 3 + 2 + 3, write 3 + 3 = 21 words
+# Algorithmic bytes per padded cell of one launch of the two stencil kernels (what each
+# launch must move at least once; FP32 words unless stated):
+#   fused forward step: read vx vz sxx szz sxz + lambda mu mu_xz b_x b_z, write 5 = 60 B;
+#     a launch that keeps v^{n+1/2} for the adjoint also writes vx, vz once more (8 B in FP32,
+#     4 B as FP16/BF16 snapshots)
+#   fused adjoint step: read 5 adjoint fields + 5 materials + 5 imaging sums, write 5 + 5
+#     = 100 B, plus the forward vx, vz of the step (8 B FP32, 4 B FP16/BF16)
+#   plain stress half-step: read vx vz + 3 stresses + lambda mu mu_xz, write 3 = 44 B
+#   plain adjoint stress half-step: read 2 + 2 + 3 + 3 + 2 + 3, write 3 + 3 = 84 B
 KERNELS = {
-    ("batched", "step"): ("forward_step (velocity + stress + source, all shots)", 60.0),
-    ("batched", "adj"): ("adjoint_step (transposed step + imaging, all shots)", 108.0),
-    ("plain", "step"): ("k_stress (forward stress half-step, one shot)", 44.0),
-    ("plain", "adj"): ("k_adj_stress (adjoint stress half-step + imaging, one shot)", 84.0),
+    ("batched", "step"): "forward_step (velocity + stress + source, all shots)",
+    ("batched", "adj"): "adjoint_step (transposed step + imaging, all shots)",
+    ("plain", "step"): "k_stress (forward stress half-step, one shot)",
+    ("plain", "adj"): "k_adj_stress (adjoint stress half-step + imaging, one shot)",
 }
+NOMINAL_HBM_GBS = 7900.0
+
+
+def snap_bytes(info):
+    """Bytes of one stored forward-velocity element (FP32, or FP16/BF16 snapshots)."""
+    return 4.0 if info.get("snap_store", 0) == 0 else 2.0
+
+
+def kernel_bytes(exec_, info, nt):
+    """Algorithmic bytes per padded cell of the average forward-step launch of one
+    gradient and of the adjoint-step launch.  With sqrt(nt) checkpoints half of the
+    forward-step launches (the recompute) keep v^{n+1/2}; with every step stored all do."""
+    if exec_ == "plain":
+        return 44.0, 84.0
+    v = 2 * snap_bytes(info)
+    fwd = 60.0 + v if info["ckpt_interval"] >= nt else 60.0 + v / 2
+    return fwd, 100.0 + v
 
 
 # DRAM traffic per padded cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
 # captures of the 8-shot case of this workload with the same kernel variant, scaled to a launch by its
-# cells.  Keyed by (kernel, staging, tile, variant details); any other variant, or a kernel changed
-# since its capture, reports traffic null.
-TRAFFIC_PER_CELL = {
-    ("step", 3, 32, 16, 3, 0): 54.87,   # TMA, split layout, per-thread stores, 32x16
-    ("adj", 1, 32, 16, 1): 94.87,       # per-thread loads, persistent grid, 32x16
-}
+# cells.  Keyed by (kernel, staging, tile, variant details, snapshot store, every step stored); any
+# other variant, or a kernel changed since its capture, reports traffic null.
+TRAFFIC_PER_CELL = {}
 
 
 # Algorithmic bytes of one whole gradient per padded cell and time step: the forward
-# pass (60 B), the recompute of every checkpoint segment, which also writes vx, vz of
-# each step to the segment buffer (60 + 8 B), and the adjoint step (108 B).  With every
-# step stored the recompute drops and the forward pass writes the velocities: 68 + 108 =
-# 176 B, the floor of the method (forward, adjoint, velocity hand-off, imaging sums).
+# pass (60 B), the recompute of every checkpoint segment, which also keeps vx, vz of
+# each step (60 + 8 B), and the adjoint step (100 + 8 B).  With every step stored the
+# recompute drops and the forward pass keeps the velocities: 68 + 108 = 176 B, the floor
+# of the method with FP32 velocities (forward, adjoint, velocity hand-off, imaging
+# sums); FP16/BF16 snapshots halve the hand-off (168 B, or 228 B with the recompute).
 GRAD_FLOOR_BYTES = 176.0
 
 
 def gradient_roofline(info, nt, s_per_grad):
     """Bandwidth of the whole gradient (one GPU's shots, every kernel of the step
-    included) at the algorithmic bytes of its schedule and at the floor of 176 B per
-    padded cell-step, both against the measured HBM peak."""
+    included) at the algorithmic bytes of its schedule and at the FP32 floor of 176 B
+    per padded cell-step, both against the measured HBM peak."""
     hbm, peak_kind = peaks()
     sqrt_ckpt = info["ckpt_interval"] < nt
-    bpc = (60.0 + 68.0 + 108.0) if sqrt_ckpt else GRAD_FLOOR_BYTES
+    v = 2 * snap_bytes(info)
+    bpc = (60.0 + (60.0 + v) + (100.0 + v)) if sqrt_ckpt else (60.0 + v) + (100.0 + v)
     work = info["padded_cells"] * nt / s_per_grad / 1e9
     return {"bound": "hbm", "unit": "GB/s", "peak": hbm, "peak_kind": peak_kind,
             "schedule": "sqrt(nt) checkpoints + recompute" if sqrt_ckpt else "every step stored",
+            "snapshots": {0: "fp32", 1: "fp16", 2: "bf16"}[info.get("snap_store", 0)],
             "bytes_per_cell_step": bpc, "achieved": bpc * work, "frac": bpc * work / hbm,
             "floor_bytes_per_cell_step": GRAD_FLOOR_BYTES, "floor_frac": GRAD_FLOOR_BYTES * work / hbm}
 
 
 def roofline(exec_, info, prof, nt, ns):
-    """Roofline entries of the dominant and of the other stencil kernel."""
+    """Roofline entries of the dominant and of the other stencil kernel: achieved =
+    algorithmic bytes x cells of a launch / its mean CUDA-event duration, as a fraction
+    of the measured HBM peak (frac) and of the nominal 7.9 TB/s (frac_nominal); with
+    an ncu capture of the variant, the DRAM bytes it moved per launch (traffic) and
+    traffic / duration as a fraction of the measured peak (frac_traffic)."""
     hbm, peak_kind = peaks()
     cells = info["padded_cells"] if exec_ == "batched" else info["padded_cells"] / ns
     per_grad = {"step": 2 * nt if info["ckpt_interval"] < nt else nt, "adj": nt}
+    bytes_of = dict(zip(("step", "adj"), kernel_bytes(exec_, info, nt)))
     out = []
     for k in ("step", "adj"):
         ms, n = prof[k]
         if not n:
             continue
-        name, bpc = KERNELS[(exec_, k)]
+        name, bpc = KERNELS[(exec_, k)], bytes_of[k]
         if exec_ == "batched":
             kind = info["stencil"] if k == "step" else info["adj_stencil"]
             tile = (info["tile_x"], info["tile_z"]) if k == "step" else (info["adj_tile_x"], info["adj_tile_z"])
@@ -197,10 +227,13 @@ def roofline(exec_, info, prof, nt, ns):
                 key = key + (info["layout"], info["staged_stores"])
             if k == "adj" and info["adj_stencil"] == 1:
                 key = key + (info["adj_persistent"],)
+            key = key + (info.get("snap_store", 0), int(info["ckpt_interval"] >= nt))
             if key in TRAFFIC_PER_CELL:
                 traffic = TRAFFIC_PER_CELL[key] * cells
         out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": traffic, "kernel": name, "bytes_per_cell": bpc, "cells_per_launch": cells,
+                    "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                    "traffic": traffic, "frac_traffic": None if traffic is None else traffic / avg / 1e9 / hbm,
+                    "kernel": name, "bytes_per_cell": bpc, "cells_per_launch": cells,
                     "peak_kind": peak_kind, "launches_timed": n, "avg_us": avg * 1e6,
                     "time_share_est": avg * per_grad[k]})
     tot = sum(r["time_share_est"] for r in out) or 1.0
@@ -308,6 +341,172 @@ def aggregate(ms, cells_per_rank, steps, world, device="cuda"):
     return ms, s, cells_per_rank * world / s / 1e9
 
 
+def reduced_storage(efwi, acq, m, d_obs, zoi, eta, ref, plain_s, args):
+    """The same workload with FP16 checkpoints and FP16 forward-velocity snapshots,
+    every step stored when it fits the device (no recompute): seconds per gradient
+    (data term + consistency term, as the headline step), its kernels' rooflines and
+    its error against the FP32 path's outputs (ref: phi, g_vp, g_vs, g_rho)."""
+    import torch
+    ns = acq.ns
+    plan = efwi.Plan(acq, exec="batched", ckpt_store="fp16", snap_store="fp16", ckpt_interval="auto")
+    b, bp, sink = zoi
+    g = tuple(torch.empty_like(m[0]) for _ in range(3))
+
+    def step():
+        phi, *_ = plan.gradient(*m, d_obs, out=g)
+        for mm, gm, e in zip(m, g, eta):
+            plan.regularization_grad(mm, b, bp, sink, e, g=gm)
+        return phi
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    plan.prof_enable(97)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(2, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(steps):
+        phi = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s_grad = e0.elapsed_time(e1) / 1e3 / steps
+    prof = {k: plan.prof_read(k) for k in ("step", "adj")}
+    plan.prof_enable(0)
+    info = plan.info()
+    rel = lambda a, r: float(torch.linalg.vector_norm((a - r).double()) / torch.linalg.vector_norm(r.double()))
+    errs = {"phi": abs(float(phi.item()) - float(ref[0].item())) / abs(float(ref[0].item())),
+            "g_vp": rel(g[0], ref[1]), "g_vs": rel(g[1], ref[2]), "g_rho": rel(g[2], ref[3])}
+    cells = ns * acq.nx * acq.nz * acq.nt
+    roofs = roofline("batched", info, prof, acq.nt, ns)
+    out = {"config": {"ckpt_store": "fp16", "snap_store": "fp16", "ckpt_interval": info["ckpt_interval"],
+                      "schedule": "every step stored" if info["ckpt_interval"] >= acq.nt else "sqrt(nt) + recompute"},
+           "steps": steps, "s_per_gradient": s_grad, "value": cells / s_grad / 1e9, "unit": UNIT,
+           "speedup_vs_plain_fp32": None if plain_s is None else plain_s / s_grad,
+           "rel_err_vs_fp32_path": errs, "roofline": roofs[0], "roofline_other": roofs[1],
+           "gradient_roofline": gradient_roofline(info, acq.nt, s_grad), "workspace_GB": info["workspace_bytes"] / 1e9}
+    plan.close()
+    return out
+
+
+def full_iteration(efwi, args):
+    """One iteration of the 4000x1200 extended problem (128 sources with seeded source
+    errors, 1500 channels, nt = 8000, FP16 checkpoints and snapshots): the data-term
+    gradient of all 128 components runs in groups of 8 shots through one plan, created
+    once and rebound to each group's sources and receivers; then the consistency-term
+    gradient of the 128 components (Vp, Vs, rho) and the l-BFGS update (two-loop
+    recursion with 5 stored pairs) over the whole 3 x 128 x 4.8 M vector.  The first
+    `groups` groups are timed (the first gradient call of a plan captures its graphs);
+    the gradient of all 16 is their sum when all are timed, else 16 x the steady
+    per-group time (every group runs the same kernels on the same shapes).  Observed
+    data are zeros: the cost does not depend on them."""
+    import torch
+    import workloads as W
+    from paper_2305_14130_gb300.groups import group_acquisition
+    from paper_2305_14130_gb300.optim import LBFGS
+    t_gen = time.perf_counter()
+    p = W.full_iteration_4000x1200()
+    acq = p.acq
+    acq.wavelet = np.asarray(acq.wavelet, np.float32).astype(np.float64)
+    t_gen = time.perf_counter() - t_gen
+    ns, nz, nx, nt = acq.ns, acq.nz, acq.nx, acq.nt
+    gsize = 8
+    ngroups = ns // gsize
+    groups = max(1, min(args.full_iteration_groups, ngroups))
+    dev = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")
+    base = [dev(v[0]) for v in (p.vp, p.vs, p.rho)]
+    x = torch.empty((3, ns, nz, nx), device="cuda")
+    for k in range(3):
+        x[k].copy_(base[k][None].expand(ns, nz, nx))
+    del base
+    gr = torch.empty_like(x)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    timings = []
+    t0 = time.perf_counter()
+    plan = None
+    create_s, rebind_s = 0.0, []
+    try:
+        for gi in range(groups):
+            shots = list(range(gi * gsize, (gi + 1) * gsize))
+            gacq, idx = group_acquisition(acq, shots)
+            t = time.perf_counter()
+            if plan is None:
+                plan = efwi.Plan(gacq, exec="batched", ckpt_store="fp16", snap_store="fp16")
+                torch.cuda.synchronize()
+                create_s = time.perf_counter() - t
+            else:
+                plan.rebind(gacq)
+                torch.cuda.synchronize()
+                rebind_s.append(time.perf_counter() - t)
+            d_obs = torch.zeros((len(idx), nt), device="cuda")
+            sl = slice(shots[0], shots[-1] + 1)
+            a, b_ = ev(), ev()
+            a.record()
+            plan.gradient(x[0, sl], x[1, sl], x[2, sl], d_obs, out=(gr[0, sl], gr[1, sl], gr[2, sl]))
+            b_.record()
+            b_.synchronize()
+            timings.append(a.elapsed_time(b_) / 1e3)
+            del d_obs
+        info = plan.info()
+        plan.sync_status()
+        # consistency term of all 128 components, evaluated with the group's plan
+        zb, zbp, zsink = efwi.zoi_weights(ns, nx, nz, acq.dx, acq.dz, p.zoi)
+        a, b_ = ev(), ev()
+        a.record()
+        for k in range(3):
+            plan.regularization_grad(x[k], zb, zbp, zsink, p.eta[k], g=gr[k])
+        b_.record()
+        b_.synchronize()
+        reg_s = a.elapsed_time(b_) / 1e3
+        del zb, zbp, zsink
+    finally:
+        if plan is not None:
+            plan.close()
+    # l-BFGS update over the full vector: 5 stored pairs, then the direction
+    n = x.numel()
+    opt = LBFGS(n, m=5)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    sv = torch.empty(n, device="cuda")
+    yv = torch.empty(n, device="cuda")
+    for _ in range(5):
+        sv.normal_(generator=gen)
+        yv.copy_(sv).mul_(2.0).add_(torch.randn(n, device="cuda", generator=gen), alpha=0.1)
+        opt.push(sv, yv)
+    del sv, yv
+    gflat = gr.reshape(-1)
+    opt.direction(gflat)
+    torch.cuda.synchronize()
+    a, b_ = ev(), ev()
+    a.record()
+    d = opt.direction(gflat)
+    b_.record()
+    b_.synchronize()
+    lbfgs_s = a.elapsed_time(b_) / 1e3
+    del d
+    opt.close()
+    wall = time.perf_counter() - t0
+    steady = timings[1:] if len(timings) > 1 else timings
+    per_group = float(np.median(steady))
+    measured_all = groups == ngroups
+    rebind_mean = float(np.mean(rebind_s)) if rebind_s else None
+    grad_s = (sum(timings) + sum(rebind_s)) if measured_all else \
+        ngroups * per_group + (ngroups - 1) * (rebind_mean or 0.0)
+    iter_s = grad_s + reg_s + lbfgs_s
+    cells = ns * nx * nz * nt
+    return {"workload": "full_iteration_4000x1200: 128 MT sources with seeded errors (amplitude, shift, rotation), "
+                        "1500 DAS ch (0.5 m, 10 m gauge), nt=8000, dt=0.05ms, dx=0.5m; groups of 8 shots",
+            "precision": "FP32 stepping, FP16 checkpoints, FP16 snapshots", "ckpt_interval": info["ckpt_interval"],
+            "groups_total": ngroups, "groups_timed": groups, "group_gradient_s": timings,
+            "group_gradient_s_steady": per_group, "plan_create_s": create_s, "rebind_s": rebind_s,
+            "regularization_s": reg_s, "lbfgs_direction_s": lbfgs_s, "lbfgs_n": n,
+            "s_per_gradient_128": grad_s,
+            "s_per_gradient_128_kind": "measured (all groups)" if measured_all else
+            f"{ngroups} x the steady group time of {groups} timed groups + rebinds",
+            "s_per_iteration": iter_s + create_s, "s_per_iteration_excl_plan_create": iter_s,
+            "Gcell_updates_s": cells / grad_s / 1e9, "group_workspace_GB": info["workspace_bytes"] / 1e9,
+            "observed_data": "zeros (cost independent of the data)", "wall_s": wall, "generate_s": t_gen}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -331,7 +530,8 @@ def run_ours(args):
     tile = tuple(int(v) for v in args.tile.lower().split("x"))
     adj_tile = tuple(int(v) for v in args.adj_tile.lower().split("x"))
     plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store, stencil=args.stencil, tile=tile,
-                     adj_stencil=args.adj_stencil, adj_tile=adj_tile, overlap=args.overlap)
+                     adj_stencil=args.adj_stencil, adj_tile=adj_tile, overlap=args.overlap,
+                     snap_store=args.snap_store, ckpt_interval=args.ckpt if args.ckpt == "auto" else int(args.ckpt))
     # observed data: the same sources in the model with the Gaussian anomaly
     ns = acq.ns
     tv = lambda m: dev(np.repeat(np.asarray(m)[None], ns, 0))
@@ -413,6 +613,13 @@ def run_ours(args):
         e2e = {"value": cells * world / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "s_per_gradient": el}
 
+    # the FP32 path's outputs, for the reduced-storage record's errors
+    ref = plan.gradient(vp, vs, rho, d_obs)             # (phi, g_vp, g_vs, g_rho), fresh tensors
+    for m, gm, e in zip((vp, vs, rho), ref[1:], eta):
+        plan.regularization_grad(m, b, bp, sink, e, g=gm)
+    torch.cuda.synchronize()
+    plan.close()
+
     plain = None
     if not args.no_plain and args.exec == "batched":
         pl = efwi.Plan(acq, exec="plain")
@@ -432,6 +639,17 @@ def run_ours(args):
                  "grad_vp_rel_diff": rel}
         pl.close()
 
+    reduced = None
+    if world == 1 and not args.no_reduced and args.exec == "batched":
+        reduced = reduced_storage(efwi, acq, (vp, vs, rho), d_obs, (b, bp, sink), eta, ref,
+                                  plain["s_per_gradient"] if plain else None, args)
+        reduced["speedup_vs_fp32_path"] = s_per_grad / reduced["s_per_gradient"]
+    del ref, g, d_obs, b, bp, sink
+    full_it = None
+    if world == 1 and args.full_iteration_groups > 0 and args.exec == "batched":
+        torch.cuda.empty_cache()
+        full_it = full_iteration(efwi, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(p)
@@ -441,6 +659,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "exec": args.exec, "ckpt_store": args.ckpt_store,
+                           "snap_store": args.snap_store,
                            "ckpt_interval": info["ckpt_interval"], "tile": [info["tile_x"], info["tile_z"]],
                            "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
                            "stencil": {1: "loads", 2: "tma", 3: "tma_pairs", 4: "tma_staged"}.get(info["stencil"], "?"), "stages": info["stages"], "layout": info["layout"],
@@ -455,9 +674,9 @@ def run_ours(args):
                 "roofline_other": roofs[1],
                 "gradient_roofline": gradient_roofline(info, acq.nt, s_per_grad),
                 "e2e": e2e, "plain_fp32": plain, "cpu_baseline": cpu,
-                "workspace_GB": info["workspace_bytes"] / 1e9}
+                "workspace_GB": info["workspace_bytes"] / 1e9,
+                "reduced_storage": reduced, "full_iteration": full_it}
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         dist.destroy_process_group()
 

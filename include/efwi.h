@@ -78,8 +78,14 @@ enum efwi_status {
  *  VELOCITY     particle-velocity receiver (2-C geophones: one trace per component):
  *               t.v(c) at the channel point c; the gauge is not used                */
 enum efwi_das_mode { EFWI_DAS_STRAIN = 0, EFWI_DAS_STRAIN_RATE = 1, EFWI_DAS_VELOCITY = 2 };
-/* storage precision of the wavefield checkpoints (the time stepping is FP32) */
+/* storage precision of the wavefield checkpoints and of the forward-velocity
+ * snapshots (the time stepping is FP32).  FP16/BF16 store x as RNE(x 2^k) with
+ * s 2^k in [2^14, 2^15), s = max |x| of the snapshot field and shot: per
+ * element |x^ - x| <= 2^-11 |x| (FP16; every |x| >= s 2^-28) or 2^-8 |x| (BF16) */
 enum efwi_store { EFWI_STORE_FP32 = 0, EFWI_STORE_FP16 = 1, EFWI_STORE_BF16 = 2 };
+/* ckpt_interval value: store every step when the snapshots fit the device's
+ * free memory at plan creation, else ceil(sqrt(nt)) */
+#define EFWI_CKPT_AUTO (-1)
 /* execution strategy:
  *  PLAIN   one shot per launch, one kernel per half-step, no graph, no tuning
  *  BATCHED all shots (any window sizes) in one fused launch per time step,
@@ -122,7 +128,11 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *                      takes its edge values, so only physical cells are
  *                      inversion variables
  *   ckpt_interval      steps between wavefield checkpoints for the gradient:
- *                      0 = ceil(sqrt(nt)); >= nt = store every step (no recompute)
+ *                      0 = ceil(sqrt(nt)); >= nt = store every step (no recompute);
+ *                      EFWI_CKPT_AUTO = every step if all nt snapshots (at
+ *                      snap_store precision) fit in the free device memory
+ *                      after the rest of the workspace, with 5 % + 2 GB left
+ *                      over, else ceil(sqrt(nt))
  *   ckpt_store         EFWI_STORE_* precision of the checkpoints
  *   exec               EFWI_EXEC_*
  *   tile_x, tile_z     stencil tile for EXEC_BATCHED (0, 0 = autotune at plan creation)
@@ -138,6 +148,11 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *                      case), replacing the moment tensors (mt is then ignored):
  *                      v^{n+1/2} += dt b F w(t_n) delta_h on the staggered v
  *                      grids (bilinear delta_h / (dx dz)); NULL = moment tensors
+ *   snap_store         EFWI_STORE_* precision of the forward velocities
+ *                      v^{n+1/2} kept for the imaging condition (every step with
+ *                      full storage, the steps of one segment otherwise); FP16
+ *                      and BF16 halve their memory and traffic and need
+ *                      EXEC_BATCHED (and no forced overlap)
  */
 typedef struct efwi_plan_desc {
     int nx, nz;
@@ -167,6 +182,7 @@ typedef struct efwi_plan_desc {
     int adj_stencil;
     int overlap;
     const double *force;
+    int snap_store;
 } efwi_plan_desc;
 
 /* What a plan chose and holds (filled by efwi_plan_info). */
@@ -191,6 +207,7 @@ typedef struct efwi_plan_info_t {
                                    on the velocity halo ring); 0 otherwise */
     int staged_stores;          /* TMA forward step writes its outputs by bulk tensor stores */
     int adj_persistent;         /* per-thread-load adjoint step runs on a persistent grid */
+    int snap_store;             /* EFWI_STORE_* of the forward-velocity snapshots */
 } efwi_plan_info_t;
 
 /* Zone-of-influence description (eq. 10), host memory.  Per source s:
@@ -231,6 +248,20 @@ const char *efwi_last_error(const efwi_plan *plan);
 
 int efwi_plan_info(const efwi_plan *plan, efwi_plan_info_t *info);
 
+/* Bind a plan to another acquisition of the same shape: the next group of
+ * shots of an extended problem whose sources do not fit one plan (each
+ * component is independent through eqs. 1-6, so a group is a slice of the
+ * problem).  Source positions, moment tensors or forces, wavelets and
+ * receiver positions and tangents are taken from desc; the grid, time axis,
+ * CPML, reference model, checkpoint schedule, windows and traces per shot
+ * must equal the plan's (EFWI_ERR_ARG otherwise, the plan unchanged).  No
+ * workspace is re-allocated and the tile autotuner does not run again; the
+ * captured time loops are kept when the adjoint-source gather keeps its
+ * shape, else they are captured again on the next call.  The uploads are
+ * enqueued on stream after the caller's earlier work there; calls of the
+ * plan on other streams must have completed.                               */
+int efwi_plan_rebind(efwi_plan *plan, const efwi_plan_desc *desc, efwi_stream_t stream);
+
 /* Synchronise the stream and report device-side failures of earlier calls on
  * this plan: EFWI_ERR_TIMEOUT if a kernel gave up a bounded wait (its results
  * are then invalid), EFWI_ERR_NAN if a model passed to a call held a
@@ -266,13 +297,22 @@ int efwi_adjoint_gradient(efwi_plan *plan, const float *vp, const float *vs, con
 int efwi_zoi_weights(int ns, int nx, int nz, double dx, double dz, const efwi_zoi_desc *zoi,
                      float *b, float *bp, uint8_t *sink, efwi_stream_t stream);
 
+/* Zone-of-influence weights held by the plan: efwi_zoi_weights of the plan's
+ * ns sources on its grid, computed on the device into plan-owned arrays
+ * (allocated by the first call, which synchronises the device).  Afterwards
+ * efwi_regularization_grad, efwi_regularization_grad_n (with the plan's ns)
+ * and efwi_extended_objective take NULL b, bp, sink to mean these weights.
+ * Errors as efwi_zoi_weights, EFWI_ERR_OOM.                                 */
+int efwi_plan_set_zoi(efwi_plan *plan, const efwi_zoi_desc *zoi, efwi_stream_t stream);
+
 /* Consistency term of eq. 8 for one parameter field and its gradient:
  *   phi_reg = 1/2 eta^2 || (I - S^T S_w) W m~ ||^2,
  *   g      += eta^2 W^T (I - S^T S_w)^T (I - S^T S_w) W m~
  * with W of eq. 11 and S_w of eq. 12, per pixel over the ns components.  The
  * residual (I - S^T S_w) W m~ and its norm are FP64; the gradient increment is
  * FP64 at pixels where some component has its sinkhole and FP32 elsewhere.
- *   m, b, bp   device [ns][nz][nx] FP32; sink device [ns][nz][nx] uint8
+ *   m, b, bp   device [ns][nz][nx] FP32; sink device [ns][nz][nx] uint8;
+ *              b, bp, sink all NULL: the plan's weights (efwi_plan_set_zoi)
  *   phi_reg    device double (overwritten; FP64 reduction)
  *   g          device [ns][nz][nx] FP32, accumulated into (+=)             */
 int efwi_regularization_grad(efwi_plan *plan, const float *m, const float *b, const float *bp,
@@ -297,11 +337,15 @@ int efwi_regularization_grad_n(efwi_plan *plan, int ns, const float *m, const fl
  * arguments and results as efwi_regularization_grad but no plan: ns, nx, nz
  * give the sizes of the [ns][nz][nx] arrays.  It calls no cudaMalloc or
  * cudaFree.  Its only scratch (FP64 block partials of phi_reg) is a static
- * 32 KB device array that every GPU loading the library holds until exit;
- * the first call on each device looks up that array's address (call it once
- * before any stream capture).  Limit: nx * nz <= 1048576 pixels, larger
- * sizes return EFWI_ERR_ARG without launching anything.  All calls share the
- * array, so calls that overlap on the GPU race on it.                       */
+ * 32 KB device array that every GPU loading the library holds until exit.
+ * Every call made outside a stream capture looks up that array's address on
+ * the current device; a call inside a capture reuses the address found by
+ * the last uncaptured call on that device, so call it once before any
+ * capture (a captured first call returns EFWI_ERR_CUDA).  A cudaDeviceReset
+ * may move the array: later uncaptured calls find it again, graphs captured
+ * before the reset must not be replayed.  Limit: nx * nz <= 1048576 pixels,
+ * larger sizes return EFWI_ERR_ARG without launching anything.  All calls
+ * share the array, so calls that overlap on the GPU race on it.             */
 int efwi_regularization_grad_noalloc(int ns, int nx, int nz, const float *m, const float *b,
                                      const float *bp, const uint8_t *sink, double eta,
                                      double *phi_reg, float *g, efwi_stream_t stream);
@@ -414,7 +458,8 @@ int efwi_lbfgs_run(efwi_lbfgs *h, float *x, float *g, efwi_objective_fn fn, void
 
 /* Extended objective of eq. 8: phi_data (as efwi_forward + misfit) and
  * phi_reg summed over the three parameter fields (Vp, Vs, rho) with their
- * own eta[3].  Both results are device doubles (overwritten).               */
+ * own eta[3].  Both results are device doubles (overwritten).  b, bp, sink
+ * as in efwi_regularization_grad (all NULL: the plan's weights).            */
 int efwi_extended_objective(efwi_plan *plan, const float *vp, const float *vs, const float *rho,
                             const float *d_obs, const double eta[3], const float *b,
                             const float *bp, const uint8_t *sink, double *phi_data,
@@ -427,6 +472,27 @@ int efwi_extended_objective(efwi_plan *plan, const float *vp, const float *vs, c
  * next efwi_sync_status on the plan then returns EFWI_ERR_TIMEOUT and clears
  * the flag.  Nothing faults, traps or hangs.                                */
 int efwi_selftest_timeout(efwi_plan *plan, long long budget_cycles, efwi_stream_t stream);
+
+/* Numerics self-tests (no counterpart in the paper): the device routines that
+ * the time loops use for reduced-precision snapshots and for the Kahan fold
+ * of the imaging sums, applied to caller arrays so that tests can check them
+ * against FP64 arithmetic and the stated error bounds.
+ *
+ * efwi_selftest_store: treats x (device [n] FP32) as one snapshot field,
+ *   writes s = max |x| to s_out (device float), encodes x into enc (device
+ *   [n] elements of 2 bytes) as checkpoints and stored forward velocities
+ *   are encoded -- RNE(x 2^k) with s 2^k in [2^14, 2^15) -- and decodes enc
+ *   into y (device [n] FP32).  Per element |y - x| <= 2^-11 |x| (FP16) or
+ *   2^-8 |x| (BF16) where x 2^k is a normal number of the format, and
+ *   <= 2^-25 2^-k (FP16) below that.  store = EFWI_STORE_FP32 copies x
+ *   (enc unused).
+ * efwi_selftest_kahan: folds the nterms arrays terms[k] (device
+ *   [nterms][n] FP32, consumed: zeroed) one after another into tot (device
+ *   [n] FP32) with Kahan (1965) compensation cmp (device [n] FP32); tot and
+ *   cmp start from zero.                                                    */
+int efwi_selftest_store(int store, long long n, const float *x, void *enc, float *y, float *s_out,
+                        efwi_stream_t stream);
+int efwi_selftest_kahan(long long n, int nterms, float *terms, float *tot, float *cmp, efwi_stream_t stream);
 
 /* Kernel timing for measurements.  When every > 0 the plan brackets every
  * every-th launch of its two dominant stencil kernels with CUDA events on the

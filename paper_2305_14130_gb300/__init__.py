@@ -23,7 +23,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import EfwiError, STORE, EXEC, STENCIL, OVERLAP
+from ._abi import EfwiError, STORE, EXEC, STENCIL, OVERLAP, CKPT_AUTO
 
 __all__ = ["Plan", "zoi_weights", "collapse", "EfwiError", "load_library", "DataMisfit", "Consistency", "extended_objective"]
 
@@ -66,13 +66,35 @@ class Plan:
     include/efwi.h): nx, nz, dx, dz, nt, dt, npml, pml_R, pml_vmax, pml_f0,
     src_xz, mt, wavelet, tr_ptr, ch_xz, ch_t, gauge, das_mode, win,
     ref_vp, ref_vs, ref_rho.
+
+    ``ckpt_interval``: 0 = ceil(sqrt(nt)) steps per checkpoint, >= nt = every
+    step stored, "auto" = every step stored when the snapshots fit the free
+    device memory.  ``snap_store``: precision of those stored forward
+    velocities ("fp32", "fp16", "bf16"; the latter two need exec="batched").
     """
 
-    def __init__(self, acq, exec: str = "batched", ckpt_interval: int = 0, ckpt_store: str = "fp32",
+    def __init__(self, acq, exec: str = "batched", ckpt_interval=0, ckpt_store: str = "fp32",
                  tile=(0, 0), stencil: str = "auto", adj_tile=(0, 0), adj_stencil: str = "auto",
-                 overlap: str = "auto"):
+                 overlap: str = "auto", snap_store: str = "fp32"):
         lib = _abi.load()
+        self._opts = dict(exec=exec, ckpt_interval=ckpt_interval, ckpt_store=ckpt_store, tile=tile, stencil=stencil,
+                          adj_tile=adj_tile, adj_stencil=adj_stencil, overlap=overlap, snap_store=snap_store)
+        d, keep = self._desc(acq)
+        self.exec, self.ckpt_store, self.snap_store = exec, ckpt_store, snap_store
+        h = C.c_void_p()
+        torch.cuda.init()
+        rc = lib.efwi_plan_create(C.byref(h), C.byref(d))
+        _abi.check(rc, None)
+        self._h = h
+        self._lib = lib
+        self.model_numel = self.ns * self.nz * self.nx
+        self.data_shape = (self.ntr, self.nt)
+
+    def _desc(self, acq):
+        """efwi_plan_desc of an acquisition with this plan's options, and the host
+        arrays it points into (kept alive by the caller until the call returns)."""
         a = acq
+        o = self._opts
         self.nx, self.nz, self.nt = int(a.nx), int(a.nz), int(a.nt)
         self.ns = int(np.asarray(a.src_xz).shape[0])
         self.ntr = int(np.asarray(a.ch_xz).reshape(-1, 2).shape[0])
@@ -105,24 +127,25 @@ class Plan:
         d.das_mode = int(getattr(a, "das_mode", 0))
         d.win = P(keep["win"], C.c_int)
         d.ref_vp, d.ref_vs, d.ref_rho = P(keep["rvp"], C.c_float), P(keep["rvs"], C.c_float), P(keep["rrho"], C.c_float)
-        d.ckpt_interval = int(ckpt_interval)
-        d.ckpt_store = STORE[ckpt_store]
-        d.exec = EXEC[exec]
-        d.tile_x, d.tile_z = int(tile[0]), int(tile[1])
-        d.stencil = STENCIL[stencil]
-        d.adj_tile_x, d.adj_tile_z = int(adj_tile[0]), int(adj_tile[1])
-        d.adj_stencil = STENCIL[adj_stencil]
-        d.overlap = OVERLAP[overlap]
+        d.ckpt_interval = CKPT_AUTO if o["ckpt_interval"] == "auto" else int(o["ckpt_interval"])
+        d.snap_store = STORE[o["snap_store"]]
+        d.ckpt_store = STORE[o["ckpt_store"]]
+        d.exec = EXEC[o["exec"]]
+        d.tile_x, d.tile_z = int(o["tile"][0]), int(o["tile"][1])
+        d.stencil = STENCIL[o["stencil"]]
+        d.adj_tile_x, d.adj_tile_z = int(o["adj_tile"][0]), int(o["adj_tile"][1])
+        d.adj_stencil = STENCIL[o["adj_stencil"]]
+        d.overlap = OVERLAP[o["overlap"]]
         d.force = P(keep["force"], C.c_double)
-        self.exec, self.ckpt_store = exec, ckpt_store
-        h = C.c_void_p()
-        torch.cuda.init()
-        rc = lib.efwi_plan_create(C.byref(h), C.byref(d))
-        _abi.check(rc, None)
-        self._h = h
-        self._lib = lib
-        self.model_numel = self.ns * self.nz * self.nx
-        self.data_shape = (self.ntr, self.nt)
+        return d, keep
+
+    def rebind(self, acq):
+        """Bind the plan to another acquisition of the same shape (the next shot
+        group of an extended problem): new sources, wavelets and receivers on the
+        same grid, windows and trace counts, with no re-allocation or re-tuning
+        (efwi_plan_rebind)."""
+        d, keep = self._desc(acq)
+        self._check(self._lib.efwi_plan_rebind(self._h, C.byref(d), _stream()))
 
     # -- lifecycle -----------------------------------------------------------
     def close(self):
@@ -172,8 +195,16 @@ class Plan:
             _ptr(dmod, "d_out", self.ntr * self.nt, allow_none=True), _stream()))
         return (phi, *out, dmod) if return_data else (phi, *out)
 
+    def set_zoi(self, zoi):
+        """Zone-of-influence weights of the plan's sources held by the plan
+        (efwi_plan_set_zoi): afterwards b, bp, sink may be None in
+        regularization_grad and extended_objective."""
+        z, keep = _zoi_desc(zoi)
+        self._check(self._lib.efwi_plan_set_zoi(self._h, C.byref(z), _stream()))
+
     def regularization_grad(self, m, b, bp, sink, eta, g=None):
-        """phi_reg (device float64) and g += eta^2 A^T A m for one parameter field.
+        """phi_reg (device float64) and g += eta^2 A^T A m for one parameter field
+        (b, bp, sink None: the weights set with set_zoi).
 
         m may hold any number of components [ns', nz, nx] on the plan's grid (for
         shot groups: every component of the extended problem, evaluated with the
@@ -194,8 +225,8 @@ class Plan:
             g = torch.zeros_like(m)
         phi = torch.empty((), dtype=torch.float64, device=m.device)
         self._check(self._lib.efwi_regularization_grad(
-            self._h, _ptr(m, "m", n), _ptr(b, "b", n), _ptr(bp, "bp", n), _ptr(sink, "sink", n, torch.uint8),
-            float(eta), _ptr(phi, "phi", 1, torch.float64), _ptr(g, "g", n), _stream()))
+            self._h, _ptr(m, "m", n), _ptr(b, "b", n, allow_none=True), _ptr(bp, "bp", n, allow_none=True),
+            _ptr(sink, "sink", n, torch.uint8, allow_none=True), float(eta), _ptr(phi, "phi", 1, torch.float64), _ptr(g, "g", n), _stream()))
         return phi, g
 
     def extended_objective(self, vp, vs, rho, d_obs, eta, b, bp, sink):
@@ -206,8 +237,9 @@ class Plan:
         pr = torch.empty((), dtype=torch.float64, device=vp.device)
         e = (C.c_double * 3)(*[float(x) for x in eta])
         self._check(self._lib.efwi_extended_objective(
-            self._h, *m, _ptr(d_obs, "d_obs", self.ntr * self.nt), e, _ptr(b, "b", n), _ptr(bp, "bp", n),
-            _ptr(sink, "sink", n, torch.uint8), _ptr(pd, "phi_data", 1, torch.float64),
+            self._h, *m, _ptr(d_obs, "d_obs", self.ntr * self.nt), e, _ptr(b, "b", n, allow_none=True),
+            _ptr(bp, "bp", n, allow_none=True),
+            _ptr(sink, "sink", n, torch.uint8, allow_none=True), _ptr(pd, "phi_data", 1, torch.float64),
             _ptr(pr, "phi_reg", 1, torch.float64), _stream()))
         return pd, pr
 
@@ -238,9 +270,8 @@ class Plan:
         return ms.value, cnt.value
 
 
-def zoi_weights(ns, nx, nz, dx, dz, zoi, device="cuda"):
-    """b, b' [ns, nz, nx] float32 and the sinkhole flags (uint8) of eq. 10 on the device."""
-    lib = _abi.load()
+def _zoi_desc(zoi):
+    """efwi_zoi_desc of a zone-of-influence description and the arrays it points into."""
     act = _np(zoi.active_x, np.float64)
     tap = _np(zoi.taper, np.float64)
     sxz = _np(zoi.sink_xz, np.float64)
@@ -249,6 +280,13 @@ def zoi_weights(ns, nx, nz, dx, dz, zoi, device="cuda"):
     PD = C.POINTER(C.c_double)
     z = _abi.ZoiDesc(act.ctypes.data_as(PD), tap.ctypes.data_as(PD), sxz.ctypes.data_as(PD),
                      axes.ctypes.data_as(PD), float(zoi.n), float(zoi.nu))
+    return z, (act, tap, sxz, axes)
+
+
+def zoi_weights(ns, nx, nz, dx, dz, zoi, device="cuda"):
+    """b, b' [ns, nz, nx] float32 and the sinkhole flags (uint8) of eq. 10 on the device."""
+    lib = _abi.load()
+    z, keep = _zoi_desc(zoi)
     b = torch.empty((ns, nz, nx), dtype=torch.float32, device=device)
     bp = torch.empty_like(b)
     sink = torch.empty((ns, nz, nx), dtype=torch.uint8, device=device)

@@ -14,6 +14,7 @@ STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXEC = {"plain": 0, "batched": 1}
 STENCIL = {"auto": 0, "loads": 1, "tma": 2, "tma_pairs": 3, "tma_staged": 4}
 OVERLAP = {"auto": 0, "off": 1, "on": 2}
+CKPT_AUTO = -1
 
 PD = C.POINTER(C.c_double)
 PF = C.POINTER(C.c_float)
@@ -29,7 +30,7 @@ class PlanDesc(C.Structure):
                 ("ref_vp", PF), ("ref_vs", PF), ("ref_rho", PF), ("ckpt_interval", C.c_int),
                 ("ckpt_store", C.c_int), ("exec", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
                 ("stencil", C.c_int), ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("adj_stencil", C.c_int),
-                ("overlap", C.c_int), ("force", PD)]
+                ("overlap", C.c_int), ("force", PD), ("snap_store", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -39,7 +40,7 @@ class PlanInfo(C.Structure):
                 ("overlap_fwd_blocks", C.c_int), ("overlap_adj_blocks", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong), ("layout", C.c_int),
-                ("staged_stores", C.c_int), ("adj_persistent", C.c_int)]
+                ("staged_stores", C.c_int), ("adj_persistent", C.c_int), ("snap_store", C.c_int)]
 
 
 class ZoiDesc(C.Structure):
@@ -58,6 +59,8 @@ OBJECTIVE_FN = C.CFUNCTYPE(C.c_int, VP, VP, C.POINTER(C.c_double), VP, VP)
 SIGNATURES = {
     "efwi_plan_create": (C.c_int, [C.POINTER(VP), C.POINTER(PlanDesc)]),
     "efwi_plan_destroy": (C.c_int, [VP]),
+    "efwi_plan_rebind": (C.c_int, [VP, C.POINTER(PlanDesc), VP]),
+    "efwi_plan_set_zoi": (C.c_int, [VP, C.POINTER(ZoiDesc), VP]),
     "efwi_last_error": (C.c_char_p, [VP]),
     "efwi_plan_info": (C.c_int, [VP, C.POINTER(PlanInfo)]),
     "efwi_sync_status": (C.c_int, [VP, VP]),
@@ -83,6 +86,8 @@ SIGNATURES = {
     "efwi_pseudo_hessian": (C.c_int, [VP, VP, VP, VP, C.c_double, VP, VP, VP]),
     "efwi_prof_enable": (C.c_int, [VP, C.c_int]),
     "efwi_selftest_timeout": (C.c_int, [VP, C.c_longlong, VP]),
+    "efwi_selftest_store": (C.c_int, [C.c_int, C.c_longlong, VP, VP, VP, VP, VP]),
+    "efwi_selftest_kahan": (C.c_int, [C.c_longlong, C.c_int, VP, VP, VP, VP]),
     "efwi_prof_read": (C.c_int, [VP, C.c_int, PD, C.POINTER(C.c_longlong)]),
 }
 

@@ -31,6 +31,7 @@
 // bits of a plan's device error flag (read and cleared by efwi_sync_status)
 #define EFWI_FLAG_TIMEOUT 1      // a kernel gave up a bounded wait
 #define EFWI_FLAG_BAD_MODEL 2    // a model value was not finite, or a density not positive
+#define EFWI_FLAG_SELFTEST 4     // the timeout self-test's wait expired (as intended)
 
 #define EFWI_GX 4
 #define EFWI_GZ 2
@@ -98,6 +99,113 @@ __device__ __forceinline__ int zstrip(const ShotDev &s, int j) {
     if (j >= 0 && j < s.P) return j;
     if (j >= s.NZ - s.P && j < s.NZ) return j - s.NZ + 2 * s.P;
     return -1;
+}
+
+// Reduced-precision storage of a wavefield snapshot (checkpoints and stored
+// forward velocities): with s = max |x| over the snapshot, every element is
+// stored as RNE(x * 2^k), k chosen from the exponent of s so that s * 2^k lies in
+// [2^14, 2^15) (clamped to |k| <= 126 for extreme s), and read back as y * 2^-k.
+// Both multiplications by a power of two are exact, so the only error is the
+// rounding to the storage type, and magnitudes down to s * 2^-28 stay normal FP16
+// numbers (relative error <= 2^-11; BF16: 2^-8).
+__device__ __forceinline__ int store_exp(float s) {
+    const int E = (__float_as_int(fabsf(s)) >> 23) & 0xff;   // biased exponent of s (0 for s = 0)
+    const int k = 141 - E;                                    // 15 - e with s = m 2^e, m in [0.5, 1)
+    return k < -126 ? -126 : (k > 126 ? 126 : k);
+}
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }   // |k| <= 126
+
+template <class T>
+__device__ __forceinline__ T to_store(float v);
+template <>
+__device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+__device__ __forceinline__ float from_store(__half v) { return __half2float(v); }
+__device__ __forceinline__ float from_store(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Forward velocities v^{n+1/2} kept for the adjoint in FP16 / BF16 ("snapshots").
+// The step that computes v^{n+1/2} accumulates max |vx| and max |vz| of every shot
+// (atomicMax on the float bits after a per-tile reduction); the maxima are complete
+// when that launch ends, so the NEXT step, which stages v^{n+1/2} in shared memory
+// anyway, writes the scaled 2-byte copy of its own tile cells (a separate small
+// kernel packs the last step of a pass).  Maxima of one snapshot: [2][ns] floats,
+// each in its own 128-byte line (kMaxPad floats apart) so the atomics of different
+// shots and fields do not serialise on one line.
+constexpr int kMaxPad = 32;
+
+struct SnapW {                 // reduced-precision snapshot work of one forward step
+    void *h;                   // copy of the previous step's v: vx at [F], vz at [F + F]; null = none
+    const float *hmax;         // maxima of that previous step's snapshot
+    float *amax;               // maxima accumulator of this step's snapshot, or null
+    long long F;               // elements per field (fsz_total)
+    int ns, kind;              // shots; EFWI_STORE_FP16 or EFWI_STORE_BF16
+};
+
+struct SnapR {                 // reduced-precision forward velocities read by an adjoint step
+    const void *h;             // vx at [0, F), vz at [F, 2F); null = FP32 velocities
+    const float *hmax;
+    long long F;
+    int ns, kind;
+};
+
+__device__ __forceinline__ float snap_scale_up(const float *mx, int f, int shot, int ns) {
+    return pow2f(store_exp(__ldg(mx + (long long)(f * ns + shot) * kMaxPad)));
+}
+__device__ __forceinline__ float snap_scale_down(const float *mx, int f, int shot, int ns) {
+    return pow2f(-store_exp(__ldg(mx + (long long)(f * ns + shot) * kMaxPad)));
+}
+
+// two adjacent elements (idx even, 4-byte aligned) / one element of a 2-byte snapshot;
+// SK = EFWI_STORE_FP16 or EFWI_STORE_BF16 (compile time in the stencil kernels)
+template <int SK>
+__device__ __forceinline__ void snap_put2(void *h, long long idx, float a, float b) {
+    if constexpr (SK == EFWI_STORE_FP16)
+        *reinterpret_cast<__half2 *>(static_cast<__half *>(h) + idx) = __floats2half2_rn(a, b);
+    else
+        *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(h) + idx) = __floats2bfloat162_rn(a, b);
+}
+template <int SK>
+__device__ __forceinline__ void snap_put1(void *h, long long idx, float a) {
+    if constexpr (SK == EFWI_STORE_FP16) static_cast<__half *>(h)[idx] = __float2half_rn(a);
+    else static_cast<__nv_bfloat16 *>(h)[idx] = __float2bfloat16_rn(a);
+}
+// read-only 2-byte load asking L2 for the 256-byte block around it (the neighbouring
+// tile reads the rest of the block soon after), widened exactly to FP32
+template <int SK>
+__device__ __forceinline__ float snap_get(const void *h, long long idx) {
+    unsigned short u;
+    asm("ld.global.nc.L2::256B.b16 %0, [%1];"
+        : "=h"(u)
+        : "l"(static_cast<const unsigned short *>(h) + idx));
+    if constexpr (SK == EFWI_STORE_FP16) return __half2float(__ushort_as_half(u));
+    else return __bfloat162float(__ushort_as_bfloat16(u));
+}
+__device__ __forceinline__ float snap_get_rt(const void *h, long long idx, int kind) {
+    return kind == EFWI_STORE_FP16 ? snap_get<EFWI_STORE_FP16>(h, idx) : snap_get<EFWI_STORE_BF16>(h, idx);
+}
+
+// Per-tile maximum of |v| for the snapshot scale: every thread passes its running
+// maxima (non-negative), each warp reduces them, and lane 0 leaves them in wsm
+// ([2][warps]); after the next __syncthreads snap_max_commit folds the warps and
+// issues one atomicMax per field.  Must be called by every thread of the block.
+__device__ __forceinline__ void snap_max_warp(float mx, float mz, unsigned *wsm) {
+    const unsigned ux = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+    const unsigned uz = __reduce_max_sync(0xffffffffu, __float_as_uint(mz));
+    if ((threadIdx.x & 31) == 0) {
+        wsm[threadIdx.x >> 5] = ux;
+        wsm[(blockDim.x >> 5) + (threadIdx.x >> 5)] = uz;
+    }
+}
+__device__ __forceinline__ void snap_max_commit(const unsigned *wsm, float *amax, int shot, int ns) {
+    const int nw = blockDim.x >> 5;
+    unsigned ux = 0, uz = 0;
+    for (int w = 0; w < nw; ++w) {
+        ux = max(ux, wsm[w]);
+        uz = max(uz, wsm[nw + w]);
+    }
+    atomicMax(reinterpret_cast<unsigned *>(amax + (long long)shot * kMaxPad), ux);
+    atomicMax(reinterpret_cast<unsigned *>(amax + (long long)(ns + shot) * kMaxPad), uz);
 }
 
 // 4th-order staggered differences (unscaled).

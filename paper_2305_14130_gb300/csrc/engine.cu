@@ -8,6 +8,10 @@
 //   segment keeping v^{n+1/2} of each step, then run the adjoint steps
 //   n1-1 .. n0, each accumulating the zero-lag imaging sums.  With K >= nt the
 //   first forward pass already keeps every v^{n+1/2} and nothing is recomputed.
+// The kept velocities ("snapshots", one slot per step of a segment) are FP32,
+// written by the step that computes them, or scaled FP16/BF16: the step that
+// computes v^{n+1/2} accumulates its maxima into the slot's scale, the next
+// step writes the 2-byte copy, and a small kernel packs the segment's last step.
 // EXEC_PLAIN launches one kernel per half-step and shot; EXEC_BATCHED runs all
 // shots in fused launches and replays the time loop from CUDA graphs.
 #include <algorithm>
@@ -41,6 +45,10 @@ int cuda_status(efwi_plan *p, const char *where) {
 }
 
 int check_model_args(efwi_plan *p, const float *vp, const float *vs, const float *rho) {
+    if (p->broken) {
+        p->err = "a bounded device wait of an earlier call expired; destroy this plan and create it again";
+        return EFWI_ERR_TIMEOUT;
+    }
     if (!vp || !vs || !rho) {
         p->err = "model pointers must be non-NULL device pointers";
         return EFWI_ERR_ARG;
@@ -63,35 +71,54 @@ float *seg_z(efwi_plan *p, int slot) { return p->seg + (size_t)slot * 2 * p->fsz
 // slot of the segment buffer half used by segment sgi in the overlapped schedule
 int seg_slot(efwi_plan *p, int sgi, int k) { return (p->seg_double ? (sgi & 1) * p->K : 0) + k; }
 
+bool half_snaps(const efwi_plan *p) { return p->snap_store != EFWI_STORE_FP32; }
+
+// maxima of the reduced-precision snapshot slots [k0, k1) start from zero
+void clear_snap_max(efwi_plan *p, int k0, int k1, cudaStream_t st) {
+    if (half_snaps(p) && k1 > k0)
+        cudaMemsetAsync(efwi::snap_max(p, k0), 0, sizeof(float) * (size_t)(k1 - k0) * 2 * p->d.ns * kMaxPad, st);
+}
+
 // One forward step of every shot; d == nullptr skips the DAS sampling.
-void forward_step(efwi_plan *p, int n, float *d, float *sx, float *sz, cudaStream_t st) {
+void forward_step(efwi_plan *p, int n, float *d, const SnapOut &so, cudaStream_t st) {
     if (p->d.exec == EFWI_EXEC_PLAIN) {
         Fields F = state_fields(p, 0);
         for (int s = 0; s < p->d.ns; ++s) {
-            launch_vel_plain(p, s, sx, sz, st);
-            launch_force(p, F, n, s, sx, sz, st);
+            launch_vel_plain(p, s, so.fx, so.fz, st);
+            launch_force(p, F, n, s, so.fx, so.fz, st);
             if (d) launch_das_fwd(p, F, n, d, s, st);
             launch_stress_plain(p, s, st);
             launch_inject(p, F, n, s, st);
         }
     } else {
-        launch_step_fused(p, n, sx, sz, st);   // leaves v^{n+1/2}, sigma^{n+1} in state[scur]
+        launch_step_fused(p, n, so, st);       // leaves v^{n+1/2}, sigma^{n+1} in state[scur]
         if (d) launch_das_fwd(p, state_fields(p, p->scur), n, d, -1, st);
     }
 }
 
-void adjoint_step(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaStream_t st) {
+// Forward steps n0 .. n1-1 keeping every v^{n+1/2} in slots k0 + (n - n0) (with
+// reduced-precision snapshots the last one is packed after the loop).
+void forward_keep(efwi_plan *p, int n0, int n1, int k0, float *d, cudaStream_t st) {
+    clear_snap_max(p, k0, k0 + (n1 - n0), st);
+    for (int n = n0; n < n1; ++n) {
+        const int k = k0 + (n - n0);
+        forward_step(p, n, d, snap_out(p, k, n > n0 ? k - 1 : -1), st);
+    }
+    if (half_snaps(p) && n1 > n0) launch_snap_tail(p, snap_out(p, -1, k0 + (n1 - n0) - 1).sw, st);
+}
+
+void adjoint_step(efwi_plan *p, int n, const SnapIn &si, cudaStream_t st) {
     if (p->d.exec == EFWI_EXEC_PLAIN) {
         Fields A = adj_fields(p, 0);
         for (int s = 0; s < p->d.ns; ++s) {
-            launch_das_adj(p, A, vfx, vfz, G_field(p, 3), G_field(p, 4), n, s, st);
-            launch_adj_vel_plain(p, s, vfx, vfz, st);
-            launch_adj_stress_plain(p, s, vfx, vfz, st);
+            launch_das_adj(p, A, si, G_field(p, 3), G_field(p, 4), n, s, st);
+            launch_adj_vel_plain(p, s, si.fx, si.fz, st);
+            launch_adj_stress_plain(p, s, si.fx, si.fz, st);
         }
         p->apsi_v ^= 1;
     } else {
-        launch_das_adj(p, adj_fields(p, p->acur), vfx, vfz, G_field(p, 3), G_field(p, 4), n, -1, st);
-        launch_adj_fused(p, n, vfx, vfz, st);   // flips acur and the adjoint psi blocks
+        launch_das_adj(p, adj_fields(p, p->acur), si, G_field(p, 3), G_field(p, 4), n, -1, st);
+        launch_adj_fused(p, n, si, st);        // flips acur and the adjoint psi blocks
     }
 }
 
@@ -99,16 +126,54 @@ void adjoint_step(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaS
 
 namespace efwi {
 
+float *snap_max(efwi_plan *p, int slot) { return p->segmax + (size_t)slot * 2 * p->d.ns * kMaxPad; }
+
+void *snap_half(efwi_plan *p, int slot) {
+    return static_cast<char *>(p->segh) + (size_t)slot * 2 * p->fsz_total * 2;
+}
+
+SnapOut snap_out(efwi_plan *p, int slot, int prev) {
+    SnapOut so;
+    if (!half_snaps(p)) {
+        if (slot >= 0) { so.fx = seg_x(p, slot); so.fz = seg_z(p, slot); }
+        return so;
+    }
+    so.sw.F = p->fsz_total;
+    so.sw.ns = p->d.ns;
+    so.sw.kind = p->snap_store;
+    if (slot >= 0) so.sw.amax = snap_max(p, slot);
+    if (prev >= 0) { so.sw.h = snap_half(p, prev); so.sw.hmax = snap_max(p, prev); }
+    return so;
+}
+
+SnapIn snap_in(efwi_plan *p, int slot) {
+    SnapIn si;
+    if (!half_snaps(p)) {
+        si.fx = seg_x(p, slot);
+        si.fz = seg_z(p, slot);
+        return si;
+    }
+    si.sr.h = snap_half(p, slot);
+    si.sr.hmax = snap_max(p, slot);
+    si.sr.F = p->fsz_total;
+    si.sr.ns = p->d.ns;
+    si.sr.kind = p->snap_store;
+    return si;
+}
+
 // Forward pass over all steps; keeps checkpoints when ck and every v^{n+1/2}
-// in the segment buffer when the plan stores all steps.
+// in the snapshot slots when the plan stores all steps.
 void forward_loop(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
     reset_forward_state(p, st);
-    const bool full = p->K >= p->d.nt;
-    for (int n = 0; n < p->d.nt; ++n) {
+    const int nt = p->d.nt;
+    if (ck && p->K >= nt) {
+        launch_ckpt_save(p, 0, st);
+        forward_keep(p, 0, nt, 0, d, st);
+        return;
+    }
+    for (int n = 0; n < nt; ++n) {
         if (ck && n % p->K == 0) launch_ckpt_save(p, n / p->K, st);
-        float *sx = (ck && full) ? seg_x(p, n) : nullptr;
-        float *sz = (ck && full) ? seg_z(p, n) : nullptr;
-        forward_step(p, n, d, sx, sz, st);
+        forward_step(p, n, d, SnapOut{}, st);
     }
 }
 
@@ -140,8 +205,7 @@ void adjoint_loop(efwi_plan *p, cudaStream_t st) {
             const int n0 = s * K, n1 = std::min(n0 + K, nt);
             launch_ckpt_load(p, s, sr);
             p->grid_fwd_override = p->ov_fwd * p->n_sms;
-            for (int n = n0; n < n1; ++n)
-                forward_step(p, n, nullptr, seg_x(p, seg_slot(p, s, n - n0)), seg_z(p, seg_slot(p, s, n - n0)), sr);
+            forward_keep(p, n0, n1, seg_slot(p, s, 0), nullptr, sr);   // FP32 snapshots (the overlap needs them)
             p->grid_fwd_override = 0;
             cudaEventRecord(evR[s], sr);
         };
@@ -151,8 +215,7 @@ void adjoint_loop(efwi_plan *p, cudaStream_t st) {
             cudaStreamWaitEvent(st, evR[sgi]);
             const int n0 = sgi * K, n1 = std::min(n0 + K, nt);
             p->grid_adj_override = p->ov_adj * p->n_sms;
-            for (int n = n1 - 1; n >= n0; --n)
-                adjoint_step(p, n, seg_x(p, seg_slot(p, sgi, n - n0)), seg_z(p, seg_slot(p, sgi, n - n0)), st);
+            for (int n = n1 - 1; n >= n0; --n) adjoint_step(p, n, snap_in(p, seg_slot(p, sgi, n - n0)), st);
             p->grid_adj_override = 0;
             if (p->Gtot) launch_kahan_fold(p, st);
             cudaEventRecord(evA[sgi], st);
@@ -165,9 +228,9 @@ void adjoint_loop(efwi_plan *p, cudaStream_t st) {
         const int n0 = sgi * K, n1 = std::min(n0 + K, nt);
         if (!full) {
             launch_ckpt_load(p, sgi, st);
-            for (int n = n0; n < n1; ++n) forward_step(p, n, nullptr, seg_x(p, n - n0), seg_z(p, n - n0), st);
+            forward_keep(p, n0, n1, 0, nullptr, st);
         }
-        for (int n = n1 - 1; n >= n0; --n) adjoint_step(p, n, seg_x(p, n - n0), seg_z(p, n - n0), st);
+        for (int n = n1 - 1; n >= n0; --n) adjoint_step(p, n, snap_in(p, n - n0), st);
         if (p->Gtot) launch_kahan_fold(p, st);
     }
 }
@@ -292,7 +355,7 @@ extern "C" int efwi_pseudo_hessian(efwi_plan *p, const float *vp, const float *v
         reset_forward_state(p, cs);
         cudaMemsetAsync(acc, 0, sizeof(float) * 2 * p->fsz_total, cs);
         for (int n = 0; n < p->d.nt; ++n) {
-            forward_step(p, n, nullptr, nullptr, nullptr, cs);
+            forward_step(p, n, nullptr, SnapOut{}, cs);
             launch_vel_energy(p, state_fields(p, p->d.exec == EFWI_EXEC_PLAIN ? 0 : p->scur), acc, cmp, cs);
         }
     };
@@ -312,7 +375,8 @@ extern "C" int efwi_extended_objective(efwi_plan *p, const float *vp, const floa
     if (!p) return EFWI_ERR_ARG;
     int rc = check_model_args(p, vp, vs, rho);
     if (rc) return rc;
-    if ((!d_obs && p->d.ntr > 0) || !eta || !b || !bp || !sink || !phi_data || !phi_reg) {
+    if ((rc = resolve_zoi(p, p->d.ns, b, bp, sink))) return rc;
+    if ((!d_obs && p->d.ntr > 0) || !eta || !phi_data || !phi_reg) {
         p->err = "NULL argument to efwi_extended_objective";
         return EFWI_ERR_ARG;
     }

@@ -44,16 +44,19 @@ struct FwdArgs {
     const float *wv;            // w_n / (dx dz) of force sources (null without)
     int nt, n;
     float dt, rdx, rdz;
+    SnapW sw;                   // reduced-precision snapshot work (sw.h / sw.amax null: none)
 };
 
-template <int TX, int TZ>
+template <int TX, int TZ, int SK = 0>
 __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
+    constexpr bool SNAP = SK != 0;   // FP16 / BF16 snapshot work compiled in
     constexpr int SX = TX + 8, SZ = TZ + 8;     // sigma staging: tile + 4 halo
     constexpr int VX = TX + 4, VZ = TZ + 4;     // velocity: tile + 2 halo
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     float *sxx = sm, *szz = sm + SX * SZ, *sxz = sm + 2 * SX * SZ;
     float *svx = sm + 3 * SX * SZ, *svz = svx + VX * VZ;
+    __shared__ unsigned wmax_s[2 * (kThreads / 32)];   // per-warp snapshot maxima of a tile
     const int tid = threadIdx.x;
 
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -65,6 +68,11 @@ __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
         const int i0 = tl.y, j0 = tl.z;
         const int rowlim = pitch - EFWI_GX;
         const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
+        // scales of the previous step's snapshot (written for the tile's own cells) and
+        // this thread's max |v^{n+1/2}| for the scale of this step's
+        const float upx = SNAP && a.sw.h ? snap_scale_up(a.sw.hmax, 0, tl.x, a.sw.ns) : 1.f;
+        const float upz = SNAP && a.sw.h ? snap_scale_up(a.sw.hmax, 1, tl.x, a.sw.ns) : 1.f;
+        float mxv = 0.f, mzv = 0.f;
 
         // 1. sigma^n with a 4-cell halo (zero outside the padded grid)
         constexpr int Q4 = SX / 4;
@@ -114,8 +122,9 @@ __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
                         e2 += p2; e4 += p4;
                     }
                 }
-                vx = __ldg(a.in.vx + c) + dt * __ldg(a.M.bx + c) * (e1 + e2);
-                vz = __ldg(a.in.vz + c) + dt * __ldg(a.M.bz + c) * (e3 + e4);
+                const float vxo = __ldg(a.in.vx + c), vzo = __ldg(a.in.vz + c);
+                vx = vxo + dt * __ldg(a.M.bx + c) * (e1 + e2);
+                vz = vzo + dt * __ldg(a.M.bz + c) * (e3 + e4);
                 if (tl.w & 8) {                      // vector force of this shot (k_force's expression)
                     const int lc = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                     const float wvn = a.wv[(long long)tl.x * a.nt + a.n];
@@ -129,12 +138,20 @@ __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
                     a.out.vx[c] = vx;
                     a.out.vz[c] = vz;
                     if (a.segx) { a.segx[c] = vx; a.segz[c] = vz; }
+                    if (SNAP && a.sw.h) {            // snapshot of v^{n-1/2}
+                        snap_put1<SK>(a.sw.h, c, vxo * upx);
+                        snap_put1<SK>(a.sw.h, a.sw.F + c, vzo * upz);
+                    }
+                    mxv = fmaxf(mxv, fabsf(vx));
+                    mzv = fmaxf(mzv, fabsf(vz));
                 }
             }
             svx[q] = vx;
             svz[q] = vz;
         }
+        if (SNAP && a.sw.amax) snap_max_warp(mxv, mzv, wmax_s);
         __syncthreads();
+        if (SNAP && a.sw.amax && tid == 32) snap_max_commit(wmax_s, a.sw.amax, tl.x, a.sw.ns);
 
         // 3. sigma^{n+1} on the tile, then the moment-tensor source
         const bool inj = (tl.w & 1) != 0;
@@ -202,7 +219,8 @@ struct AdjArgsF {
     Pml pml;                    // current adjoint PML memory (V and S blocks, read)
     float *n1, *n3, *n2, *n4;   // next V block
     float *n5, *n8, *n6, *n7;   // next S block
-    const float *vfx, *vfz;     // forward v^{n+1/2}
+    const float *vfx, *vfz;     // forward v^{n+1/2} (FP32), or
+    SnapR sr;                   // its reduced-precision snapshot (sr.h non-null)
     float *Glam, *Gmu, *Gmuxz, *Gbx, *Gbz;
     float dt, rdx, rdz;
 };
@@ -223,8 +241,9 @@ __device__ __forceinline__ float ldg256(const float *p) {
     return v;
 }
 
-template <int TX, int TZ>
+template <int TX, int TZ, int SK = 0>
 __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(AdjArgsF a) {
+    // SK: the forward velocities are FP32 (0) or FP16 / BF16 snapshots
     constexpr int SX = TX + 8, SZ = TZ + 8;
     constexpr int VX = TX + 4, VZ = TZ + 4;
     extern __shared__ float4 smem4[];
@@ -258,6 +277,8 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
             constexpr bool edge = decltype(edge_c)::value;   // 4-cell halo touches a strip or the grid edge
             const int i0 = tl.y, j0 = tl.z;
             const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
+            const float dnx = SK ? snap_scale_down(a.sr.hmax, 0, tl.x, a.sr.ns) : 1.f;
+            const float dnz = SK ? snap_scale_down(a.sr.hmax, 1, tl.x, a.sr.ns) : 1.f;
 
             // Each phase first issues every global load of the thread's cells into
             // registers (no store in between, so all are in flight together), then
@@ -337,7 +358,12 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                     const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                     lvx[r] = ldg256(a.in.vx + c); lvz[r] = ldg256(a.in.vz + c);
                     lbx[r] = ldg256(a.M.bx + c); lbz[r] = ldg256(a.M.bz + c);
-                    lfx[r] = ldg256(a.vfx + c); lfz[r] = ldg256(a.vfz + c);
+                    if constexpr (SK != 0) {
+                        lfx[r] = snap_get<SK>(a.sr.h, c) * dnx;
+                        lfz[r] = snap_get<SK>(a.sr.h, a.sr.F + c) * dnz;
+                    } else {
+                        lfx[r] = ldg256(a.vfx + c); lfz[r] = ldg256(a.vfz + c);
+                    }
                     const bool own = x >= 2 && x < TX + 2 && y >= 2 && y < TZ + 2 && (!edge || (i < NX && j < NZ));
                     if (own && (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP))) {
                         lgx[r] = ld256(a.Gbx + c); lgz[r] = ld256(a.Gbz + c);
@@ -468,19 +494,30 @@ constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 size_t fwd_smem(int tx, int tz) { return sizeof(float) * (3 * (tx + 8) * (tz + 8) + 2 * (tx + 4) * (tz + 4)); }
 size_t adj_smem(int tx, int tz) { return sizeof(float) * (4 * (tx + 8) * (tz + 8) + 6 * (tx + 4) * (tz + 4)); }
 
+// sk: the plan's snapshot store (EFWI_STORE_*), a compile-time parameter of the kernels
 template <int TX, int TZ>
-void fwd_launch(const FwdArgs &a, int grid, cudaStream_t st) {
-    k_step_fused<TX, TZ><<<grid, kThreads, fwd_smem(TX, TZ), st>>>(a);
+void fwd_launch(const FwdArgs &a, int grid, cudaStream_t st, int sk) {
+    if (sk == EFWI_STORE_FP16) k_step_fused<TX, TZ, EFWI_STORE_FP16><<<grid, kThreads, fwd_smem(TX, TZ), st>>>(a);
+    else if (sk == EFWI_STORE_BF16) k_step_fused<TX, TZ, EFWI_STORE_BF16><<<grid, kThreads, fwd_smem(TX, TZ), st>>>(a);
+    else k_step_fused<TX, TZ><<<grid, kThreads, fwd_smem(TX, TZ), st>>>(a);
 }
 template <int TX, int TZ>
-void adj_launch(const AdjArgsF &a, int grid, cudaStream_t st) {
-    k_adj_fused<TX, TZ><<<grid, kThreads, adj_smem(TX, TZ), st>>>(a);
+void adj_launch(const AdjArgsF &a, int grid, cudaStream_t st, int sk) {
+    if (sk == EFWI_STORE_FP16) k_adj_fused<TX, TZ, EFWI_STORE_FP16><<<grid, kThreads, adj_smem(TX, TZ), st>>>(a);
+    else if (sk == EFWI_STORE_BF16) k_adj_fused<TX, TZ, EFWI_STORE_BF16><<<grid, kThreads, adj_smem(TX, TZ), st>>>(a);
+    else k_adj_fused<TX, TZ><<<grid, kThreads, adj_smem(TX, TZ), st>>>(a);
 }
 
+template <int TX, int TZ, int SK>
+void set_attrs_sk() {
+    cudaFuncSetAttribute(k_step_fused<TX, TZ, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(TX, TZ));
+    cudaFuncSetAttribute(k_adj_fused<TX, TZ, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem(TX, TZ));
+}
 template <int TX, int TZ>
 void set_attrs() {
-    cudaFuncSetAttribute(k_step_fused<TX, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(TX, TZ));
-    cudaFuncSetAttribute(k_adj_fused<TX, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem(TX, TZ));
+    set_attrs_sk<TX, TZ, 0>();
+    set_attrs_sk<TX, TZ, EFWI_STORE_FP16>();
+    set_attrs_sk<TX, TZ, EFWI_STORE_BF16>();
 }
 
 void set_all_attrs() {
@@ -554,9 +591,21 @@ int upload_tiles(efwi_plan *p, TileList &tl, int tx, int tz) {
     return EFWI_OK;
 }
 
+// Recompute the flags of a tile list (source and force cells) for the plan's
+// current acquisition and copy them over the list in place (same geometry, so
+// the same tiles; the pointer, which captured graphs hold, stays).
+int refresh_tiles(efwi_plan *p, TileList &tl, cudaStream_t st) {
+    if (!tl.tiles) return EFWI_OK;
+    std::vector<int4> t = make_tiles(p, tl.tx, tl.tz);
+    if ((int)t.size() != tl.n) return EFWI_ERR_ARG;
+    cudaMemcpyAsync(tl.tiles, t.data(), sizeof(int4) * t.size(), cudaMemcpyHostToDevice, st);
+    return EFWI_OK;
+}
+
 namespace {
 
-FwdArgs fwd_args(efwi_plan *p, int n, float *segx, float *segz) {
+FwdArgs fwd_args(efwi_plan *p, int n, const SnapOut &so) {
+    float *segx = so.fx, *segz = so.fz;
     FwdArgs a;
     a.shots = p->shots_d;
     a.tiles = p->tiles.tiles;
@@ -575,10 +624,12 @@ FwdArgs fwd_args(efwi_plan *p, int n, float *segx, float *segz) {
     a.dt = (float)p->d.dt;
     a.rdx = (float)(1.0 / p->d.dx);
     a.rdz = (float)(1.0 / p->d.dz);
+    a.sw = so.sw;
     return a;
 }
 
-AdjArgsF adj_args_f(efwi_plan *p, const float *vfx, const float *vfz) {
+AdjArgsF adj_args_f(efwi_plan *p, const SnapIn &si) {
+    const float *vfx = si.fx, *vfz = si.fz;
     AdjArgsF a;
     a.shots = p->shots_d;
     a.tiles = p->adj_tiles.tiles;
@@ -592,6 +643,7 @@ AdjArgsF adj_args_f(efwi_plan *p, const float *vfx, const float *vfz) {
     a.n1 = vn; a.n3 = vn + X; a.n2 = vn + 2 * X; a.n4 = vn + 2 * X + Z;
     a.n5 = sn; a.n8 = sn + X; a.n6 = sn + 2 * X; a.n7 = sn + 2 * X + Z;
     a.vfx = vfx; a.vfz = vfz;
+    a.sr = si.sr;
     a.Glam = G_field(p, 0); a.Gmu = G_field(p, 1); a.Gmuxz = G_field(p, 2);
     a.Gbx = G_field(p, 3); a.Gbz = G_field(p, 4);
     a.dt = (float)p->d.dt;
@@ -602,15 +654,15 @@ AdjArgsF adj_args_f(efwi_plan *p, const float *vfx, const float *vfz) {
 
 }  // namespace
 
-void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaStream_t st) {
+void launch_step_fused(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st) {
     int slot;
     prof_begin(p, st, &slot, EFWI_KERNEL_STEP);
     if (p->stencil >= EFWI_STENCIL_TMA) {
-        launch_step_tma(p, n, vseg_x, vseg_z, st);
+        launch_step_tma(p, n, so, st);
     } else {
-        FwdArgs a = fwd_args(p, n, vseg_x, vseg_z);
+        FwdArgs a = fwd_args(p, n, so);
         const int grid = p->grid_fwd_override > 0 ? std::min(p->grid_fwd_override, a.ntiles) : a.ntiles;
-        EFWI_DISPATCH(p->tiles.tx, p->tiles.tz, fwd_launch, a, grid, st);
+        EFWI_DISPATCH(p->tiles.tx, p->tiles.tz, fwd_launch, a, grid, st, p->snap_store);
     }
     prof_end(p, st, slot);
     p->launches++;
@@ -618,18 +670,18 @@ void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaSt
     p->psi_v ^= 1;
 }
 
-void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaStream_t st) {
+void launch_adj_fused(efwi_plan *p, int n, const SnapIn &si, cudaStream_t st) {
     (void)n;
     int slot;
     prof_begin(p, st, &slot, EFWI_KERNEL_ADJ);
     if (p->adj_stencil == EFWI_STENCIL_TMA) {
-        launch_adj_tma(p, vfx, st);
+        launch_adj_tma(p, si.fx, st);         // FP32 snapshots only (the autotuner's candidates)
     } else {
-        AdjArgsF a = adj_args_f(p, vfx, vfz);
+        AdjArgsF a = adj_args_f(p, si);
         const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles)
                          : p->adj_grid > 0        ? std::min(p->adj_grid, a.ntiles)
                                                   : a.ntiles;
-        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st);
+        EFWI_DISPATCH(p->adj_tiles.tx, p->adj_tiles.tz, adj_launch, a, grid, st, p->snap_store);
     }
     prof_end(p, st, slot);
     p->launches++;
@@ -653,14 +705,17 @@ struct Variant {
 };
 
 float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-    float *vs_x = p->seg, *vs_z = p->seg + p->fsz_total;
+    // the snapshot traffic of a real step: FP32 copy of v into slot 0, or the
+    // reduced-precision pack of slot 0 and the maxima of slot 1
+    const SnapOut so = snap_out(p, p->K > 1 ? 1 : 0, 0);
+    const SnapIn si = snap_in(p, 0);
     const int reps = 3;
     float t = 0;
     for (int w = 0; w < 2; ++w) {              // warm-up, then timed
         cudaEventRecord(e0, st);
         for (int r = 0; r < reps; ++r) {
-            if (adj) launch_adj_fused(p, 0, vs_x, vs_z, st);
-            else launch_step_fused(p, 0, vs_x, vs_z, st);
+            if (adj) launch_adj_fused(p, 0, si, st);
+            else launch_step_fused(p, 0, so, st);
         }
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
@@ -674,7 +729,14 @@ int select_adj(efwi_plan *p, const Variant &v) {
     p->adj_grid = 0;
     if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2 && v.tx == 32 && v.tz == 16) {   // loads: vec 2 = persistent
         int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
+        if (p->snap_store == EFWI_STORE_FP16)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16, EFWI_STORE_FP16>, kThreads,
+                                                          adj_smem(32, 16));
+        else if (p->snap_store == EFWI_STORE_BF16)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16, EFWI_STORE_BF16>, kThreads,
+                                                          adj_smem(32, 16));
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16>, kThreads, adj_smem(32, 16));
         p->adj_grid = std::max(1, nb) * p->n_sms;
     }
     int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
@@ -715,7 +777,7 @@ int efwi_autotune(efwi_plan *p) {
                 if (want != EFWI_STENCIL_AUTO && want != kind) continue;
                 for (int nst = 2; nst <= 4; ++nst)
                     if ((!only_nst || nst == only_nst) && (!only_vec || vec == only_vec || vec == 1) &&
-                        tma_shape_ok(s.tx, s.tz, nst, vec, stg))
+                        tma_shape_ok(s.tx, s.tz, nst, vec, stg, p->snap_store))
                         fwd.push_back({kind, s.tx, s.tz, nst, vec, stg});
             }
     }
@@ -733,8 +795,8 @@ int efwi_autotune(efwi_plan *p) {
             if (only_p <= 0) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
             if (s.tx == 32 && s.tz == 16 && only_p != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
         }
-        for (int nst = 1; nst <= 2; ++nst)
-            if (wa != EFWI_STENCIL_LOADS && tma_adj_shape_ok(s.tx, s.tz, nst))
+        for (int nst = 1; nst <= 2; ++nst)   // (the TMA adjoint reads FP32 snapshots only)
+            if (wa != EFWI_STENCIL_LOADS && p->snap_store == EFWI_STORE_FP32 && tma_adj_shape_ok(s.tx, s.tz, nst))
                 adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, nst});
     }
     // a requested staging without an instantiation for this tile falls back to per-thread loads
@@ -787,7 +849,7 @@ int efwi_autotune(efwi_plan *p) {
     p->ov_fwd = p->ov_adj = 0;
     const long long segbytes = sizeof(float) * (long long)p->K * 2 * p->fsz_total;
     float *seg2 = nullptr;
-    if (!rc && p->K < p->d.nt && p->d.overlap != EFWI_OVERLAP_OFF &&
+    if (!rc && p->K < p->d.nt && p->d.overlap != EFWI_OVERLAP_OFF && p->snap_store == EFWI_STORE_FP32 &&
         cudaMalloc((void **)&seg2, segbytes) != cudaSuccess) {
         cudaGetLastError();
         seg2 = nullptr;
@@ -814,10 +876,14 @@ int efwi_autotune(efwi_plan *p) {
                 cudaEventRecord(e0, sa);
                 cudaStreamWaitEvent(sr, e0);
                 p->grid_fwd_override = of * p->n_sms;
-                for (int r = 0; r < reps; ++r) launch_step_fused(p, 0, sx1, sz1, of ? sr : sa);
+                SnapOut so1;
+                so1.fx = sx1; so1.fz = sz1;
+                for (int r = 0; r < reps; ++r) launch_step_fused(p, 0, so1, of ? sr : sa);
                 p->grid_fwd_override = 0;
                 p->grid_adj_override = oa * p->n_sms;
-                for (int r = 0; r < reps; ++r) launch_adj_fused(p, 0, sx0, sz0, sa);
+                SnapIn si0;
+                si0.fx = sx0; si0.fz = sz0;
+                for (int r = 0; r < reps; ++r) launch_adj_fused(p, 0, si0, sa);
                 p->grid_adj_override = 0;
                 cudaEventRecord(ej, sr);
                 cudaStreamWaitEvent(sa, ej);
@@ -868,7 +934,7 @@ int efwi_autotune(efwi_plan *p) {
     cudaMemset(p->psi, 0, sizeof(float) * 4 * p->H);
     cudaMemset(p->apsi, 0, sizeof(float) * 4 * p->H);
     cudaMemset(p->G, 0, sizeof(float) * 5 * p->fsz_total);
-    cudaMemset(p->seg, 0, sizeof(float) * (p->seg_double ? 2 : 1) * p->K * 2 * p->fsz_total);
+    if (p->seg) cudaMemset(p->seg, 0, sizeof(float) * (p->seg_double ? 2 : 1) * p->K * 2 * p->fsz_total);
     cudaMemset(p->dev_err, 0, sizeof(int));
     p->scur = p->acur = p->psi_v = p->psi_s = p->apsi_v = p->apsi_s = 0;
     p->launches = 0;

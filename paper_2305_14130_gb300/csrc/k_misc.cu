@@ -2,6 +2,7 @@
 // DAS sampling and its transpose, FP64 misfit, chain rule to (Vp, Vs, rho),
 // Kahan folding of per-segment imaging sums, wavefield checkpoints (FP32 or
 // scaled FP16/BF16), zone-of-influence weights and the consistency term.
+#include <algorithm>
 #include <cmath>
 
 #include "plan.hpp"
@@ -149,18 +150,21 @@ __global__ void k_das_adj_prep(const float *resid, double *acc, float *coef, int
 // Transposed sampling as a deterministic gather over the cells touched by gauge
 // ends; also the b-imaging contribution of this adjoint increment.
 __global__ void k_das_adj_gather(const ShotDev *shots, GatherCSR g, const float *coef, Fields A, const float *vfx,
-                                 const float *vfz, float *Gbx, float *Gbz, int g0, int gn) {
+                                 const float *vfz, SnapR sr, float *Gbx, float *Gbz, int g0, int gn) {
     const int k = g0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= g0 + gn) return;
     float inc = 0.f;
     for (int e = g.ptr[k]; e < g.ptr[k + 1]; ++e) inc += g.w[e] * coef[g.tr[e]];
-    const long long c = shots[g.tgt_shot[k]].off + g.tgt_off[k];
+    const int shot = g.tgt_shot[k];
+    const long long c = shots[shot].off + g.tgt_off[k];
     if (g.tgt_field[k] == 0) {
         A.vx[c] += inc;
-        Gbx[c] += vfx[c] * inc;
+        const float v = sr.h ? snap_get_rt(sr.h, c, sr.kind) * snap_scale_down(sr.hmax, 0, shot, sr.ns) : vfx[c];
+        Gbx[c] += v * inc;
     } else {
         A.vz[c] += inc;
-        Gbz[c] += vfz[c] * inc;
+        const float v = sr.h ? snap_get_rt(sr.h, sr.F + c, sr.kind) * snap_scale_down(sr.hmax, 1, shot, sr.ns) : vfz[c];
+        Gbz[c] += v * inc;
     }
 }
 
@@ -263,41 +267,45 @@ __global__ void k_kahan(float *G, float *tot, float *cmp, long long n) {
 }
 
 // --------------------------------------------------------------------------
-// Checkpoints in scaled FP16 / BF16: per snapshot, per field and shot, scale
-// s = max |x| and store x / s rounded to nearest even.
+// Checkpoints in scaled FP16 / BF16: per snapshot, per field and shot, s = max |x|
+// and x stored as RNE(x 2^k) with the power of two of store_exp(s).
 // --------------------------------------------------------------------------
-__global__ void k_absmax(const ShotDev *shots, const float *fields, long long F, float *scale, int ns) {
-    const int f = blockIdx.y, shot = blockIdx.z;
-    const ShotDev s = shots[shot];
-    const long long n = (long long)(s.NZ + 2 * EFWI_GZ) * s.pitch;
-    const float *x = fields + f * F + s.off;
+// grid-stride pieces shared by the checkpoint kernels and the store self-test
+__device__ __forceinline__ void absmax_span(const float *x, long long n, float *s) {
     float m = 0.f;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
         m = fmaxf(m, fabsf(x[k]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax((int *)&scale[f * ns + shot], __float_as_int(m));
+    if ((threadIdx.x & 31) == 0) atomicMax((int *)s, __float_as_int(m));   // non-negative floats order as ints
 }
 
 template <class T>
-__device__ __forceinline__ T to_store(float v);
-template <>
-__device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-__device__ __forceinline__ float from_store(__half v) { return __half2float(v); }
-__device__ __forceinline__ float from_store(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ void pack_span(const float *x, long long n, float s, T *y) {
+    const float up = pow2f(store_exp(s));
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        y[k] = to_store<T>(x[k] * up);
+}
+
+template <class T>
+__device__ __forceinline__ void unpack_span(const T *y, long long n, float s, float *x) {
+    const float down = pow2f(-store_exp(s));
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        x[k] = from_store(y[k]) * down;
+}
+
+__global__ void k_absmax(const ShotDev *shots, const float *fields, long long F, float *scale, int ns) {
+    const int f = blockIdx.y, shot = blockIdx.z;
+    const ShotDev s = shots[shot];
+    const long long n = (long long)(s.NZ + 2 * EFWI_GZ) * s.pitch;
+    absmax_span(fields + f * F + s.off, n, &scale[f * ns + shot]);
+}
 
 template <class T>
 __global__ void k_pack(const ShotDev *shots, const float *fields, long long F, const float *scale, T *out, int ns) {
     const int f = blockIdx.y, shot = blockIdx.z;
     const ShotDev s = shots[shot];
     const long long n = (long long)(s.NZ + 2 * EFWI_GZ) * s.pitch;
-    const float sc = scale[f * ns + shot];
-    const float inv = sc > 0.f ? 1.f / sc : 0.f;
-    const float *x = fields + f * F + s.off;
-    T *y = out + f * F + s.off;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        y[k] = to_store<T>(x[k] * inv);
+    pack_span<T>(fields + f * F + s.off, n, scale[f * ns + shot], out + f * F + s.off);
 }
 
 template <class T>
@@ -305,12 +313,27 @@ __global__ void k_unpack(const ShotDev *shots, float *fields, long long F, const
     const int f = blockIdx.y, shot = blockIdx.z;
     const ShotDev s = shots[shot];
     const long long n = (long long)(s.NZ + 2 * EFWI_GZ) * s.pitch;
-    const float sc = scale[f * ns + shot];
-    float *x = fields + f * F + s.off;
-    const T *y = in + f * F + s.off;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
-        x[k] = from_store(y[k]) * sc;
+    unpack_span<T>(in + f * F + s.off, n, scale[f * ns + shot], fields + f * F + s.off);
 }
+
+// The reduced-precision snapshot of the velocities of state buffer `vx, vz` (the
+// last step of a pass, which no later step stages): per shot (blockIdx.z) and
+// field (blockIdx.y) the whole block with the maxima its step accumulated.
+template <class T>
+__global__ void k_snap_tail(const ShotDev *shots, const float *vx, const float *vz, SnapW sw) {
+    const int f = blockIdx.y, shot = blockIdx.z;
+    const ShotDev s = shots[shot];
+    const long long n = (long long)(s.NZ + 2 * EFWI_GZ) * s.pitch;
+    const float mx = sw.hmax[(long long)(f * sw.ns + shot) * kMaxPad];
+    pack_span<T>((f ? vz : vx) + s.off, n, mx, static_cast<T *>(sw.h) + f * sw.F + s.off);
+}
+
+// Self-test kernels: one array as one snapshot field.
+__global__ void k_selftest_absmax(const float *x, long long n, float *s) { absmax_span(x, n, s); }
+template <class T>
+__global__ void k_selftest_pack(const float *x, long long n, const float *s, T *y) { pack_span<T>(x, n, *s, y); }
+template <class T>
+__global__ void k_selftest_unpack(const T *y, long long n, const float *s, float *x) { unpack_span<T>(y, n, *s, x); }
 
 // --------------------------------------------------------------------------
 // Zone of influence (eq. 10) and the consistency term (eqs. 8, 11, 12).
@@ -414,8 +437,8 @@ void launch_das_fwd(efwi_plan *p, Fields F, int n, float *d, int shot, cudaStrea
     p->launches++;
 }
 
-void launch_das_adj(efwi_plan *p, Fields A, const float *vfx, const float *vfz, float *Gbx, float *Gbz, int n,
-                    int shot, cudaStream_t st) {
+void launch_das_adj(efwi_plan *p, Fields A, const SnapIn &si, float *Gbx, float *Gbz, int n, int shot,
+                    cudaStream_t st) {
     const int t0 = shot < 0 ? 0 : p->shots[shot].tr0;
     const int cnt = shot < 0 ? p->d.ntr : p->shots[shot].ntr;
     if (cnt == 0) return;
@@ -425,7 +448,8 @@ void launch_das_adj(efwi_plan *p, Fields A, const float *vfx, const float *vfz, 
     const int gn = shot < 0 ? p->gather.n_tgt : p->gather_ptr[shot + 1] - p->gather_ptr[shot];
     p->launches++;
     if (gn == 0) return;
-    k_das_adj_gather<<<(gn + 127) / 128, 128, 0, st>>>(p->shots_d, p->gather, p->tr_coef, A, vfx, vfz, Gbx, Gbz, g0, gn);
+    k_das_adj_gather<<<(gn + 127) / 128, 128, 0, st>>>(p->shots_d, p->gather, p->tr_coef, A, si.fx, si.fz, si.sr,
+                                                       Gbx, Gbz, g0, gn);
     p->launches++;
 }
 
@@ -479,6 +503,14 @@ void launch_ckpt_save(efwi_plan *p, int slot, cudaStream_t st) {
         k_pack<__nv_bfloat16><<<g, 256, 0, st>>>(p->shots_d, src, F, sc,
                                                   (__nv_bfloat16 *)p->ck.fields + (size_t)slot * 5 * F, ns);
     p->launches += 2;
+}
+
+void launch_snap_tail(efwi_plan *p, const SnapW &sw, cudaStream_t st) {
+    const Fields F = state_fields(p, p->scur);
+    dim3 g(64, 2, p->d.ns);
+    if (sw.kind == EFWI_STORE_FP16) k_snap_tail<__half><<<g, 256, 0, st>>>(p->shots_d, F.vx, F.vz, sw);
+    else k_snap_tail<__nv_bfloat16><<<g, 256, 0, st>>>(p->shots_d, F.vx, F.vz, sw);
+    p->launches++;
 }
 
 void launch_ckpt_load(efwi_plan *p, int slot, cudaStream_t st) {
@@ -547,3 +579,56 @@ void launch_reg(efwi_plan *p, const float *m, const float *b, const float *bp, c
 }
 
 }  // namespace efwi
+
+// --------------------------------------------------------------------------
+// Numerics self-tests: the reduced-precision store and the Kahan fold on
+// caller arrays, through the device routines the time loops use.
+// --------------------------------------------------------------------------
+extern "C" int efwi_selftest_store(int store, long long n, const float *x, void *enc, float *y, float *s_out,
+                                   efwi_stream_t stream) {
+    using namespace efwi;
+    if (n < 1 || !x || !y || !s_out || (store != EFWI_STORE_FP32 && !enc) || store < EFWI_STORE_FP32 ||
+        store > EFWI_STORE_BF16) {
+        set_thread_error("efwi_selftest_store: n >= 1, x, y, s_out (and enc for FP16/BF16) required");
+        return EFWI_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemsetAsync(s_out, 0, sizeof(float), st);
+    const int g = (int)std::min<long long>((n + 255) / 256, 4 * 152);
+    k_selftest_absmax<<<g, 256, 0, st>>>(x, n, s_out);
+    if (store == EFWI_STORE_FP32) {
+        cudaMemcpyAsync(y, x, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
+    } else if (store == EFWI_STORE_FP16) {
+        k_selftest_pack<__half><<<g, 256, 0, st>>>(x, n, s_out, (__half *)enc);
+        k_selftest_unpack<__half><<<g, 256, 0, st>>>((const __half *)enc, n, s_out, y);
+    } else {
+        k_selftest_pack<__nv_bfloat16><<<g, 256, 0, st>>>(x, n, s_out, (__nv_bfloat16 *)enc);
+        k_selftest_unpack<__nv_bfloat16><<<g, 256, 0, st>>>((const __nv_bfloat16 *)enc, n, s_out, y);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_thread_error(std::string("efwi_selftest_store: ") + cudaGetErrorString(e));
+        return EFWI_ERR_CUDA;
+    }
+    return EFWI_OK;
+}
+
+extern "C" int efwi_selftest_kahan(long long n, int nterms, float *terms, float *tot, float *cmp,
+                                   efwi_stream_t stream) {
+    using namespace efwi;
+    if (n < 1 || nterms < 1 || !terms || !tot || !cmp) {
+        set_thread_error("efwi_selftest_kahan: n, nterms >= 1 and non-NULL arrays required");
+        return EFWI_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemsetAsync(tot, 0, sizeof(float) * n, st);
+    cudaMemsetAsync(cmp, 0, sizeof(float) * n, st);
+    const int g = (int)std::min<long long>((n + 255) / 256, 4 * 152);
+    for (int k = 0; k < nterms; ++k) k_kahan<<<g, 256, 0, st>>>(terms + (size_t)k * n, tot, cmp, n);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_thread_error(std::string("efwi_selftest_kahan: ") + cudaGetErrorString(e));
+        return EFWI_ERR_CUDA;
+    }
+    return EFWI_OK;
+}

@@ -45,6 +45,7 @@ struct TmaFwdArgs {
     int *err;
     int ofield;                 // state-map field of the written buffer's vx (output staging)
     int segf;                   // segment-map field of this step's vx, or -1 (output staging)
+    SnapW sw;                   // reduced-precision snapshot work (sw.h / sw.amax null: none)
 };
 
 // Shared-memory stage of one tile.  Fields are staged on the tile + 4-cell halo in x
@@ -103,15 +104,18 @@ __device__ __forceinline__ void store_fwd(const TmaFwdArgs &a, int4 tl, const fl
     bulk_commit();
 }
 
-template <int TX, int TZ, int NST, int VEC, int ST = 0>
+template <int TX, int TZ, int NST, int VEC, int ST = 0, int SK = 0>
 __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
     static_assert(ST == 0 || VEC >= 2, "output staging is implemented for cell pairs");
+    // SK: EFWI_STORE_FP16 / BF16 compiles the reduced-precision snapshot work in (0: none)
+    constexpr bool SNAP = SK != 0;
     using L = FwdLayout<TX, TZ, NST, VEC>;
     constexpr int SX = L::SX;
     extern __shared__ float4 smem_raw[];
     float *smb = align128(smem_raw);
     __shared__ __align__(8) uint64_t bar[NST];
     __shared__ int ok_s;
+    __shared__ unsigned wmax_s[2 * (kThreads / 32)];   // per-warp snapshot maxima of a tile
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int b = 0; b < NST; ++b) mbar_init(&bar[b], 1);
@@ -139,12 +143,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         const int NX = __ldg(&sp->NX), NZ = __ldg(&sp->NZ), P = __ldg(&sp->P), profx = __ldg(&sp->profx),
                   pitch = __ldg(&sp->pitch);
         const long long off = __ldg(&sp->off), psx = __ldg(&sp->psx), psz = __ldg(&sp->psz);
+        // scales of the previous step's snapshot, written below for this tile's own cells
+        const float upx = SNAP && a.sw.h ? snap_scale_up(a.sw.hmax, 0, tl.x, a.sw.ns) : 1.f;
+        const float upz = SNAP && a.sw.h ? snap_scale_up(a.sw.hmax, 1, tl.x, a.sw.ns) : 1.f;
         if (t + gridDim.x < a.ntiles) tl_next = __ldg(a.tiles + t + gridDim.x);
         if (tid == 0) ok_s = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
         __syncthreads();
         if (!ok_s) {
             if (tid == 0) {
                 atomicOr(a.err, EFWI_FLAG_TIMEOUT);
+                // copies in flight: this tile's and the next NST-2 tiles' (the refill of the
+                // NST-1-th follows the wait); no copy is issued after this point
+                int inflight = 0;
+                for (int j = 0; j < NST - 1; ++j)
+                    if (t + j * (int)gridDim.x < a.ntiles) ++inflight;
+                mbar_drain_bounded(bar, phase, k, NST, inflight);
                 if (ST) bulk_wait0();       // stores already issued finish before the CTA exits
             }
             return;
@@ -180,6 +193,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
             float *__restrict__ ovx = a.out.vx + off;
             float *__restrict__ ovz = a.out.vz + off;
             const float dt = a.dt, rdx = a.rdx, rdz = a.rdz;
+            float mxv = 0.f, mzv = 0.f;                     // this thread's max |v^{n+1/2}| (snapshot scale)
 
             if constexpr (VEC >= 2) {
                 // Cell pairs (x, x+1) in halo-4 coordinates, x even: adjacent x-stencils share
@@ -249,6 +263,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                     }
                     st2(svx + o, vx);
                     st2(svz + o, vz);
+                    if (SNAP && own && (a.sw.h || a.sw.amax)) {
+                        // snapshot of v^{n-1/2} (staged input of this step) and the scale of v^{n+1/2}
+                        const long long c = off + (j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                        if (a.sw.h) {
+                            if (!edge || (i + 1 < NX && j < NZ)) {
+                                snap_put2<SK>(a.sw.h, c, vxo.x * upx, vxo.y * upx);
+                                snap_put2<SK>(a.sw.h, a.sw.F + c, vzo.x * upz, vzo.y * upz);
+                            } else if (i < NX && j < NZ) {
+                                snap_put1<SK>(a.sw.h, c, vxo.x * upx);
+                                snap_put1<SK>(a.sw.h, a.sw.F + c, vzo.x * upz);
+                            }
+                        }
+                        mxv = fmaxf(mxv, fmaxf(fabsf(vx.x), fabsf(vx.y)));
+                        mzv = fmaxf(mzv, fmaxf(fabsf(vz.x), fabsf(vz.y)));
+                    }
                     if (!ST && own) {
                         const int c = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                         if (!edge || (i + 1 < NX && j < NZ)) {
@@ -330,7 +359,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                         vpair(2 + 2 * (q - yy * NPX), 2 + yy);
                     }
                 }
+                if (SNAP && a.sw.amax) snap_max_warp(mxv, mzv, wmax_s);
                 __syncthreads();
+                if (SNAP && a.sw.amax && tid == 32) snap_max_commit(wmax_s, a.sw.amax, tl.x, a.sw.ns);
 
                 float *__restrict__ oxx = a.out.sxx + off;
                 float *__restrict__ ozz = a.out.szz + off;
@@ -466,8 +497,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                                 e2 += p2; e4 += p4;
                             }
                         }
-                        vx = svx[o] + dt * sbx[o] * (e1 + e2);
-                        vz = svz[o] + dt * sbz[o] * (e3 + e4);
+                        const float vxo = svx[o], vzo = svz[o];
+                        vx = vxo + dt * sbx[o] * (e1 + e2);
+                        vz = vzo + dt * sbz[o] * (e3 + e4);
                         if (tl.w & 8) {              // vector force of this shot (k_force's expression)
                             const int lc = (j + EFWI_GZ) * pitch + (i + EFWI_GX);
                             const float wvn = a.wv[(long long)tl.x * a.nt + a.n];
@@ -482,12 +514,20 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                             ovx[c] = vx;
                             ovz[c] = vz;
                             if (a.segx) { a.segx[off + c] = vx; a.segz[off + c] = vz; }
+                            if (SNAP && a.sw.h) {    // snapshot of v^{n-1/2}
+                                snap_put1<SK>(a.sw.h, off + c, vxo * upx);
+                                snap_put1<SK>(a.sw.h, a.sw.F + off + c, vzo * upz);
+                            }
+                            mxv = fmaxf(mxv, fabsf(vx));
+                            mzv = fmaxf(mzv, fabsf(vz));
                         }
                     }
                     svx[o] = vx;
                     svz[o] = vz;
                 }
+                if (SNAP && a.sw.amax) snap_max_warp(mxv, mzv, wmax_s);
                 __syncthreads();
+                if (SNAP && a.sw.amax && tid == 32) snap_max_commit(wmax_s, a.sw.amax, tl.x, a.sw.ns);
     
                 // sigma^{n+1} on the tile, then the moment-tensor source
                 float *__restrict__ oxx = a.out.sxx + off;
@@ -570,18 +610,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int TX, int TZ, int NST, int VEC, int ST>
+template <int TX, int TZ, int NST, int VEC, int ST, int SK = 0>
 void launch_tma(const TmaFwdArgs &a, int grid, cudaStream_t st) {
-    k_step_tma<TX, TZ, NST, VEC, ST><<<grid, kThreads, FwdLayout<TX, TZ, NST, VEC>::smem(), st>>>(a);
+    k_step_tma<TX, TZ, NST, VEC, ST, SK><<<grid, kThreads, FwdLayout<TX, TZ, NST, VEC>::smem(), st>>>(a);
 }
 
-template <int TX, int TZ, int NST, int VEC, int ST>
+template <int TX, int TZ, int NST, int VEC, int ST, int SK = 0>
 int occupancy() {
-    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST, VEC, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST, VEC, ST, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)FwdLayout<TX, TZ, NST, VEC>::smem());
-    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST, VEC, ST>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_step_tma<TX, TZ, NST, VEC, ST, SK>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<TX, TZ, NST, VEC, ST>, kThreads,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tma<TX, TZ, NST, VEC, ST, SK>, kThreads,
                                                   FwdLayout<TX, TZ, NST, VEC>::smem());
     return nb;
 }
@@ -593,6 +633,9 @@ int occupancy() {
     X(32, 8, 2, 1, 0) X(32, 8, 3, 1, 0) X(32, 16, 2, 1, 0) X(64, 8, 2, 1, 0) X(64, 16, 2, 1, 0)          \
     X(32, 8, 2, 2, 0) X(32, 8, 3, 2, 0) X(32, 16, 2, 2, 0) X(32, 16, 3, 2, 0) X(64, 8, 2, 2, 0)          \
     X(64, 16, 2, 2, 0) X(32, 16, 2, 2, 1) X(32, 16, 2, 3, 0) X(32, 16, 2, 3, 1)
+// the variants also compiled with FP16 / BF16 snapshot work (plans with a reduced-precision snapshot store)
+#define EFWI_TMA_SNAP_VARIANTS(X) \
+    X(32, 16, 2, 1, 0) X(32, 16, 2, 2, 0) X(32, 16, 2, 2, 1) X(32, 16, 2, 3, 0) X(32, 16, 2, 3, 1) X(32, 8, 2, 2, 0)
 
 }  // namespace
 
@@ -611,8 +654,12 @@ int encode_map(CUtensorMap *m, float *base, const ShotDev &s, long long F, int n
     return r == CUDA_SUCCESS ? EFWI_OK : EFWI_ERR_CUDA;
 }
 
-bool tma_shape_ok(int tx, int tz, int nst, int vec, int st) {
+bool tma_shape_ok(int tx, int tz, int nst, int vec, int st, int snap) {
 #define EFWI_OK_X(a, b, c, d, e) if (tx == a && tz == b && nst == c && vec == d && st == e) return true;
+    if (snap != EFWI_STORE_FP32) {
+        EFWI_TMA_SNAP_VARIANTS(EFWI_OK_X)
+        return false;
+    }
     EFWI_TMA_VARIANTS(EFWI_OK_X)
 #undef EFWI_OK_X
     return false;
@@ -631,7 +678,7 @@ int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int stg) {
         if (!rc) rc = encode_map(&h[s].mc, p->mat, sh, F, 5, tx, tz, 3);
         if (!rc) rc = encode_map(&h[s].o2, p->state[0], sh, F, 10, tx, tz, 2);
         if (!rc) rc = encode_map(&h[s].o3, p->state[0], sh, F, 10, tx, tz, 3);
-        if (!rc) rc = encode_map(&h[s].sg, p->seg, sh, F, (p->seg_double ? 4 : 2) * p->K, tx, tz, 2);
+        if (!rc && p->seg) rc = encode_map(&h[s].sg, p->seg, sh, F, (p->seg_double ? 4 : 2) * p->K, tx, tz, 2);
         if (rc) {
             p->err = "cuTensorMapEncodeTiled failed for the forward maps";
             return rc;
@@ -641,10 +688,17 @@ int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int stg) {
         return EFWI_ERR_OOM;
     cudaMemcpy(p->fwd_maps, h.data(), sizeof(FwdMaps) * p->d.ns, cudaMemcpyHostToDevice);
     int nb = 0;
+    const int sk = p->snap_store;
 #define EFWI_OCC_X(a, b, c, d, e) \
     if (tx == a && tz == b && nst == c && vec == d && stg == e) nb = occupancy<a, b, c, d, e>();
-    EFWI_TMA_VARIANTS(EFWI_OCC_X)
+#define EFWI_OCC_SNAP_X(a, b, c, d, e)                                                                 \
+    if (tx == a && tz == b && nst == c && vec == d && stg == e)                                        \
+        nb = sk == EFWI_STORE_FP16 ? occupancy<a, b, c, d, e, EFWI_STORE_FP16>()                       \
+                                   : occupancy<a, b, c, d, e, EFWI_STORE_BF16>();
+    if (sk == EFWI_STORE_FP32) { EFWI_TMA_VARIANTS(EFWI_OCC_X) }
+    else { EFWI_TMA_SNAP_VARIANTS(EFWI_OCC_SNAP_X) }
 #undef EFWI_OCC_X
+#undef EFWI_OCC_SNAP_X
     p->tma_stages = nst;
     p->tma_vec = vec;
     p->tma_store = stg;
@@ -655,7 +709,8 @@ int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int stg) {
     return EFWI_OK;
 }
 
-void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t st) {
+void launch_step_tma(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st) {
+    float *segx = so.fx, *segz = so.fz;
     TmaFwdArgs a;
     a.shots = p->shots_d;
     a.tiles = p->tiles.tiles;
@@ -677,12 +732,21 @@ void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t
     a.err = p->dev_err;
     a.ofield = 5 * (1 - p->scur);
     a.segf = segx ? (int)((segx - p->seg) / p->fsz_total) : -1;
+    a.sw = so.sw;
     const int grid = std::min(p->grid_fwd_override > 0 ? p->grid_fwd_override : p->tma_grid, a.ntiles);
     const int tx = p->tiles.tx, tz = p->tiles.tz, nst = p->tma_stages, vec = p->tma_vec, stg = p->tma_store;
+    const int sk = p->snap_store;
 #define EFWI_LAUNCH_X(a_, b_, c_, d_, e_) \
     if (tx == a_ && tz == b_ && nst == c_ && vec == d_ && stg == e_) launch_tma<a_, b_, c_, d_, e_>(a, grid, st);
-    EFWI_TMA_VARIANTS(EFWI_LAUNCH_X)
+#define EFWI_LAUNCH_SNAP_X(a_, b_, c_, d_, e_)                                                         \
+    if (tx == a_ && tz == b_ && nst == c_ && vec == d_ && stg == e_) {                                 \
+        if (sk == EFWI_STORE_FP16) launch_tma<a_, b_, c_, d_, e_, EFWI_STORE_FP16>(a, grid, st);       \
+        else launch_tma<a_, b_, c_, d_, e_, EFWI_STORE_BF16>(a, grid, st);                             \
+    }
+    if (sk == EFWI_STORE_FP32) { EFWI_TMA_VARIANTS(EFWI_LAUNCH_X) }
+    else { EFWI_TMA_SNAP_VARIANTS(EFWI_LAUNCH_SNAP_X) }
 #undef EFWI_LAUNCH_X
+#undef EFWI_LAUNCH_SNAP_X
 }
 
 }  // namespace efwi
@@ -773,7 +837,15 @@ __global__ void __launch_bounds__(256) k_adj_tma(TmaAdjArgs a) {
         if (tid == 0) ok_s = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
         __syncthreads();
         if (!ok_s) {
-            if (tid == 0) atomicOr(a.err, EFWI_FLAG_TIMEOUT);
+            if (tid == 0) {
+                atomicOr(a.err, EFWI_FLAG_TIMEOUT);
+                // copies in flight: this tile's and, with a pipeline, the next NST-1 tiles'
+                // (their refill precedes the wait); no copy is issued after this point
+                int inflight = 0;
+                for (int j = 0; j < (NST > 1 ? NST : 1); ++j)
+                    if (t + j * (int)gridDim.x < a.ntiles) ++inflight;
+                mbar_drain_bounded(bar, phase, k, NST, inflight);
+            }
             return;
         }
         mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
@@ -1043,7 +1115,7 @@ __global__ void k_selftest_timeout(long long budget, int *err) {
     efwi::mbar_init(&bar, 2);
     efwi::fence_mbar_init();
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(efwi::smem_u32(&bar)) : "memory");
-    if (!efwi::mbar_wait_bounded(&bar, 0u, budget)) atomicOr(err, EFWI_FLAG_TIMEOUT);
+    if (!efwi::mbar_wait_bounded(&bar, 0u, budget)) atomicOr(err, EFWI_FLAG_SELFTEST);
 }
 
 }  // namespace

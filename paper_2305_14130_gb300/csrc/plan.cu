@@ -170,13 +170,139 @@ void prof_end(efwi_plan *p, cudaStream_t st, int slot) {
 
 }  // namespace efwi
 
+// Host-side precompute of an acquisition on a plan's shot geometry: source
+// injection weights (eq. 2), receiver interpolation weights (eq. 3), the
+// deterministic gather of the adjoint source and the wavelet increments.
+struct AcqHost {
+    std::vector<ShotDev> shots;            // geometry of the plan + the source fields of this acquisition
+    std::vector<int> trace_shot;
+    std::vector<int> h_off;                // [ntr][16]
+    std::vector<float> h_w;
+    std::vector<int> g_shot, g_field, g_off, g_ptr, g_tr;
+    std::vector<float> g_w;
+    std::vector<int> gather_ptr;           // [ns + 1]
+    std::vector<float> h_dw, h_wv;
+    bool has_force = false;
+};
+
+static int build_acq(const efwi_plan_desc &dd, const std::vector<ShotDev> &geom, AcqHost &h, std::string &err) {
+    const efwi_plan_desc *d = &dd;
+    const int ns = d->ns, nt = d->nt;
+    h.shots = geom;
+    const double cellA = d->dx * d->dz;
+    for (int s = 0; s < ns; ++s) {
+        ShotDev &sh = h.shots[s];
+        sh.mxx = (float)d->mt[3 * s]; sh.mzz = (float)d->mt[3 * s + 1]; sh.mxz = (float)d->mt[3 * s + 2];
+        Corner cn[4], cx[4];
+        if (!bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.0, 0.0, cn) ||
+            !bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.5, 0.5, cx)) {
+            err = "source " + std::to_string(s) + " outside its window";
+            return EFWI_ERR_ARG;
+        }
+        for (int q = 0; q < 4; ++q) {
+            sh.inj_n[q] = local_off(sh, cn[q].i, cn[q].j); sh.inj_nw[q] = (float)(cn[q].w / cellA);
+            sh.inj_x[q] = local_off(sh, cx[q].i, cx[q].j); sh.inj_xw[q] = (float)(cx[q].w / cellA);
+        }
+        // vector force (eq. 2, second case) on the staggered v grids; it replaces the
+        // moment tensor (whose injection then adds zeros)
+        Corner fxc[4], fzc[4];
+        bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.5, 0.0, fxc);
+        bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.0, 0.5, fzc);
+        for (int q = 0; q < 4; ++q) {
+            sh.inj_vx[q] = local_off(sh, fxc[q].i, fxc[q].j); sh.inj_vxw[q] = (float)fxc[q].w;
+            sh.inj_vz[q] = local_off(sh, fzc[q].i, fzc[q].j); sh.inj_vzw[q] = (float)fzc[q].w;
+        }
+        sh.fx = sh.fz = 0.f;
+        if (d->force) {
+            sh.fx = (float)d->force[2 * s];
+            sh.fz = (float)d->force[2 * s + 1];
+            sh.mxx = sh.mzz = sh.mxz = 0.f;
+        }
+    }
+    h.has_force = d->force != nullptr;
+
+    // DAS gauges: 4 components x 4 corners per trace
+    const int ntr = d->ntr;
+    h.h_off.assign((size_t)std::max(ntr, 1) * 16, 0);
+    h.h_w.assign((size_t)std::max(ntr, 1) * 16, 0.f);
+    h.trace_shot.assign(ntr, 0);
+    // gather: (shot, field, off) -> list of (trace, weight)
+    std::map<std::tuple<int, int, int>, std::vector<std::pair<int, float>>> gmap;
+    for (int s = 0; s < ns; ++s) {
+        const ShotDev &sh = h.shots[s];
+        for (int c = d->tr_ptr[s]; c < d->tr_ptr[s + 1]; ++c) {
+            h.trace_shot[c] = s;
+            const double cx = d->ch_xz[2 * c], cz = d->ch_xz[2 * c + 1];
+            const double tx = d->ch_t[2 * c], tz = d->ch_t[2 * c + 1];
+            // DAS: gauge ends p+- = c +- (L/2) t with weights +-t/L; particle-velocity
+            // receiver: the point c with weight t (the second "end" carries zero weight)
+            const bool point = d->das_mode == EFWI_DAS_VELOCITY;
+            const double hl = point ? 0.0 : 0.5 * d->gauge;
+            const double scale = point ? 1.0 : 1.0 / d->gauge;
+            const double ends[2][2] = {{cx + hl * tx, cz + hl * tz}, {cx - hl * tx, cz - hl * tz}};
+            for (int k = 0; k < 4; ++k) {
+                const int e = k >> 1, field = k & 1;
+                const double sgn = e == 0 ? 1.0 : (point ? 0.0 : -1.0);
+                const double tcomp = field == 0 ? tx : tz;
+                Corner cr[4];
+                if (!bilinear(*d, sh, ends[e][0], ends[e][1], field == 0 ? 0.5 : 0.0, field == 0 ? 0.0 : 0.5, cr)) {
+                    err = "gauge end of trace " + std::to_string(c) + " outside the window of shot " +
+                          std::to_string(s);
+                    return EFWI_ERR_ARG;
+                }
+                for (int q = 0; q < 4; ++q) {
+                    const int o = local_off(sh, cr[q].i, cr[q].j);
+                    const float wq = (float)(cr[q].w * sgn * tcomp * scale);
+                    h.h_off[(size_t)c * 16 + k * 4 + q] = o;
+                    h.h_w[(size_t)c * 16 + k * 4 + q] = wq;
+                    if (wq != 0.f) gmap[std::make_tuple(s, field, o)].push_back({c, wq});
+                }
+            }
+        }
+    }
+    h.g_ptr.assign(1, 0);
+    for (auto &kv : gmap) {
+        h.g_shot.push_back(std::get<0>(kv.first));
+        h.g_field.push_back(std::get<1>(kv.first));
+        h.g_off.push_back(std::get<2>(kv.first));
+        for (auto &e : kv.second) { h.g_tr.push_back(e.first); h.g_w.push_back(e.second); }
+        h.g_ptr.push_back((int)h.g_tr.size());
+    }
+    h.gather_ptr.assign(ns + 1, 0);
+    for (int s : h.g_shot) h.gather_ptr[s + 1]++;
+    for (int s = 0; s < ns; ++s) h.gather_ptr[s + 1] += h.gather_ptr[s];
+
+    // wavelet increments (moment tensors) and samples / (dx dz) (forces)
+    h.h_dw.resize((size_t)ns * nt);
+    for (int s = 0; s < ns; ++s)
+        for (int n = 0; n < nt; ++n)
+            h.h_dw[(size_t)s * nt + n] =
+                (float)((double)d->wavelet[(size_t)s * (nt + 1) + n + 1] - (double)d->wavelet[(size_t)s * (nt + 1) + n]);
+    h.h_wv.assign(h.has_force ? (size_t)ns * nt : 0, 0.f);
+    for (size_t k = 0; k < h.h_wv.size(); ++k) {
+        const size_t s = k / nt, n = k % nt;
+        h.h_wv[k] = (float)((double)d->wavelet[s * (nt + 1) + n] / cellA);
+    }
+    return EFWI_OK;
+}
+
+// The host-side part of an acquisition becomes the plan's.
+static void commit_acq(efwi_plan *p, const AcqHost &h) {
+    p->shots = h.shots;
+    p->trace_shot = h.trace_shot;
+    p->has_force = h.has_force;
+    p->gather.n_tgt = (int)h.g_shot.size();
+    p->gather_ptr = h.gather_ptr;
+    p->gather_nnz = (int)h.g_tr.size();
+}
+
 static void free_plan(efwi_plan *p) {
     if (!p) return;
     void *ptrs[] = {p->shots_d, p->state[0], p->mat, p->adj[0], p->fwd_maps, p->adj_maps, p->dev_err, p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
                     p->prof, p->dw, p->wv, p->ref, p->tr_shot, p->tr_off, p->tr_w, p->tr_acc, p->tr_coef,
                     p->gather.tgt_shot, p->gather.tgt_field, p->gather.tgt_off, p->gather.ptr, p->gather.tr,
                     p->gather.w, p->tiles.tiles, p->adj_tiles.tiles, p->resid, p->dbuf, p->partial, p->seg, p->ck.fields, p->ck.psi,
-                    p->ck.scale};
+                    p->ck.scale, p->segh, p->segmax, p->zoi_b, p->zoi_bp, p->zoi_sink};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj, &p->g_ph})
@@ -210,7 +336,14 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (d->ckpt_store < EFWI_STORE_FP32 || d->ckpt_store > EFWI_STORE_BF16)
         return fail(nullptr, EFWI_ERR_ARG, "unknown ckpt_store");
     if (d->exec != EFWI_EXEC_PLAIN && d->exec != EFWI_EXEC_BATCHED) return fail(nullptr, EFWI_ERR_ARG, "unknown exec");
-    if (d->ckpt_interval < 0) return fail(nullptr, EFWI_ERR_ARG, "ckpt_interval must be >= 0");
+    if (d->ckpt_interval < EFWI_CKPT_AUTO)
+        return fail(nullptr, EFWI_ERR_ARG, "ckpt_interval must be >= 0 or EFWI_CKPT_AUTO");
+    if (d->snap_store < EFWI_STORE_FP32 || d->snap_store > EFWI_STORE_BF16)
+        return fail(nullptr, EFWI_ERR_ARG, "unknown snap_store");
+    if (d->snap_store != EFWI_STORE_FP32 && d->exec != EFWI_EXEC_BATCHED)
+        return fail(nullptr, EFWI_ERR_ARG, "FP16/BF16 snapshots need EXEC_BATCHED (EXEC_PLAIN keeps FP32)");
+    if (d->snap_store != EFWI_STORE_FP32 && d->overlap == EFWI_OVERLAP_ON)
+        return fail(nullptr, EFWI_ERR_ARG, "the overlapped recompute schedule keeps FP32 snapshots");
     if (d->tr_ptr[0] != 0 || d->tr_ptr[d->ns] != d->ntr) return fail(nullptr, EFWI_ERR_ARG, "tr_ptr must run 0..ntr");
     for (int s = 0; s < d->ns; ++s)
         if (d->tr_ptr[s + 1] < d->tr_ptr[s]) return fail(nullptr, EFWI_ERR_ARG, "tr_ptr must be non-decreasing");
@@ -292,103 +425,23 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     p->H = 2 * psx + 2 * psz;
     p->prof_x_total = profx;
 
-    // --- source injection weights --------------------------------------------
-    const double cellA = d->dx * d->dz;
-    for (int s = 0; s < ns; ++s) {
-        ShotDev &sh = p->shots[s];
-        Corner cn[4], cx[4];
-        if (!bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.0, 0.0, cn) ||
-            !bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.5, 0.5, cx)) {
+    // --- sources, receivers, adjoint gather, wavelet increments -------------------
+    AcqHost acq;
+    {
+        std::string err;
+        if (build_acq(*d, p->shots, acq, err) != EFWI_OK) {
             free_plan(p);
-            return fail(nullptr, EFWI_ERR_ARG, "source " + std::to_string(s) + " outside its window");
+            return fail(nullptr, EFWI_ERR_ARG, err);
         }
-        for (int q = 0; q < 4; ++q) {
-            sh.inj_n[q] = local_off(sh, cn[q].i, cn[q].j); sh.inj_nw[q] = (float)(cn[q].w / cellA);
-            sh.inj_x[q] = local_off(sh, cx[q].i, cx[q].j); sh.inj_xw[q] = (float)(cx[q].w / cellA);
-        }
-        // vector force (eq. 2, second case) on the staggered v grids; it replaces the
-        // moment tensor (whose injection then adds zeros)
-        Corner fxc[4], fzc[4];
-        bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.5, 0.0, fxc);
-        bilinear(*d, sh, d->src_xz[2 * s], d->src_xz[2 * s + 1], 0.0, 0.5, fzc);
-        for (int q = 0; q < 4; ++q) {
-            sh.inj_vx[q] = local_off(sh, fxc[q].i, fxc[q].j); sh.inj_vxw[q] = (float)fxc[q].w;
-            sh.inj_vz[q] = local_off(sh, fzc[q].i, fzc[q].j); sh.inj_vzw[q] = (float)fzc[q].w;
-        }
-        sh.fx = sh.fz = 0.f;
-        if (d->force) {
-            sh.fx = (float)d->force[2 * s];
-            sh.fz = (float)d->force[2 * s + 1];
-            sh.mxx = sh.mzz = sh.mxz = 0.f;
-        }
+        commit_acq(p, acq);
     }
-    p->has_force = d->force != nullptr;
-
-    // --- DAS gauges: 4 components x 4 corners per trace ------------------------
     const int ntr = d->ntr;
-    std::vector<int> h_off((size_t)std::max(ntr, 1) * 16, 0);
-    std::vector<float> h_w((size_t)std::max(ntr, 1) * 16, 0.f);
-    p->trace_shot.assign(ntr, 0);
-    // gather: (shot, field, off) -> list of (trace, weight)
-    std::map<std::tuple<int, int, int>, std::vector<std::pair<int, float>>> gmap;
-    for (int s = 0; s < ns; ++s) {
-        const ShotDev &sh = p->shots[s];
-        for (int c = d->tr_ptr[s]; c < d->tr_ptr[s + 1]; ++c) {
-            p->trace_shot[c] = s;
-            const double cx = d->ch_xz[2 * c], cz = d->ch_xz[2 * c + 1];
-            const double tx = d->ch_t[2 * c], tz = d->ch_t[2 * c + 1];
-            // DAS: gauge ends p+- = c +- (L/2) t with weights +-t/L; particle-velocity
-            // receiver: the point c with weight t (the second "end" carries zero weight)
-            const bool point = d->das_mode == EFWI_DAS_VELOCITY;
-            const double hl = point ? 0.0 : 0.5 * d->gauge;
-            const double scale = point ? 1.0 : 1.0 / d->gauge;
-            const double ends[2][2] = {{cx + hl * tx, cz + hl * tz}, {cx - hl * tx, cz - hl * tz}};
-            for (int k = 0; k < 4; ++k) {
-                const int e = k >> 1, field = k & 1;
-                const double sgn = e == 0 ? 1.0 : (point ? 0.0 : -1.0);
-                const double tcomp = field == 0 ? tx : tz;
-                Corner cr[4];
-                if (!bilinear(*d, sh, ends[e][0], ends[e][1], field == 0 ? 0.5 : 0.0, field == 0 ? 0.0 : 0.5, cr)) {
-                    free_plan(p);
-                    return fail(nullptr, EFWI_ERR_ARG,
-                                "gauge end of trace " + std::to_string(c) + " outside the window of shot " +
-                                    std::to_string(s));
-                }
-                for (int q = 0; q < 4; ++q) {
-                    const int o = local_off(sh, cr[q].i, cr[q].j);
-                    const float wq = (float)(cr[q].w * sgn * tcomp * scale);
-                    h_off[(size_t)c * 16 + k * 4 + q] = o;
-                    h_w[(size_t)c * 16 + k * 4 + q] = wq;
-                    if (wq != 0.f) gmap[std::make_tuple(s, field, o)].push_back({c, wq});
-                }
-            }
-        }
-    }
-    std::vector<int> g_shot, g_field, g_off, g_ptr{0}, g_tr;
-    std::vector<float> g_w;
-    for (auto &kv : gmap) {
-        g_shot.push_back(std::get<0>(kv.first));
-        g_field.push_back(std::get<1>(kv.first));
-        g_off.push_back(std::get<2>(kv.first));
-        for (auto &e : kv.second) { g_tr.push_back(e.first); g_w.push_back(e.second); }
-        g_ptr.push_back((int)g_tr.size());
-    }
-    p->gather.n_tgt = (int)g_shot.size();
-    p->gather_ptr.assign(ns + 1, 0);
-    for (int s : g_shot) p->gather_ptr[s + 1]++;
-    for (int s = 0; s < ns; ++s) p->gather_ptr[s + 1] += p->gather_ptr[s];
+    std::vector<int> &h_off = acq.h_off;
+    std::vector<float> &h_w = acq.h_w, &h_dw = acq.h_dw, &h_wv = acq.h_wv;
+    std::vector<int> &g_shot = acq.g_shot, &g_field = acq.g_field, &g_off = acq.g_off, &g_ptr = acq.g_ptr,
+                     &g_tr = acq.g_tr;
+    std::vector<float> &g_w = acq.g_w;
 
-    // --- wavelet increments and CPML profiles ----------------------------------
-    std::vector<float> h_dw((size_t)ns * nt);
-    for (int s = 0; s < ns; ++s)
-        for (int n = 0; n < nt; ++n)
-            h_dw[(size_t)s * nt + n] =
-                (float)((double)d->wavelet[(size_t)s * (nt + 1) + n + 1] - (double)d->wavelet[(size_t)s * (nt + 1) + n]);
-    std::vector<float> h_wv(p->has_force ? (size_t)ns * nt : 0);
-    for (size_t k = 0; k < h_wv.size(); ++k) {
-        const size_t s = k / nt, n = k % nt;
-        h_wv[k] = (float)((double)d->wavelet[s * (nt + 1) + n] / cellA);
-    }
     const int X = p->prof_x_total;
     std::vector<float> h_prof(4 * (size_t)X + 4 * (size_t)NZ);
     for (int s = 0; s < ns; ++s) {
@@ -401,17 +454,13 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     cpml_axis(NZ, P, d->dz, d->npml, d->pml_R, vmax, d->pml_f0, d->dt, false, zp, zp + NZ);
     cpml_axis(NZ, P, d->dz, d->npml, d->pml_R, vmax, d->pml_f0, d->dt, true, zp + 2 * NZ, zp + 3 * NZ);
 
-    // --- checkpoint schedule ---------------------------------------------------
-    int K = d->ckpt_interval;
-    if (K == 0) K = (int)std::ceil(std::sqrt((double)nt));
-    K = std::min(K, nt);
-    p->K = K;
-    p->ck.store = d->ckpt_store;
-    p->ck.n = (nt + K - 1) / K;
-
     // --- device allocation -------------------------------------------------------
+    // (the snapshot slots and the checkpoints come last: their number depends on the
+    // checkpoint schedule, which EFWI_CKPT_AUTO chooses from the memory left)
     Alloc A{p};
     const long long F = p->fsz_total;
+    p->snap_store = d->snap_store;
+    p->ck.store = d->ckpt_store;
     A(&p->shots_d, (size_t)ns, "shots");
     const bool batched = d->exec == EFWI_EXEC_BATCHED;
     // the batched path's two state buffers are one allocation (one tensor map covers both)
@@ -446,10 +495,41 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     A(&p->resid, (size_t)std::max(ntr, 1) * nt, "residual");
     A(&p->dbuf, (size_t)std::max(ntr, 1) * nt, "data buffer");
     A(&p->partial, (size_t)kPartials + 8, "reduction scratch");
+
+    // --- checkpoint schedule ---------------------------------------------------
+    const size_t snap_el = p->snap_store == EFWI_STORE_FP32 ? 4 : 2;
+    const size_t ck_el = p->ck.store == EFWI_STORE_FP32 ? 4 : 2;
+    // device bytes of K snapshot slots (with their maxima) and of ceil(nt / K) checkpoints
+    auto sched_bytes = [&](int k) {
+        const size_t nck = (size_t)((nt + k - 1) / k);
+        return (size_t)k * 2 * F * snap_el + (size_t)k * 2 * ns * kMaxPad * 4 +
+               nck * (5 * F * ck_el + 2 * p->H * 4 + 5 * ns * 4);
+    };
+    int K = d->ckpt_interval;
+    const int Ksqrt = std::min(nt, (int)std::ceil(std::sqrt((double)nt)));
+    if (K == EFWI_CKPT_AUTO) {
+        size_t fr = 0, tot = 0;
+        if (A.ok && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+            const size_t keep = tot / 20 + (2ull << 30);
+            K = fr > keep && sched_bytes(nt) <= fr - keep ? nt : Ksqrt;
+        } else {
+            cudaGetLastError();
+            K = Ksqrt;
+        }
+    }
+    if (K == 0) K = Ksqrt;
+    K = std::min(K, nt);
+    p->K = K;
+    p->ck.n = (nt + K - 1) / K;
     // the second half of the segment buffer exists only if the autotuner keeps the
     // overlapped recompute/adjoint schedule (or the caller forces it)
     p->seg_double = false;
-    A(&p->seg, (size_t)K * 2 * F, "segment buffer");
+    if (p->snap_store == EFWI_STORE_FP32) {
+        A(&p->seg, (size_t)K * 2 * F, "segment buffer");
+    } else {
+        A((__half **)&p->segh, (size_t)K * 2 * F, "FP16/BF16 snapshots");
+        A(&p->segmax, (size_t)K * 2 * ns * kMaxPad, "snapshot maxima");
+    }
     const size_t nck_el = (size_t)p->ck.n * 5 * F;
     if (p->ck.store == EFWI_STORE_FP32) A((float **)&p->ck.fields, nck_el, "checkpoints");
     else {
@@ -555,6 +635,7 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->layout = p->stencil >= EFWI_STENCIL_TMA ? p->tma_vec : 0;
     info->staged_stores = p->stencil >= EFWI_STENCIL_TMA ? p->tma_store : 0;
     info->adj_persistent = p->adj_stencil == EFWI_STENCIL_LOADS && p->adj_grid > 0;
+    info->snap_store = p->snap_store;
     return EFWI_OK;
 }
 
@@ -566,8 +647,15 @@ extern "C" int efwi_sync_status(efwi_plan *p, efwi_stream_t stream) {
     cudaMemcpy(&flag, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (flag) {
         cudaMemset(p->dev_err, 0, sizeof(int));
-        if (flag & EFWI_FLAG_TIMEOUT)
-            return fail(p, EFWI_ERR_TIMEOUT, "a kernel gave up a bounded wait; results of that call are invalid");
+        if (flag & EFWI_FLAG_TIMEOUT) {
+            // a copy may have stalled in hardware: the workspace and its pipelines are no
+            // longer trusted, so every later call on this plan fails until it is recreated
+            p->broken = true;
+            return fail(p, EFWI_ERR_TIMEOUT, "a kernel gave up a bounded wait; results of that call are invalid "
+                                             "and the plan must be destroyed and created again");
+        }
+        if (flag & EFWI_FLAG_SELFTEST)
+            return fail(p, EFWI_ERR_TIMEOUT, "the timeout self-test's bounded wait expired (as intended)");
         return fail(p, EFWI_ERR_NAN, "the model holds a non-finite value or a non-positive density; results of "
                                      "that call are invalid");
     }
@@ -618,12 +706,51 @@ extern "C" int efwi_collapse(int ns, int nx, int nz, const float *x, const float
     return EFWI_OK;
 }
 
+// b, bp, sink all given, or all NULL for the weights the plan holds (ns components)
+int efwi::resolve_zoi(efwi_plan *p, int ns, const float *&b, const float *&bp, const uint8_t *&sink) {
+    if (b && bp && sink) return EFWI_OK;
+    if (b || bp || sink)
+        return fail(p, EFWI_ERR_ARG, "b, bp and sink must all be given, or all be NULL for the plan's weights");
+    if (!p->zoi_b)
+        return fail(p, EFWI_ERR_ARG, "no zone-of-influence weights: pass b, bp, sink or call efwi_plan_set_zoi");
+    if (ns != p->d.ns)
+        return fail(p, EFWI_ERR_ARG, "the plan's zone-of-influence weights hold its own ns components");
+    b = p->zoi_b;
+    bp = p->zoi_bp;
+    sink = p->zoi_sink;
+    return EFWI_OK;
+}
+
+extern "C" int efwi_plan_set_zoi(efwi_plan *p, const efwi_zoi_desc *z, efwi_stream_t stream) {
+    if (!p) return fail(nullptr, EFWI_ERR_ARG, "plan is NULL");
+    const size_t n = (size_t)p->d.ns * p->d.nz * p->d.nx;
+    if (!p->zoi_b) {
+        Alloc A{p};
+        A(&p->zoi_b, n, "zone-of-influence b");
+        A(&p->zoi_bp, n, "zone-of-influence b'");
+        A(&p->zoi_sink, n, "sinkhole flags");
+        if (!A.ok) {
+            for (void *q : {(void *)p->zoi_b, (void *)p->zoi_bp, (void *)p->zoi_sink})
+                if (q) cudaFree(q);
+            p->zoi_b = p->zoi_bp = nullptr;
+            p->zoi_sink = nullptr;
+            return fail(p, EFWI_ERR_OOM, A.what);
+        }
+    }
+    std::string err;
+    const int rc = launch_zoi(p->d.ns, p->d.nx, p->d.nz, p->d.dx, p->d.dz, z, p->zoi_b, p->zoi_bp, p->zoi_sink,
+                              (cudaStream_t)stream, err);
+    if (rc != EFWI_OK) return fail(p, rc, err);
+    return EFWI_OK;
+}
+
 extern "C" int efwi_regularization_grad_n(efwi_plan *p, int ns, const float *m, const float *b, const float *bp,
                                           const uint8_t *sink, double eta, double *phi_reg, float *g,
                                           efwi_stream_t stream) {
     if (!p) return fail(nullptr, EFWI_ERR_ARG, "plan is NULL");
     if (ns < 1) return fail(p, EFWI_ERR_ARG, "ns must be >= 1");
-    if (!m || !b || !bp || !sink || !phi_reg || !g) return fail(p, EFWI_ERR_ARG, "NULL device pointer");
+    if (int rc = resolve_zoi(p, ns, b, bp, sink)) return rc;
+    if (!m || !phi_reg || !g) return fail(p, EFWI_ERR_ARG, "NULL device pointer");
     if (!std::isfinite(eta)) return fail(p, EFWI_ERR_ARG, "eta must be finite");
     nvtxRangePushA("efwi consistency term");
     launch_reg(p, m, b, bp, sink, eta, phi_reg, g, 0, (cudaStream_t)stream, ns);
@@ -637,12 +764,102 @@ extern "C" int efwi_regularization_grad(efwi_plan *p, const float *m, const floa
                                         const uint8_t *sink, double eta, double *phi_reg, float *g,
                                         efwi_stream_t stream) {
     if (!p) return fail(nullptr, EFWI_ERR_ARG, "plan is NULL");
-    if (!m || !b || !bp || !sink || !phi_reg || !g) return fail(p, EFWI_ERR_ARG, "NULL device pointer");
+    if (int rc = resolve_zoi(p, p->d.ns, b, bp, sink)) return rc;
+    if (!m || !phi_reg || !g) return fail(p, EFWI_ERR_ARG, "NULL device pointer");
     if (!std::isfinite(eta)) return fail(p, EFWI_ERR_ARG, "eta must be finite");
     nvtxRangePushA("efwi consistency term");
     launch_reg(p, m, b, bp, sink, eta, phi_reg, g, 0, (cudaStream_t)stream);
     nvtxRangePop();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(p, EFWI_ERR_CUDA, cudaGetErrorString(e));
+    return EFWI_OK;
+}
+
+extern "C" int efwi_plan_rebind(efwi_plan *p, const efwi_plan_desc *d, efwi_stream_t stream) {
+    if (!p || !d) return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: plan and desc must be non-NULL");
+    if (p->broken)
+        return fail(p, EFWI_ERR_TIMEOUT, "a bounded device wait of an earlier call expired; destroy this plan");
+    const efwi_plan_desc &o = p->d;
+    const bool gauge_used = d->ntr > 0 && d->das_mode != EFWI_DAS_VELOCITY;
+    if (d->nx != o.nx || d->nz != o.nz || d->dx != o.dx || d->dz != o.dz || d->nt != o.nt || d->dt != o.dt ||
+        d->npml != o.npml || d->ns != o.ns || d->ntr != o.ntr || d->das_mode != o.das_mode ||
+        (gauge_used && d->gauge != o.gauge))
+        return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: grid, time axis, npml, ns, ntr, das_mode and gauge "
+                                     "must equal the plan's");
+    if (!d->src_xz || !d->mt || !d->wavelet || !d->tr_ptr || (d->ntr > 0 && (!d->ch_xz || !d->ch_t)))
+        return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: a required host array is NULL");
+    for (int s = 0; s < d->ns; ++s) {
+        const ShotDev &sh = p->shots[s];
+        const int x0 = d->win ? d->win[2 * s] : 0, w = d->win ? d->win[2 * s + 1] : d->nx;
+        if (d->tr_ptr[s] != sh.tr0 || d->tr_ptr[s + 1] - d->tr_ptr[s] != sh.ntr || x0 != sh.x0 || w != sh.w)
+            return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: the windows and traces per shot must equal the "
+                                         "plan's (shot " + std::to_string(s) + ")");
+    }
+    if ((d->force != nullptr) != p->has_force)
+        return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: force sources must stay force sources (and moment "
+                                     "tensors moment tensors)");
+    if (d->force)
+        for (int k = 0; k < 2 * d->ns; ++k)
+            if (!std::isfinite(d->force[k])) return fail(p, EFWI_ERR_ARG, "force components must be finite");
+    AcqHost h;
+    std::string err;
+    if (build_acq(*d, p->shots, h, err) != EFWI_OK) return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: " + err);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool same_shape = (int)h.g_shot.size() == p->gather.n_tgt && h.gather_ptr == p->gather_ptr &&
+                            (int)h.g_tr.size() == p->gather_nnz;
+    if (!same_shape) {
+        // the captured time loops hold the gather's launch shape and arrays: drop them
+        cudaStreamSynchronize(st);
+        cudaDeviceSynchronize();
+        for (GraphCache *g : {&p->g_fwd, &p->g_fwd_ck, &p->g_adj, &p->g_ph})
+            if (g->exec) { cudaGraphExecDestroy(g->exec); g->exec = nullptr; }
+        GatherCSR &G = p->gather;
+        p->bytes -= (size_t)p->gather.n_tgt * 4 * 3 + (size_t)(p->gather.n_tgt + 1) * 4 + (size_t)p->gather_nnz * 8;
+        for (void *q : {(void *)G.tgt_shot, (void *)G.tgt_field, (void *)G.tgt_off, (void *)G.ptr, (void *)G.tr,
+                        (void *)G.w})
+            if (q) cudaFree(q);
+        G.tgt_shot = G.tgt_field = G.tgt_off = G.ptr = G.tr = nullptr;
+        G.w = nullptr;
+        Alloc A{p};
+        if (!h.g_shot.empty()) {
+            A(&G.tgt_shot, h.g_shot.size(), "gather");
+            A(&G.tgt_field, h.g_field.size(), "gather");
+            A(&G.tgt_off, h.g_off.size(), "gather");
+            A(&G.ptr, h.g_ptr.size(), "gather");
+            A(&G.tr, h.g_tr.size(), "gather");
+            A(&G.w, h.g_w.size(), "gather");
+        }
+        if (!A.ok) {
+            p->broken = true;
+            return fail(p, EFWI_ERR_OOM, "efwi_plan_rebind: " + A.what + "; the plan must be destroyed");
+        }
+    }
+    commit_acq(p, h);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (bytes && dst) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    up(p->shots_d, p->shots.data(), sizeof(ShotDev) * p->shots.size());
+    up(p->dw, h.h_dw.data(), 4 * h.h_dw.size());
+    if (p->has_force) up(p->wv, h.h_wv.data(), 4 * h.h_wv.size());
+    if (d->ntr > 0) {
+        up(p->tr_off, h.h_off.data(), 4 * h.h_off.size());
+        up(p->tr_w, h.h_w.data(), 4 * h.h_w.size());
+    }
+    if (p->gather.n_tgt > 0) {
+        up(p->gather.tgt_shot, h.g_shot.data(), 4 * h.g_shot.size());
+        up(p->gather.tgt_field, h.g_field.data(), 4 * h.g_field.size());
+        up(p->gather.tgt_off, h.g_off.data(), 4 * h.g_off.size());
+        up(p->gather.ptr, h.g_ptr.data(), 4 * h.g_ptr.size());
+        up(p->gather.tr, h.g_tr.data(), 4 * h.g_tr.size());
+        up(p->gather.w, h.g_w.data(), 4 * h.g_w.size());
+    }
+    int rc = refresh_tiles(p, p->tiles, st);
+    if (!rc) rc = refresh_tiles(p, p->adj_tiles, st);
+    if (rc) {
+        p->broken = true;
+        return fail(p, rc, "efwi_plan_rebind: tile list mismatch; the plan must be destroyed");
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(p, EFWI_ERR_CUDA, std::string("efwi_plan_rebind: ") + cudaGetErrorString(e));
     return EFWI_OK;
 }

@@ -24,6 +24,18 @@ struct GatherCSR {
     float *w = nullptr;          // [nnz] bilinear weight * (+-t_k) / L
 };
 
+// What a forward step hands to the adjoint besides the state: the FP32 copy of
+// its v^{n+1/2} (fx, fz: segment-buffer slots) or, with a reduced-precision
+// snapshot store, the snapshot work of SnapW; and what an adjoint step reads.
+struct SnapOut {
+    float *fx = nullptr, *fz = nullptr;
+    SnapW sw{};
+};
+struct SnapIn {
+    const float *fx = nullptr, *fz = nullptr;
+    SnapR sr{};
+};
+
 // An instantiated CUDA graph of a time loop and the kernels it launches.
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
@@ -91,13 +103,19 @@ struct efwi_plan {
     float *tr_coef = nullptr;              // [ntr] adjoint-source coefficient of the current step
     efwi::GatherCSR gather;
     std::vector<int> gather_ptr;           // [ns+1] per-shot range of gather targets
+    int gather_nnz = 0;                    // (trace, weight) entries of the gather
     efwi::TileList tiles;                  // forward fused-step work items
     efwi::TileList adj_tiles;              // adjoint fused-step work items
     float *resid = nullptr;                // [ntr][nt]
     float *dbuf = nullptr;                 // [ntr][nt]
     double *partial = nullptr;             // reduction scratch
-    float *seg = nullptr;                  // segment buffer: (1 or 2) x K x 2 x fsz_total
+    float *seg = nullptr;                  // segment buffer: (1 or 2) x K x 2 x fsz_total (FP32 snapshots)
+    int snap_store = EFWI_STORE_FP32;      // precision of the stored forward velocities
+    void *segh = nullptr;                  // FP16/BF16 snapshots: K x 2 x fsz_total elements of 2 bytes
+    float *segmax = nullptr;               // their maxima: K x [2][ns][kMaxPad] floats
     efwi::CkptStore ck;
+    float *zoi_b = nullptr, *zoi_bp = nullptr;   // zone-of-influence weights held by the plan (efwi_plan_set_zoi)
+    uint8_t *zoi_sink = nullptr;
     int K = 0;                             // checkpoint interval
     int tile_x = 0, tile_z = 0;            // forward tile
     int stencil = EFWI_STENCIL_LOADS;      // staging of the forward step (after tuning)
@@ -111,6 +129,7 @@ struct efwi_plan {
     int tma_adj_grid = 0, tma_adj_stages = 1;
     int adj_grid = 0;                      // per-thread-load adjoint: persistent grid (0 = one CTA per tile)
     int *dev_err = nullptr;                // device flag: a bounded wait expired
+    bool broken = false;                   // a real bounded wait expired: the plan is not used again
     int adj_tile_x = 0, adj_tile_z = 0;    // adjoint tile
     size_t bytes = 0;
     long long launches = 0;
@@ -147,8 +166,10 @@ void launch_materials(efwi_plan *p, const float *vp, const float *vs, const floa
 void launch_inject(efwi_plan *p, Fields F, int n, int shot /* -1 = all */, cudaStream_t st);
 void launch_force(efwi_plan *p, Fields F, int n, int shot, float *segx, float *segz, cudaStream_t st);
 void launch_das_fwd(efwi_plan *p, Fields F, int n, float *d, int shot, cudaStream_t st);
-void launch_das_adj(efwi_plan *p, Fields A, const float *vf_x, const float *vf_z, float *Gbx, float *Gbz,
-                    int n, int shot, cudaStream_t st);
+void launch_das_adj(efwi_plan *p, Fields A, const SnapIn &si, float *Gbx, float *Gbz, int n, int shot,
+                    cudaStream_t st);
+// packs v of state buffer scur (the last step of a pass) into the snapshot slot sw.h with maxima sw.hmax
+void launch_snap_tail(efwi_plan *p, const SnapW &sw, cudaStream_t st);
 void launch_residual(efwi_plan *p, const float *d, const float *dobs, double *phi, cudaStream_t st);
 void launch_chain_rule(efwi_plan *p, const float *vp, const float *vs, const float *rho, const float *const *G,
                        const float *mask, float *gvp, float *gvs, float *grho, cudaStream_t st);
@@ -175,19 +196,29 @@ void launch_adj_vel_plain(efwi_plan *p, int shot, const float *vfx, const float 
 void launch_adj_stress_plain(efwi_plan *p, int shot, const float *vfx, const float *vfz, cudaStream_t st);
 
 // --- k_tma.cu ----------------------------------------------------------------
-bool tma_shape_ok(int tx, int tz, int nst, int vec, int st);
+bool tma_shape_ok(int tx, int tz, int nst, int vec, int st, int snap);
 int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int st);
-void launch_step_tma(efwi_plan *p, int n, float *segx, float *segz, cudaStream_t st);
+void launch_step_tma(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st);
 bool tma_adj_shape_ok(int tx, int tz, int nst);
 int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst);
 void launch_adj_tma(efwi_plan *p, const float *vfx, cudaStream_t st);
 
 // --- k_fused.cu --------------------------------------------------------------
-void launch_step_fused(efwi_plan *p, int n, float *vseg_x, float *vseg_z, cudaStream_t st);
-void launch_adj_fused(efwi_plan *p, int n, const float *vfx, const float *vfz, cudaStream_t st);
+void launch_step_fused(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st);
+void launch_adj_fused(efwi_plan *p, int n, const SnapIn &si, cudaStream_t st);
 int upload_tiles(efwi_plan *p, TileList &tl, int tx, int tz);
+int refresh_tiles(efwi_plan *p, TileList &tl, cudaStream_t st);
+
+// snapshot slots (engine.cu): slot >= 0 this step's slot, prev >= 0 the previous
+// step's slot whose reduced-precision copy the step writes (-1: none)
+SnapOut snap_out(efwi_plan *p, int slot, int prev);
+SnapIn snap_in(efwi_plan *p, int slot);
+float *snap_max(efwi_plan *p, int slot);
+void *snap_half(efwi_plan *p, int slot);
 
 // helpers (plan.cu)
+// b, bp, sink all given, or all NULL for the plan's own weights (EFWI_ERR_ARG otherwise)
+int resolve_zoi(efwi_plan *p, int ns, const float *&b, const float *&bp, const uint8_t *&sink);
 void set_thread_error(const std::string &msg);  // message for efwi_last_error(NULL)
 Fields state_fields(efwi_plan *p, int which);   // which: 0/1 buffer
 Fields adj_fields(efwi_plan *p, int which);

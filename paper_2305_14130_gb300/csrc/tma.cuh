@@ -72,6 +72,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// Failure path of a bounded wait that expired: the stages of the pipeline that still
+// have a copy in flight (count of them, the first being stage `b0` of the CTA's k-th
+// tile) are each waited for once more with a bounded wait, so that, as far as the
+// hardware lets a stalled copy finish, no copy lands in the shared memory of a CTA
+// that has exited.  Best effort: a copy that never completes is abandoned after the
+// budget.  Called by the thread that issues the copies; the caller issues no copy
+// after the first failed wait.
+__device__ __forceinline__ void mbar_drain_bounded(uint64_t *bar, uint32_t phase, int k, int nst, int count,
+                                                   long long budget = 1LL << 31) {
+    for (int j = 0; j < count; ++j) {
+        const int b = (k + j) % nst;
+        mbar_wait_bounded(&bar[b], (phase >> b) & 1u, budget);
+    }
+}
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"

@@ -1,11 +1,12 @@
 """Extended problems whose shots do not fit one plan: the data term and its
-gradient for every component, with the shots run in groups, one plan per
-group, created, used and destroyed in turn.
+gradient for every component, with the shots run in groups through one plan
+at a time.
 
 Each component (shot) of the extended model is independent through the
 forward, adjoint and imaging steps (eq. 6 applied to each m_s), so a group
 is an independent slice of the problem: the gradient rows of its shots are
-those a single plan holding every shot would produce.  This module only
+those a single plan holding every shot would produce.  Groups of the same shape
+share one plan, rebound to each group's sources and receivers.  This module only
 slices the acquisition and the device tensors and sums the groups' misfits;
 all arithmetic runs in the library's kernels.  The consistency term couples
 the groups through per-pixel sums over all components; evaluate it with any
@@ -40,23 +41,54 @@ def group_acquisition(acq, shots):
     return dataclasses.replace(acq, **sub), idx
 
 
-def grouped_gradient(acq, vp, vs, rho, d_obs, group_size, out=None, times=None, **plan_kwargs):
+def _shape(acq, shots):
+    """What a plan's workspace depends on besides the grid: shots, traces per shot, windows."""
+    win = getattr(acq, "win", None)
+    ptr = np.asarray(acq.tr_ptr)
+    return (len(shots), tuple(int(ptr[s + 1] - ptr[s]) for s in shots),
+            None if win is None else tuple(tuple(int(v) for v in np.asarray(win)[s]) for s in shots),
+            getattr(acq, "force", None) is None)
+
+
+def grouped_gradient(acq, vp, vs, rho, d_obs, group_size, out=None, times=None, reuse=True, stats=None,
+                     **plan_kwargs):
     """phi_data (float) and the gradients (g_vp, g_vs, g_rho) [ns, nz, nx] of every
-    component, the shots taken group_size at a time (one plan per group).
+    component, the shots taken group_size at a time.
 
     vp, vs, rho: device [ns, nz, nx] float32; d_obs: device [ntr, nt].  plan_kwargs
-    go to every group's Plan (checkpoint store, stencil, ...).  When `times` is a
-    list, the seconds of each group's gradient call (after its plan exists) are
-    appended to it."""
+    go to the group plans (checkpoint store, stencil, ...).  With reuse, a group of
+    the same shape as the previous one rebinds the previous group's plan to its
+    sources and receivers (no new workspace, no new tuning); otherwise every group
+    creates its own plan.  When `times` is a list, the seconds of each group's
+    gradient call are appended to it; `stats` (a dict) receives the seconds spent
+    creating plans ("create_s") and rebinding them ("rebind_s")."""
+    import time
     ns = int(np.asarray(acq.src_xz).shape[0])
     if out is None:
         out = tuple(torch.empty_like(vp) for _ in range(3))
+    if stats is not None:
+        stats.setdefault("create_s", 0.0)
+        stats.setdefault("rebind_s", 0.0)
     phi = 0.0
-    for s0 in range(0, ns, group_size):
-        shots = list(range(s0, min(ns, s0 + group_size)))
-        gacq, idx = group_acquisition(acq, shots)
-        plan = Plan(gacq, **plan_kwargs)
-        try:
+    plan, shape = None, None
+    try:
+        for s0 in range(0, ns, group_size):
+            shots = list(range(s0, min(ns, s0 + group_size)))
+            gacq, idx = group_acquisition(acq, shots)
+            sh = _shape(acq, shots)
+            t0 = time.perf_counter()
+            if plan is not None and reuse and sh == shape:
+                plan.rebind(gacq)
+                key = "rebind_s"
+            else:
+                if plan is not None:
+                    plan.close()
+                plan = Plan(gacq, **plan_kwargs)
+                shape = sh
+                key = "create_s"
+            torch.cuda.synchronize()
+            if stats is not None:
+                stats[key] += time.perf_counter() - t0
             sl = slice(shots[0], shots[-1] + 1)
             tr = torch.as_tensor(idx, device=d_obs.device)
             dg = d_obs.index_select(0, tr) if len(idx) else d_obs[:0]
@@ -73,6 +105,7 @@ def grouped_gradient(acq, vp, vs, rho, d_obs, group_size, out=None, times=None, 
                 times.append(start.elapsed_time(end) / 1e3)
             phi += float(p.item())
             plan.sync_status()
-        finally:
+    finally:
+        if plan is not None:
             plan.close()
     return phi, out

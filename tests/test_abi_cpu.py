@@ -93,6 +93,10 @@ def _desc(p, **over):
     ({"ckpt_store": 9}, -1, "ckpt_store"),
     ({"npml": 0}, -1, "npml"),
     ({"tile_x": 8, "tile_z": 0}, -1, "tile"),
+    ({"ckpt_interval": -2}, -1, "ckpt_interval"),
+    ({"snap_store": 5}, -1, "snap_store"),
+    ({"snap_store": 1, "exec": 0}, -1, "EXEC_BATCHED"),
+    ({"snap_store": 2, "overlap": 2}, -1, "FP32 snapshots"),
 ])
 def test_plan_create_rejects_bad_descriptions(lib, over, code, msg):
     d, keep = _desc(W.tiny(), **over)
@@ -157,7 +161,7 @@ def test_enum_values_match_binding(tmp_path):
     names = list(_abi.STATUS.values())
     names += [f"EFWI_STORE_{k.upper()}" for k in _abi.STORE] + [f"EFWI_EXEC_{k.upper()}" for k in _abi.EXEC]
     names += [f"EFWI_STENCIL_{k.upper()}" for k in _abi.STENCIL] + [f"EFWI_OVERLAP_{k.upper()}" for k in _abi.OVERLAP]
-    names += ["EFWI_DAS_STRAIN", "EFWI_DAS_STRAIN_RATE", "EFWI_DAS_VELOCITY"]
+    names += ["EFWI_DAS_STRAIN", "EFWI_DAS_STRAIN_RATE", "EFWI_DAS_VELOCITY", "EFWI_CKPT_AUTO"]
     prog = tmp_path / "enums.c"
     prog.write_text("\n".join(['#include <stdio.h>', '#include "efwi.h"', 'int main(void) {']
                               + [f'printf("%d\\n", (int){n});' for n in names] + ['return 0; }']))
@@ -173,3 +177,4 @@ def test_enum_values_match_binding(tmp_path):
             assert got[f"EFWI_{prefix}_{k.upper()}"] == v, k
     assert (got["EFWI_DAS_STRAIN"], got["EFWI_DAS_STRAIN_RATE"], got["EFWI_DAS_VELOCITY"]) == \
         (W.STRAIN, W.STRAIN_RATE, W.VELOCITY) == (_abi.DAS_STRAIN, _abi.DAS_STRAIN_RATE, _abi.DAS_VELOCITY)
+    assert got["EFWI_CKPT_AUTO"] == _abi.CKPT_AUTO

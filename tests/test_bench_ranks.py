@@ -51,36 +51,48 @@ def test_aggregate_single_rank():
     assert ms == 50.0 and abs(s - 0.01) < 1e-15 and abs(value - 100.0) < 1e-9
 
 
-def test_roofline_entries_from_kernel_timings():
+def test_roofline_entries_from_kernel_timings(monkeypatch):
     """bench.roofline: achieved = algorithmic bytes x cells / mean launch time,
-    frac = achieved / measured peak, traffic only for captured variants, the
-    kernel with the larger share of the gradient first."""
+    frac = achieved / measured peak, traffic (and its fraction) only for captured
+    variants, the kernel with the larger share of the gradient first."""
     sys.path.insert(0, ROOT)
     import bench
     peak, kind = bench.peaks()
     info = {"padded_cells": 1_000_000, "ckpt_interval": 64, "stencil": 3, "adj_stencil": 1, "tile_x": 32,
-            "tile_z": 16, "adj_tile_x": 32, "adj_tile_z": 16, "layout": 3, "staged_stores": 0, "adj_persistent": 1}
+            "tile_z": 16, "adj_tile_x": 32, "adj_tile_z": 16, "layout": 3, "staged_stores": 0, "adj_persistent": 1,
+            "snap_store": 0}
+    monkeypatch.setattr(bench, "TRAFFIC_PER_CELL", {("step", 3, 32, 16, 3, 0, 0, 0): 55.0,
+                                                    ("adj", 1, 32, 16, 1, 0, 0): 95.0})
     prof = {"step": (10.0, 100), "adj": (20.0, 50)}          # ms summed, launches timed
     first, second = bench.roofline("batched", info, prof, nt=4000, ns=32)
     step = first if first["kernel"].startswith("forward") else second
     adj = second if step is first else first
     assert abs(step["avg_us"] - 100.0) < 1e-9 and abs(adj["avg_us"] - 400.0) < 1e-9
-    assert abs(step["achieved"] - 60.0 * 1e6 / 100e-6 / 1e9) < 1e-6
+    # sqrt(nt) checkpoints, FP32 velocities: half the forward launches keep v (60 and 68 B)
+    assert step["bytes_per_cell"] == 64.0 and adj["bytes_per_cell"] == 108.0
+    assert abs(step["achieved"] - 64.0 * 1e6 / 100e-6 / 1e9) < 1e-6
     assert abs(adj["achieved"] - 108.0 * 1e6 / 400e-6 / 1e9) < 1e-6
     assert abs(step["frac"] - step["achieved"] / peak) < 1e-12 and step["peak_kind"] == kind
-    assert step["traffic"] == bench.TRAFFIC_PER_CELL[("step", 3, 32, 16, 3, 0)] * 1e6
-    assert adj["traffic"] == bench.TRAFFIC_PER_CELL[("adj", 1, 32, 16, 1)] * 1e6
+    assert abs(step["frac_nominal"] - step["achieved"] / 7900.0) < 1e-12
+    assert step["traffic"] == 55.0 * 1e6 and adj["traffic"] == 95.0 * 1e6
+    assert abs(step["frac_traffic"] - 55.0 * 1e6 / 100e-6 / 1e9 / peak) < 1e-12
     # forward and recompute: 2 x 4000 x 100 us = 0.8 s against 4000 x 400 us = 1.6 s
     assert first is adj and abs(adj["time_share_est"] - 2 / 3) < 1e-12
     info2 = dict(info, layout=2)                             # a variant without a capture
     s2 = [r for r in bench.roofline("batched", info2, prof, nt=4000, ns=32) if r["kernel"].startswith("forward")][0]
-    assert s2["traffic"] is None
+    assert s2["traffic"] is None and s2["frac_traffic"] is None
+    # every step stored with FP16 snapshots: 60 + 4 B forward, 100 + 4 B adjoint
+    info3 = dict(info, ckpt_interval=4000, snap_store=1)
+    r3 = {r["kernel"].split(" ")[0]: r for r in bench.roofline("batched", info3, prof, nt=4000, ns=32)}
+    assert r3["forward_step"]["bytes_per_cell"] == 64.0 and r3["adjoint_step"]["bytes_per_cell"] == 104.0
+    assert r3["forward_step"]["traffic"] is None             # captured with other snapshots
 
 
 def test_gradient_roofline_bytes_and_fractions():
     """bench.gradient_roofline: 236 B per padded cell-step with sqrt(nt) checkpoints
     (forward, recompute with the velocity hand-off, adjoint), 176 B with every step
-    stored; the floor fraction always uses 176 B."""
+    stored, 168 B with FP16 snapshots of every step; the floor fraction always uses
+    176 B."""
     sys.path.insert(0, ROOT)
     import bench
     peak, _ = bench.peaks()
@@ -92,3 +104,6 @@ def test_gradient_roofline_bytes_and_fractions():
     assert abs(r["floor_frac"] - 176.0 * work / peak) < 1e-12
     full = bench.gradient_roofline(dict(info, ckpt_interval=4000), nt=4000, s_per_grad=2.0)
     assert full["bytes_per_cell_step"] == 176.0 and full["frac"] == full["floor_frac"]
+    half = bench.gradient_roofline(dict(info, ckpt_interval=4000, snap_store=1), nt=4000, s_per_grad=2.0)
+    assert half["bytes_per_cell_step"] == 168.0 and half["snapshots"] == "fp16"
+    assert bench.gradient_roofline(dict(info, snap_store=2), nt=4000, s_per_grad=2.0)["bytes_per_cell_step"] == 228.0
