@@ -664,7 +664,7 @@ def run_ours(args):
                            "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
                            "stencil": {1: "loads", 2: "tma", 3: "tma_pairs", 4: "tma_staged"}.get(info["stencil"], "?"), "stages": info["stages"], "layout": info["layout"],
                            "adj_stencil": {1: "loads", 2: "tma"}.get(info["adj_stencil"], "?"),
-                           "adj_stages": info["adj_stages"],
+                           "adj_stages": info["adj_stages"], "l2_prefetch": info["prefetch"],
                            "overlap_blocks_per_sm": [info["overlap_fwd_blocks"], info["overlap_adj_blocks"]],
                            "l2": "working set > L2 (wavefields, checkpoints, data >> 129 MB)",
                            "parallelism": f"replicas x{world} (independent extended problems)"},

@@ -208,6 +208,7 @@ typedef struct efwi_plan_info_t {
     int staged_stores;          /* TMA forward step writes its outputs by bulk tensor stores */
     int adj_persistent;         /* per-thread-load adjoint step runs on a persistent grid */
     int snap_store;             /* EFWI_STORE_* of the forward-velocity snapshots */
+    int prefetch;               /* L2 prefetch one tile ahead: bit 0 forward step, bit 1 adjoint step */
 } efwi_plan_info_t;
 
 /* Zone-of-influence description (eq. 10), host memory.  Per source s:
@@ -235,6 +236,7 @@ typedef struct efwi_zoi_desc {
  *   EFWI_TMA_VEC=v        only forward layout v (1 single cells, 2 cell pairs,
  *                         3 cell pairs with the halo ring as single cells)
  *   EFWI_ADJ_PERSIST=0|1  only the one-CTA-per-tile / persistent-grid adjoint
+ *   EFWI_PREFETCH=0|1     L2 prefetch one tile ahead off / on (else timed)
  *   EFWI_AUTOTUNE_LOG=1   print every timed variant on stderr
  *   EFWI_TEST_FAIL_ALLOC=k  make the k-th workspace allocation fail with
  *                         EFWI_ERR_OOM (tests of the clean-up path)        */

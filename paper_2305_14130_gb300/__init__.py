@@ -25,10 +25,11 @@ import torch
 from . import _abi
 from ._abi import EfwiError, STORE, EXEC, STENCIL, OVERLAP, CKPT_AUTO
 
-__all__ = ["Plan", "zoi_weights", "collapse", "EfwiError", "load_library", "DataMisfit", "Consistency", "extended_objective"]
+__all__ = ["Plan", "zoi_weights", "collapse", "EfwiError", "load_library", "DataMisfit", "Consistency",
+           "ExtendedFWI", "extended_objective"]
 
 
-from .autograd import DataMisfit, Consistency, extended_objective  # noqa: E402
+from .autograd import DataMisfit, Consistency, ExtendedFWI, extended_objective  # noqa: E402
 
 
 def load_library():

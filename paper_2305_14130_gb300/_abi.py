@@ -40,7 +40,8 @@ class PlanInfo(C.Structure):
                 ("overlap_fwd_blocks", C.c_int), ("overlap_adj_blocks", C.c_int),
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong), ("layout", C.c_int),
-                ("staged_stores", C.c_int), ("adj_persistent", C.c_int), ("snap_store", C.c_int)]
+                ("staged_stores", C.c_int), ("adj_persistent", C.c_int), ("snap_store", C.c_int),
+                ("prefetch", C.c_int)]
 
 
 class ZoiDesc(C.Structure):

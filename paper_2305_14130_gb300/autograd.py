@@ -10,7 +10,13 @@ gradients by the incoming grad_output.
 ``Consistency.apply(m, plan, b, bp, sink, eta)`` returns phi_reg of one
 parameter field and backpropagates eta^2 W^T P^T P W m (eqs. 8, 11, 12).
 
-``extended_objective(...)`` adds both terms for (Vp, Vs, rho).
+``ExtendedFWI.apply(vp, vs, rho, plan, d_obs, eta, b, bp, sink, mask)`` is the
+whole extended objective of eq. 8 in one Function: the data term of every
+component plus the consistency term of each parameter field with its eta
+(b, bp, sink None: the zone-of-influence weights the plan holds).
+
+``extended_objective(...)`` adds both terms for (Vp, Vs, rho) from the two
+Functions above.
 """
 from __future__ import annotations
 
@@ -52,3 +58,22 @@ def extended_objective(plan, vp, vs, rho, d_obs, eta, b, bp, sink, mask=None):
     for m, e in zip((vp, vs, rho), eta):
         phi = phi + Consistency.apply(m, plan, b, bp, sink, float(e))
     return phi
+
+
+class ExtendedFWI(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, vp, vs, rho, plan, d_obs, eta, b=None, bp=None, sink=None, mask=None):
+        ms = [t.detach().contiguous() for t in (vp, vs, rho)]
+        phi, gvp, gvs, grho = plan.gradient(*ms, d_obs, mask=mask)
+        grads = (gvp, gvs, grho)
+        for m, gm, e in zip(ms, grads, eta):
+            phi_r, _ = plan.regularization_grad(m, b, bp, sink, float(e), g=gm)
+            phi = phi + phi_r
+        ctx.save_for_backward(*grads)
+        return phi
+
+    @staticmethod
+    def backward(ctx, grad_phi):
+        s = grad_phi.to(torch.float32)
+        gvp, gvs, grho = ctx.saved_tensors
+        return s * gvp, s * gvs, s * grho, None, None, None, None, None, None, None

@@ -224,13 +224,16 @@ void adjoint_loop(efwi_plan *p, cudaStream_t st) {
         cudaStreamWaitEvent(st, join);
         return;
     }
-    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-        const int n0 = sgi * K, n1 = std::min(n0 + K, nt);
+    // segments of K steps (recompute, then adjoint); with every step stored, chunks of
+    // ceil(sqrt(nt)) steps, so that the imaging sums are Kahan-folded as often
+    const int KF = full ? std::min(nt, (int)std::ceil(std::sqrt((double)nt))) : K;
+    for (int sgi = (nt + KF - 1) / KF - 1; sgi >= 0; --sgi) {
+        const int n0 = sgi * KF, n1 = std::min(n0 + KF, nt);
         if (!full) {
             launch_ckpt_load(p, sgi, st);
             forward_keep(p, n0, n1, 0, nullptr, st);
         }
-        for (int n = n1 - 1; n >= n0; --n) adjoint_step(p, n, snap_in(p, n - n0), st);
+        for (int n = n1 - 1; n >= n0; --n) adjoint_step(p, n, snap_in(p, full ? n : n - n0), st);
         if (p->Gtot) launch_kahan_fold(p, st);
     }
 }

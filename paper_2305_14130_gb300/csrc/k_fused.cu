@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "plan.hpp"
+#include "tma.cuh"
 
 namespace efwi {
 namespace {
@@ -223,6 +224,10 @@ struct AdjArgsF {
     SnapR sr;                   // its reduced-precision snapshot (sr.h non-null)
     float *Glam, *Gmu, *Gmuxz, *Gbx, *Gbz;
     float dt, rdx, rdz;
+    // L2 prefetch of the CTA's next tile (persistent grid): tensor maps, on/off, the
+    // read adjoint buffer's first field, the forward velocities' first field (-1: none)
+    const AdjMaps *maps;
+    int pf, acur5, sgf;
 };
 
 // Read-only load that asks L2 to fetch the 256-byte block around the address: the
@@ -341,6 +346,14 @@ __global__ void __launch_bounds__(kThreads, TX * TZ <= 512 ? 4 : 2) k_adj_fused(
                 }
                 f1s[q] = g1; f2s[q] = g2; f3s[q] = g3;
                 if (edge) f4s[q] = g4;                     // f^4 == f^3 away from the CPML
+            }
+            if (a.pf && tid == 0 && t + (int)gridDim.x < a.ntiles) {
+                // the next tile's inputs into L2 while this one computes
+                const AdjMaps *mp = a.maps + tl_next.x;
+                tma_prefetch_3d(&mp->ad, tl_next.y, tl_next.z - 2, a.acur5);
+                tma_prefetch_3d(&mp->m5, tl_next.y, tl_next.z - 2, 0);
+                if (a.sgf >= 0) tma_prefetch_3d(&mp->sg, tl_next.y, tl_next.z - 2, a.sgf);
+                tma_prefetch_3d(&mp->gi, tl_next.y + 4, tl_next.z + 2, 0);
             }
             __syncthreads();
 
@@ -644,6 +657,10 @@ AdjArgsF adj_args_f(efwi_plan *p, const SnapIn &si) {
     a.n5 = sn; a.n8 = sn + X; a.n6 = sn + 2 * X; a.n7 = sn + 2 * X + Z;
     a.vfx = vfx; a.vfz = vfz;
     a.sr = si.sr;
+    a.maps = p->adj_maps;
+    a.pf = p->adj_pf && p->adj_maps && p->adj_grid > 0;
+    a.acur5 = 5 * p->acur;
+    a.sgf = (vfx && p->seg) ? (int)(2 * ((vfx - p->seg) / (2 * p->fsz_total))) : -1;
     a.Glam = G_field(p, 0); a.Gmu = G_field(p, 1); a.Gmuxz = G_field(p, 2);
     a.Gbx = G_field(p, 3); a.Gbz = G_field(p, 4);
     a.dt = (float)p->d.dt;
@@ -704,12 +721,11 @@ struct Variant {
     int kind, tx, tz, nst, vec = 1, st = 0;
 };
 
-float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps = 3) {
     // the snapshot traffic of a real step: FP32 copy of v into slot 0, or the
     // reduced-precision pack of slot 0 and the maxima of slot 1
     const SnapOut so = snap_out(p, p->K > 1 ? 1 : 0, 0);
     const SnapIn si = snap_in(p, 0);
-    const int reps = 3;
     float t = 0;
     for (int w = 0; w < 2; ++w) {              // warm-up, then timed
         cudaEventRecord(e0, st);
@@ -846,6 +862,43 @@ int efwi_autotune(efwi_plan *p) {
     // splits of the SMs' blocks, against running them one after the other
     rc = select_fwd(p, bf);
     if (!rc) rc = select_adj(p, ba);
+    // L2 prefetch one tile beyond what the chosen forward (TMA) and adjoint (persistent
+    // per-thread loads) steps load: kept when it saves more than 1 %.  EFWI_PREFETCH=0|1
+    // forces it off or on (reproducible profiles and tests of one variant).
+    {
+        const char *fe = getenv("EFWI_PREFETCH");
+        const int force_pf = fe ? atoi(fe) : -1;
+        p->tma_pf = p->adj_pf = 0;
+        const bool fwd_ok = !rc && p->stencil >= EFWI_STENCIL_TMA;
+        const bool adj_ok = !rc && p->adj_stencil == EFWI_STENCIL_LOADS && p->adj_grid > 0 &&
+                            tma_encode_adj_maps(p, p->adj_tile_x, p->adj_tile_z) == EFWI_OK;
+        if (force_pf >= 0) {
+            p->tma_pf = fwd_ok && force_pf;
+            p->adj_pf = adj_ok && force_pf;
+        } else if (fwd_ok || adj_ok) {
+            cudaStream_t st;
+            cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            const char *lg = getenv("EFWI_AUTOTUNE_LOG");
+            const bool log = lg && lg[0] == '1';
+            for (int adj = 0; adj < 2; ++adj) {
+                if (!(adj ? adj_ok : fwd_ok)) continue;
+                int &flag = adj ? p->adj_pf : p->tma_pf;
+                flag = 0;
+                const float t0 = time_steps(p, adj, st, e0, e1, 12);
+                flag = 1;
+                const float t1 = time_steps(p, adj, st, e0, e1, 12);
+                if (log) fprintf(stderr, "efwi autotune %s L2 prefetch: off %.1f us, on %.1f us\n", adj ? "adj" : "fwd",
+                                 t0 * 1e3f / 12, t1 * 1e3f / 12);
+                flag = t1 < 0.99f * t0;
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaStreamDestroy(st);
+        }
+    }
     p->ov_fwd = p->ov_adj = 0;
     const long long segbytes = sizeof(float) * (long long)p->K * 2 * p->fsz_total;
     float *seg2 = nullptr;

@@ -46,6 +46,7 @@ struct TmaFwdArgs {
     int ofield;                 // state-map field of the written buffer's vx (output staging)
     int segf;                   // segment-map field of this step's vx, or -1 (output staging)
     SnapW sw;                   // reduced-precision snapshot work (sw.h / sw.amax null: none)
+    int pf;                     // 1: L2 prefetch of the tile one beyond the shared-memory pipeline
 };
 
 // Shared-memory stage of one tile.  Fields are staged on the tile + 4-cell halo in x
@@ -84,6 +85,18 @@ __device__ __forceinline__ void issue_fwd(const TmaFwdArgs &a, int t, float *buf
     tma_load_3d(buf + L::OSXZ, &m->s3, bar, tl.y, tl.z - 2, f + 4); // sigma_xz: rows 0..
     tma_load_3d(buf + L::OBX, &m->mb, bar, tl.y, tl.z, 3);          // b_x, b_z: rows 2..
     tma_load_3d(buf + L::OLAM, &m->mc, bar, tl.y + 4, tl.z + 2, 0); // lambda, mu, mu_xz: tile
+}
+
+// The boxes issue_fwd copies, brought into L2 only (a tile beyond the pipeline).
+__device__ __forceinline__ void prefetch_fwd(const TmaFwdArgs &a, int4 tl) {
+    const FwdMaps *m = a.maps + tl.x;
+    const int f = 5 * a.scur;
+    tma_prefetch_3d(&m->s2, tl.y, tl.z, f);
+    tma_prefetch_3d(&m->s1, tl.y, tl.z, f + 2);
+    tma_prefetch_3d(&m->s3, tl.y, tl.z - 1, f + 3);
+    tma_prefetch_3d(&m->s3, tl.y, tl.z - 2, f + 4);
+    tma_prefetch_3d(&m->mb, tl.y, tl.z, 3);
+    tma_prefetch_3d(&m->mc, tl.y + 4, tl.z + 2, 0);
 }
 
 // Shared-memory output staging (ST = 1, cell pairs only): the new stresses of the
@@ -147,6 +160,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
         const float upx = SNAP && a.sw.h ? snap_scale_up(a.sw.hmax, 0, tl.x, a.sw.ns) : 1.f;
         const float upz = SNAP && a.sw.h ? snap_scale_up(a.sw.hmax, 1, tl.x, a.sw.ns) : 1.f;
         if (t + gridDim.x < a.ntiles) tl_next = __ldg(a.tiles + t + gridDim.x);
+        const int tp = t + NST * gridDim.x;                      // L2 prefetch target (pf)
+        const int4 tl_pf = a.pf && tid == 0 && tp < a.ntiles ? __ldg(a.tiles + tp) : make_int4(0, 0, 0, 0);
         if (tid == 0) ok_s = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
         __syncthreads();
         if (!ok_s) {
@@ -174,6 +189,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                 bulk_wait_read0();
             }
             if (tn < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, tn, smb + bn * L::BUF, &bar[bn]);
+            if (a.pf && tp < a.ntiles) prefetch_fwd(a, tl_pf);
         }
         tl_prev = tl;
 
@@ -733,6 +749,7 @@ void launch_step_tma(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st) {
     a.ofield = 5 * (1 - p->scur);
     a.segf = segx ? (int)((segx - p->seg) / p->fsz_total) : -1;
     a.sw = so.sw;
+    a.pf = p->tma_pf;
     const int grid = std::min(p->grid_fwd_override > 0 ? p->grid_fwd_override : p->tma_grid, a.ntiles);
     const int tx = p->tiles.tx, tz = p->tiles.tz, nst = p->tma_stages, vec = p->tma_vec, stg = p->tma_store;
     const int sk = p->snap_store;
@@ -1044,14 +1061,16 @@ bool tma_adj_shape_ok(int tx, int tz, int nst) {
     return false;
 }
 
-int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst) {
+// Encode the adjoint maps of every shot for tile shape (tx, tz) into p->adj_maps.
+int tma_encode_adj_maps(efwi_plan *p, int tx, int tz) {
     std::vector<AdjMaps> h(p->d.ns);
     const long long F = p->fsz_total;
     for (int s = 0; s < p->d.ns; ++s) {
         const ShotDev &sh = p->shots[s];
         int rc = encode_map(&h[s].ad, p->adj[0], sh, F, 10, tx + 8, tz + 8, 5);
         if (!rc) rc = encode_map(&h[s].m5, p->mat, sh, F, 5, tx + 8, tz + 8, 5);
-        if (!rc) rc = encode_map(&h[s].sg, p->seg, sh, F, (p->seg_double ? 4 : 2) * p->K, tx + 8, tz + 8, 2);
+        if (!rc && p->seg) rc = encode_map(&h[s].sg, p->seg, sh, F, (p->seg_double ? 4 : 2) * p->K, tx + 8, tz + 8, 2);
+        if (!rc) rc = encode_map(&h[s].gi, p->G, sh, F, 5, tx, tz, 5);
         if (rc) {
             p->err = "cuTensorMapEncodeTiled failed for the adjoint maps";
             return rc;
@@ -1060,6 +1079,12 @@ int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst) {
     if (!p->adj_maps && cudaMalloc((void **)&p->adj_maps, sizeof(AdjMaps) * p->d.ns) != cudaSuccess)
         return EFWI_ERR_OOM;
     cudaMemcpy(p->adj_maps, h.data(), sizeof(AdjMaps) * p->d.ns, cudaMemcpyHostToDevice);
+    return EFWI_OK;
+}
+
+int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst) {
+    const int rc = tma_encode_adj_maps(p, tx, tz);
+    if (rc) return rc;
     int nb = 0;
 #define EFWI_OCC_X(a_, b_, c_) if (tx == a_ && tz == b_ && nst == c_) nb = adj_occupancy<a_, b_, c_>();
     EFWI_TMA_ADJ_VARIANTS(EFWI_OCC_X)

@@ -636,6 +636,7 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->staged_stores = p->stencil >= EFWI_STENCIL_TMA ? p->tma_store : 0;
     info->adj_persistent = p->adj_stencil == EFWI_STENCIL_LOADS && p->adj_grid > 0;
     info->snap_store = p->snap_store;
+    info->prefetch = (p->stencil >= EFWI_STENCIL_TMA && p->tma_pf ? 1 : 0) | (p->adj_pf ? 2 : 0);
     return EFWI_OK;
 }
 

@@ -124,6 +124,8 @@ struct efwi_plan {
     int tma_stages = 2;                    // shared-memory pipeline depth of the TMA forward step
     int tma_vec = 1;                       // cells per thread and shared-memory access (1 or 2)
     int tma_store = 0;                     // forward outputs staged in shared memory, bulk-stored
+    int tma_pf = 0;                        // forward step: L2 prefetch of the tile beyond the pipeline
+    int adj_pf = 0;                        // per-thread-load adjoint: L2 prefetch of the CTA's next tile
     int adj_stencil = EFWI_STENCIL_LOADS;  // staging of the adjoint step (after tuning)
     efwi::AdjMaps *adj_maps = nullptr;
     int tma_adj_grid = 0, tma_adj_stages = 1;
@@ -201,6 +203,7 @@ int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int st);
 void launch_step_tma(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st);
 bool tma_adj_shape_ok(int tx, int tz, int nst);
 int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst);
+int tma_encode_adj_maps(efwi_plan *p, int tx, int tz);
 void launch_adj_tma(efwi_plan *p, const float *vfx, cudaStream_t st);
 
 // --- k_fused.cu --------------------------------------------------------------

@@ -21,9 +21,10 @@ struct __align__(64) FwdMaps {
 
 // Tensor maps of one shot for the adjoint step: adjoint state (both buffers,
 // 10 fields) and the 5 materials on the halo box, the forward velocities of
-// the segment buffer (2 fields per stored step) on the halo box.
+// the segment buffer (2 fields per stored step) on the halo box; gi: the 5
+// imaging sums on the tile (L2 prefetch of the per-thread-load adjoint).
 struct __align__(64) AdjMaps {
-    CUtensorMap ad, m5, sg;
+    CUtensorMap ad, m5, sg, gi;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -85,6 +86,13 @@ __device__ __forceinline__ void mbar_drain_bounded(uint64_t *bar, uint32_t phase
         const int b = (k + j) % nst;
         mbar_wait_bounded(&bar[b], (phase >> b) & 1u, budget);
     }
+}
+
+// Bring a box of the tensor into L2 (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {

@@ -143,3 +143,26 @@ def test_single_source_and_no_traces(efwi):
     assert d.shape == (0, q.acq.nt)
     assert phi.item() == 0.0 and not gvp.any() and not gvs.any() and not grho.any()
     plan.close()
+
+
+def test_extended_fwi_function_matches_the_two_terms(efwi):
+    """ExtendedFWI.apply (eq. 8 in one Function, with the plan's zone-of-influence
+    weights) gives the objective and gradients of DataMisfit + Consistency."""
+    from paper_2305_14130_gb300.autograd import extended_objective
+    p = rounded(W.tiny(nx=40, nz=30, ns=3, nt=60, npml=6))
+    d_obs = dev(observed(p))
+    acq = p.acq
+    eta = (2e-4, 3e-4, 5e-4)
+    plan = efwi.Plan(acq, exec="batched")
+    plan.set_zoi(p.zoi)
+    b, bp, sink = efwi.zoi_weights(acq.ns, acq.nx, acq.nz, acq.dx, acq.dz, p.zoi)
+    a = [dev(m).requires_grad_() for m in (p.vp, p.vs, p.rho)]
+    phi_a = efwi.ExtendedFWI.apply(*a, plan, d_obs, eta)
+    phi_a.backward()
+    c = [dev(m).requires_grad_() for m in (p.vp, p.vs, p.rho)]
+    phi_c = extended_objective(plan, *c, d_obs, eta, b, bp, sink)
+    phi_c.backward()
+    assert phi_a.item() == pytest.approx(phi_c.item(), rel=1e-12)
+    for x, y in zip(a, c):
+        assert rel_l2(x.grad.cpu().numpy(), y.grad.cpu().numpy()) <= 1e-6
+    plan.close()

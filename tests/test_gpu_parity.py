@@ -15,10 +15,14 @@ from oracle import extension as X
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
-# Reduced-precision storage (checkpoints or forward-velocity snapshots) rounds every
-# stored element with relative error <= u (u = 2^-11 FP16, 2^-8 BF16); the gradients'
-# rel-L2 error then measures 0.16-0.39 u in every case here.  Stated bound: u / 2.
-RED_BOUND = {"fp16": 2.0 ** -12, "bf16": 2.0 ** -9}
+# Reduced-precision storage rounds every stored element with relative error <= u
+# (u = 2^-11 FP16, 2^-8 BF16).  Checkpoints perturb the recomputed wavefields, and the
+# gradients' rel-L2 error measures 0.16-0.39 u: stated bound u / 2.  Snapshots feed
+# the imaging's strain rates directly, whose finite differences cancel part of the
+# stored magnitude: 0.2-0.55 u measured, stated bound u.
+UNIT = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+CKPT_BOUND = {k: v / 2 for k, v in UNIT.items()}
+SNAP_BOUND = dict(UNIT)
 
 
 @pytest.fixture(scope="module")
@@ -136,7 +140,7 @@ def test_reduced_precision_checkpoints(efwi, store):
     (BF16) (power-of-two scaling, round to nearest even); the gradient error this
     causes is measured here and bounded by half the format's unit roundoff.
     """
-    bound = RED_BOUND[store]
+    bound = CKPT_BOUND[store]
     p = rounded(W.tiny(nx=40, nz=30, ns=2, nt=90, npml=6))
     d_obs = observed(p)
     args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
@@ -182,11 +186,12 @@ def test_uneven_windows_subset_against_oracle(efwi, uneven_subset, store, snap):
     snapshots, on the 256x128 subset of the uneven-window configuration (6 shots
     on windows of 55-138 cells, one launch per step): every output against the
     FP64 oracle.  All-FP32 storage meets the parity tolerance; with FP16 / BF16
-    storage the errors are printed and bounded by half the unit roundoff of the
-    coarsest format used (every stored element errs by <= 2^-11 |x| / 2^-8 |x|).
-    FP16 snapshots are kept for every step (no recompute)."""
+    storage the errors are printed and bounded by CKPT_BOUND / SNAP_BOUND of the
+    formats used (every stored element errs by <= 2^-11 |x| / 2^-8 |x|).
+    Reduced-precision snapshots are kept for every step (no recompute)."""
     p, d_obs, (phi_o, gvp_o, gvs_o, grho_o), d_o = uneven_subset
-    bound = max([TOL] + [RED_BOUND[x] for x in (store, snap) if x != "fp32"])
+    bound = max([TOL] + ([CKPT_BOUND[store]] if store != "fp32" else [])
+                + ([SNAP_BOUND[snap]] if snap != "fp32" else []))
     plan = efwi.Plan(p.acq, exec="batched", ckpt_store=store, snap_store=snap,
                      ckpt_interval=p.acq.nt if snap != "fp32" else 0)
     phi, gvp, gvs, grho, d = plan.gradient(dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs), return_data=True)
@@ -508,3 +513,23 @@ def test_plan_held_zoi_weights(efwi):
     torch.cuda.synchronize()
     assert e1[0].item() == e2[0].item() and e1[1].item() == e2[1].item()
     plan.close()
+
+
+def test_l2_prefetch_does_not_change_results(efwi, monkeypatch):
+    """The L2 prefetch of the tile beyond the forward pipeline and of the adjoint's
+    next tile only moves data earlier: identical data, misfit and gradients."""
+    p = rounded(W.tiny(nx=70, nz=41, ns=3, nt=40, npml=5, win=[[0, 45], [13, 57], [30, 40]]))
+    d_obs = observed(p)
+    args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
+    monkeypatch.setenv("EFWI_ADJ_PERSIST", "1")
+    outs = []
+    for pf in ("0", "1"):
+        monkeypatch.setenv("EFWI_PREFETCH", pf)
+        plan = efwi.Plan(p.acq, exec="batched", tile=(32, 16), stencil="tma_pairs", adj_tile=(32, 16),
+                         adj_stencil="loads")
+        assert plan.info()["prefetch"] == (3 if pf == "1" else 0)
+        outs.append([t.clone() for t in plan.gradient(*args, return_data=True)])
+        plan.sync_status()
+        plan.close()
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
