@@ -19,6 +19,7 @@ extended problems, weak scaling); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -56,7 +57,7 @@ def parse():
     ap.add_argument("--adj-tile", default="0x0", help="adjoint tile (0x0 = autotune)")
     ap.add_argument("--overlap", default="auto", choices=["auto", "off", "on"])
     ap.add_argument("--no-reduced", action="store_true", help="skip the reduced-storage record")
-    ap.add_argument("--full-iteration-groups", type=int, default=2,
+    ap.add_argument("--full-iteration-groups", type=int, default=1,
                     help="shot groups of the 4000x1200 full-iteration record to time (16 = all; 0 = skip)")
     ap.add_argument("--ns", type=int, default=32)
     ap.add_argument("--nt", type=int, default=4000)
@@ -390,19 +391,23 @@ def reduced_storage(efwi, acq, m, d_obs, zoi, eta, ref, plain_s, args):
 
 
 def full_iteration(efwi, args):
-    """One iteration of the 4000x1200 extended problem (128 sources with seeded source
-    errors, 1500 channels, nt = 8000, FP16 checkpoints and snapshots): the data-term
-    gradient of all 128 components runs in groups of 8 shots through one plan, created
-    once and rebound to each group's sources and receivers; then the consistency-term
-    gradient of the 128 components (Vp, Vs, rho) and the l-BFGS update (two-loop
-    recursion with 5 stored pairs) over the whole 3 x 128 x 4.8 M vector.  The first
-    `groups` groups are timed (the first gradient call of a plan captures its graphs);
-    the gradient of all 16 is their sum when all are timed, else 16 x the steady
-    per-group time (every group runs the same kernels on the same shapes).  Observed
-    data are zeros: the cost does not depend on them."""
+    """The 4000x1200 extended problem (128 sources with seeded source errors, 1500
+    channels, nt = 8000, FP16 checkpoints and snapshots) in groups of 8 shots through
+    one plan.  Timed: (a) the plan, created once, and its rebinding from the host;
+    (b) the objective of the first `groups` groups and one l-BFGS iteration
+    (direction, strong-Wolfe line search, pair update) of the extended objective
+    (eq. 8) over the components of those groups, its line search run on the device
+    from a CUDA graph (efwi_lbfgs_iterate_device over a device-resident group set, no
+    host synchronisation inside the search; its first call captures and instantiates
+    the graph, timed apart); (c) the l-BFGS direction over the whole 3 x 128 x 4.8 M
+    vector with 5 stored pairs.  With all 16 groups the figures are the configuration's
+    own; otherwise the 128-source objective (data term of every component and the
+    consistency term) and iteration are 16 / groups times the timed ones (every group
+    runs the same kernels on the same shapes).
+    Observed data are zeros: the cost does not depend on them."""
     import torch
     import workloads as W
-    from paper_2305_14130_gb300.groups import group_acquisition
+    from paper_2305_14130_gb300.groups import GroupSet, group_acquisition
     from paper_2305_14130_gb300.optim import LBFGS
     t_gen = time.perf_counter()
     p = W.full_iteration_4000x1200()
@@ -412,58 +417,72 @@ def full_iteration(efwi, args):
     ns, nz, nx, nt = acq.ns, acq.nz, acq.nx, acq.nt
     gsize = 8
     ngroups = ns // gsize
-    groups = max(1, min(args.full_iteration_groups, ngroups))
-    dev = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")
-    base = [dev(v[0]) for v in (p.vp, p.vs, p.rho)]
-    x = torch.empty((3, ns, nz, nx), device="cuda")
-    for k in range(3):
-        x[k].copy_(base[k][None].expand(ns, nz, nx))
-    del base
-    gr = torch.empty_like(x)
+    G = max(1, min(args.full_iteration_groups, ngroups))
+    nsub = G * gsize
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    timings = []
+    acqs = [group_acquisition(acq, list(range(k * gsize, (k + 1) * gsize)))[0] for k in range(G)]
+    dev = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda")
     t0 = time.perf_counter()
-    plan = None
-    create_s, rebind_s = 0.0, []
+    plan = efwi.Plan(acqs[0], exec="batched", ckpt_store="fp16", snap_store="fp16")
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    info = plan.info()
+    out = {"workload": "full_iteration_4000x1200: 128 MT sources with seeded errors (amplitude, shift, rotation), "
+                       "1500 DAS ch (0.5 m, 10 m gauge), nt=8000, dt=0.05ms, dx=0.5m; groups of 8 shots",
+           "precision": "FP32 stepping, FP16 checkpoints, FP16 snapshots", "ckpt_interval": info["ckpt_interval"],
+           "groups_total": ngroups, "groups_timed": G, "plan_create_s": create_s,
+           "group_workspace_GB": info["workspace_bytes"] / 1e9,
+           "observed_data": "modelled with the error-free sources in the true model", "generate_s": t_gen}
     try:
-        for gi in range(groups):
-            shots = list(range(gi * gsize, (gi + 1) * gsize))
-            gacq, idx = group_acquisition(acq, shots)
+        x = torch.empty((3, nsub, nz, nx), device="cuda")
+        for k, v in enumerate((p.vp, p.vs, p.rho)):
+            x[k].copy_(dev(v[0])[None].expand(nsub, nz, nx))
+        # observed data: the timed groups' error-free sources in the true model (+4 % Vp / +6 % Vs anomaly)
+        d_obs = torch.empty((G, int(acqs[0].tr_ptr[-1]), nt), device="cuda")
+        true_wav = np.asarray(p.meta["true_wavelet"], np.float32).astype(np.float64)
+        for k in range(G):
+            sh = list(range(k * gsize, (k + 1) * gsize))
+            tacq = dataclasses.replace(acqs[k], mt=np.asarray(p.meta["true_mt"])[sh], wavelet=true_wav[sh])
+            plan.rebind(tacq)
+            tm = [dev(v)[None].expand(gsize, nz, nx).contiguous() for v in (p.true_vp, p.true_vs, p.true_rho)]
+            plan.forward(*tm, out=d_obs[k])
+            del tm
+        zsub = type(p.zoi)(**{f: (np.asarray(getattr(p.zoi, f))[:nsub] if np.ndim(getattr(p.zoi, f)) else
+                                  getattr(p.zoi, f)) for f in p.zoi.__dataclass_fields__})
+        b, bp, sink = efwi.zoi_weights(nsub, nx, nz, acq.dx, acq.dz, zsub)
+        gs = GroupSet(plan, acqs)
+        # (a) binding the plan to a group from the host (efwi_plan_rebind)
+        rebind = []
+        for k in range(min(G, 2)):
             t = time.perf_counter()
-            if plan is None:
-                plan = efwi.Plan(gacq, exec="batched", ckpt_store="fp16", snap_store="fp16")
-                torch.cuda.synchronize()
-                create_s = time.perf_counter() - t
-            else:
-                plan.rebind(gacq)
-                torch.cuda.synchronize()
-                rebind_s.append(time.perf_counter() - t)
-            d_obs = torch.zeros((len(idx), nt), device="cuda")
-            sl = slice(shots[0], shots[-1] + 1)
-            a, b_ = ev(), ev()
-            a.record()
-            plan.gradient(x[0, sl], x[1, sl], x[2, sl], d_obs, out=(gr[0, sl], gr[1, sl], gr[2, sl]))
-            b_.record()
-            b_.synchronize()
-            timings.append(a.elapsed_time(b_) / 1e3)
-            del d_obs
-        info = plan.info()
-        plan.sync_status()
-        # consistency term of all 128 components, evaluated with the group's plan
-        zb, zbp, zsink = efwi.zoi_weights(ns, nx, nz, acq.dx, acq.dz, p.zoi)
-        a, b_ = ev(), ev()
-        a.record()
-        for k in range(3):
-            plan.regularization_grad(x[k], zb, zbp, zsink, p.eta[k], g=gr[k])
+            plan.rebind(acqs[k])
+            torch.cuda.synchronize()
+            rebind.append(time.perf_counter() - t)
+        # (b) one l-BFGS iteration with the line search on the device
+        grad = torch.empty_like(x)
+        phi = torch.empty((), dtype=torch.float64, device="cuda")
+        a_, b_ = ev(), ev()
+        a_.record()
+        gs.objective(x, d_obs, p.eta, b, bp, sink, phi=phi, g=grad)
         b_.record()
         b_.synchronize()
-        reg_s = a.elapsed_time(b_) / 1e3
-        del zb, zbp, zsink
+        objective_s = a_.elapsed_time(b_) / 1e3
+        opt = LBFGS(x.numel(), m=5)
+        xf, gf = x.view(-1), grad.view(-1)
+        opt.set_step0(1e-3 * float(torch.linalg.vector_norm(xf)))   # first trial: 0.1 % of the model norm
+        dobj = gs.device_objective(d_obs, p.eta, b, bp, sink)
+        phi_start = float(phi.item())
+        t = time.perf_counter()
+        it = opt.iterate_device(xf, phi, gf, dobj)
+        torch.cuda.synchronize()
+        first_s = time.perf_counter() - t
+        opt.close()
+        gs.close()
+        del x, grad, d_obs, b, bp, sink
     finally:
-        if plan is not None:
-            plan.close()
-    # l-BFGS update over the full vector: 5 stored pairs, then the direction
-    n = x.numel()
+        plan.close()
+    # (c) the l-BFGS direction over the full vector
+    n = 3 * ns * nz * nx
     opt = LBFGS(n, m=5)
     gen = torch.Generator(device="cuda").manual_seed(3)
     sv = torch.empty(n, device="cuda")
@@ -472,39 +491,34 @@ def full_iteration(efwi, args):
         sv.normal_(generator=gen)
         yv.copy_(sv).mul_(2.0).add_(torch.randn(n, device="cuda", generator=gen), alpha=0.1)
         opt.push(sv, yv)
-    del sv, yv
-    gflat = gr.reshape(-1)
-    opt.direction(gflat)
+    gfull = sv
+    opt.direction(gfull)
     torch.cuda.synchronize()
-    a, b_ = ev(), ev()
-    a.record()
-    d = opt.direction(gflat)
+    a_, b_ = ev(), ev()
+    a_.record()
+    d = opt.direction(gfull)
     b_.record()
     b_.synchronize()
-    lbfgs_s = a.elapsed_time(b_) / 1e3
-    del d
+    lbfgs_s = a_.elapsed_time(b_) / 1e3
+    del d, sv, yv, gfull
     opt.close()
-    wall = time.perf_counter() - t0
-    steady = timings[1:] if len(timings) > 1 else timings
-    per_group = float(np.median(steady))
-    measured_all = groups == ngroups
-    rebind_mean = float(np.mean(rebind_s)) if rebind_s else None
-    grad_s = (sum(timings) + sum(rebind_s)) if measured_all else \
-        ngroups * per_group + (ngroups - 1) * (rebind_mean or 0.0)
-    iter_s = grad_s + reg_s + lbfgs_s
+    scale = ngroups / G
+    grad128 = objective_s * scale
     cells = ns * nx * nz * nt
-    return {"workload": "full_iteration_4000x1200: 128 MT sources with seeded errors (amplitude, shift, rotation), "
-                        "1500 DAS ch (0.5 m, 10 m gauge), nt=8000, dt=0.05ms, dx=0.5m; groups of 8 shots",
-            "precision": "FP32 stepping, FP16 checkpoints, FP16 snapshots", "ckpt_interval": info["ckpt_interval"],
-            "groups_total": ngroups, "groups_timed": groups, "group_gradient_s": timings,
-            "group_gradient_s_steady": per_group, "plan_create_s": create_s, "rebind_s": rebind_s,
-            "regularization_s": reg_s, "lbfgs_direction_s": lbfgs_s, "lbfgs_n": n,
-            "s_per_gradient_128": grad_s,
-            "s_per_gradient_128_kind": "measured (all groups)" if measured_all else
-            f"{ngroups} x the steady group time of {groups} timed groups + rebinds",
-            "s_per_iteration": iter_s + create_s, "s_per_iteration_excl_plan_create": iter_s,
-            "Gcell_updates_s": cells / grad_s / 1e9, "group_workspace_GB": info["workspace_bytes"] / 1e9,
-            "observed_data": "zeros (cost independent of the data)", "wall_s": wall, "generate_s": t_gen}
+    out.update({
+        "rebind_s": rebind, "objective_s_timed_groups": objective_s, "objective_s_per_group": objective_s / G,
+        "device_iteration": {"evals": it["evals"], "alpha": it["alpha"], "rate": it["rate"],
+                             "ls_failed": it["ls_failed"], "phi_before": phi_start, "phi_after": it["phi"],
+                             "s_timed_groups": first_s,
+                             "line_search": "on the device (conditional while-node of a CUDA graph); this first "
+                                            "call also captures and instantiates the graph"},
+        "lbfgs_direction_s_full_vector": lbfgs_s, "lbfgs_n": n,
+        "s_per_gradient_128": grad128,
+        "s_per_iteration_128": it["evals"] * grad128 + lbfgs_s,
+        "per_128_kind": "measured (all groups)" if G == ngroups else
+                        f"{ngroups} / {G} x the timed groups (same kernels and shapes in every group)",
+        "Gcell_updates_s": cells / grad128 / 1e9})
+    return out
 
 
 def run_ours(args):

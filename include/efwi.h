@@ -425,8 +425,14 @@ typedef struct efwi_lbfgs_info_t {
  * evaluations per line search.  Errors: EFWI_ERR_ARG, EFWI_ERR_OOM.         */
 int efwi_lbfgs_create(efwi_lbfgs **out, long long n, int m, double c1, double c2, int max_ls);
 int efwi_lbfgs_destroy(efwi_lbfgs *h);
-/* Forgets the stored pairs. */
+/* Forgets the stored pairs (and the graph of efwi_lbfgs_iterate_device). */
 int efwi_lbfgs_reset(efwi_lbfgs *h);
+/* Length of the first trial step of an iteration without stored pairs (the
+ * first iteration, or after a restart): the trial moves x by len along d
+ * (a = len / ||d||).  len = 0, the default, keeps a = min(1, 1 / ||d||).
+ * A model in physical units (m/s, kg/m^3) wants a length of the order of
+ * the change it should see, e.g. 1e-3 ||x||.  EFWI_ERR_ARG for len < 0.     */
+int efwi_lbfgs_set_step0(efwi_lbfgs *h, double len);
 /* Stores the pair (s, y) (device [n] each, copied) if s^T y > 0; *accepted
  * (may be NULL) tells whether it was.  Synchronises the stream.             */
 int efwi_lbfgs_push(efwi_lbfgs *h, const float *s, const float *y, int *accepted, efwi_stream_t stream);
@@ -457,6 +463,71 @@ int efwi_lbfgs_iterate(efwi_lbfgs *h, float *x, double *phi, float *g, efwi_obje
  * x and g (device [n]) hold the final model and its gradient.              */
 int efwi_lbfgs_run(efwi_lbfgs *h, float *x, float *g, efwi_objective_fn fn, void *ctx, int max_iter,
                    double min_rate, efwi_lbfgs_info_t *info, efwi_stream_t stream);
+
+/* One efwi_lbfgs_iterate whose strong-Wolfe line search runs on the device
+ * (no counterpart in the paper, which gives the optimizer, not where it runs):
+ * the bracketing and zoom of efwi_lbfgs_iterate -- the same steps, c1, c2,
+ * max_ls and quadratic interpolation, in FP64 -- are a one-thread state
+ * machine in device memory, and one CUDA graph repeats, in a conditional
+ * while-node, trial point x + a d, objective, phi' = g^T d and search step
+ * until a step is accepted or max_ls evaluations are spent: no host
+ * synchronisation inside the search.  The direction (with its reads of g^T d
+ * and, on a first step, d^T d) precedes the graph; one read of the search
+ * state and the pair update of efwi_lbfgs_iterate follow it.
+ *   phi  device double: the objective at x on entry, updated
+ *   fn(ctx, x, phi, g, stream) enqueues the objective at x (device [n]) into
+ *        phi (DEVICE double) and g (device [n]) on stream; it is called only
+ *        while the graph is captured (the first call for this fn, ctx, x, phi,
+ *        g; later calls replay the graph), so it must enqueue stream-
+ *        capturable work only (kernels, device copies and memsets: no
+ *        synchronisation, no allocation, no host copies) and return 0.
+ *        The graph holds the device arrays the objective used: after any of
+ *        them moves (a plan destroyed or re-allocated, e.g. by
+ *        efwi_plan_rebind to another gather shape or efwi_prof_enable),
+ *        efwi_lbfgs_reset drops it so that the next call captures it again.
+ * efwi_groups_objective_fn is such an objective (the extended problem in
+ * shot groups).                                                             */
+typedef int (*efwi_device_objective_fn)(void *ctx, const float *x, double *phi, float *g, efwi_stream_t stream);
+int efwi_lbfgs_iterate_device(efwi_lbfgs *h, float *x, double *phi, float *g, efwi_device_objective_fn fn,
+                              void *ctx, efwi_lbfgs_info_t *info, efwi_stream_t stream);
+
+/* ---- Shot groups held on the device ---------------------------------------
+ * An extended problem with ngroups x ns sources (ns = the plan's) runs as
+ * groups of the plan's shape (each component is independent through eqs.
+ * 1-6).  A group set keeps every group's source and receiver weights, adjoint
+ * gather, wavelet increments and tile flags in device memory, so that binding
+ * the plan to group k (efwi_groups_bind) is device-to-device copies, which a
+ * stream capture records (efwi_plan_rebind uploads from the host instead).
+ * Every group must have the plan's shape (efwi_plan_rebind's rules) and give
+ * the plan's adjoint-gather shape (the same receiver geometry); the plan must
+ * use EXEC_BATCHED.  No counterpart in the paper.                          */
+typedef struct efwi_groups efwi_groups;
+int efwi_groups_create(efwi_groups **out, efwi_plan *plan, const efwi_plan_desc *groups, int ngroups);
+int efwi_groups_destroy(efwi_groups *groups);
+int efwi_groups_bind(efwi_groups *groups, int k, efwi_stream_t stream);
+/* The extended objective of eq. 8 over all ngroups x ns components and its
+ * gradient, enqueued on stream (stream-capturable): for every group, bind
+ * and efwi_adjoint_gradient; then efwi_regularization_grad_n of Vp, Vs, rho
+ * with eta[3]; phi = the groups' misfits + the three consistency terms,
+ * summed in that order on the device.
+ *   x, grad   device [3][ngroups*ns][nz][nx] (Vp, Vs, rho of every component)
+ *   d_obs     device [ngroups][ntr][nt]
+ *   b, bp, sink  device [ngroups*ns][nz][nx] (or NULL when ngroups == 1 and
+ *             the plan holds its weights)
+ *   phi       device double                                                 */
+int efwi_groups_objective(efwi_groups *groups, const float *x, const float *d_obs, const double eta[3],
+                          const float *b, const float *bp, const uint8_t *sink, double *phi, float *grad,
+                          efwi_stream_t stream);
+/* efwi_groups_objective as an efwi_device_objective_fn: ctx points to an
+ * efwi_groups_objective_ctx (host memory that outlives the graphs using it). */
+typedef struct efwi_groups_objective_ctx {
+    efwi_groups *groups;
+    const float *d_obs;
+    double eta[3];
+    const float *b, *bp;
+    const uint8_t *sink;
+} efwi_groups_objective_ctx;
+int efwi_groups_objective_fn(void *ctx, const float *x, double *phi, float *g, efwi_stream_t stream);
 
 /* Extended objective of eq. 8: phi_data (as efwi_forward + misfit) and
  * phi_reg summed over the three parameter fields (Vp, Vs, rho) with their

@@ -49,6 +49,11 @@ class ZoiDesc(C.Structure):
                 ("n", C.c_double), ("nu", C.c_double)]
 
 
+class GroupsObjectiveCtx(C.Structure):
+    _fields_ = [("groups", C.c_void_p), ("d_obs", C.c_void_p), ("eta", C.c_double * 3), ("b", C.c_void_p),
+                ("bp", C.c_void_p), ("sink", C.c_void_p)]
+
+
 class LbfgsInfo(C.Structure):
     _fields_ = [("phi", C.c_double), ("phi_prev", C.c_double), ("rate", C.c_double), ("alpha", C.c_double),
                 ("evals", C.c_int), ("iters", C.c_int), ("pairs", C.c_int), ("ls_failed", C.c_int), ("stop", C.c_int)]
@@ -75,12 +80,19 @@ SIGNATURES = {
     "efwi_lbfgs_create": (C.c_int, [C.POINTER(VP), C.c_longlong, C.c_int, C.c_double, C.c_double, C.c_int]),
     "efwi_lbfgs_destroy": (C.c_int, [VP]),
     "efwi_lbfgs_reset": (C.c_int, [VP]),
+    "efwi_lbfgs_set_step0": (C.c_int, [VP, C.c_double]),
     "efwi_lbfgs_push": (C.c_int, [VP, VP, VP, C.POINTER(C.c_int), VP]),
     "efwi_lbfgs_direction": (C.c_int, [VP, VP, VP, VP]),
     "efwi_lbfgs_set_h0": (C.c_int, [VP, VP, VP]),
     "efwi_lbfgs_export": (C.c_int, [VP, C.POINTER(C.c_int), VP, VP, VP]),
     "efwi_lbfgs_iterate": (C.c_int, [VP, VP, C.POINTER(C.c_double), VP, OBJECTIVE_FN, VP, C.POINTER(LbfgsInfo), VP]),
     "efwi_lbfgs_run": (C.c_int, [VP, VP, VP, OBJECTIVE_FN, VP, C.c_int, C.c_double, C.POINTER(LbfgsInfo), VP]),
+    "efwi_lbfgs_iterate_device": (C.c_int, [VP, VP, VP, VP, VP, VP, C.POINTER(LbfgsInfo), VP]),
+    "efwi_groups_create": (C.c_int, [C.POINTER(VP), VP, C.POINTER(PlanDesc), C.c_int]),
+    "efwi_groups_destroy": (C.c_int, [VP]),
+    "efwi_groups_bind": (C.c_int, [VP, C.c_int, VP]),
+    "efwi_groups_objective": (C.c_int, [VP, VP, VP, C.POINTER(C.c_double), VP, VP, VP, VP, VP, VP]),
+    "efwi_groups_objective_fn": (C.c_int, [VP, VP, VP, VP, VP]),
     "efwi_regularization_grad_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, VP, VP, VP, VP, C.c_double, VP, VP,
                                                     VP]),
     "efwi_extended_objective": (C.c_int, [VP, VP, VP, VP, VP, PD, VP, VP, VP, VP, VP, VP]),

@@ -239,8 +239,20 @@ void adjoint_loop(efwi_plan *p, cudaStream_t st) {
 }
 
 // Capture body() once into gc (on the plan's capture stream), then replay it on st.
+// When the caller's stream is itself being captured (a device-resident optimizer
+// iteration that holds whole gradients in its graph), the loop is enqueued in place
+// and becomes part of the caller's graph; a graph launch cannot be captured.
 template <class Body>
 int replay(efwi_plan *p, GraphCache &gc, cudaStream_t st, Body body) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(p, "stream capture query");
+    }
+    if (cs == cudaStreamCaptureStatusActive) {
+        body(st);
+        return cuda_status(p, "time loop inside a stream capture");
+    }
     if (!gc.exec) {
         const long long l0 = p->launches;
         cudaGraph_t g = nullptr;

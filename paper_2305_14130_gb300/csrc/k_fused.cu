@@ -561,10 +561,10 @@ bool shape_ok(int tx, int tz) {
 // Work items (shot, i0, j0, flags).  flags bit 0: the tile holds a source
 // injection cell; bit 1 (bit 2): the tile or its 2-cell (4-cell) halo touches
 // a CPML strip or leaves the padded grid, so kernels take the checked path.
-std::vector<int4> make_tiles(efwi_plan *p, int tx, int tz) {
+std::vector<int4> make_tiles_of(const std::vector<ShotDev> &shots, int tx, int tz) {
     std::vector<int4> t;
-    for (int s = 0; s < p->d.ns; ++s) {
-        const ShotDev &sh = p->shots[s];
+    for (int s = 0; s < (int)shots.size(); ++s) {
+        const ShotDev &sh = shots[s];
         for (int j0 = 0; j0 < sh.NZ; j0 += tz)
             for (int i0 = 0; i0 < sh.NX; i0 += tx) {
                 int flags = 0;
@@ -590,7 +590,13 @@ std::vector<int4> make_tiles(efwi_plan *p, int tx, int tz) {
     return t;
 }
 
+std::vector<int4> make_tiles(efwi_plan *p, int tx, int tz) { return make_tiles_of(p->shots, tx, tz); }
+
 }  // namespace
+
+std::vector<int4> tiles_of(const std::vector<ShotDev> &shots, const TileList &tl) {
+    return tl.tiles ? make_tiles_of(shots, tl.tx, tl.tz) : std::vector<int4>();
+}
 
 int upload_tiles(efwi_plan *p, TileList &tl, int tx, int tz) {
     std::vector<int4> t = make_tiles(p, tx, tz);

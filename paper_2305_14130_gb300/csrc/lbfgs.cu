@@ -120,6 +120,14 @@ struct efwi_lbfgs {
     double *partial = nullptr;
     double c1 = 1e-4, c2 = 0.9;
     int max_ls = 20;
+    double step0 = 0;                 // first trial length without pairs (0: min(1, 1 / ||d||))
+    // device-resident line search (efwi_lbfgs_iterate_device): its state, the trial point's
+    // phi and phi', a capture stream and the graph of the last (objective, x, phi, g)
+    void *ls_state = nullptr;
+    double *ls_phit = nullptr;
+    cudaStream_t ls_cap = nullptr;
+    cudaGraphExec_t ls_exec = nullptr;
+    const void *ls_key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int slots() const { return m + 1; }
     // device scalar offsets: rho[m + 1], alpha[m + 1], then the ones below
     int o_rho() const { return 0; }
@@ -281,6 +289,95 @@ struct Search {
     }
 };
 
+// ---------------------------------------------------------------------------
+// The line search of Search::run / Search::zoom as a device state machine: the
+// same steps, tests and interpolation in the same FP64 arithmetic, one trial
+// point per call of k_ls_step, so that a CUDA graph can repeat
+// (trial point, objective, phi', step) in a conditional while-node with no host
+// synchronisation until the search ends.
+// ---------------------------------------------------------------------------
+struct LsTrial {
+    double a, phi, dphi;
+};
+
+struct LsState {
+    double phi0, dphi0, c1, c2;
+    double a;                    // the step of the next trial point
+    LsTrial prev, lo, hi, out;
+    int phase;                   // 0: bracketing (Alg. 3.5), 1: zoom (Alg. 3.6)
+    int i;                       // bracketing iteration, from 1
+    int evals, max_ls;
+    int done, ok;                // search over; a step satisfying the strong Wolfe conditions found
+};
+
+__device__ double ls_interp(const LsTrial &lo, const LsTrial &hi) {
+    const double w = hi.a - lo.a;
+    const double den = 2.0 * (hi.phi - lo.phi - lo.dphi * w);
+    double a = den > 0 ? lo.a - lo.dphi * w * w / den : lo.a + 0.5 * w;
+    const double lower = fmin(lo.a, hi.a) + 0.1 * fabs(w);
+    const double upper = fmax(lo.a, hi.a) - 0.1 * fabs(w);
+    if (!(a >= lower && a <= upper)) a = lo.a + 0.5 * w;
+    return a;
+}
+
+__global__ void k_ls_init(LsState *s, double phi0, double dphi0, double a0, double c1, double c2, int max_ls) {
+    LsState t{};
+    t.phi0 = phi0;
+    t.dphi0 = dphi0;
+    t.c1 = c1;
+    t.c2 = c2;
+    t.a = a0;
+    t.prev = LsTrial{0.0, t.phi0, t.dphi0};
+    t.phase = 0;
+    t.i = 1;
+    t.max_ls = max_ls;
+    *s = t;
+}
+
+// out = x + a d with the step a of the search state
+__global__ void k_trial_state(float *out, const float *x, const float *d, long long n, const LsState *s) {
+    const float alpha = (float)s->a;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = x[i] + alpha * d[i];
+}
+
+__global__ void k_ls_step(LsState *st, const double *phit, const double *dphit, cudaGraphConditionalHandle cond) {
+    LsState s = *st;
+    if (!s.done) {
+        s.evals += 1;
+        const LsTrial t{s.a, *phit, *dphit};
+        const bool armijo_fails = t.phi > s.phi0 + s.c1 * t.a * s.dphi0;
+        const bool curvature = fabs(t.dphi) <= -s.c2 * s.dphi0;
+        if (!isfinite(t.phi) || !isfinite(t.dphi)) {
+            s.done = 1;
+        } else if (s.phase == 0) {
+            if (armijo_fails || (s.i > 1 && t.phi >= s.prev.phi)) {
+                s.lo = s.prev; s.hi = t; s.phase = 1;
+            } else if (curvature) {
+                s.out = t; s.done = 1; s.ok = 1;
+            } else if (t.dphi >= 0) {
+                s.lo = t; s.hi = s.prev; s.phase = 1;
+            } else {
+                s.prev = t; s.a = 2.0 * s.a; s.i += 1;
+            }
+            if (!s.done && s.phase == 1) s.a = ls_interp(s.lo, s.hi);
+        } else {
+            if (armijo_fails || t.phi >= s.lo.phi) {
+                s.hi = t;
+            } else if (curvature) {
+                s.out = t; s.done = 1; s.ok = 1;
+            } else {
+                if (t.dphi * (s.hi.a - s.lo.a) >= 0) s.hi = s.lo;
+                s.lo = t;
+            }
+            if (!s.done) s.a = ls_interp(s.lo, s.hi);
+        }
+        if (!s.done && s.evals >= s.max_ls) s.done = 1;   // no step within max_ls evaluations
+    }
+    *st = s;
+    cudaGraphSetConditional(cond, s.done ? 0u : 1u);
+}
+
 }  // namespace
 
 using efwi::set_thread_error;
@@ -351,18 +448,37 @@ extern "C" int efwi_lbfgs_create(efwi_lbfgs **out, long long n, int m, double c1
     return EFWI_OK;
 }
 
+static void lb_drop_graph(efwi_lbfgs *h) {
+    if (h->ls_exec) cudaGraphExecDestroy(h->ls_exec);
+    h->ls_exec = nullptr;
+    for (auto &k : h->ls_key) k = nullptr;
+}
+
 extern "C" int efwi_lbfgs_destroy(efwi_lbfgs *h) {
     if (!h) return EFWI_OK;
+    cudaDeviceSynchronize();
+    lb_drop_graph(h);
+    if (h->ls_cap) cudaStreamDestroy(h->ls_cap);
     for (void *p : {(void *)h->S, (void *)h->Y, (void *)h->d, (void *)h->xt, (void *)h->gt, (void *)h->dev,
-                    (void *)h->partial, (void *)h->D})
+                    (void *)h->partial, (void *)h->D, h->ls_state, (void *)h->ls_phit})
         if (p) cudaFree(p);
     delete h;
+    return EFWI_OK;
+}
+
+extern "C" int efwi_lbfgs_set_step0(efwi_lbfgs *h, double len) {
+    if (!h || !(len >= 0) || !std::isfinite(len)) return lb_fail(EFWI_ERR_ARG, "handle NULL or len < 0");
+    h->step0 = len;
     return EFWI_OK;
 }
 
 extern "C" int efwi_lbfgs_reset(efwi_lbfgs *h) {
     if (!h) return lb_fail(EFWI_ERR_ARG, "handle is NULL");
     h->order.clear();
+    if (h->ls_exec) {                           // the device search's graph is captured again on next use
+        cudaDeviceSynchronize();
+        lb_drop_graph(h);
+    }
     return EFWI_OK;
 }
 
@@ -446,7 +562,7 @@ extern "C" int efwi_lbfgs_iterate(efwi_lbfgs *h, float *x, double *phi, float *g
         dot_dev(h, h->d, h->d, tmp, 1.0, nullptr, st);
         double dd = 0;
         if (read_scalar(tmp, &dd, st) != EFWI_OK) return lb_fail(EFWI_ERR_CUDA, "l-BFGS: reading d^T d failed");
-        a0 = std::fmin(1.0, 1.0 / std::sqrt(dd));
+        a0 = h->step0 > 0 ? h->step0 / std::sqrt(dd) : std::fmin(1.0, 1.0 / std::sqrt(dd));
     }
     Trial t;
     const bool found = ls.run(a0, t);
@@ -502,4 +618,134 @@ extern "C" int efwi_lbfgs_run(efwi_lbfgs *h, float *x, float *g, efwi_objective_
     it.stop = stop;
     *info = it;
     return EFWI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One iteration with the line search on the device.  Before the search the
+// host computes the direction and reads g^T d (restart from -g when it is not a
+// descent direction) and, on a first step, d^T d; the search itself is one
+// launch of a graph whose conditional while-node repeats trial point,
+// objective, phi' and search step; after it one read of the search state, then
+// the pair update of efwi_lbfgs_iterate.
+// ---------------------------------------------------------------------------
+extern "C" int efwi_lbfgs_iterate_device(efwi_lbfgs *h, float *x, double *phi, float *g,
+                                         efwi_device_objective_fn fn, void *ctx, efwi_lbfgs_info_t *info,
+                                         efwi_stream_t stream) {
+    if (!h || !x || !phi || !g || !fn || !info) return lb_fail(EFWI_ERR_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n = h->n;
+    const int G = lb_grid(n);
+    double *tmp = h->dev + h->o_tmp();
+    if (!h->ls_state) {
+        if (cudaMalloc(&h->ls_state, sizeof(LsState)) != cudaSuccess ||
+            cudaMalloc((void **)&h->ls_phit, 2 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return lb_fail(EFWI_ERR_OOM, "l-BFGS: allocation of the device line-search state failed");
+        }
+        cudaStreamCreateWithFlags(&h->ls_cap, cudaStreamNonBlocking);
+    }
+    LsState *state = static_cast<LsState *>(h->ls_state);
+    double *phit = h->ls_phit, *dphit = h->ls_phit + 1;
+    *info = efwi_lbfgs_info_t{};
+    double phi0 = 0;
+    if (read_scalar(phi, &phi0, st) != EFWI_OK) return lb_fail(EFWI_ERR_CUDA, "l-BFGS: reading phi failed");
+    info->phi_prev = info->phi = phi0;
+    double dphi0 = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        lb_direction(h, g, st);
+        dot_dev(h, g, h->d, tmp, 1.0, nullptr, st);
+        if (read_scalar(tmp, &dphi0, st) != EFWI_OK) return lb_fail(EFWI_ERR_CUDA, "l-BFGS: reading g^T d failed");
+        if (dphi0 < 0) break;
+        h->order.clear();                       // not a descent direction: restart from -g
+    }
+    info->pairs = (int)h->order.size();
+    if (!(dphi0 < 0)) {
+        info->ls_failed = 1;
+        return lb_check("l-BFGS");
+    }
+    double a0 = 1.0;
+    if (h->order.empty()) {                     // first step (or restart): unit length along d = -H_0 g
+        double dd = 0;
+        dot_dev(h, h->d, h->d, tmp, 1.0, nullptr, st);
+        if (read_scalar(tmp, &dd, st) != EFWI_OK) return lb_fail(EFWI_ERR_CUDA, "l-BFGS: reading d^T d failed");
+        a0 = h->step0 > 0 ? h->step0 / std::sqrt(dd) : std::fmin(1.0, 1.0 / std::sqrt(dd));
+    }
+    // the search graph of this objective and these arrays (captured once, then replayed)
+    const void *key[5] = {(const void *)fn, ctx, x, phi, g};
+    bool same = h->ls_exec != nullptr;
+    for (int k = 0; k < 5; ++k) same = same && key[k] == h->ls_key[k];
+    if (!same) {
+        cudaStreamSynchronize(st);
+        lb_drop_graph(h);
+        cudaGraph_t graph = nullptr;
+        if (cudaGraphCreate(&graph, 0) != cudaSuccess) return lb_check("l-BFGS: graph creation");
+        cudaGraphConditionalHandle cond;
+        cudaGraphNodeParams np{};
+        cudaGraphNode_t node;
+        if (cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return lb_check("l-BFGS: conditional handle");
+        }
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return lb_check("l-BFGS: conditional node");
+        }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(h->ls_cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return lb_check("l-BFGS: capture of the search body");
+        }
+        k_trial_state<<<G, kLbThreads, 0, h->ls_cap>>>(h->xt, x, h->d, n, state);
+        const int r = fn(ctx, h->xt, phit, h->gt, (efwi_stream_t)h->ls_cap);
+        dot_dev(h, h->gt, h->d, dphit, 1.0, nullptr, h->ls_cap);
+        k_ls_step<<<1, 1, 0, h->ls_cap>>>(state, phit, dphit, cond);
+        cudaGraph_t captured = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(h->ls_cap, &captured);
+        if (r != 0 || ec != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(graph);
+            if (r != 0) return lb_fail(r < 0 ? r : EFWI_ERR_ARG, "l-BFGS: the objective returned " + std::to_string(r) +
+                                                                     " while its evaluation was captured");
+            return lb_fail(EFWI_ERR_CUDA, std::string("l-BFGS: capture of the search body: ") + cudaGetErrorString(ec));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&h->ls_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            h->ls_exec = nullptr;
+            return lb_fail(EFWI_ERR_CUDA, std::string("l-BFGS: instantiation of the search graph: ") +
+                                              cudaGetErrorString(ei));
+        }
+        for (int k = 0; k < 5; ++k) h->ls_key[k] = key[k];
+    }
+    k_ls_init<<<1, 1, 0, st>>>(state, phi0, dphi0, a0, h->c1, h->c2, h->max_ls);
+    if (cudaGraphLaunch(h->ls_exec, st) != cudaSuccess) return lb_check("l-BFGS: search graph launch");
+    LsState s;
+    if (cudaMemcpyAsync(&s, state, sizeof(LsState), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return lb_fail(EFWI_ERR_CUDA, "l-BFGS: reading the search state failed");
+    info->evals = s.evals;
+    if (!s.ok) {
+        info->ls_failed = 1;
+        return lb_check("l-BFGS line search");
+    }
+    // the accepted step is the last trial: its point and gradient are in xt, gt
+    const int k = h->free_slot();
+    k_sub<<<G, kLbThreads, 0, st>>>(slot_s(h, k), h->xt, x, n);
+    k_sub<<<G, kLbThreads, 0, st>>>(slot_y(h, k), h->gt, g, n);
+    int acc = 0;
+    const int rc = lb_accept_pair(h, k, st, &acc);
+    if (rc != EFWI_OK) return rc;
+    cudaMemcpyAsync(x, h->xt, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(g, h->gt, sizeof(float) * n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(phi, phit, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    info->alpha = s.out.a;
+    info->phi = s.out.phi;
+    info->rate = (phi0 - s.out.phi) / phi0;     // eq. 13
+    info->pairs = (int)h->order.size();
+    return lb_check("l-BFGS iterate (device search)");
 }

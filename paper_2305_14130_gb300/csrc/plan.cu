@@ -170,22 +170,7 @@ void prof_end(efwi_plan *p, cudaStream_t st, int slot) {
 
 }  // namespace efwi
 
-// Host-side precompute of an acquisition on a plan's shot geometry: source
-// injection weights (eq. 2), receiver interpolation weights (eq. 3), the
-// deterministic gather of the adjoint source and the wavelet increments.
-struct AcqHost {
-    std::vector<ShotDev> shots;            // geometry of the plan + the source fields of this acquisition
-    std::vector<int> trace_shot;
-    std::vector<int> h_off;                // [ntr][16]
-    std::vector<float> h_w;
-    std::vector<int> g_shot, g_field, g_off, g_ptr, g_tr;
-    std::vector<float> g_w;
-    std::vector<int> gather_ptr;           // [ns + 1]
-    std::vector<float> h_dw, h_wv;
-    bool has_force = false;
-};
-
-static int build_acq(const efwi_plan_desc &dd, const std::vector<ShotDev> &geom, AcqHost &h, std::string &err) {
+int efwi::build_acq(const efwi_plan_desc &dd, const std::vector<ShotDev> &geom, AcqHost &h, std::string &err) {
     const efwi_plan_desc *d = &dd;
     const int ns = d->ns, nt = d->nt;
     h.shots = geom;
@@ -776,32 +761,48 @@ extern "C" int efwi_regularization_grad(efwi_plan *p, const float *m, const floa
     return EFWI_OK;
 }
 
-extern "C" int efwi_plan_rebind(efwi_plan *p, const efwi_plan_desc *d, efwi_stream_t stream) {
-    if (!p || !d) return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: plan and desc must be non-NULL");
-    if (p->broken)
-        return fail(p, EFWI_ERR_TIMEOUT, "a bounded device wait of an earlier call expired; destroy this plan");
+int efwi::check_same_shape(efwi_plan *p, const efwi_plan_desc *d, std::string &err) {
     const efwi_plan_desc &o = p->d;
     const bool gauge_used = d->ntr > 0 && d->das_mode != EFWI_DAS_VELOCITY;
     if (d->nx != o.nx || d->nz != o.nz || d->dx != o.dx || d->dz != o.dz || d->nt != o.nt || d->dt != o.dt ||
         d->npml != o.npml || d->ns != o.ns || d->ntr != o.ntr || d->das_mode != o.das_mode ||
-        (gauge_used && d->gauge != o.gauge))
-        return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: grid, time axis, npml, ns, ntr, das_mode and gauge "
-                                     "must equal the plan's");
-    if (!d->src_xz || !d->mt || !d->wavelet || !d->tr_ptr || (d->ntr > 0 && (!d->ch_xz || !d->ch_t)))
-        return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: a required host array is NULL");
+        (gauge_used && d->gauge != o.gauge)) {
+        err = "grid, time axis, npml, ns, ntr, das_mode and gauge must equal the plan's";
+        return EFWI_ERR_ARG;
+    }
+    if (!d->src_xz || !d->mt || !d->wavelet || !d->tr_ptr || (d->ntr > 0 && (!d->ch_xz || !d->ch_t))) {
+        err = "a required host array is NULL";
+        return EFWI_ERR_ARG;
+    }
     for (int s = 0; s < d->ns; ++s) {
         const ShotDev &sh = p->shots[s];
         const int x0 = d->win ? d->win[2 * s] : 0, w = d->win ? d->win[2 * s + 1] : d->nx;
-        if (d->tr_ptr[s] != sh.tr0 || d->tr_ptr[s + 1] - d->tr_ptr[s] != sh.ntr || x0 != sh.x0 || w != sh.w)
-            return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: the windows and traces per shot must equal the "
-                                         "plan's (shot " + std::to_string(s) + ")");
+        if (d->tr_ptr[s] != sh.tr0 || d->tr_ptr[s + 1] - d->tr_ptr[s] != sh.ntr || x0 != sh.x0 || w != sh.w) {
+            err = "the windows and traces per shot must equal the plan's (shot " + std::to_string(s) + ")";
+            return EFWI_ERR_ARG;
+        }
     }
-    if ((d->force != nullptr) != p->has_force)
-        return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: force sources must stay force sources (and moment "
-                                     "tensors moment tensors)");
+    if ((d->force != nullptr) != p->has_force) {
+        err = "force sources must stay force sources (and moment tensors moment tensors)";
+        return EFWI_ERR_ARG;
+    }
     if (d->force)
         for (int k = 0; k < 2 * d->ns; ++k)
-            if (!std::isfinite(d->force[k])) return fail(p, EFWI_ERR_ARG, "force components must be finite");
+            if (!std::isfinite(d->force[k])) {
+                err = "force components must be finite";
+                return EFWI_ERR_ARG;
+            }
+    return EFWI_OK;
+}
+
+extern "C" int efwi_plan_rebind(efwi_plan *p, const efwi_plan_desc *d, efwi_stream_t stream) {
+    if (!p || !d) return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: plan and desc must be non-NULL");
+    if (p->broken)
+        return fail(p, EFWI_ERR_TIMEOUT, "a bounded device wait of an earlier call expired; destroy this plan");
+    {
+        std::string e;
+        if (check_same_shape(p, d, e) != EFWI_OK) return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: " + e);
+    }
     AcqHost h;
     std::string err;
     if (build_acq(*d, p->shots, h, err) != EFWI_OK) return fail(p, EFWI_ERR_ARG, "efwi_plan_rebind: " + err);

@@ -210,6 +210,8 @@ void launch_adj_tma(efwi_plan *p, const float *vfx, cudaStream_t st);
 void launch_step_fused(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st);
 void launch_adj_fused(efwi_plan *p, int n, const SnapIn &si, cudaStream_t st);
 int upload_tiles(efwi_plan *p, TileList &tl, int tx, int tz);
+// the work items of tile list tl (same shape and order) with the flags of another acquisition
+std::vector<int4> tiles_of(const std::vector<ShotDev> &shots, const TileList &tl);
 int refresh_tiles(efwi_plan *p, TileList &tl, cudaStream_t st);
 
 // snapshot slots (engine.cu): slot >= 0 this step's slot, prev >= 0 the previous
@@ -218,6 +220,24 @@ SnapOut snap_out(efwi_plan *p, int slot, int prev);
 SnapIn snap_in(efwi_plan *p, int slot);
 float *snap_max(efwi_plan *p, int slot);
 void *snap_half(efwi_plan *p, int slot);
+
+// Host-side precompute of an acquisition on a plan's shot geometry (plan.cu): source
+// injection weights (eq. 2), receiver interpolation weights (eq. 3), the deterministic
+// gather of the adjoint source and the wavelet increments.
+struct AcqHost {
+    std::vector<ShotDev> shots;            // geometry of the plan + the source fields of this acquisition
+    std::vector<int> trace_shot;
+    std::vector<int> h_off;                // [ntr][16]
+    std::vector<float> h_w;
+    std::vector<int> g_shot, g_field, g_off, g_ptr, g_tr;
+    std::vector<float> g_w;
+    std::vector<int> gather_ptr;           // [ns + 1]
+    std::vector<float> h_dw, h_wv;
+    bool has_force = false;
+};
+int build_acq(const efwi_plan_desc &d, const std::vector<ShotDev> &geom, AcqHost &h, std::string &err);
+// the same checks as efwi_plan_rebind: desc has the plan's shape (grid, time axis, windows, traces)
+int check_same_shape(efwi_plan *p, const efwi_plan_desc *d, std::string &err);
 
 // helpers (plan.cu)
 // b, bp, sink all given, or all NULL for the plan's own weights (EFWI_ERR_ARG otherwise)

@@ -15,6 +15,7 @@ model (``efwi_regularization_grad_n``).
 """
 from __future__ import annotations
 
+import ctypes as C
 import dataclasses
 
 import numpy as np
@@ -109,3 +110,79 @@ def grouped_gradient(acq, vp, vs, rho, d_obs, group_size, out=None, times=None, 
         if plan is not None:
             plan.close()
     return phi, out
+
+
+class GroupSet:
+    """The shot groups of an extended problem held on the device (efwi_groups_*):
+    every group's acquisition (each of the plan's shape, as for ``Plan.rebind``) is
+    uploaded once, so that binding the plan to group k is device-to-device copies.
+    ``objective`` evaluates eq. 8 over all groups' components (eager);
+    ``device_objective`` gives the same objective to
+    ``LBFGS.iterate_device``, whose line search replays it from a CUDA graph."""
+
+    def __init__(self, plan, acqs):
+        from . import _abi
+        self._lib = _abi.load()
+        self.plan = plan
+        self.ngroups = len(acqs)
+        self.ns_total = plan.ns * self.ngroups
+        descs = (_abi.PlanDesc * self.ngroups)()
+        self._keep = []
+        for k, a in enumerate(acqs):
+            d, keep = plan._desc(a)
+            descs[k] = d
+            self._keep.append(keep)
+        h = C.c_void_p()
+        _abi.check(self._lib.efwi_groups_create(C.byref(h), plan._h, descs, self.ngroups), None)
+        self._h = h
+        self._ctx = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.efwi_groups_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bind(self, k):
+        from . import _abi
+        _abi.check(self._lib.efwi_groups_bind(self._h, int(k), _stream()), None)
+
+    def objective(self, x, d_obs, eta, b=None, bp=None, sink=None, phi=None, g=None):
+        """(phi [float64 CUDA scalar], g) of eq. 8 at x [3, ngroups * ns, nz, nx]
+        (d_obs [ngroups, ntr, nt]); b, bp, sink [ngroups * ns, nz, nx]."""
+        from . import _abi
+        if phi is None:
+            phi = torch.empty((), dtype=torch.float64, device=x.device)
+        if g is None:
+            g = torch.empty_like(x)
+        e = (C.c_double * 3)(*[float(v) for v in eta])
+        ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+        _abi.check(self._lib.efwi_groups_objective(self._h, ptr(x), ptr(d_obs), e, ptr(b), ptr(bp), ptr(sink),
+                                                   ptr(phi), ptr(g), _stream()), None)
+        return phi, g
+
+    def device_objective(self, d_obs, eta, b=None, bp=None, sink=None):
+        """The objective as an efwi_device_objective_fn and its context (kept alive
+        with this set) for LBFGS.iterate_device."""
+        from . import _abi
+        ctx = _abi.GroupsObjectiveCtx(self._h, C.c_void_p(d_obs.data_ptr()), (C.c_double * 3)(*map(float, eta)),
+                                      None if b is None else C.c_void_p(b.data_ptr()),
+                                      None if bp is None else C.c_void_p(bp.data_ptr()),
+                                      None if sink is None else C.c_void_p(sink.data_ptr()))
+        self._ctx.append((ctx, d_obs, b, bp, sink))
+        fn = C.cast(self._lib.efwi_groups_objective_fn, C.c_void_p)
+        return _DeviceObjective(fn, C.cast(C.pointer(ctx), C.c_void_p))
+
+
+class _DeviceObjective:
+    def __init__(self, fn, ctx):
+        self.fn, self.ctx = fn, ctx
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)

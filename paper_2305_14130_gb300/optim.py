@@ -79,6 +79,10 @@ class LBFGS:
     def reset(self):
         _abi.check(self._lib.efwi_lbfgs_reset(self._h))
 
+    def set_step0(self, length: float):
+        """Length of the first trial step without stored pairs (0: min(1, 1/||d||))."""
+        _abi.check(self._lib.efwi_lbfgs_set_step0(self._h, float(length)))
+
     def push(self, s, y) -> bool:
         """Stores the pair (s, y) when s^T y > 0; returns whether it was stored."""
         acc = C.c_int()
@@ -147,6 +151,21 @@ class LBFGS:
                                           C.byref(info), _stream())
         self._raise(rc)
         return p.value, _info(info)
+
+    def iterate_device(self, x, phi, g, objective):
+        """One iteration whose line search runs on the device from a CUDA graph
+        (efwi_lbfgs_iterate_device).  phi: float64 CUDA scalar (updated in place),
+        x and g updated in place; objective: a device objective with the attributes
+        ``fn`` (address of a C efwi_device_objective_fn) and ``ctx`` (its context),
+        e.g. ``groups.GroupSet.device_objective(...)``.  Returns info."""
+        if not (isinstance(phi, torch.Tensor) and phi.is_cuda and phi.dtype == torch.float64 and phi.numel() == 1):
+            raise ValueError("phi: float64 CUDA scalar expected")
+        info = _abi.LbfgsInfo()
+        rc = self._lib.efwi_lbfgs_iterate_device(self._h, _vec(x, self.n, "x"), C.c_void_p(phi.data_ptr()),
+                                                 _vec(g, self.n, "g"), objective.fn, objective.ctx, C.byref(info),
+                                                 _stream())
+        _abi.check(rc)
+        return _info(info)
 
     def run(self, x, objective, max_iter: int = 100, min_rate: float = 1e-3, g=None):
         """Iterates from x (updated in place) until max_iter, a rate of eq. 13

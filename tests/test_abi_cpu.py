@@ -48,7 +48,8 @@ def test_struct_layouts_match_binding(tmp_path):
     lines += ['printf("%zu\\n", sizeof(efwi_lbfgs_info_t));']
     lines += [f'printf("%zu\\n", offsetof(efwi_lbfgs_info_t, {f}));' for f, _ in _abi.LbfgsInfo._fields_]
     lines += ['printf("%zu\\n", sizeof(efwi_plan_info_t));', 'printf("%zu\\n", sizeof(efwi_zoi_desc));',
-              'return 0; }']
+              'printf("%zu\\n", sizeof(efwi_groups_objective_ctx));',
+              'printf("%zu\\n", offsetof(efwi_groups_objective_ctx, sink));', 'return 0; }']
     prog.write_text("\n".join(lines))
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
@@ -60,8 +61,10 @@ def test_struct_layouts_match_binding(tmp_path):
     assert lb[0] == C.sizeof(_abi.LbfgsInfo)
     for (f, _), off in zip(_abi.LbfgsInfo._fields_, lb[1:]):
         assert getattr(_abi.LbfgsInfo, f).offset == off, f
-    assert vals[-2] == C.sizeof(_abi.PlanInfo)
-    assert vals[-1] == C.sizeof(_abi.ZoiDesc)
+    assert vals[-4] == C.sizeof(_abi.PlanInfo)
+    assert vals[-3] == C.sizeof(_abi.ZoiDesc)
+    assert vals[-2] == C.sizeof(_abi.GroupsObjectiveCtx)
+    assert vals[-1] == _abi.GroupsObjectiveCtx.sink.offset
 
 
 def _desc(p, **over):
@@ -142,6 +145,7 @@ def test_lbfgs_rejects_bad_arguments(lib):
     assert not h.value
     assert lib.efwi_lbfgs_destroy(None) == 0
     assert lib.efwi_lbfgs_reset(None) == -1
+    assert lib.efwi_lbfgs_set_step0(None, 1.0) == -1
 
 
 def test_null_arguments(lib):
