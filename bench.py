@@ -163,7 +163,15 @@ def kernel_bytes(exec_, info, nt):
 # captures of the 8-shot case of this workload with the same kernel variant, scaled to a launch by its
 # cells.  Keyed by (kernel, staging, tile, variant details, snapshot store, every step stored); any
 # other variant, or a kernel changed since its capture, reports traffic null.
-TRAFFIC_PER_CELL = {}
+TRAFFIC_PER_CELL = {
+    # forward step, TMA cell pairs, tile 32x16: mean of a forward-pass and a recompute step
+    ("step", 3, 32, 16, 3, 0, 0, 0): 57.65,
+    # adjoint step, per-thread loads, tile 32x16, persistent grid, FP32 velocities
+    ("adj", 1, 32, 16, 1, 0, 0): 94.97,
+    # the same two with FP16 snapshots of every step
+    ("step", 3, 32, 16, 3, 0, 1, 1): 57.57,
+    ("adj", 1, 32, 16, 1, 1, 1): 90.35,
+}
 
 
 # Algorithmic bytes of one whole gradient per padded cell and time step: the forward
