@@ -47,7 +47,13 @@ def parse():
     ap.add_argument("--ckpt-store", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--snap-store", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="precision of the stored forward velocities")
-    ap.add_argument("--ckpt", default="0", help="checkpoint interval: 0 = sqrt(nt), n, or auto")
+    ap.add_argument("--ckpt", default="auto",
+                    help="checkpoint interval: 0 = sqrt(nt), n, or auto (every step stored when it fits, "
+                         "else sqrt(nt) with as many final steps kept by the forward pass as fit)")
+    ap.add_argument("--stored-steps", type=int, default=0,
+                    help="final steps kept by the forward pass with an explicit interval")
+    ap.add_argument("--no-sqrt", action="store_true",
+                    help="skip the record of the sqrt(nt) schedule (no steps kept by the forward pass)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -148,29 +154,47 @@ def snap_bytes(info):
     return 4.0 if info.get("snap_store", 0) == 0 else 2.0
 
 
+def recomputed_steps(info, nt):
+    """Steps the adjoint recomputes from checkpoints: those before the first step the
+    forward pass keeps (none with every step stored)."""
+    return 0 if info["ckpt_interval"] >= nt else nt - info["stored_steps"]
+
+
+def schedule_name(info, nt):
+    if info["ckpt_interval"] >= nt:
+        return "every step stored"
+    if info["stored_steps"] == 0:
+        return "sqrt(nt) checkpoints + recompute"
+    return (f"sqrt(nt) checkpoints + recompute of the first {nt - info['stored_steps']} steps, "
+            f"final {info['stored_steps']} kept by the forward pass")
+
+
 def kernel_bytes(exec_, info, nt):
     """Algorithmic bytes per padded cell of the average forward-step launch of one
-    gradient and of the adjoint-step launch.  With sqrt(nt) checkpoints half of the
-    forward-step launches (the recompute) keep v^{n+1/2}; with every step stored all do."""
+    gradient and of the adjoint-step launch.  Every step's v^{n+1/2} is written once,
+    by the forward pass or by its recompute, so of the nt + (recomputed steps)
+    forward-step launches nt write it."""
     if exec_ == "plain":
         return 44.0, 84.0
     v = 2 * snap_bytes(info)
-    fwd = 60.0 + v if info["ckpt_interval"] >= nt else 60.0 + v / 2
-    return fwd, 100.0 + v
+    nrec = recomputed_steps(info, nt)
+    return 60.0 + v * nt / (nt + nrec), 100.0 + v
 
 
 # DRAM traffic per padded cell of one launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu
 # captures of the 8-shot case of this workload with the same kernel variant, scaled to a launch by its
-# cells.  Keyed by (kernel, staging, tile, variant details, snapshot store, every step stored); any
-# other variant, or a kernel changed since its capture, reports traffic null.
+# cells.  Keyed by (kernel, staging, tile, variant details, snapshot store); the forward step has one
+# figure for a step that writes no velocities ("pass") and one for a step that keeps them ("keep"), mixed
+# in the proportion of the gradient's schedule.  Any other variant, or a kernel changed since its
+# capture, reports traffic null.
 TRAFFIC_PER_CELL = {
-    # forward step, TMA cell pairs, tile 32x16: mean of a forward-pass and a recompute step
-    ("step", 3, 32, 16, 3, 0, 0, 0): 57.65,
+    # forward step, TMA cell pairs, tile 32x16
+    ("step", 3, 32, 16, 3, 0, 0): {"pass": 54.99, "keep": 60.31},
     # adjoint step, per-thread loads, tile 32x16, persistent grid, FP32 velocities
-    ("adj", 1, 32, 16, 1, 0, 0): 94.97,
-    # the same two with FP16 snapshots of every step
-    ("step", 3, 32, 16, 3, 0, 1, 1): 57.57,
-    ("adj", 1, 32, 16, 1, 1, 1): 90.35,
+    ("adj", 1, 32, 16, 1, 0): 94.97,
+    # the same two with FP16 snapshots (every step stored)
+    ("step", 3, 32, 16, 3, 0, 1): {"keep": 57.57},
+    ("adj", 1, 32, 16, 1, 1): 90.35,
 }
 
 
@@ -180,6 +204,7 @@ TRAFFIC_PER_CELL = {
 # recompute drops and the forward pass keeps the velocities: 68 + 108 = 176 B, the floor
 # of the method with FP32 velocities (forward, adjoint, velocity hand-off, imaging
 # sums); FP16/BF16 snapshots halve the hand-off (168 B, or 228 B with the recompute).
+# Steps kept by the forward pass are not recomputed: 176 + 60 x (recomputed / nt) B.
 GRAD_FLOOR_BYTES = 176.0
 
 
@@ -188,12 +213,11 @@ def gradient_roofline(info, nt, s_per_grad):
     included) at the algorithmic bytes of its schedule and at the FP32 floor of 176 B
     per padded cell-step, both against the measured HBM peak."""
     hbm, peak_kind = peaks()
-    sqrt_ckpt = info["ckpt_interval"] < nt
     v = 2 * snap_bytes(info)
-    bpc = (60.0 + (60.0 + v) + (100.0 + v)) if sqrt_ckpt else (60.0 + v) + (100.0 + v)
+    bpc = 60.0 + 60.0 * recomputed_steps(info, nt) / nt + (v + 100.0 + v)
     work = info["padded_cells"] * nt / s_per_grad / 1e9
     return {"bound": "hbm", "unit": "GB/s", "peak": hbm, "peak_kind": peak_kind,
-            "schedule": "sqrt(nt) checkpoints + recompute" if sqrt_ckpt else "every step stored",
+            "schedule": schedule_name(info, nt),
             "snapshots": {0: "fp32", 1: "fp16", 2: "bf16"}[info.get("snap_store", 0)],
             "bytes_per_cell_step": bpc, "achieved": bpc * work, "frac": bpc * work / hbm,
             "floor_bytes_per_cell_step": GRAD_FLOOR_BYTES, "floor_frac": GRAD_FLOOR_BYTES * work / hbm}
@@ -207,7 +231,8 @@ def roofline(exec_, info, prof, nt, ns):
     traffic / duration as a fraction of the measured peak (frac_traffic)."""
     hbm, peak_kind = peaks()
     cells = info["padded_cells"] if exec_ == "batched" else info["padded_cells"] / ns
-    per_grad = {"step": 2 * nt if info["ckpt_interval"] < nt else nt, "adj": nt}
+    nrec = recomputed_steps(info, nt)
+    per_grad = {"step": nt + nrec, "adj": nt}
     bytes_of = dict(zip(("step", "adj"), kernel_bytes(exec_, info, nt)))
     out = []
     for k in ("step", "adj"):
@@ -236,9 +261,16 @@ def roofline(exec_, info, prof, nt, ns):
                 key = key + (info["layout"], info["staged_stores"])
             if k == "adj" and info["adj_stencil"] == 1:
                 key = key + (info["adj_persistent"],)
-            key = key + (info.get("snap_store", 0), int(info["ckpt_interval"] >= nt))
-            if key in TRAFFIC_PER_CELL:
-                traffic = TRAFFIC_PER_CELL[key] * cells
+            key = key + (info.get("snap_store", 0),)
+            t = TRAFFIC_PER_CELL.get(key)
+            if isinstance(t, dict):
+                n_pass = 0 if info["ckpt_interval"] >= nt else nt - info["stored_steps"]
+                if n_pass == 0 or "pass" in t:
+                    t = (t.get("pass", 0.0) * n_pass + t["keep"] * (nt + nrec - n_pass)) / (nt + nrec)
+                else:
+                    t = None
+            if t is not None:
+                traffic = t * cells
         out.append({"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                     "frac_nominal": achieved / NOMINAL_HBM_GBS,
                     "traffic": traffic, "frac_traffic": None if traffic is None else traffic / avg / 1e9 / hbm,
@@ -389,13 +421,54 @@ def reduced_storage(efwi, acq, m, d_obs, zoi, eta, ref, plain_s, args):
     cells = ns * acq.nx * acq.nz * acq.nt
     roofs = roofline("batched", info, prof, acq.nt, ns)
     out = {"config": {"ckpt_store": "fp16", "snap_store": "fp16", "ckpt_interval": info["ckpt_interval"],
-                      "schedule": "every step stored" if info["ckpt_interval"] >= acq.nt else "sqrt(nt) + recompute"},
+                      "stored_steps": info["stored_steps"], "schedule": schedule_name(info, acq.nt)},
            "steps": steps, "s_per_gradient": s_grad, "value": cells / s_grad / 1e9, "unit": UNIT,
            "speedup_vs_plain_fp32": None if plain_s is None else plain_s / s_grad,
            "rel_err_vs_fp32_path": errs, "roofline": roofs[0], "roofline_other": roofs[1],
            "gradient_roofline": gradient_roofline(info, acq.nt, s_grad), "workspace_GB": info["workspace_bytes"] / 1e9}
     plan.close()
     return out
+
+
+def sqrt_schedule(efwi, acq, m, d_obs, zoi, eta, ref, args):
+    """The headline step on the plain sqrt(nt) schedule (every segment recomputed,
+    no step kept by the forward pass): seconds per gradient, and whether its outputs
+    equal the headline schedule's bit for bit (ref: phi, g_vp, g_vs, g_rho)."""
+    import torch
+    plan = efwi.Plan(acq, exec="batched", ckpt_store=args.ckpt_store, snap_store=args.snap_store,
+                     ckpt_interval=0, overlap=args.overlap)
+    b, bp, sink = zoi
+    g = tuple(torch.empty_like(m[0]) for _ in range(3))
+
+    def step():
+        phi, *_ = plan.gradient(*m, d_obs, out=g)
+        for mm, gm, e in zip(m, g, eta):
+            plan.regularization_grad(mm, b, bp, sink, e, g=gm)
+        return phi
+
+    step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(2, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(steps):
+        phi = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s_grad = e0.elapsed_time(e1) / 1e3 / steps
+    info = plan.info()
+    same = bool(torch.equal(phi, ref[0]) and all(torch.equal(a, r) for a, r in zip(g, ref[1:])))
+    out = {"schedule": schedule_name(info, acq.nt), "ckpt_interval": info["ckpt_interval"], "steps": steps,
+           "s_per_gradient": s_grad, "value": acq.ns * acq.nx * acq.nz * acq.nt / s_grad / 1e9, "unit": UNIT,
+           "outputs_bitwise_equal_to_headline": same, "workspace_GB": info["workspace_bytes"] / 1e9}
+    plan.close()
+    return out
+
+
+# objective evaluations the timed l-BFGS iteration of the 4000x1200 record may spend
+# (one evaluation = every timed group's gradient, about 15 s per group)
+FULL_ITERATION_MAX_LS = 5
 
 
 def full_iteration(efwi, args):
@@ -475,9 +548,13 @@ def full_iteration(efwi, args):
         b_.record()
         b_.synchronize()
         objective_s = a_.elapsed_time(b_) / 1e3
-        opt = LBFGS(x.numel(), m=5)
+        opt = LBFGS(x.numel(), m=5, max_ls=FULL_ITERATION_MAX_LS)
         xf, gf = x.view(-1), grad.view(-1)
-        opt.set_step0(1e-3 * float(torch.linalg.vector_norm(xf)))   # first trial: 0.1 % of the model norm
+        # first trial along d = -g: the largest change of any model value is 1 % of the
+        # largest model value (||a d|| = 0.01 max|x| ||g|| / max|g|)
+        gmax = float(gf.abs().max())
+        if gmax > 0 and np.isfinite(gmax):
+            opt.set_step0(0.01 * float(xf.abs().max()) * float(torch.linalg.vector_norm(gf.double())) / gmax)
         dobj = gs.device_objective(d_obs, p.eta, b, bp, sink)
         phi_start = float(phi.item())
         t = time.perf_counter()
@@ -516,8 +593,9 @@ def full_iteration(efwi, args):
     out.update({
         "rebind_s": rebind, "objective_s_timed_groups": objective_s, "objective_s_per_group": objective_s / G,
         "device_iteration": {"evals": it["evals"], "alpha": it["alpha"], "rate": it["rate"],
-                             "ls_failed": it["ls_failed"], "phi_before": phi_start, "phi_after": it["phi"],
-                             "s_timed_groups": first_s,
+                             "ls_failed": it["ls_failed"], "max_ls": FULL_ITERATION_MAX_LS,
+                             "phi_before": phi_start, "phi_after": it["phi"],
+                             "first_trial": "largest model change 1 % of max |x|", "s_timed_groups": first_s,
                              "line_search": "on the device (conditional while-node of a CUDA graph); this first "
                                             "call also captures and instantiates the graph"},
         "lbfgs_direction_s_full_vector": lbfgs_s, "lbfgs_n": n,
@@ -553,7 +631,8 @@ def run_ours(args):
     adj_tile = tuple(int(v) for v in args.adj_tile.lower().split("x"))
     plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store, stencil=args.stencil, tile=tile,
                      adj_stencil=args.adj_stencil, adj_tile=adj_tile, overlap=args.overlap,
-                     snap_store=args.snap_store, ckpt_interval=args.ckpt if args.ckpt == "auto" else int(args.ckpt))
+                     snap_store=args.snap_store, ckpt_interval=args.ckpt if args.ckpt == "auto" else int(args.ckpt),
+                     stored_steps=args.stored_steps)
     # observed data: the same sources in the model with the Gaussian anomaly
     ns = acq.ns
     tv = lambda m: dev(np.repeat(np.asarray(m)[None], ns, 0))
@@ -661,6 +740,12 @@ def run_ours(args):
                  "grad_vp_rel_diff": rel}
         pl.close()
 
+    sqrt_rec = None
+    if world == 1 and not args.no_sqrt and args.exec == "batched" and info["ckpt_interval"] < acq.nt \
+            and info["stored_steps"] > 0:
+        sqrt_rec = sqrt_schedule(efwi, acq, (vp, vs, rho), d_obs, (b, bp, sink), eta, ref, args)
+        sqrt_rec["headline_speedup"] = sqrt_rec["s_per_gradient"] / s_per_grad
+
     reduced = None
     if world == 1 and not args.no_reduced and args.exec == "batched":
         reduced = reduced_storage(efwi, acq, (vp, vs, rho), d_obs, (b, bp, sink), eta, ref,
@@ -682,7 +767,8 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "exec": args.exec, "ckpt_store": args.ckpt_store,
                            "snap_store": args.snap_store,
-                           "ckpt_interval": info["ckpt_interval"], "tile": [info["tile_x"], info["tile_z"]],
+                           "ckpt_interval": info["ckpt_interval"], "stored_steps": info["stored_steps"],
+                           "schedule": schedule_name(info, acq.nt), "tile": [info["tile_x"], info["tile_z"]],
                            "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
                            "stencil": {1: "loads", 2: "tma", 3: "tma_pairs", 4: "tma_staged"}.get(info["stencil"], "?"), "stages": info["stages"], "layout": info["layout"],
                            "adj_stencil": {1: "loads", 2: "tma"}.get(info["adj_stencil"], "?"),
@@ -697,7 +783,7 @@ def run_ours(args):
                 "gradient_roofline": gradient_roofline(info, acq.nt, s_per_grad),
                 "e2e": e2e, "plain_fp32": plain, "cpu_baseline": cpu,
                 "workspace_GB": info["workspace_bytes"] / 1e9,
-                "reduced_storage": reduced, "full_iteration": full_it}
+                "sqrt_schedule": sqrt_rec, "reduced_storage": reduced, "full_iteration": full_it}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

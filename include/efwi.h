@@ -84,7 +84,8 @@ enum efwi_das_mode { EFWI_DAS_STRAIN = 0, EFWI_DAS_STRAIN_RATE = 1, EFWI_DAS_VEL
  * element |x^ - x| <= 2^-11 |x| (FP16; every |x| >= s 2^-28) or 2^-8 |x| (BF16) */
 enum efwi_store { EFWI_STORE_FP32 = 0, EFWI_STORE_FP16 = 1, EFWI_STORE_BF16 = 2 };
 /* ckpt_interval value: store every step when the snapshots fit the device's
- * free memory at plan creation, else ceil(sqrt(nt)) */
+ * free memory at plan creation, else ceil(sqrt(nt)) with as many stored final
+ * steps as fit (see stored_steps) */
 #define EFWI_CKPT_AUTO (-1)
 /* execution strategy:
  *  PLAIN   one shot per launch, one kernel per half-step, no graph, no tuning
@@ -132,7 +133,9 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *                      EFWI_CKPT_AUTO = every step if all nt snapshots (at
  *                      snap_store precision) fit in the free device memory
  *                      after the rest of the workspace, with 5 % + 2 GB left
- *                      over, else ceil(sqrt(nt))
+ *                      over, else ceil(sqrt(nt)) with the largest stored_steps
+ *                      that fits (stored_steps is then ignored; 0 when the
+ *                      overlapped schedule is forced)
  *   ckpt_store         EFWI_STORE_* precision of the checkpoints
  *   exec               EFWI_EXEC_*
  *   tile_x, tile_z     stencil tile for EXEC_BATCHED (0, 0 = autotune at plan creation)
@@ -153,6 +156,16 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *                      full storage, the steps of one segment otherwise); FP16
  *                      and BF16 halve their memory and traffic and need
  *                      EXEC_BATCHED (and no forced overlap)
+ *   stored_steps       with ckpt_interval K < nt: the forward pass also keeps the
+ *                      velocities of the final stored_steps steps, rounded down so
+ *                      that the steps before them form whole K-step segments; the
+ *                      adjoint reads those directly and recomputes only the
+ *                      segments before them from their checkpoints (no checkpoints
+ *                      are taken inside the stored part).  0 = none (the whole
+ *                      sqrt(nt) schedule); results equal those of stored_steps = 0
+ *                      bit for bit with FP32 checkpoints (the imaging sums are
+ *                      folded at the same segment ends).  Not combinable with a
+ *                      forced overlapped schedule.
  */
 typedef struct efwi_plan_desc {
     int nx, nz;
@@ -183,6 +196,7 @@ typedef struct efwi_plan_desc {
     int overlap;
     const double *force;
     int snap_store;
+    int stored_steps;
 } efwi_plan_desc;
 
 /* What a plan chose and holds (filled by efwi_plan_info). */
@@ -209,6 +223,8 @@ typedef struct efwi_plan_info_t {
     int adj_persistent;         /* per-thread-load adjoint step runs on a persistent grid */
     int snap_store;             /* EFWI_STORE_* of the forward-velocity snapshots */
     int prefetch;               /* L2 prefetch one tile ahead: bit 0 forward step, bit 1 adjoint step */
+    int stored_steps;           /* final steps whose velocities the forward pass keeps
+                                   (nt with every step stored, 0 for the sqrt(nt) schedule) */
 } efwi_plan_info_t;
 
 /* Zone-of-influence description (eq. 10), host memory.  Per source s:
@@ -398,6 +414,9 @@ int efwi_pseudo_hessian(efwi_plan *plan, const float *vp, const float *vs, const
  *   fn(ctx, x, phi, g, stream): x device [n] (read only), phi HOST double
  *   (written), g device [n] (written); returns 0, or nonzero to abort (a
  *   negative value is passed on as the status).
+ * A trial point whose objective or slope is not finite (a step so long that
+ * the modelling becomes unstable) counts as failing sufficient decrease: it
+ * bounds the bracket from above and the zoom bisects towards shorter steps.
  * A pair is stored only when s^T y > 0.                                     */
 typedef struct efwi_lbfgs efwi_lbfgs;
 typedef int (*efwi_objective_fn)(void *ctx, const float *x, double *phi, float *g, efwi_stream_t stream);

@@ -14,10 +14,18 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   and H_0 = D without pairs.
 * ``two_loop``: the same product H g by the two-loop recursion (Nocedal &
   Wright, Alg. 7.4), for vectors too long for a dense matrix.
-* ``wolfe_search``: Nocedal & Wright Alg. 3.5 (bracketing by doubling the
-  step) and Alg. 3.6 (zoom); the zoom trial is the minimiser of the quadratic
+* ``wolfe_search``: Nocedal & Wright Alg. 3.5 (bracketing: while the trial
+  meets sufficient decrease and phi' < 0, the next, longer trial is the zero
+  of the secant of phi' through the last two points, kept within 2 to 10 times
+  the current step, or twice the step when phi' did not increase; the
+  algorithm leaves the choice in (a_i, a_max) open) and Alg. 3.6 (zoom); the
+  zoom trial is the minimiser of the quadratic
   through phi(lo), phi'(lo), phi(hi), replaced by the bracket midpoint when it
   falls outside the inner 80 % of the bracket or the quadratic is not convex.
+  A trial without a finite objective or slope (outside the algorithm, which
+  assumes a smooth objective: a step that makes the modelling unstable) is
+  read as failing sufficient decrease, phi = +inf, so the zoom bisects
+  towards the shorter end of the bracket.
 * ``lbfgs``: the iteration: d = -H g (restart from -H_0 g if d is not a
   descent direction), first step 1/||d|| without stored pairs else 1, store the pair
   only when s^T y > 0, keep the newest m pairs, rate_{k+1} = (Phi_k -
@@ -79,6 +87,18 @@ def _interp(lo, hi):
     return a
 
 
+def _extrapolate(prev, t):
+    """Next bracketing trial after t = (a, phi, dphi), which met sufficient decrease
+    with phi'(a) < 0 (the minimum lies further): the zero of the secant of phi'
+    through prev and t when phi' increased (exact for a quadratic), kept within
+    [2 a, 10 a]; 2 a otherwise."""
+    a = t[0]
+    if t[2] > prev[2]:
+        sec = a - t[2] * (a - prev[0]) / (t[2] - prev[2])
+        return min(max(sec, 2.0 * a), 10.0 * a)
+    return 2.0 * a
+
+
 def wolfe_search(f, x, phi0, g0, d, a0, c1=1e-4, c2=0.9, max_ls=20):
     """Step a with phi(a) <= phi0 + c1 a phi'(0) and |phi'(a)| <= -c2 phi'(0).
 
@@ -91,7 +111,10 @@ def wolfe_search(f, x, phi0, g0, d, a0, c1=1e-4, c2=0.9, max_ls=20):
         nonlocal evals
         evals += 1
         phi, g = f(x + a * d)
-        return (a, float(phi), float(g @ d)), g
+        phi, dphi = float(phi), float(g @ d)
+        if not (np.isfinite(phi) and np.isfinite(dphi)):
+            phi = np.inf             # no finite value: the step is too long (fails sufficient decrease)
+        return (a, phi, dphi), g
 
     def armijo_fails(t):
         return t[1] > phi0 + c1 * t[0] * dphi0
@@ -125,8 +148,8 @@ def wolfe_search(f, x, phi0, g0, d, a0, c1=1e-4, c2=0.9, max_ls=20):
         if t[2] >= 0:
             t, g = zoom(t, prev)
             break
+        a = _extrapolate(prev, t)
         prev = t
-        a = 2.0 * a
         i += 1
     else:
         t = None

@@ -70,16 +70,21 @@ class Plan:
 
     ``ckpt_interval``: 0 = ceil(sqrt(nt)) steps per checkpoint, >= nt = every
     step stored, "auto" = every step stored when the snapshots fit the free
-    device memory.  ``snap_store``: precision of those stored forward
+    device memory, else ceil(sqrt(nt)) with as many stored final steps as fit.
+    ``stored_steps``: with an interval K < nt, the forward pass also keeps the
+    velocities of the final stored_steps steps (rounded down to leave whole
+    K-step segments before them), which the adjoint then reads without a
+    recompute.  ``snap_store``: precision of those stored forward
     velocities ("fp32", "fp16", "bf16"; the latter two need exec="batched").
     """
 
     def __init__(self, acq, exec: str = "batched", ckpt_interval=0, ckpt_store: str = "fp32",
                  tile=(0, 0), stencil: str = "auto", adj_tile=(0, 0), adj_stencil: str = "auto",
-                 overlap: str = "auto", snap_store: str = "fp32"):
+                 overlap: str = "auto", snap_store: str = "fp32", stored_steps: int = 0):
         lib = _abi.load()
         self._opts = dict(exec=exec, ckpt_interval=ckpt_interval, ckpt_store=ckpt_store, tile=tile, stencil=stencil,
-                          adj_tile=adj_tile, adj_stencil=adj_stencil, overlap=overlap, snap_store=snap_store)
+                          adj_tile=adj_tile, adj_stencil=adj_stencil, overlap=overlap, snap_store=snap_store,
+                          stored_steps=stored_steps)
         d, keep = self._desc(acq)
         self.exec, self.ckpt_store, self.snap_store = exec, ckpt_store, snap_store
         h = C.c_void_p()
@@ -130,6 +135,7 @@ class Plan:
         d.ref_vp, d.ref_vs, d.ref_rho = P(keep["rvp"], C.c_float), P(keep["rvs"], C.c_float), P(keep["rrho"], C.c_float)
         d.ckpt_interval = CKPT_AUTO if o["ckpt_interval"] == "auto" else int(o["ckpt_interval"])
         d.snap_store = STORE[o["snap_store"]]
+        d.stored_steps = int(o["stored_steps"])
         d.ckpt_store = STORE[o["ckpt_store"]]
         d.exec = EXEC[o["exec"]]
         d.tile_x, d.tile_z = int(o["tile"][0]), int(o["tile"][1])

@@ -30,7 +30,8 @@ class PlanDesc(C.Structure):
                 ("ref_vp", PF), ("ref_vs", PF), ("ref_rho", PF), ("ckpt_interval", C.c_int),
                 ("ckpt_store", C.c_int), ("exec", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
                 ("stencil", C.c_int), ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("adj_stencil", C.c_int),
-                ("overlap", C.c_int), ("force", PD), ("snap_store", C.c_int)]
+                ("overlap", C.c_int), ("force", PD), ("snap_store", C.c_int),
+                ("stored_steps", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -41,7 +42,7 @@ class PlanInfo(C.Structure):
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong), ("layout", C.c_int),
                 ("staged_stores", C.c_int), ("adj_persistent", C.c_int), ("snap_store", C.c_int),
-                ("prefetch", C.c_int)]
+                ("prefetch", C.c_int), ("stored_steps", C.c_int)]
 
 
 class ZoiDesc(C.Structure):

@@ -161,8 +161,9 @@ SnapIn snap_in(efwi_plan *p, int slot) {
     return si;
 }
 
-// Forward pass over all steps; keeps checkpoints when ck and every v^{n+1/2}
-// in the snapshot slots when the plan stores all steps.
+// Forward pass over all steps; when ck, keeps a checkpoint at the start of every
+// segment that the adjoint recomputes and every v^{n+1/2}, n >= n_split, in the
+// snapshot slots (all steps when the plan stores all of them).
 void forward_loop(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
     reset_forward_state(p, st);
     const int nt = p->d.nt;
@@ -171,10 +172,12 @@ void forward_loop(efwi_plan *p, float *d, bool ck, cudaStream_t st) {
         forward_keep(p, 0, nt, 0, d, st);
         return;
     }
-    for (int n = 0; n < nt; ++n) {
+    const int n_keep = ck ? p->n_split : nt;
+    for (int n = 0; n < n_keep; ++n) {
         if (ck && n % p->K == 0) launch_ckpt_save(p, n / p->K, st);
         forward_step(p, n, d, SnapOut{}, st);
     }
+    if (n_keep < nt) forward_keep(p, n_keep, nt, p->K, d, st);
 }
 
 void adjoint_loop(efwi_plan *p, cudaStream_t st) {
@@ -192,7 +195,7 @@ void adjoint_loop(efwi_plan *p, cudaStream_t st) {
     const int nt = p->d.nt, K = p->K;
     const bool full = K >= nt;
     const int nseg = (nt + K - 1) / K;
-    if (!full && p->ov_fwd > 0 && p->seg_double) {
+    if (!full && p->ov_fwd > 0 && p->seg_double && p->n_split >= nt) {
         // recompute of segment s-1 (stream sr) runs concurrently with the adjoint of
         // segment s (stream st); the two alternate between the segment-buffer halves
         cudaStream_t sr = p->cap2;
@@ -224,16 +227,19 @@ void adjoint_loop(efwi_plan *p, cudaStream_t st) {
         cudaStreamWaitEvent(st, join);
         return;
     }
-    // segments of K steps (recompute, then adjoint); with every step stored, chunks of
-    // ceil(sqrt(nt)) steps, so that the imaging sums are Kahan-folded as often
+    // segments of K steps (recompute, then adjoint; the steps from n_split on were kept
+    // by the forward pass); with every step stored, chunks of ceil(sqrt(nt)) steps, so
+    // that the imaging sums are Kahan-folded as often
     const int KF = full ? std::min(nt, (int)std::ceil(std::sqrt((double)nt))) : K;
     for (int sgi = (nt + KF - 1) / KF - 1; sgi >= 0; --sgi) {
         const int n0 = sgi * KF, n1 = std::min(n0 + KF, nt);
-        if (!full) {
+        const bool kept = full || n0 >= p->n_split;     // n_split is a multiple of K
+        if (!kept) {
             launch_ckpt_load(p, sgi, st);
             forward_keep(p, n0, n1, 0, nullptr, st);
         }
-        for (int n = n1 - 1; n >= n0; --n) adjoint_step(p, n, snap_in(p, full ? n : n - n0), st);
+        for (int n = n1 - 1; n >= n0; --n)
+            adjoint_step(p, n, snap_in(p, full ? n : kept ? K + (n - p->n_split) : n - n0), st);
         if (p->Gtot) launch_kahan_fold(p, st);
     }
 }

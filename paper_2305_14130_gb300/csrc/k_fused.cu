@@ -908,7 +908,8 @@ int efwi_autotune(efwi_plan *p) {
     p->ov_fwd = p->ov_adj = 0;
     const long long segbytes = sizeof(float) * (long long)p->K * 2 * p->fsz_total;
     float *seg2 = nullptr;
-    if (!rc && p->K < p->d.nt && p->d.overlap != EFWI_OVERLAP_OFF && p->snap_store == EFWI_STORE_FP32 &&
+    if (!rc && p->K < p->d.nt && p->n_split >= p->d.nt && p->d.overlap != EFWI_OVERLAP_OFF &&
+        p->snap_store == EFWI_STORE_FP32 &&
         cudaMalloc((void **)&seg2, segbytes) != cudaSuccess) {
         cudaGetLastError();
         seg2 = nullptr;
@@ -979,6 +980,7 @@ int efwi_autotune(efwi_plan *p) {
                 p->seg = both;
                 p->bytes += segbytes;
                 p->seg_double = true;
+                p->nslots = 2 * p->K;
                 rc = select_adj(p, ba);
                 if (!rc) rc = select_fwd(p, bf);   // the forward segment map covers both halves
             }
@@ -993,7 +995,7 @@ int efwi_autotune(efwi_plan *p) {
     cudaMemset(p->psi, 0, sizeof(float) * 4 * p->H);
     cudaMemset(p->apsi, 0, sizeof(float) * 4 * p->H);
     cudaMemset(p->G, 0, sizeof(float) * 5 * p->fsz_total);
-    if (p->seg) cudaMemset(p->seg, 0, sizeof(float) * (p->seg_double ? 2 : 1) * p->K * 2 * p->fsz_total);
+    if (p->seg) cudaMemset(p->seg, 0, sizeof(float) * (size_t)p->nslots * 2 * p->fsz_total);
     cudaMemset(p->dev_err, 0, sizeof(int));
     p->scur = p->acur = p->psi_v = p->psi_s = p->apsi_v = p->apsi_s = 0;
     p->launches = 0;

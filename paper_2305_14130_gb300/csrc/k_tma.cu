@@ -694,7 +694,7 @@ int tma_prepare_fwd(efwi_plan *p, int tx, int tz, int nst, int vec, int stg) {
         if (!rc) rc = encode_map(&h[s].mc, p->mat, sh, F, 5, tx, tz, 3);
         if (!rc) rc = encode_map(&h[s].o2, p->state[0], sh, F, 10, tx, tz, 2);
         if (!rc) rc = encode_map(&h[s].o3, p->state[0], sh, F, 10, tx, tz, 3);
-        if (!rc && p->seg) rc = encode_map(&h[s].sg, p->seg, sh, F, (p->seg_double ? 4 : 2) * p->K, tx, tz, 2);
+        if (!rc && p->seg) rc = encode_map(&h[s].sg, p->seg, sh, F, 2 * p->nslots, tx, tz, 2);
         if (rc) {
             p->err = "cuTensorMapEncodeTiled failed for the forward maps";
             return rc;
@@ -1069,7 +1069,7 @@ int tma_encode_adj_maps(efwi_plan *p, int tx, int tz) {
         const ShotDev &sh = p->shots[s];
         int rc = encode_map(&h[s].ad, p->adj[0], sh, F, 10, tx + 8, tz + 8, 5);
         if (!rc) rc = encode_map(&h[s].m5, p->mat, sh, F, 5, tx + 8, tz + 8, 5);
-        if (!rc && p->seg) rc = encode_map(&h[s].sg, p->seg, sh, F, (p->seg_double ? 4 : 2) * p->K, tx + 8, tz + 8, 2);
+        if (!rc && p->seg) rc = encode_map(&h[s].sg, p->seg, sh, F, 2 * p->nslots, tx + 8, tz + 8, 2);
         if (!rc) rc = encode_map(&h[s].gi, p->G, sh, F, 5, tx, tz, 5);
         if (rc) {
             p->err = "cuTensorMapEncodeTiled failed for the adjoint maps";

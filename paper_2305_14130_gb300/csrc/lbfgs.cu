@@ -233,7 +233,11 @@ struct Search {
         }
         t.a = a;
         t.phi = phi;
-        return std::isfinite(phi) && std::isfinite(t.dphi);
+        // a trial whose objective or slope is not finite (a step long enough to make
+        // the modelling unstable) fails sufficient decrease: phi = +inf, so that it
+        // bounds the bracket from above and the zoom bisects towards the shorter step
+        if (!std::isfinite(phi) || !std::isfinite(t.dphi)) t.phi = HUGE_VAL;
+        return true;
     }
     bool armijo_fails(const Trial &t) const { return t.phi > phi0 + h->c1 * t.a * dphi0; }
     bool curvature_holds(const Trial &t) const { return std::fabs(t.dphi) <= -h->c2 * dphi0; }
@@ -283,9 +287,21 @@ struct Search {
                 return true;
             }
             if (t.dphi >= 0) return zoom(t, prev, out);
+            a = extrapolate(prev, t);
             prev = t;
-            a = 2.0 * a;
         }
+    }
+
+    // next bracketing trial after t (sufficient decrease holds, phi'(t) < 0): the zero
+    // of the secant of phi' through prev and t when phi' increased (the minimiser of a
+    // quadratic), kept within [2 a, 10 a]; 2 a otherwise
+    static double extrapolate(const Trial &prev, const Trial &t) {
+        const double a = t.a;
+        if (t.dphi > prev.dphi) {
+            const double sec = a - t.dphi * (a - prev.a) / (t.dphi - prev.dphi);
+            return std::fmin(std::fmax(sec, 2.0 * a), 10.0 * a);
+        }
+        return 2.0 * a;
     }
 };
 
@@ -320,6 +336,16 @@ __device__ double ls_interp(const LsTrial &lo, const LsTrial &hi) {
     return a;
 }
 
+// Search::extrapolate
+__device__ double ls_extrapolate(const LsTrial &prev, const LsTrial &t) {
+    const double a = t.a;
+    if (t.dphi > prev.dphi) {
+        const double sec = a - t.dphi * (a - prev.a) / (t.dphi - prev.dphi);
+        return fmin(fmax(sec, 2.0 * a), 10.0 * a);
+    }
+    return 2.0 * a;
+}
+
 __global__ void k_ls_init(LsState *s, double phi0, double dphi0, double a0, double c1, double c2, int max_ls) {
     LsState t{};
     t.phi0 = phi0;
@@ -345,12 +371,11 @@ __global__ void k_ls_step(LsState *st, const double *phit, const double *dphit, 
     LsState s = *st;
     if (!s.done) {
         s.evals += 1;
-        const LsTrial t{s.a, *phit, *dphit};
+        LsTrial t{s.a, *phit, *dphit};
+        if (!isfinite(t.phi) || !isfinite(t.dphi)) t.phi = HUGE_VAL;   // as in Search::eval
         const bool armijo_fails = t.phi > s.phi0 + s.c1 * t.a * s.dphi0;
         const bool curvature = fabs(t.dphi) <= -s.c2 * s.dphi0;
-        if (!isfinite(t.phi) || !isfinite(t.dphi)) {
-            s.done = 1;
-        } else if (s.phase == 0) {
+        if (s.phase == 0) {
             if (armijo_fails || (s.i > 1 && t.phi >= s.prev.phi)) {
                 s.lo = s.prev; s.hi = t; s.phase = 1;
             } else if (curvature) {
@@ -358,7 +383,7 @@ __global__ void k_ls_step(LsState *st, const double *phit, const double *dphit, 
             } else if (t.dphi >= 0) {
                 s.lo = t; s.hi = s.prev; s.phase = 1;
             } else {
-                s.prev = t; s.a = 2.0 * s.a; s.i += 1;
+                s.a = ls_extrapolate(s.prev, t); s.prev = t; s.i += 1;
             }
             if (!s.done && s.phase == 1) s.a = ls_interp(s.lo, s.hi);
         } else {

@@ -323,6 +323,10 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (d->exec != EFWI_EXEC_PLAIN && d->exec != EFWI_EXEC_BATCHED) return fail(nullptr, EFWI_ERR_ARG, "unknown exec");
     if (d->ckpt_interval < EFWI_CKPT_AUTO)
         return fail(nullptr, EFWI_ERR_ARG, "ckpt_interval must be >= 0 or EFWI_CKPT_AUTO");
+    if (d->stored_steps < 0) return fail(nullptr, EFWI_ERR_ARG, "stored_steps must be >= 0");
+    if (d->stored_steps > 0 && d->overlap == EFWI_OVERLAP_ON && d->ckpt_interval != EFWI_CKPT_AUTO &&
+        d->ckpt_interval < d->nt)
+        return fail(nullptr, EFWI_ERR_ARG, "stored_steps > 0 cannot be combined with a forced overlap");
     if (d->snap_store < EFWI_STORE_FP32 || d->snap_store > EFWI_STORE_BF16)
         return fail(nullptr, EFWI_ERR_ARG, "unknown snap_store");
     if (d->snap_store != EFWI_STORE_FP32 && d->exec != EFWI_EXEC_BATCHED)
@@ -484,36 +488,54 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     // --- checkpoint schedule ---------------------------------------------------
     const size_t snap_el = p->snap_store == EFWI_STORE_FP32 ? 4 : 2;
     const size_t ck_el = p->ck.store == EFWI_STORE_FP32 ? 4 : 2;
-    // device bytes of K snapshot slots (with their maxima) and of ceil(nt / K) checkpoints
-    auto sched_bytes = [&](int k) {
-        const size_t nck = (size_t)((nt + k - 1) / k);
-        return (size_t)k * 2 * F * snap_el + (size_t)k * 2 * ns * kMaxPad * 4 +
-               nck * (5 * F * ck_el + 2 * p->H * 4 + 5 * ns * 4);
+    const size_t slot_bytes = 2 * F * snap_el + (size_t)2 * ns * kMaxPad * 4;
+    const size_t ck_bytes = 5 * F * ck_el + 2 * p->H * 4 + 5 * ns * 4;
+    // device bytes of a schedule: interval k, the steps before n_split recomputed
+    // from checkpoints (k slots), the rest kept by the forward pass
+    auto sched_bytes = [&](int k, int split) {
+        if (k >= nt) return (size_t)nt * slot_bytes + ck_bytes;
+        return (size_t)(k + nt - split) * slot_bytes + (size_t)((split + k - 1) / k) * ck_bytes;
     };
     int K = d->ckpt_interval;
     const int Ksqrt = std::min(nt, (int)std::ceil(std::sqrt((double)nt)));
+    int split = nt;
     if (K == EFWI_CKPT_AUTO) {
         size_t fr = 0, tot = 0;
+        K = Ksqrt;
         if (A.ok && cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
             const size_t keep = tot / 20 + (2ull << 30);
-            K = fr > keep && sched_bytes(nt) <= fr - keep ? nt : Ksqrt;
+            const size_t room = fr > keep ? fr - keep : 0;
+            if (sched_bytes(nt, 0) <= room) {
+                K = nt;
+            } else if (K < nt && d->overlap != EFWI_OVERLAP_ON) {
+                // fewest recomputed segments whose schedule fits
+                for (int m = 1; m * K < nt; ++m)
+                    if (sched_bytes(K, m * K) <= room) { split = m * K; break; }
+            }
         } else {
             cudaGetLastError();
-            K = Ksqrt;
+        }
+    } else {
+        if (K == 0) K = Ksqrt;
+        K = std::min(K, nt);
+        if (K < nt && d->stored_steps > 0) {
+            const long long first = std::max(0LL, (long long)nt - d->stored_steps);
+            split = (int)std::min((long long)nt, (first + K - 1) / K * K);
         }
     }
-    if (K == 0) K = Ksqrt;
-    K = std::min(K, nt);
+    if (K < nt && split == 0) K = nt;          // every step kept: the full-storage schedule
     p->K = K;
-    p->ck.n = (nt + K - 1) / K;
+    p->n_split = K >= nt ? 0 : split;
+    p->ck.n = K >= nt ? 1 : (p->n_split + K - 1) / K;
+    p->nslots = K >= nt ? nt : K + (nt - p->n_split);
     // the second half of the segment buffer exists only if the autotuner keeps the
     // overlapped recompute/adjoint schedule (or the caller forces it)
     p->seg_double = false;
     if (p->snap_store == EFWI_STORE_FP32) {
-        A(&p->seg, (size_t)K * 2 * F, "segment buffer");
+        A(&p->seg, (size_t)p->nslots * 2 * F, "snapshot slots");
     } else {
-        A((__half **)&p->segh, (size_t)K * 2 * F, "FP16/BF16 snapshots");
-        A(&p->segmax, (size_t)K * 2 * ns * kMaxPad, "snapshot maxima");
+        A((__half **)&p->segh, (size_t)p->nslots * 2 * F, "FP16/BF16 snapshots");
+        A(&p->segmax, (size_t)p->nslots * 2 * ns * kMaxPad, "snapshot maxima");
     }
     const size_t nck_el = (size_t)p->ck.n * 5 * F;
     if (p->ck.store == EFWI_STORE_FP32) A((float **)&p->ck.fields, nck_el, "checkpoints");
@@ -603,6 +625,7 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     if (!p || !info) return fail(nullptr, EFWI_ERR_ARG, "NULL argument");
     info->ckpt_interval = p->K;
     info->n_ckpt = p->ck.n;
+    info->stored_steps = p->d.nt - p->n_split;
     info->tile_x = p->tile_x;
     info->tile_z = p->tile_z;
     info->adj_tile_x = p->adj_tile_x;

@@ -109,10 +109,16 @@ struct efwi_plan {
     float *resid = nullptr;                // [ntr][nt]
     float *dbuf = nullptr;                 // [ntr][nt]
     double *partial = nullptr;             // reduction scratch
-    float *seg = nullptr;                  // segment buffer: (1 or 2) x K x 2 x fsz_total (FP32 snapshots)
+    // Snapshot slots, one per kept step v^{n+1/2} (x and z planes): slots 0 .. K-1 hold the
+    // segment being recomputed (two such halves with the overlapped schedule), slots
+    // K + (n - n_split) the steps n >= n_split that the forward pass keeps; with every
+    // step stored (K >= nt) slot n is step n.
+    float *seg = nullptr;                  // FP32 snapshots: nslots x 2 x fsz_total
     int snap_store = EFWI_STORE_FP32;      // precision of the stored forward velocities
-    void *segh = nullptr;                  // FP16/BF16 snapshots: K x 2 x fsz_total elements of 2 bytes
-    float *segmax = nullptr;               // their maxima: K x [2][ns][kMaxPad] floats
+    void *segh = nullptr;                  // FP16/BF16 snapshots: nslots x 2 x fsz_total elements of 2 bytes
+    float *segmax = nullptr;               // their maxima: nslots x [2][ns][kMaxPad] floats
+    int nslots = 0;                        // snapshot slots allocated
+    int n_split = 0;                       // first step the forward pass keeps (0 with K >= nt, nt for none)
     efwi::CkptStore ck;
     float *zoi_b = nullptr, *zoi_bp = nullptr;   // zone-of-influence weights held by the plan (efwi_plan_set_zoi)
     uint8_t *zoi_sink = nullptr;

@@ -100,6 +100,8 @@ def _desc(p, **over):
     ({"snap_store": 5}, -1, "snap_store"),
     ({"snap_store": 1, "exec": 0}, -1, "EXEC_BATCHED"),
     ({"snap_store": 2, "overlap": 2}, -1, "FP32 snapshots"),
+    ({"stored_steps": -1}, -1, "stored_steps"),
+    ({"stored_steps": 10, "overlap": 2}, -1, "forced overlap"),
 ])
 def test_plan_create_rejects_bad_descriptions(lib, over, code, msg):
     d, keep = _desc(W.tiny(), **over)

@@ -60,9 +60,9 @@ def test_roofline_entries_from_kernel_timings(monkeypatch):
     peak, kind = bench.peaks()
     info = {"padded_cells": 1_000_000, "ckpt_interval": 64, "stencil": 3, "adj_stencil": 1, "tile_x": 32,
             "tile_z": 16, "adj_tile_x": 32, "adj_tile_z": 16, "layout": 3, "staged_stores": 0, "adj_persistent": 1,
-            "snap_store": 0}
-    monkeypatch.setattr(bench, "TRAFFIC_PER_CELL", {("step", 3, 32, 16, 3, 0, 0, 0): 55.0,
-                                                    ("adj", 1, 32, 16, 1, 0, 0): 95.0})
+            "snap_store": 0, "stored_steps": 0}
+    monkeypatch.setattr(bench, "TRAFFIC_PER_CELL", {("step", 3, 32, 16, 3, 0, 0): {"pass": 50.0, "keep": 60.0},
+                                                    ("adj", 1, 32, 16, 1, 0): 95.0})
     prof = {"step": (10.0, 100), "adj": (20.0, 50)}          # ms summed, launches timed
     first, second = bench.roofline("batched", info, prof, nt=4000, ns=32)
     step = first if first["kernel"].startswith("forward") else second
@@ -86,6 +86,14 @@ def test_roofline_entries_from_kernel_timings(monkeypatch):
     r3 = {r["kernel"].split(" ")[0]: r for r in bench.roofline("batched", info3, prof, nt=4000, ns=32)}
     assert r3["forward_step"]["bytes_per_cell"] == 64.0 and r3["adjoint_step"]["bytes_per_cell"] == 104.0
     assert r3["forward_step"]["traffic"] is None             # captured with other snapshots
+    # sqrt(nt) checkpoints with the final 3000 steps kept by the forward pass: 5000 forward
+    # launches (4000 + 1000 recomputed), 4000 of which keep v: 60 + 8 x 4000 / 5000 B;
+    # traffic mixes 1000 passes at 50 B with 4000 keeps at 60 B
+    info4 = dict(info, stored_steps=3000)
+    r4 = {r["kernel"].split(" ")[0]: r for r in bench.roofline("batched", info4, prof, nt=4000, ns=32)}
+    assert abs(r4["forward_step"]["bytes_per_cell"] - 66.4) < 1e-12
+    assert abs(r4["forward_step"]["traffic"] - (1000 * 50.0 + 4000 * 60.0) / 5000 * 1e6) < 1e-6
+    assert abs(r4["adjoint_step"]["time_share_est"] - 1.6 / (1.6 + 0.5)) < 1e-12
 
 
 def test_gradient_roofline_bytes_and_fractions():
@@ -96,7 +104,7 @@ def test_gradient_roofline_bytes_and_fractions():
     sys.path.insert(0, ROOT)
     import bench
     peak, _ = bench.peaks()
-    info = {"padded_cells": 2_000_000, "ckpt_interval": 64}
+    info = {"padded_cells": 2_000_000, "ckpt_interval": 64, "stored_steps": 0}
     r = bench.gradient_roofline(info, nt=4000, s_per_grad=2.0)
     work = 2e6 * 4000 / 2.0 / 1e9
     assert r["bytes_per_cell_step"] == 236.0 and abs(r["achieved"] - 236.0 * work) < 1e-9
@@ -107,3 +115,6 @@ def test_gradient_roofline_bytes_and_fractions():
     half = bench.gradient_roofline(dict(info, ckpt_interval=4000, snap_store=1), nt=4000, s_per_grad=2.0)
     assert half["bytes_per_cell_step"] == 168.0 and half["snapshots"] == "fp16"
     assert bench.gradient_roofline(dict(info, snap_store=2), nt=4000, s_per_grad=2.0)["bytes_per_cell_step"] == 228.0
+    # the final 3000 steps kept by the forward pass: 1000 recomputed steps, 176 + 60 / 4 B
+    part = bench.gradient_roofline(dict(info, stored_steps=3000), nt=4000, s_per_grad=2.0)
+    assert part["bytes_per_cell_step"] == 191.0 and "final 3000" in part["schedule"]

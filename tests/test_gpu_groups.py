@@ -134,12 +134,14 @@ def test_group_set_objective_equals_rebound_plans(efwi):
     plan.close()
 
 
-@pytest.mark.parametrize("step0", [0.0, 1e-3])
+@pytest.mark.parametrize("step0", [0.0, 1e-3, 1.0])
 def test_device_line_search_matches_host_line_search(efwi, step0):
     """Three l-BFGS iterations of the 6-source problem in groups: the line search as a
     device state machine replayed from a CUDA graph (efwi_lbfgs_iterate_device)
     against the host line search (efwi_lbfgs_iterate) on the same objective: the same
-    accepted steps and evaluation counts, the same iterates and objective values."""
+    accepted steps and evaluation counts, the same iterates and objective values.
+    A first trial of the model's own length (step0 = 1) makes the modelling
+    unstable; both searches must back off from the non-finite trial alike."""
     from paper_2305_14130_gb300.groups import GroupSet
     from paper_2305_14130_gb300.optim import LBFGS
     p, acqs = _three_groups()

@@ -106,6 +106,53 @@ def test_iterations_match_oracle_on_a_quadratic(efwi):
     opt.close()
 
 
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_search_backs_off_from_non_finite_trials(efwi, bad):
+    """phi(x) = (x_0 - 1)^2 + 1 + 1/2 |x_1..|^2, not finite for x_0 >= 3 (as an unstable
+    simulation gives); the first trial moves x by 8 along d = -g and lands there.
+    The device iteration takes the oracle's trial points and accepted step."""
+    from paper_2305_14130_gb300.optim import LBFGS
+    n = 5
+    trials = []
+
+    def obj(x, g):
+        xv = x.double().cpu().numpy()
+        trials.append(float(xv[0]))
+        if xv[0] >= 3.0:
+            g.fill_(bad)
+            return bad
+        gv = xv.copy()
+        gv[0] = 2.0 * (xv[0] - 1.0)
+        g.copy_(torch.tensor(gv, dtype=torch.float32))
+        return float((xv[0] - 1.0) ** 2 + 1.0 + 0.5 * np.sum(xv[1:] ** 2))
+
+    ref_trials = []
+
+    def f(x):
+        ref_trials.append(float(x[0]))
+        if x[0] >= 3.0:
+            return bad, np.full(n, bad)
+        gv = x.copy()
+        gv[0] = 2.0 * (x[0] - 1.0)
+        return float((x[0] - 1.0) ** 2 + 1.0 + 0.5 * np.sum(x[1:] ** 2)), gv
+
+    x0 = np.zeros(n)
+    phi0, g0 = f(x0)
+    d = -g0
+    a_ref, phi_ref, _, evals_ref = L.wolfe_search(f, x0, phi0, g0, d, 8.0 / np.linalg.norm(d))
+    opt = LBFGS(n, m=5)
+    opt.set_step0(8.0)
+    x = torch.zeros(n, device="cuda")
+    g = torch.empty(n, device="cuda")
+    phi = obj(x, g)
+    phi, info = opt.iterate(x, phi, g, obj)
+    assert not info["ls_failed"] and info["evals"] == evals_ref
+    assert trials[1:] == pytest.approx(ref_trials[1:], rel=1e-6)
+    assert trials[1] >= 3.0 and phi == pytest.approx(phi_ref, rel=1e-6)
+    assert info["alpha"] == pytest.approx(a_ref, rel=1e-6)
+    opt.close()
+
+
 def test_run_stops_on_the_eq13_rate(efwi):
     from paper_2305_14130_gb300.optim import LBFGS
     n = 4096

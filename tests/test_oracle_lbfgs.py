@@ -111,6 +111,50 @@ def test_lbfgs_minimises_a_convex_quadratic_and_reports_eq13_rates():
         assert r["phi"] <= phis[k]
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_search_backs_off_from_non_finite_trials(bad):
+    """phi(x) = (x - 1)^2 + 1 is defined only for x < 3 (beyond, a value that is not
+    finite, as an unstable simulation gives).  From x = 0 along d = 1 with first trial
+    a = 8 the search must bisect back into [0, 3) and return a strong-Wolfe step
+    there: phi(a) <= phi0 + c1 a phi'(0) and |phi'(a)| <= c2 |phi'(0)|."""
+    calls = []
+
+    def f(x):
+        calls.append(float(x[0]))
+        if x[0] >= 3.0:
+            return bad, np.array([bad])
+        return float((x[0] - 1.0) ** 2 + 1.0), np.array([2.0 * (x[0] - 1.0)])
+    x0 = np.zeros(1)
+    phi0, g0 = f(x0)
+    d = np.ones(1)
+    c1, c2 = 1e-4, 0.9
+    a, phi, g, evals = L.wolfe_search(f, x0, phi0, g0, d, 8.0, c1, c2, max_ls=20)
+    assert a is not None and 0 < a < 3.0
+    assert phi <= phi0 + c1 * a * (g0 @ d)
+    assert abs(g @ d) <= -c2 * (g0 @ d)
+    # 8 and 4 are not finite: the bracket [0, 8] is halved twice; at 2 the sufficient
+    # decrease fails (phi(2) = phi(0)), and the quadratic through phi(0), phi'(0), phi(2)
+    # has its minimum at 1, the exact minimiser
+    assert calls[1:] == [8.0, 4.0, 2.0, 1.0] and evals == 4 and a == 1.0
+
+
+def test_bracketing_extrapolates_by_the_secant_of_the_slope():
+    """phi(x) = (x - 50)^2 from x = 0 along d = 1, first trial 1: phi'(0) = -100 and
+    phi'(1) = -98, whose secant vanishes at 50, clipped to 10 x the step; at 10 the
+    secant through (1, -98), (10, -80) vanishes at 50 (within [20, 100]): the exact
+    minimiser, where phi' = 0 meets the curvature condition (c2 = 0.1, so that 10,
+    with |phi'| = 80, does not)."""
+    calls = []
+
+    def f(x):
+        calls.append(float(x[0]))
+        return float((x[0] - 50.0) ** 2), np.array([2.0 * (x[0] - 50.0)])
+    x0 = np.zeros(1)
+    phi0, g0 = f(x0)
+    a, phi, g, evals = L.wolfe_search(f, x0, phi0, g0, np.ones(1), 1.0, c2=0.1)
+    assert calls[1:] == [1.0, 10.0, 50.0] and evals == 3 and a == 50.0 and phi == 0.0
+
+
 def test_failed_search_keeps_the_point():
     """A direction of ascent never satisfies the sufficient decrease."""
     def f(x):
