@@ -151,3 +151,32 @@ def test_guided_wave_stored_steps_bitwise(efwi):
         plan.close()
     for a, b in zip(*outs):
         assert torch.equal(a, b)
+
+
+def test_guided_wave_full_size_auto_schedule_equals_sqrt(efwi):
+    """The bench's workload and launch configuration at full size (1000x300, 32 shots,
+    4000 steps, ckpt_interval = auto, which keeps the final steps that fit the device):
+    the gradient equals the sqrt(nt) schedule's bit for bit, and the schedule keeps
+    most of the steps (the rest of HBM holds their velocities)."""
+    p = rounded(W.guided_wave_1000x300())
+    acq = p.acq
+    m = (dev(p.vp), dev(p.vs), dev(p.rho))
+    ns = acq.ns
+    tv = lambda x: dev(np.repeat(np.asarray(x)[None], ns, 0))
+    outs, infos = [], []
+    d_obs = None
+    for ck in (0, "auto"):
+        plan = efwi.Plan(acq, exec="batched", ckpt_interval=ck)
+        if d_obs is None:
+            d_obs = plan.forward(tv(p.true_vp), tv(p.true_vs), tv(p.true_rho)).clone()
+        outs.append([t.clone() for t in plan.gradient(*m, d_obs, return_data=True)])
+        infos.append(plan.info())
+        plan.sync_status()
+        plan.close()
+        torch.cuda.empty_cache()
+    assert infos[0]["stored_steps"] == 0
+    K = infos[1]["ckpt_interval"]
+    assert K < acq.nt and infos[1]["stored_steps"] >= acq.nt // 2
+    assert (acq.nt - infos[1]["stored_steps"]) % K == 0
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
