@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--adj-stencil", default="auto", choices=["auto", "loads", "tma"])
     ap.add_argument("--adj-tile", default="0x0", help="adjoint tile (0x0 = autotune)")
     ap.add_argument("--overlap", default="auto", choices=["auto", "off", "on"])
+    ap.add_argument("--adj-form", default="auto", choices=["auto", "stress", "scaled"],
+                    help="adjoint stress variable: sigma^ (stress) or F = dt C sigma^ (scaled)")
     ap.add_argument("--no-reduced", action="store_true", help="skip the reduced-storage record")
     ap.add_argument("--full-iteration-groups", type=int, default=1,
                     help="shot groups of the 4000x1200 full-iteration record to time (16 = all; 0 = skip)")
@@ -137,7 +139,9 @@ def peaks():
 #     a launch that keeps v^{n+1/2} for the adjoint also writes vx, vz once more (8 B in FP32,
 #     4 B as FP16/BF16 snapshots)
 #   fused adjoint step: read 5 adjoint fields + 5 materials + 5 imaging sums, write 5 + 5
-#     = 100 B, plus the forward vx, vz of the step (8 B FP32, 4 B FP16/BF16)
+#     = 100 B, plus the forward vx, vz of the step (8 B FP32, 4 B FP16/BF16); the same in
+#     the scaled-stress form, whose 5 adjoint fields hold v^ and F = dt C sigma^ and whose
+#     materials (b_x, b_z on the velocity halo, lambda, mu, mu_xz on the tile) are read once
 #   plain stress half-step: read vx vz + 3 stresses + lambda mu mu_xz, write 3 = 44 B
 #   plain adjoint stress half-step: read 2 + 2 + 3 + 3 + 2 + 3, write 3 + 3 = 84 B
 KERNELS = {
@@ -190,11 +194,11 @@ def kernel_bytes(exec_, info, nt):
 TRAFFIC_PER_CELL = {
     # forward step, TMA cell pairs, tile 32x16
     ("step", 3, 32, 16, 3, 0, 0): {"pass": 54.99, "keep": 60.31},
-    # adjoint step, per-thread loads, tile 32x16, persistent grid, FP32 velocities
-    ("adj", 1, 32, 16, 1, 0): 94.97,
+    # adjoint step (stress form), per-thread loads, tile 32x16, persistent grid, FP32 velocities
+    ("adj", 1, 32, 16, 1, 1, 0): 94.97,
     # the same two with FP16 snapshots (every step stored)
     ("step", 3, 32, 16, 3, 0, 1): {"keep": 57.57},
-    ("adj", 1, 32, 16, 1, 1): 90.35,
+    ("adj", 1, 32, 16, 1, 1, 1): 90.35,
 }
 
 
@@ -249,6 +253,8 @@ def roofline(exec_, info, prof, nt, ns):
                 staging += ", halo ring as single cells"
             if k == "adj" and kind == 1 and info["adj_persistent"]:
                 staging += ", persistent grid"
+            if k == "adj" and info.get("adj_form", 1) == 2:
+                staging = "scaled-stress form, " + staging
             name = f"{name.split(' ')[0]} [{staging}, tile {tile[0]}x{tile[1]}] {' '.join(name.split(' ')[1:])}"
         avg = ms / n / 1e3
         achieved = bpc * cells / avg / 1e9
@@ -260,7 +266,7 @@ def roofline(exec_, info, prof, nt, ns):
             if k == "step" and info["stencil"] >= 2:
                 key = key + (info["layout"], info["staged_stores"])
             if k == "adj" and info["adj_stencil"] == 1:
-                key = key + (info["adj_persistent"],)
+                key = key + (info["adj_persistent"], info.get("adj_form", 1))
             key = key + (info.get("snap_store", 0),)
             t = TRAFFIC_PER_CELL.get(key)
             if isinstance(t, dict):
@@ -436,7 +442,7 @@ def sqrt_schedule(efwi, acq, m, d_obs, zoi, eta, ref, args):
     equal the headline schedule's bit for bit (ref: phi, g_vp, g_vs, g_rho)."""
     import torch
     plan = efwi.Plan(acq, exec="batched", ckpt_store=args.ckpt_store, snap_store=args.snap_store,
-                     ckpt_interval=0, overlap=args.overlap)
+                     ckpt_interval=0, overlap=args.overlap, adj_form=args.adj_form)
     b, bp, sink = zoi
     g = tuple(torch.empty_like(m[0]) for _ in range(3))
 
@@ -644,7 +650,7 @@ def run_ours(args):
     plan = efwi.Plan(acq, exec=args.exec, ckpt_store=args.ckpt_store, stencil=args.stencil, tile=tile,
                      adj_stencil=args.adj_stencil, adj_tile=adj_tile, overlap=args.overlap,
                      snap_store=args.snap_store, ckpt_interval=args.ckpt if args.ckpt == "auto" else int(args.ckpt),
-                     stored_steps=args.stored_steps)
+                     stored_steps=args.stored_steps, adj_form=args.adj_form)
     # observed data: the same sources in the model with the Gaussian anomaly
     ns = acq.ns
     tv = lambda m: dev(np.repeat(np.asarray(m)[None], ns, 0))
@@ -784,6 +790,7 @@ def run_ours(args):
                            "adj_tile": [info["adj_tile_x"], info["adj_tile_z"]],
                            "stencil": {1: "loads", 2: "tma", 3: "tma_pairs", 4: "tma_staged"}.get(info["stencil"], "?"), "stages": info["stages"], "layout": info["layout"],
                            "adj_stencil": {1: "loads", 2: "tma"}.get(info["adj_stencil"], "?"),
+                           "adj_form": {1: "stress", 2: "scaled"}.get(info["adj_form"], "?"),
                            "adj_stages": info["adj_stages"], "l2_prefetch": info["prefetch"],
                            "overlap_blocks_per_sm": [info["overlap_fwd_blocks"], info["overlap_adj_blocks"]],
                            "l2": "working set > L2 (wavefields, checkpoints, data >> 129 MB)",

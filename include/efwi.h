@@ -66,8 +66,9 @@ enum efwi_status {
     EFWI_ERR_OOM = -3,              /* device allocation failed at plan creation */
     EFWI_ERR_CUDA = -4,             /* a CUDA runtime call or kernel launch failed */
     EFWI_ERR_TIMEOUT = -5,          /* a bounded device-side wait expired */
-    EFWI_ERR_NAN = -6,              /* a model held a non-finite value or a non-positive density
-                                       (reported by efwi_sync_status) */
+    EFWI_ERR_NAN = -6,              /* a model held a non-finite value or a non-positive density,
+                                       or a gradient's model a zero shear modulus where the
+                                       gradient divides by it (reported by efwi_sync_status) */
     EFWI_ERR_NOT_IMPLEMENTED = -7
 };
 
@@ -99,6 +100,20 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
                     EFWI_STENCIL_TMA_PAIRS = 3 /* TMA, two adjacent cells per thread (forward step) */,
                     EFWI_STENCIL_TMA_STAGED = 4 /* TMA_PAIRS with the tile's outputs staged in shared
                                                    memory and written by bulk tensor stores (forward) */ };
+/* the variable in which the batched adjoint step carries the adjoint stresses:
+ *   STRESS  sigma^ itself (every staging and tile of the adjoint; EXEC_PLAIN always)
+ *   SCALED  F = dt C sigma^ (C the cell's stiffness), which the transposed step only
+ *           ever uses through C, so a step needs the stiffness on the tile alone and
+ *           no pass over the 4-cell halo to form C sigma^ (per-thread loads; the
+ *           imaging sums are converted back once per gradient).  Needs lambda + mu > 0
+ *           (Vp > Vs) and mu > 0 on the physical cells and the half cells next to
+ *           them; a gradient of a model without it is flagged (efwi_sync_status:
+ *           EFWI_ERR_NAN).  Either form's chain rule needs mu > 0 on the physical
+ *           cells, which every gradient call checks.
+ *   AUTO    SCALED with EXEC_BATCHED unless adj_stencil asks for TMA, else STRESS
+ * The two forms agree up to FP32 rounding (not bit for bit); all tiles of one form
+ * give bitwise-identical results.                                                */
+enum efwi_adj_form { EFWI_ADJ_FORM_AUTO = 0, EFWI_ADJ_FORM_STRESS = 1, EFWI_ADJ_FORM_SCALED = 2 };
 
 /*
  * Problem description (host memory; copied by efwi_plan_create).
@@ -166,6 +181,7 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *                      bit for bit with FP32 checkpoints (the imaging sums are
  *                      folded at the same segment ends).  Not combinable with a
  *                      forced overlapped schedule.
+ *   adj_form           EFWI_ADJ_FORM_*: the adjoint step's stress variable (above)
  */
 typedef struct efwi_plan_desc {
     int nx, nz;
@@ -197,6 +213,7 @@ typedef struct efwi_plan_desc {
     const double *force;
     int snap_store;
     int stored_steps;
+    int adj_form;
 } efwi_plan_desc;
 
 /* What a plan chose and holds (filled by efwi_plan_info). */
@@ -225,6 +242,7 @@ typedef struct efwi_plan_info_t {
     int prefetch;               /* L2 prefetch one tile ahead: bit 0 forward step, bit 1 adjoint step */
     int stored_steps;           /* final steps whose velocities the forward pass keeps
                                    (nt with every step stored, 0 for the sqrt(nt) schedule) */
+    int adj_form;               /* EFWI_ADJ_FORM_STRESS or _SCALED: the adjoint step in use */
 } efwi_plan_info_t;
 
 /* Zone-of-influence description (eq. 10), host memory.  Per source s:
@@ -284,7 +302,9 @@ int efwi_plan_rebind(efwi_plan *plan, const efwi_plan_desc *desc, efwi_stream_t 
  * this plan: EFWI_ERR_TIMEOUT if a kernel gave up a bounded wait (its results
  * are then invalid), EFWI_ERR_NAN if a model passed to a call held a
  * non-finite velocity or density or a non-positive density (checked on every
- * cell the call's materials read), EFWI_ERR_CUDA for an asynchronous CUDA
+ * cell the call's materials read) or, in a gradient call, mu <= 0 (or, with
+ * the scaled-stress adjoint, lambda + mu <= 0) where the gradient divides by
+ * it (efwi_adj_form), EFWI_ERR_CUDA for an asynchronous CUDA
  * error.  The device flag is cleared.                                        */
 int efwi_sync_status(efwi_plan *plan, efwi_stream_t stream);
 

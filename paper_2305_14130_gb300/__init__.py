@@ -23,7 +23,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import EfwiError, STORE, EXEC, STENCIL, OVERLAP, CKPT_AUTO
+from ._abi import EfwiError, STORE, EXEC, STENCIL, OVERLAP, ADJ_FORM, CKPT_AUTO
 
 __all__ = ["Plan", "zoi_weights", "collapse", "EfwiError", "load_library", "DataMisfit", "Consistency",
            "ExtendedFWI", "extended_objective"]
@@ -76,15 +76,19 @@ class Plan:
     K-step segments before them), which the adjoint then reads without a
     recompute.  ``snap_store``: precision of those stored forward
     velocities ("fp32", "fp16", "bf16"; the latter two need exec="batched").
+    ``adj_form``: the adjoint step's stress variable -- "scaled" (F = dt C
+    sigma^, per-thread loads; needs Vs > 0 and Vp > Vs on the imaging area),
+    "stress" (sigma^ itself, every staging) or "auto" (scaled with
+    exec="batched" unless adj_stencil asks for TMA).
     """
 
     def __init__(self, acq, exec: str = "batched", ckpt_interval=0, ckpt_store: str = "fp32",
                  tile=(0, 0), stencil: str = "auto", adj_tile=(0, 0), adj_stencil: str = "auto",
-                 overlap: str = "auto", snap_store: str = "fp32", stored_steps: int = 0):
+                 overlap: str = "auto", snap_store: str = "fp32", stored_steps: int = 0, adj_form: str = "auto"):
         lib = _abi.load()
         self._opts = dict(exec=exec, ckpt_interval=ckpt_interval, ckpt_store=ckpt_store, tile=tile, stencil=stencil,
                           adj_tile=adj_tile, adj_stencil=adj_stencil, overlap=overlap, snap_store=snap_store,
-                          stored_steps=stored_steps)
+                          stored_steps=stored_steps, adj_form=adj_form)
         d, keep = self._desc(acq)
         self.exec, self.ckpt_store, self.snap_store = exec, ckpt_store, snap_store
         h = C.c_void_p()
@@ -144,6 +148,7 @@ class Plan:
         d.adj_stencil = STENCIL[o["adj_stencil"]]
         d.overlap = OVERLAP[o["overlap"]]
         d.force = P(keep["force"], C.c_double)
+        d.adj_form = ADJ_FORM[o["adj_form"]]
         return d, keep
 
     def rebind(self, acq):

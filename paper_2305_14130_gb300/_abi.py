@@ -14,6 +14,7 @@ STORE = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXEC = {"plain": 0, "batched": 1}
 STENCIL = {"auto": 0, "loads": 1, "tma": 2, "tma_pairs": 3, "tma_staged": 4}
 OVERLAP = {"auto": 0, "off": 1, "on": 2}
+ADJ_FORM = {"auto": 0, "stress": 1, "scaled": 2}
 CKPT_AUTO = -1
 
 PD = C.POINTER(C.c_double)
@@ -31,7 +32,7 @@ class PlanDesc(C.Structure):
                 ("ckpt_store", C.c_int), ("exec", C.c_int), ("tile_x", C.c_int), ("tile_z", C.c_int),
                 ("stencil", C.c_int), ("adj_tile_x", C.c_int), ("adj_tile_z", C.c_int), ("adj_stencil", C.c_int),
                 ("overlap", C.c_int), ("force", PD), ("snap_store", C.c_int),
-                ("stored_steps", C.c_int)]
+                ("stored_steps", C.c_int), ("adj_form", C.c_int)]
 
 
 class PlanInfo(C.Structure):
@@ -42,7 +43,7 @@ class PlanInfo(C.Structure):
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong), ("layout", C.c_int),
                 ("staged_stores", C.c_int), ("adj_persistent", C.c_int), ("snap_store", C.c_int),
-                ("prefetch", C.c_int), ("stored_steps", C.c_int)]
+                ("prefetch", C.c_int), ("stored_steps", C.c_int), ("adj_form", C.c_int)]
 
 
 class ZoiDesc(C.Structure):

@@ -32,6 +32,7 @@
 #define EFWI_FLAG_TIMEOUT 1      // a kernel gave up a bounded wait
 #define EFWI_FLAG_BAD_MODEL 2    // a model value was not finite, or a density not positive
 #define EFWI_FLAG_SELFTEST 4     // the timeout self-test's wait expired (as intended)
+#define EFWI_FLAG_SHEAR 8        // a gradient call met mu <= 0 (or lambda + mu <= 0, scaled-stress adjoint)
 
 #define EFWI_GX 4
 #define EFWI_GZ 2

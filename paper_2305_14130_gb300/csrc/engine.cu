@@ -336,7 +336,7 @@ extern "C" int efwi_adjoint_gradient(efwi_plan *p, const float *vp, const float 
     cudaStream_t st = (cudaStream_t)stream;
     p->launches = 0;
     float *d = d_out ? d_out : p->dbuf;
-    launch_materials(p, vp, vs, rho, st);
+    launch_materials(p, vp, vs, rho, st, 1);
     if ((rc = run_forward(p, d, true, st))) return rc;
     {
         Phase ph("efwi residual and misfit");
@@ -346,6 +346,8 @@ extern "C" int efwi_adjoint_gradient(efwi_plan *p, const float *vp, const float 
     if ((rc = run_adjoint(p, st))) return rc;
     Phase ph("efwi chain rule");
     float *src = p->Gtot ? p->Gtot : p->G;
+    // the scaled-stress adjoint's sums (A, B, C_s) to the stress form's (lambda, mu, mu_xz)
+    if (p->adj_form == EFWI_ADJ_FORM_SCALED) launch_imag_unscale(p, src, st);
     const float *G[5];
     for (int k = 0; k < 5; ++k) G[k] = src + k * p->fsz_total;
     launch_chain_rule(p, vp, vs, rho, G, mask, g_vp, g_vs, g_rho, st);

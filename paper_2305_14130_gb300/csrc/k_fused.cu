@@ -26,6 +26,7 @@
 
 #include "plan.hpp"
 #include "tma.cuh"
+#include "adj_args.cuh"
 
 namespace efwi {
 namespace {
@@ -209,41 +210,6 @@ __global__ void __launch_bounds__(kThreads) k_step_fused(FwdArgs a) {
         }
         __syncthreads();
     }
-}
-
-struct AdjArgsF {
-    const ShotDev *shots;
-    const int4 *tiles;
-    int ntiles;
-    Fields in, out;             // adjoint fields
-    Mat M;
-    Pml pml;                    // current adjoint PML memory (V and S blocks, read)
-    float *n1, *n3, *n2, *n4;   // next V block
-    float *n5, *n8, *n6, *n7;   // next S block
-    const float *vfx, *vfz;     // forward v^{n+1/2} (FP32), or
-    SnapR sr;                   // its reduced-precision snapshot (sr.h non-null)
-    float *Glam, *Gmu, *Gmuxz, *Gbx, *Gbz;
-    float dt, rdx, rdz;
-    // L2 prefetch of the CTA's next tile (persistent grid): tensor maps, on/off, the
-    // read adjoint buffer's first field, the forward velocities' first field (-1: none)
-    const AdjMaps *maps;
-    int pf, acur5, sgf;
-};
-
-// Read-only load that asks L2 to fetch the 256-byte block around the address: the
-// adjacent 128 bytes of a row belong to the neighbouring tile, read soon after.
-// Coherent load (the imaging sums are read, then written by the same thread) with the
-// same 256-byte L2 fetch.
-__device__ __forceinline__ float ld256(const float *p) {
-    float v;
-    asm("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ float ldg256(const float *p) {
-    float v;
-    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
 }
 
 template <int TX, int TZ, int SK = 0>
@@ -647,6 +613,9 @@ FwdArgs fwd_args(efwi_plan *p, int n, const SnapOut &so) {
     return a;
 }
 
+
+}  // namespace
+
 AdjArgsF adj_args_f(efwi_plan *p, const SnapIn &si) {
     const float *vfx = si.fx, *vfz = si.fz;
     AdjArgsF a;
@@ -675,8 +644,6 @@ AdjArgsF adj_args_f(efwi_plan *p, const SnapIn &si) {
     return a;
 }
 
-}  // namespace
-
 void launch_step_fused(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st) {
     int slot;
     prof_begin(p, st, &slot, EFWI_KERNEL_STEP);
@@ -699,6 +666,8 @@ void launch_adj_fused(efwi_plan *p, int n, const SnapIn &si, cudaStream_t st) {
     prof_begin(p, st, &slot, EFWI_KERNEL_ADJ);
     if (p->adj_stencil == EFWI_STENCIL_TMA) {
         launch_adj_tma(p, si.fx, st);         // FP32 snapshots only (the autotuner's candidates)
+    } else if (p->adj_form == EFWI_ADJ_FORM_SCALED) {
+        launch_adj_scaled(p, si, st);
     } else {
         AdjArgsF a = adj_args_f(p, si);
         const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles)
@@ -749,7 +718,9 @@ float time_steps(efwi_plan *p, bool adj, cudaStream_t st, cudaEvent_t e0, cudaEv
 int select_adj(efwi_plan *p, const Variant &v) {
     p->adj_stencil = v.kind;
     p->adj_grid = 0;
-    if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2 && v.tx == 32 && v.tz == 16) {   // loads: vec 2 = persistent
+    if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2 && p->adj_form == EFWI_ADJ_FORM_SCALED) {
+        p->adj_grid = std::max(1, adj_scaled_blocks_per_sm(v.tx, v.tz, p->snap_store)) * p->n_sms;
+    } else if (v.kind == EFWI_STENCIL_LOADS && v.vec == 2 && v.tx == 32 && v.tz == 16) {   // loads: vec 2 = persistent
         int nb = 0;
         if (p->snap_store == EFWI_STORE_FP16)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_fused<32, 16, EFWI_STORE_FP16>, kThreads,
@@ -803,9 +774,32 @@ int efwi_autotune(efwi_plan *p) {
                         fwd.push_back({kind, s.tx, s.tz, nst, vec, stg});
             }
     }
+    // the adjoint's stress variable: the scaled form (per-thread loads) unless the stress
+    // form is asked for, or a TMA adjoint (which exists in the stress form only)
+    p->adj_form = p->d.adj_form == EFWI_ADJ_FORM_STRESS ? EFWI_ADJ_FORM_STRESS
+                  : p->d.adj_form == EFWI_ADJ_FORM_SCALED ? EFWI_ADJ_FORM_SCALED
+                  : (want_a == EFWI_STENCIL_AUTO || want_a == EFWI_STENCIL_LOADS) ? EFWI_ADJ_FORM_SCALED
+                                                                                   : EFWI_ADJ_FORM_STRESS;
+    const bool scaled = p->adj_form == EFWI_ADJ_FORM_SCALED;
+    if (scaled) adj_scaled_set_attrs();
     // the adjoint follows its own request, or the forward one when it has none
     const int wa = want_a != EFWI_STENCIL_AUTO ? want_a : want;
     for (auto &s : kShapes) {
+        if (!scaled) break;
+        if (!adj_scaled_shape_ok(s.tx, s.tz) || (fixed_a && (s.tx != p->adj_tile_x || s.tz != p->adj_tile_z)))
+            continue;
+        // 32x16 also on a persistent grid; EFWI_ADJ_PERSIST=0|1 keeps only one of the two
+        const char *fp = getenv("EFWI_ADJ_PERSIST");
+        const int only_p = fp ? atoi(fp) : -1;
+        if (only_p <= 0 || !(s.tx == 32 && s.tz == 16)) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+        if (s.tx == 32 && s.tz == 16 && only_p != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
+    }
+    if (scaled && adj.empty()) {
+        p->err = "the scaled-stress adjoint is compiled for tiles 32x8 32x16 64x8 64x16 (per-thread loads)";
+        return EFWI_ERR_ARG;
+    }
+    for (auto &s : kShapes) {
+        if (scaled) break;
         if (fixed_a ? (s.tx != p->adj_tile_x || s.tz != p->adj_tile_z)
                     : (fixed && (s.tx != p->tile_x || s.tz != p->tile_z)))
             continue;
@@ -825,7 +819,7 @@ int efwi_autotune(efwi_plan *p) {
     for (auto &s : kShapes) {
         if (fwd.empty() && (!fixed || (s.tx == p->tile_x && s.tz == p->tile_z)))
             fwd.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-        if (adj.empty() && (!fixed_a || (s.tx == p->adj_tile_x && s.tz == p->adj_tile_z)))
+        if (adj.empty() && !scaled && (!fixed_a || (s.tx == p->adj_tile_x && s.tz == p->adj_tile_z)))
             adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
     }
     if (fwd.empty() || adj.empty()) {
@@ -877,6 +871,7 @@ int efwi_autotune(efwi_plan *p) {
         p->tma_pf = p->adj_pf = 0;
         const bool fwd_ok = !rc && p->stencil >= EFWI_STENCIL_TMA;
         const bool adj_ok = !rc && p->adj_stencil == EFWI_STENCIL_LOADS && p->adj_grid > 0 &&
+                            p->adj_form == EFWI_ADJ_FORM_STRESS &&
                             tma_encode_adj_maps(p, p->adj_tile_x, p->adj_tile_z) == EFWI_OK;
         if (force_pf >= 0) {
             p->tma_pf = fwd_ok && force_pf;

@@ -22,6 +22,9 @@ struct MatArgs {
     Mat M;                              // outputs (const-cast inside)
     int nx, nz, shot;
     int *err;                           // device flag: bit 2 set for a non-finite or invalid model value
+    int shear;                          // a gradient call: flag mu <= 0 where the chain rule divides by it
+                                        // (1: stress-form adjoint) or where the scaled-stress adjoint's
+                                        // sums are converted, also lambda + mu <= 0 (2) (EFWI_FLAG_SHEAR)
 };
 
 __device__ void model_at(const MatArgs &a, const ShotDev &s, int shot, int i, int j, float &vp, float &vs,
@@ -62,7 +65,17 @@ __global__ void k_materials(MatArgs a) {
     if (!(isfinite(vp) && isfinite(vs) && isfinite(rho) && rho > 0.f)) atomicOr(a.err, EFWI_FLAG_BAD_MODEL);
     const long long c = cell_of(s, i, j);
     const bool zero = mu[0] == 0.f || mu[1] == 0.f || mu[2] == 0.f || mu[3] == 0.f;
-    ((float *)a.M.lam)[c] = rho * (vp * vp - 2.f * vs * vs);
+    const float lam = rho * (vp * vp - 2.f * vs * vs);
+    // the chain rule divides by mu on the physical nodes (the harmonic mean's derivative);
+    // the scaled-stress adjoint's sums are divided by 2 (lambda + mu), 2 mu and mu_xz on the
+    // physical nodes and the half cells next to them (nodes P-1 .. P+w, P-1 .. NZ-P)
+    if (a.shear) {
+        const int lo = a.shear == 2 ? s.P - 1 : s.P;
+        if (i >= lo && i <= s.P + s.w - (a.shear == 2 ? 0 : 1) && j >= lo &&
+            j <= s.NZ - s.P - (a.shear == 2 ? 0 : 1) && !(mu[0] > 0.f && (a.shear == 1 || lam + mu[0] > 0.f)))
+            atomicOr(a.err, EFWI_FLAG_SHEAR);
+    }
+    ((float *)a.M.lam)[c] = lam;
     ((float *)a.M.mu)[c] = mu[0];
     ((float *)a.M.muxz)[c] = zero ? 0.f : 4.f / (1.f / mu[0] + 1.f / mu[1] + 1.f / mu[2] + 1.f / mu[3]);
     ((float *)a.M.bx)[c] = 0.5f * (1.f / r[0] + 1.f / r[1]);
@@ -406,8 +419,10 @@ __global__ void k_reg(const float *m, const float *b, const float *bp, const uin
 // Launchers
 // ==========================================================================
 
-void launch_materials(efwi_plan *p, const float *vp, const float *vs, const float *rho, cudaStream_t st) {
-    MatArgs a{p->shots_d, vp, vs, rho, p->ref, materials(p), p->d.nx, p->d.nz, -1, p->dev_err};
+void launch_materials(efwi_plan *p, const float *vp, const float *vs, const float *rho, cudaStream_t st,
+                      int gradient) {
+    MatArgs a{p->shots_d, vp, vs, rho, p->ref, materials(p), p->d.nx, p->d.nz, -1, p->dev_err,
+              !gradient ? 0 : p->adj_form == EFWI_ADJ_FORM_SCALED ? 2 : 1};
     dim3 b(32, 8);
     dim3 g((p->max_nx + 31) / 32, (p->nzp + 7) / 8, p->d.ns);
     k_materials<<<g, b, 0, st>>>(a);

@@ -347,6 +347,12 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
         return fail(nullptr, EFWI_ERR_ARG, "adj_tile_x and adj_tile_z must both be 0 or both positive");
     if (d->overlap < EFWI_OVERLAP_AUTO || d->overlap > EFWI_OVERLAP_ON)
         return fail(nullptr, EFWI_ERR_ARG, "unknown overlap");
+    if (d->adj_form < EFWI_ADJ_FORM_AUTO || d->adj_form > EFWI_ADJ_FORM_SCALED)
+        return fail(nullptr, EFWI_ERR_ARG, "unknown adj_form");
+    if (d->adj_form == EFWI_ADJ_FORM_SCALED &&
+        (d->exec != EFWI_EXEC_BATCHED || (d->adj_stencil != EFWI_STENCIL_AUTO && d->adj_stencil != EFWI_STENCIL_LOADS)))
+        return fail(nullptr, EFWI_ERR_ARG, "the scaled-stress adjoint needs EXEC_BATCHED and per-thread loads "
+                                           "(adj_stencil AUTO or LOADS)");
     if (d->force)
         for (int k = 0; k < 2 * d->ns; ++k)
             if (!std::isfinite(d->force[k])) return fail(nullptr, EFWI_ERR_ARG, "force components must be finite");
@@ -645,6 +651,7 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->adj_persistent = p->adj_stencil == EFWI_STENCIL_LOADS && p->adj_grid > 0;
     info->snap_store = p->snap_store;
     info->prefetch = (p->stencil >= EFWI_STENCIL_TMA && p->tma_pf ? 1 : 0) | (p->adj_pf ? 2 : 0);
+    info->adj_form = p->adj_form;
     return EFWI_OK;
 }
 
@@ -665,6 +672,10 @@ extern "C" int efwi_sync_status(efwi_plan *p, efwi_stream_t stream) {
         }
         if (flag & EFWI_FLAG_SELFTEST)
             return fail(p, EFWI_ERR_TIMEOUT, "the timeout self-test's bounded wait expired (as intended)");
+        if (flag & EFWI_FLAG_SHEAR)
+            return fail(p, EFWI_ERR_NAN, "a gradient needs mu > 0 (Vs > 0) on the physical cells, and the scaled-stress "
+                                         "adjoint also lambda + mu > 0 (Vp > Vs) there and on the half cells next "
+                                         "to them; the gradient of that call is invalid");
         return fail(p, EFWI_ERR_NAN, "the model holds a non-finite value or a non-positive density; results of "
                                      "that call are invalid");
     }

@@ -133,6 +133,7 @@ struct efwi_plan {
     int tma_pf = 0;                        // forward step: L2 prefetch of the tile beyond the pipeline
     int adj_pf = 0;                        // per-thread-load adjoint: L2 prefetch of the CTA's next tile
     int adj_stencil = EFWI_STENCIL_LOADS;  // staging of the adjoint step (after tuning)
+    int adj_form = EFWI_ADJ_FORM_STRESS;   // adjoint stress variable in use (EFWI_ADJ_FORM_STRESS / _SCALED)
     efwi::AdjMaps *adj_maps = nullptr;
     int tma_adj_grid = 0, tma_adj_stages = 1;
     int adj_grid = 0;                      // per-thread-load adjoint: persistent grid (0 = one CTA per tile)
@@ -170,7 +171,9 @@ namespace efwi {
 constexpr int kPartials = 1024;            // blocks of the FP64 reductions
 
 // --- k_misc.cu ---------------------------------------------------------------
-void launch_materials(efwi_plan *p, const float *vp, const float *vs, const float *rho, cudaStream_t st);
+// gradient = 1: the call images (the shear-modulus check of the chain rule and the adjoint applies)
+void launch_materials(efwi_plan *p, const float *vp, const float *vs, const float *rho, cudaStream_t st,
+                      int gradient = 0);
 void launch_inject(efwi_plan *p, Fields F, int n, int shot /* -1 = all */, cudaStream_t st);
 void launch_force(efwi_plan *p, Fields F, int n, int shot, float *segx, float *segz, cudaStream_t st);
 void launch_das_fwd(efwi_plan *p, Fields F, int n, float *d, int shot, cudaStream_t st);
@@ -211,6 +214,14 @@ bool tma_adj_shape_ok(int tx, int tz, int nst);
 int tma_prepare_adj(efwi_plan *p, int tx, int tz, int nst);
 int tma_encode_adj_maps(efwi_plan *p, int tx, int tz);
 void launch_adj_tma(efwi_plan *p, const float *vfx, cudaStream_t st);
+
+// --- k_adjs.cu (adjoint step in scaled-stress form) ----------------------------
+bool adj_scaled_shape_ok(int tx, int tz);
+void adj_scaled_set_attrs();
+int adj_scaled_blocks_per_sm(int tx, int tz, int snap_store);
+void launch_adj_scaled(efwi_plan *p, const SnapIn &si, cudaStream_t st);
+// G: the plan's 5 imaging fields; converts the first three in place to the stress form's sums
+void launch_imag_unscale(efwi_plan *p, float *G, cudaStream_t st);
 
 // --- k_fused.cu --------------------------------------------------------------
 void launch_step_fused(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st);

@@ -82,3 +82,26 @@ def test_forced_allocation_failure(efwi, monkeypatch):
     from oracle import elastic as E
     assert rel_l2(d.cpu().numpy(), E.forward(p.acq, p.vp, p.vs, p.rho)) <= 1e-4
     plan.close()
+
+
+def test_zero_shear_modulus_is_reported_by_gradients(efwi):
+    """A gradient divides by the shear modulus (the chain rule through the harmonic
+    mean mu_xz, and the scaled-stress adjoint's conversion of its sums): a cell with
+    Vs = 0 on the physical grid is reported by a gradient call, in either adjoint
+    form, and not by forward modelling, which needs no mu > 0."""
+    p, m = _problem()
+    mb = [t.clone() for t in m]
+    mb[1][0, 14, 20] = 0.0
+    for form in ("scaled", "stress"):
+        plan = efwi.Plan(p.acq, exec="batched", adj_form=form)
+        d_obs = plan.forward(*m).clone()
+        plan.forward(*mb)
+        plan.sync_status()
+        plan.gradient(*mb, d_obs)
+        with pytest.raises(efwi.EfwiError) as e:
+            plan.sync_status()
+        assert e.value.code == ERR_NAN and "mu > 0" in str(e.value)
+        phi, *g = plan.gradient(*m, d_obs)                # the valid model afterwards: no error
+        plan.sync_status()
+        assert float(phi.item()) == 0.0
+        plan.close()
