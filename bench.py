@@ -265,8 +265,9 @@ def roofline(exec_, info, prof, nt, ns):
                    info["tile_z"] if k == "step" else info["adj_tile_z"])
             if k == "step" and info["stencil"] >= 2:
                 key = key + (info["layout"], info["staged_stores"])
-            if k == "adj" and info["adj_stencil"] == 1:
-                key = key + (info["adj_persistent"], info.get("adj_form", 1))
+            if k == "adj":
+                key = key + ((info["adj_persistent"],) if info["adj_stencil"] == 1 else ()) + \
+                    (info.get("adj_form", 1),)
             key = key + (info.get("snap_store", 0),)
             t = TRAFFIC_PER_CELL.get(key)
             if isinstance(t, dict):

@@ -77,9 +77,10 @@ class Plan:
     recompute.  ``snap_store``: precision of those stored forward
     velocities ("fp32", "fp16", "bf16"; the latter two need exec="batched").
     ``adj_form``: the adjoint step's stress variable -- "scaled" (F = dt C
-    sigma^, per-thread loads; needs Vs > 0 and Vp > Vs on the imaging area),
-    "stress" (sigma^ itself, every staging) or "auto" (scaled with
-    exec="batched" unless adj_stencil asks for TMA).
+    sigma^; per-thread loads, or TMA staging with FP32 snapshots; needs Vp > Vs
+    on the imaging area), "stress" (sigma^ itself, every staging) or "auto"
+    (scaled with exec="batched" unless the requested adjoint staging exists in
+    the stress form only).
     """
 
     def __init__(self, acq, exec: str = "batched", ckpt_interval=0, ckpt_store: str = "fp32",

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(LIBDIR, "libefwi_gb300.so")
-SOURCES = ["plan.cu", "engine.cu", "k_plain.cu", "k_misc.cu", "k_fused.cu", "k_tma.cu", "lbfgs.cu", "k_noalloc.cu", "k_hessian.cu", "groups.cu", "k_adjs.cu"]
+SOURCES = ["plan.cu", "engine.cu", "k_plain.cu", "k_misc.cu", "k_fused.cu", "k_tma.cu", "lbfgs.cu", "k_noalloc.cu", "k_hessian.cu", "groups.cu", "k_adjs.cu", "k_adjs_tma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no implicit multiply-add contraction, so every kernel (plain and
 # fused, every tile-shape instantiation) rounds each expression identically and

@@ -664,10 +664,11 @@ void launch_adj_fused(efwi_plan *p, int n, const SnapIn &si, cudaStream_t st) {
     (void)n;
     int slot;
     prof_begin(p, st, &slot, EFWI_KERNEL_ADJ);
-    if (p->adj_stencil == EFWI_STENCIL_TMA) {
+    if (p->adj_form == EFWI_ADJ_FORM_SCALED) {
+        if (p->adj_stencil == EFWI_STENCIL_TMA) launch_adj_scaled_tma(p, si, st);   // FP32 snapshots only
+        else launch_adj_scaled(p, si, st);
+    } else if (p->adj_stencil == EFWI_STENCIL_TMA) {
         launch_adj_tma(p, si.fx, st);         // FP32 snapshots only (the autotuner's candidates)
-    } else if (p->adj_form == EFWI_ADJ_FORM_SCALED) {
-        launch_adj_scaled(p, si, st);
     } else {
         AdjArgsF a = adj_args_f(p, si);
         const int grid = p->grid_adj_override > 0 ? std::min(p->grid_adj_override, a.ntiles)
@@ -733,7 +734,9 @@ int select_adj(efwi_plan *p, const Variant &v) {
         p->adj_grid = std::max(1, nb) * p->n_sms;
     }
     int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
-    if (!rc && v.kind == EFWI_STENCIL_TMA) rc = tma_prepare_adj(p, v.tx, v.tz, v.nst);
+    if (!rc && v.kind == EFWI_STENCIL_TMA)
+        rc = p->adj_form == EFWI_ADJ_FORM_SCALED ? adj_scaled_tma_prepare(p, v.tx, v.tz)
+                                                 : tma_prepare_adj(p, v.tx, v.tz, v.nst);
     p->adj_tile_x = v.tx;
     p->adj_tile_z = v.tz;
     return rc;
@@ -776,26 +779,34 @@ int efwi_autotune(efwi_plan *p) {
     }
     // the adjoint's stress variable: the scaled form (per-thread loads) unless the stress
     // form is asked for, or a TMA adjoint (which exists in the stress form only)
+    //  (TMA staging of the scaled form reads FP32 forward velocities only)
+    const bool fp32v = p->snap_store == EFWI_STORE_FP32;
     p->adj_form = p->d.adj_form == EFWI_ADJ_FORM_STRESS ? EFWI_ADJ_FORM_STRESS
                   : p->d.adj_form == EFWI_ADJ_FORM_SCALED ? EFWI_ADJ_FORM_SCALED
-                  : (want_a == EFWI_STENCIL_AUTO || want_a == EFWI_STENCIL_LOADS) ? EFWI_ADJ_FORM_SCALED
-                                                                                   : EFWI_ADJ_FORM_STRESS;
+                  : (want_a == EFWI_STENCIL_AUTO || want_a == EFWI_STENCIL_LOADS ||
+                     (want_a == EFWI_STENCIL_TMA && fp32v)) ? EFWI_ADJ_FORM_SCALED
+                                                            : EFWI_ADJ_FORM_STRESS;
     const bool scaled = p->adj_form == EFWI_ADJ_FORM_SCALED;
     if (scaled) adj_scaled_set_attrs();
     // the adjoint follows its own request, or the forward one when it has none
     const int wa = want_a != EFWI_STENCIL_AUTO ? want_a : want;
     for (auto &s : kShapes) {
         if (!scaled) break;
-        if (!adj_scaled_shape_ok(s.tx, s.tz) || (fixed_a && (s.tx != p->adj_tile_x || s.tz != p->adj_tile_z)))
-            continue;
-        // 32x16 also on a persistent grid; EFWI_ADJ_PERSIST=0|1 keeps only one of the two
+        if (fixed_a && (s.tx != p->adj_tile_x || s.tz != p->adj_tile_z)) continue;
+        // per-thread loads: every compiled tile, 32x16 also on a persistent grid
+        // (EFWI_ADJ_PERSIST=0|1 keeps only one of the two); TMA staging: 32x16
         const char *fp = getenv("EFWI_ADJ_PERSIST");
         const int only_p = fp ? atoi(fp) : -1;
-        if (only_p <= 0 || !(s.tx == 32 && s.tz == 16)) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
-        if (s.tx == 32 && s.tz == 16 && only_p != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
+        if (want_a != EFWI_STENCIL_TMA && adj_scaled_shape_ok(s.tx, s.tz)) {
+            if (only_p <= 0 || !(s.tx == 32 && s.tz == 16)) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
+            if (s.tx == 32 && s.tz == 16 && only_p != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
+        }
+        if (want_a != EFWI_STENCIL_LOADS && fp32v && adj_scaled_tma_shape_ok(s.tx, s.tz))
+            adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, 2});
     }
     if (scaled && adj.empty()) {
-        p->err = "the scaled-stress adjoint is compiled for tiles 32x8 32x16 64x8 64x16 (per-thread loads)";
+        p->err = "no scaled-stress adjoint variant matches the request (per-thread loads: tiles 32x8 32x16 64x8 "
+                 "64x16; TMA: 32x16 with FP32 snapshots)";
         return EFWI_ERR_ARG;
     }
     for (auto &s : kShapes) {

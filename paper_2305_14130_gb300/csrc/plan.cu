@@ -283,7 +283,7 @@ static void commit_acq(efwi_plan *p, const AcqHost &h) {
 
 static void free_plan(efwi_plan *p) {
     if (!p) return;
-    void *ptrs[] = {p->shots_d, p->state[0], p->mat, p->adj[0], p->fwd_maps, p->adj_maps, p->dev_err, p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
+    void *ptrs[] = {p->shots_d, p->state[0], p->mat, p->adj[0], p->fwd_maps, p->adj_maps, p->adjs_maps, p->dev_err, p->G, p->Gtot, p->Gcmp, p->psi, p->apsi,
                     p->prof, p->dw, p->wv, p->ref, p->tr_shot, p->tr_off, p->tr_w, p->tr_acc, p->tr_coef,
                     p->gather.tgt_shot, p->gather.tgt_field, p->gather.tgt_off, p->gather.ptr, p->gather.tr,
                     p->gather.w, p->tiles.tiles, p->adj_tiles.tiles, p->resid, p->dbuf, p->partial, p->seg, p->ck.fields, p->ck.psi,
@@ -350,9 +350,9 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
     if (d->adj_form < EFWI_ADJ_FORM_AUTO || d->adj_form > EFWI_ADJ_FORM_SCALED)
         return fail(nullptr, EFWI_ERR_ARG, "unknown adj_form");
     if (d->adj_form == EFWI_ADJ_FORM_SCALED &&
-        (d->exec != EFWI_EXEC_BATCHED || (d->adj_stencil != EFWI_STENCIL_AUTO && d->adj_stencil != EFWI_STENCIL_LOADS)))
-        return fail(nullptr, EFWI_ERR_ARG, "the scaled-stress adjoint needs EXEC_BATCHED and per-thread loads "
-                                           "(adj_stencil AUTO or LOADS)");
+        (d->exec != EFWI_EXEC_BATCHED || d->adj_stencil > EFWI_STENCIL_TMA))
+        return fail(nullptr, EFWI_ERR_ARG, "the scaled-stress adjoint needs EXEC_BATCHED and adj_stencil AUTO, "
+                                           "LOADS or TMA");
     if (d->force)
         for (int k = 0; k < 2 * d->ns; ++k)
             if (!std::isfinite(d->force[k])) return fail(nullptr, EFWI_ERR_ARG, "force components must be finite");

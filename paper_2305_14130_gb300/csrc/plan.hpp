@@ -10,6 +10,7 @@ namespace efwi {
 
 struct FwdMaps;   // tensor maps of one shot (tma.cuh)
 struct AdjMaps;
+struct AdjsMaps;
 
 // Adjoint-source gather (the transpose of the DAS sampling): for every grid
 // cell touched by any gauge end, the list of (trace, weight) contributions,
@@ -135,6 +136,7 @@ struct efwi_plan {
     int adj_stencil = EFWI_STENCIL_LOADS;  // staging of the adjoint step (after tuning)
     int adj_form = EFWI_ADJ_FORM_STRESS;   // adjoint stress variable in use (EFWI_ADJ_FORM_STRESS / _SCALED)
     efwi::AdjMaps *adj_maps = nullptr;
+    efwi::AdjsMaps *adjs_maps = nullptr;   // [ns] tensor maps of the TMA scaled-stress adjoint
     int tma_adj_grid = 0, tma_adj_stages = 1;
     int adj_grid = 0;                      // per-thread-load adjoint: persistent grid (0 = one CTA per tile)
     int *dev_err = nullptr;                // device flag: a bounded wait expired
@@ -222,6 +224,10 @@ int adj_scaled_blocks_per_sm(int tx, int tz, int snap_store);
 void launch_adj_scaled(efwi_plan *p, const SnapIn &si, cudaStream_t st);
 // G: the plan's 5 imaging fields; converts the first three in place to the stress form's sums
 void launch_imag_unscale(efwi_plan *p, float *G, cudaStream_t st);
+// --- k_adjs_tma.cu (the same step with TMA staging, FP32 forward velocities) ----
+bool adj_scaled_tma_shape_ok(int tx, int tz);
+int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz);   // tensor maps, persistent grid
+void launch_adj_scaled_tma(efwi_plan *p, const SnapIn &si, cudaStream_t st);
 
 // --- k_fused.cu --------------------------------------------------------------
 void launch_step_fused(efwi_plan *p, int n, const SnapOut &so, cudaStream_t st);

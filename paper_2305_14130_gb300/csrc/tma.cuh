@@ -27,6 +27,21 @@ struct __align__(64) AdjMaps {
     CUtensorMap ad, m5, sg, gi;
 };
 
+// Tensor maps of one shot for the TMA adjoint step in scaled-stress form: boxes of the
+// tile + 4-cell halo in x and, in z, the rows each field's readers use (as FwdMaps):
+// a2: v^x, v^z (tile + 2 rows each side), a1: F_xx (the same rows), a3: F_zz or F_xz
+// (tile + 3 rows on one side, 4 on the other), mb: b_x, b_z, sv: the forward v_x, v_z
+// of the step (FP32 segment buffer; tile + 2 rows), mc: lambda, mu, mu_xz and gi: the
+// five imaging sums on the tile.
+struct __align__(64) AdjsMaps {
+    CUtensorMap a2, a1, a3, mb, mc, sv, gi;
+};
+
+struct ShotDev;
+// Encode a 3D map (x, row, field) over nfield arrays of F floats of the shot's block with
+// box bx x by x bz (k_tma.cu).
+int encode_map(CUtensorMap *m, float *base, const ShotDev &s, long long F, int nfield, int bx, int by, int bz);
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }

@@ -62,7 +62,7 @@ def test_roofline_entries_from_kernel_timings(monkeypatch):
             "tile_z": 16, "adj_tile_x": 32, "adj_tile_z": 16, "layout": 3, "staged_stores": 0, "adj_persistent": 1,
             "snap_store": 0, "stored_steps": 0}
     monkeypatch.setattr(bench, "TRAFFIC_PER_CELL", {("step", 3, 32, 16, 3, 0, 0): {"pass": 50.0, "keep": 60.0},
-                                                    ("adj", 1, 32, 16, 1, 0): 95.0})
+                                                    ("adj", 1, 32, 16, 1, 1, 0): 95.0})
     prof = {"step": (10.0, 100), "adj": (20.0, 50)}          # ms summed, launches timed
     first, second = bench.roofline("batched", info, prof, nt=4000, ns=32)
     step = first if first["kernel"].startswith("forward") else second
@@ -81,6 +81,10 @@ def test_roofline_entries_from_kernel_timings(monkeypatch):
     info2 = dict(info, layout=2)                             # a variant without a capture
     s2 = [r for r in bench.roofline("batched", info2, prof, nt=4000, ns=32) if r["kernel"].startswith("forward")][0]
     assert s2["traffic"] is None and s2["frac_traffic"] is None
+    # the scaled-stress adjoint is another kernel: no traffic from the stress form's capture
+    a2 = [r for r in bench.roofline("batched", dict(info, adj_form=2), prof, nt=4000, ns=32)
+          if r["kernel"].startswith("adjoint")][0]
+    assert a2["traffic"] is None and "scaled-stress" in a2["kernel"] and a2["bytes_per_cell"] == 108.0
     # every step stored with FP16 snapshots: 60 + 4 B forward, 100 + 4 B adjoint
     info3 = dict(info, ckpt_interval=4000, snap_store=1)
     r3 = {r["kernel"].split(" ")[0]: r for r in bench.roofline("batched", info3, prof, nt=4000, ns=32)}

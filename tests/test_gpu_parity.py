@@ -354,8 +354,10 @@ STAGED_SHAPES = [(32, 16)]
 VARIANTS = [("loads", s) for s in SHAPES] + [(k, s) for k in ("tma", "tma_pairs") for s in TMA_SHAPES] + \
     [("tma_staged", s) for s in STAGED_SHAPES] + [("tma_pairs:split", (32, 16)), ("tma_staged:split", (32, 16)),
                                                    ("loads:adjp", (32, 16))]
-# tiles of the scaled-stress adjoint (per-thread loads), one-CTA-per-tile or persistent grid
-SCALED_VARIANTS = [((32, 8), 0), ((32, 16), 0), ((32, 16), 1), ((64, 8), 0), ((64, 16), 0)]
+# the scaled-stress adjoint: per-thread loads on every tile, one CTA per tile or on a
+# persistent grid, and TMA staging (32x16, persistent grid)
+SCALED_VARIANTS = [((32, 8), 0, "loads"), ((32, 16), 0, "loads"), ((32, 16), 1, "loads"), ((64, 8), 0, "loads"),
+                   ((64, 16), 0, "loads"), ((32, 16), 0, "tma")]
 
 
 @pytest.mark.parametrize("source", ["moment_tensor", "force"])
@@ -370,10 +372,10 @@ def test_stencil_variants_do_not_change_results(efwi, source, monkeypatch):
         p = W.with_forces(p)
     d_obs = observed(p)
     args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
-    runs = [(stencil, tile, "stress", None, None) for stencil, tile in VARIANTS] + \
-        [("tma_pairs:split", (32, 16), "scaled", at, persist) for at, persist in SCALED_VARIANTS]
+    runs = [(stencil, tile, "stress", None, None, "auto") for stencil, tile in VARIANTS] + \
+        [("tma_pairs:split", (32, 16), "scaled", at, persist, ast) for at, persist, ast in SCALED_VARIANTS]
     ref = {}
-    for stencil, (tx, tz), form, adj_tile, persist in runs:
+    for stencil, (tx, tz), form, adj_tile, persist, adj_stencil in runs:
         # ":split": cell pairs on the tile, the velocity halo ring as single cells
         stencil, _, layout = stencil.partition(":")
         # ":adjp": the per-thread-load adjoint on a persistent grid
@@ -384,11 +386,11 @@ def test_stencil_variants_do_not_change_results(efwi, source, monkeypatch):
         adjp = layout == "adjp" if persist is None else persist == 1
         monkeypatch.setenv("EFWI_ADJ_PERSIST", "1" if adjp else "0")
         plan = efwi.Plan(p.acq, exec="batched", tile=(tx, tz), stencil=stencil, adj_form=form,
-                         adj_tile=adj_tile or (0, 0))
+                         adj_tile=adj_tile or (0, 0), adj_stencil=adj_stencil)
         info = plan.info()
         assert (info["tile_x"], info["tile_z"]) == (tx, tz)
         assert info["stencil"] == {"loads": 1, "tma": 2, "tma_pairs": 3, "tma_staged": 4}[stencil]
-        assert info["adj_stencil"] in ((1, 2) if form == "stress" else (1,))
+        assert info["adj_stencil"] in ((1, 2) if form == "stress" else ({"loads": 1, "tma": 2}[adj_stencil],))
         assert info["adj_form"] == {"stress": 1, "scaled": 2}[form]
         if adj_tile:
             assert (info["adj_tile_x"], info["adj_tile_z"], info["adj_persistent"]) == (*adj_tile, persist)
@@ -399,7 +401,7 @@ def test_stencil_variants_do_not_change_results(efwi, source, monkeypatch):
             ref[form] = out
         else:
             for a, b in zip(ref[form], out):
-                assert torch.equal(a, b), (stencil, tx, tz, form, adj_tile, persist)
+                assert torch.equal(a, b), (stencil, tx, tz, form, adj_tile, persist, adj_stencil)
     # across the two adjoint forms: the same data and misfit, gradients within FP32 rounding
     a, b = ref["stress"], ref["scaled"]
     assert torch.equal(a[0], b[0]) and torch.equal(a[4], b[4])
@@ -421,20 +423,28 @@ def test_tma_full_size_matches_loads(efwi, monkeypatch):
     m = (dev(p.vp), dev(p.vs), dev(p.rho))
     outs = []
     d_obs = torch.zeros((acq.ntr, acq.nt), device="cuda")
-    for stencil in ("loads", "tma", "tma_pairs", "tma_staged", "tma_pairs:split", "tma_pairs:split:scaled"):
+    for stencil in ("loads", "tma", "tma_pairs", "tma_staged", "tma_pairs:split", "tma_pairs:split:scaled-loads",
+                    "tma_pairs:split:scaled-tma"):
         stencil, _, layout = stencil.partition(":")
         layout, _, form = layout.partition(":")
+        form, _, adj_stencil = form.partition("-")
         if layout == "split":
             monkeypatch.setenv("EFWI_TMA_VEC", "3")
-        plan = efwi.Plan(acq, exec="batched", stencil=stencil, ckpt_interval=30, adj_form=form or "stress")
+        plan = efwi.Plan(acq, exec="batched", stencil=stencil, ckpt_interval=30, adj_form=form or "stress",
+                         adj_stencil=adj_stencil or "auto")
+        if form:
+            assert plan.info()["adj_stencil"] == {"loads": 1, "tma": 2}[adj_stencil]
         outs.append([t.clone() for t in plan.gradient(*m, d_obs, return_data=True)])
         plan.sync_status()
         plan.close()
     # the stress-form runs (TMA adjoint with the TMA forward steps) bit for bit
-    for o in outs[1:-1]:
+    for o in outs[1:-2]:
         for a, b in zip(outs[0], o):
             assert torch.equal(a, b)
-    # the scaled-stress adjoint: the same data and misfit, gradients within FP32 rounding
+    # the scaled-stress adjoint's two stagings bit for bit, and against the stress form the
+    # same data and misfit, gradients within FP32 rounding
+    for a, b in zip(outs[-2], outs[-1]):
+        assert torch.equal(a, b)
     a, b = outs[0], outs[-1]
     assert torch.equal(a[0], b[0]) and torch.equal(a[4], b[4])
     for x, y in zip(a[1:4], b[1:4]):
