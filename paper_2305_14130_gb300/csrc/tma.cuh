@@ -46,8 +46,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ float *align128(void *p) {
-    return reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(p) + 127) & ~(uintptr_t)127);
+// The first 128-byte aligned float of a dynamic shared-memory array, as an offset from
+// the array itself: the pointer stays derived from the __shared__ symbol, so the
+// compiler keeps shared-memory loads and stores (a round trip through an integer would
+// leave it generic addresses, which the hardware resolves at every access).
+__device__ __forceinline__ float *align128(float4 *p) {
+    const uint32_t a = smem_u32(p);
+    return reinterpret_cast<float *>(p) + ((((a + 127u) & ~127u) - a) >> 2);
 }
 
 __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
