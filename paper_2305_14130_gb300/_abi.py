@@ -43,7 +43,8 @@ class PlanInfo(C.Structure):
                 ("workspace_bytes", C.c_size_t), ("padded_cells", C.c_longlong),
                 ("physical_cells", C.c_longlong), ("launches", C.c_longlong), ("layout", C.c_int),
                 ("staged_stores", C.c_int), ("adj_persistent", C.c_int), ("snap_store", C.c_int),
-                ("prefetch", C.c_int), ("stored_steps", C.c_int), ("adj_form", C.c_int)]
+                ("prefetch", C.c_int), ("stored_steps", C.c_int), ("adj_form", C.c_int),
+                ("adj_layout", C.c_int)]
 
 
 class ZoiDesc(C.Structure):

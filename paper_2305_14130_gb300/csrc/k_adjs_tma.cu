@@ -10,7 +10,8 @@
 // strip, the stress-sub-step CPML terms are added to the staged F in place (the tile's
 // F kept for its update); v^ += D^T F on the tile + 2-cell halo with e^ = dt b v^ (+
 // CPML) written over the staged v^; F += dt C (-D^T e^) on the tile with the imaging.
-// Every expression is k_adj_scaled's, so both give bitwise-identical results.
+// Every expression is k_adj_scaled's, so both give bitwise-identical results; so does the
+// cell-pair layout (VEC = 2), whose adjacent x-stencils share 64-bit shared-memory loads.
 // Out-of-range box elements are zero-filled by the copy engine, as the zero ghosts of
 // the layout.  Every mbarrier wait is bounded; on expiry the CTA records the error,
 // waits (bounded) for the copy it still has in flight and returns.
@@ -82,7 +83,12 @@ __device__ __forceinline__ void issue_adjs(const TmaAdjsArgs &a, int t, float *b
     tma_load_3d(buf + L::OG, &m->gi, bar, tl.y + 4, tl.z + 2, 0);        // imaging sums: tile
 }
 
-template <int TX, int TZ>
+// C1 (a - b) + C2 (c - d): the 4th-order staggered difference, one rounding per operation
+__device__ __forceinline__ float st4(float a, float b, float c, float d) { return C1 * (a - b) + C2 * (c - d); }
+
+// VEC = 1: one cell per thread and iteration; VEC = 2: cell pairs with 64-bit shared-memory
+// accesses (one pair of the tile per thread, the velocity halo ring as single cells)
+template <int TX, int TZ, int VEC>
 __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
     using L = AdjsLayout<TX, TZ>;
     constexpr int SX = L::SX, NC = L::NC;
@@ -194,54 +200,121 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                 __syncthreads();
             }
 
-            // 2. v^ += D^T f^ on the tile + 2-cell halo; e^ over the staged v^
-            constexpr int VX = TX + 4, VZ = TZ + 4;
-            for (int q = tid; q < VX * VZ; q += kThreads) {
-                const int yv = q / VX, xv = q - yv * VX;
-                const int i = i0 - 2 + xv, j = j0 - 2 + yv;
-                const int o = (yv + 2) * SX + (xv + 2);
+            // the velocity-sub-step adjoint CPML terms of cell (i, j) and, for an own cell, its memory
+            auto vel_pml = [&](const int i, const int j, const bool own, const float qx, const float qz, float &h1,
+                               float &h2, float &h3, float &h4) {
+                const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
+                const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
+                if (xs >= 0) {
+                    const long long kk = psx + (long long)j * 2 * PP + xs;
+                    const int pq = profx + i;
+                    const float P1 = a.pml.x[0][kk], P3 = a.pml.x[1][kk];
+                    h1 += a.pml.ax_h[pq] * (P1 + qx);
+                    h3 += a.pml.ax_i[pq] * (P3 + qz);
+                    if (own) {
+                        a.n1[kk] = a.pml.bx_h[pq] * (P1 + qx);
+                        a.n3[kk] = a.pml.bx_i[pq] * (P3 + qz);
+                    }
+                }
+                if (zs >= 0) {
+                    const long long kk = psz + (long long)zs * NX + i;
+                    const float P2 = a.pml.z[0][kk], P4 = a.pml.z[1][kk];
+                    h2 += a.pml.az_i[j] * (P2 + qx);
+                    h4 += a.pml.az_h[j] * (P4 + qz);
+                    if (own) {
+                        a.n2[kk] = a.pml.bz_i[j] * (P2 + qx);
+                        a.n4[kk] = a.pml.bz_h[j] * (P4 + qz);
+                    }
+                }
+            };
+            // the cell pair (x, x+1) of the tile at halo-4 row y, x even: every cell's expression
+            // is vcell's, term by term
+            auto vpair = [&](const int x, const int y) {
+                const int i = i0 - 4 + x, j = j0 - 4 + y;
+                const int o = y * SX + x;
+                const float2 a0 = ld2(fxx + o - 2), a1 = ld2(fxx + o), a2 = ld2(fxx + o + 2);
+                const float2 zm2 = ld2(fxz + o - 2 * SX), zm1 = ld2(fxz + o - SX), z0 = ld2(fxz + o),
+                             zp1 = ld2(fxz + o + SX);
+                const float2 cm1 = ld2(fzz + o - SX), c0 = ld2(fzz + o), cp1 = ld2(fzz + o + SX),
+                             cp2 = ld2(fzz + o + 2 * SX);
+                const float2 b0 = ld2(g4 + o - 2), b1 = ld2(g4 + o), b2 = ld2(g4 + o + 2);
+                float inc_x[2], inc_z[2];
+                inc_x[0] = -st4(a1.y, a1.x, a2.x, a0.y) * rdx - st4(z0.x, zm1.x, zp1.x, zm2.x) * rdz;
+                inc_x[1] = -st4(a2.x, a1.y, a2.y, a1.x) * rdx - st4(z0.y, zm1.y, zp1.y, zm2.y) * rdz;
+                inc_z[0] = -st4(cp1.x, c0.x, cp2.x, cm1.x) * rdz - st4(b1.x, b0.y, b1.y, b0.x) * rdx;
+                inc_z[1] = -st4(cp1.y, c0.y, cp2.y, cm1.y) * rdz - st4(b1.y, b1.x, b2.x, b0.y) * rdx;
+                const float2 vxo = ld2(svx + o), vzo = ld2(svz + o), bxo = ld2(sbx + o), bzo = ld2(sbz + o);
+                const float vx[2] = {vxo.x + inc_x[0], vxo.y + inc_x[1]};
+                const float vz[2] = {vzo.x + inc_z[0], vzo.y + inc_z[1]};
+                const float bxv[2] = {bxo.x, bxo.y}, bzv[2] = {bzo.x, bzo.y};
+                float h1[2], h2[2], h3[2], h4[2];
+                bool in[2] = {true, true};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float qx = dt * bxv[h] * vx[h], qz = dt * bzv[h] * vz[h];
+                    h1[h] = qx; h2[h] = qx; h3[h] = qz; h4[h] = qz;
+                    if (edge) {
+                        in[h] = i + h < NX && j < NZ;
+                        if (in[h]) vel_pml(i + h, j, true, qx, qz, h1[h], h2[h], h3[h], h4[h]);
+                        else h1[h] = h2[h] = h3[h] = h4[h] = 0.f;
+                    }
+                }
+                const long long c = off + (long long)(j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                const int u = (y - 4) * TX + (x - 4);
+                const float2 gbx = ld2(sg + 3 * NC + u), gbz = ld2(sg + 4 * NC + u);
+                const float2 fvx = ld2(wvx + o), fvz = ld2(wvz + o);
+                if (!edge) {
+                    st2g(a.out.vx + c, make_float2(vx[0], vx[1]));
+                    st2g(a.out.vz + c, make_float2(vz[0], vz[1]));
+                    st2g(a.Gbx + c, make_float2(gbx.x + fvx.x * inc_x[0], gbx.y + fvx.y * inc_x[1]));
+                    st2g(a.Gbz + c, make_float2(gbz.x + fvz.x * inc_z[0], gbz.y + fvz.y * inc_z[1]));
+                } else {
+                    const float gbxv[2] = {gbx.x, gbx.y}, gbzv[2] = {gbz.x, gbz.y};
+                    const float fvxv[2] = {fvx.x, fvx.y}, fvzv[2] = {fvz.x, fvz.y};
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (!in[h]) continue;
+                        const int ih = i + h;
+                        a.out.vx[c + h] = vx[h];
+                        a.out.vz[c + h] = vz[h];
+                        if (ih >= PP - 1 && ih <= PP + w && j >= PP - 1 && j <= NZ - PP) {
+                            a.Gbx[c + h] = gbxv[h] + fvxv[h] * inc_x[h];
+                            a.Gbz[c + h] = gbzv[h] + fvzv[h] * inc_z[h];
+                        }
+                    }
+                }
+                st2(svx + o, make_float2(h1[0], h1[1]));
+                st2(svz + o, make_float2(h3[0], h3[1]));
+                if (edge) {
+                    st2(e2w + o, make_float2(h2[0], h2[1]));
+                    st2(e4w + o, make_float2(h4[0], h4[1]));
+                }
+            };
+
+            // 2. v^ += D^T f^ on the tile + 2-cell halo; e^ over the staged v^.  One cell at
+            //    halo-4 (x, y): the tile's cells are own (outputs, imaging, CPML memory), the
+            //    ring around them is only staged for the update below.
+            auto vcell = [&](const int x, const int y) {
+                const int i = i0 - 4 + x, j = j0 - 4 + y;
+                const int o = y * SX + x;
                 float h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f;
                 if (!edge || (i >= 0 && i < NX && j >= 0 && j < NZ)) {
-                    const float inc_x = -(C1 * (fxx[o + 1] - fxx[o]) + C2 * (fxx[o + 2] - fxx[o - 1])) * rdx
-                                        - (C1 * (fxz[o] - fxz[o - SX]) + C2 * (fxz[o + SX] - fxz[o - 2 * SX])) * rdz;
-                    const float inc_z = -(C1 * (fzz[o + SX] - fzz[o]) + C2 * (fzz[o + 2 * SX] - fzz[o - SX])) * rdz
-                                        - (C1 * (g4[o] - g4[o - 1]) + C2 * (g4[o + 1] - g4[o - 2])) * rdx;
+                    const float inc_x = -st4(fxx[o + 1], fxx[o], fxx[o + 2], fxx[o - 1]) * rdx
+                                        - st4(fxz[o], fxz[o - SX], fxz[o + SX], fxz[o - 2 * SX]) * rdz;
+                    const float inc_z = -st4(fzz[o + SX], fzz[o], fzz[o + 2 * SX], fzz[o - SX]) * rdz
+                                        - st4(g4[o], g4[o - 1], g4[o + 1], g4[o - 2]) * rdx;
                     const float vx = svx[o] + inc_x;
                     const float vz = svz[o] + inc_z;
                     const float qx = dt * sbx[o] * vx, qz = dt * sbz[o] * vz;
                     h1 = qx; h2 = qx; h3 = qz; h4 = qz;
-                    const bool own = xv >= 2 && xv < TX + 2 && yv >= 2 && yv < TZ + 2 && (!edge || (i < NX && j < NZ));
-                    if (edge) {
-                        const int xs = i < PP ? i : (i >= NX - PP ? i - NX + 2 * PP : -1);
-                        const int zs = j < PP ? j : (j >= NZ - PP ? j - NZ + 2 * PP : -1);
-                        if (xs >= 0) {
-                            const long long kk = psx + (long long)j * 2 * PP + xs;
-                            const int pq = profx + i;
-                            const float P1 = a.pml.x[0][kk], P3 = a.pml.x[1][kk];
-                            h1 += a.pml.ax_h[pq] * (P1 + qx);
-                            h3 += a.pml.ax_i[pq] * (P3 + qz);
-                            if (own) {
-                                a.n1[kk] = a.pml.bx_h[pq] * (P1 + qx);
-                                a.n3[kk] = a.pml.bx_i[pq] * (P3 + qz);
-                            }
-                        }
-                        if (zs >= 0) {
-                            const long long kk = psz + (long long)zs * NX + i;
-                            const float P2 = a.pml.z[0][kk], P4 = a.pml.z[1][kk];
-                            h2 += a.pml.az_i[j] * (P2 + qx);
-                            h4 += a.pml.az_h[j] * (P4 + qz);
-                            if (own) {
-                                a.n2[kk] = a.pml.bz_i[j] * (P2 + qx);
-                                a.n4[kk] = a.pml.bz_h[j] * (P4 + qz);
-                            }
-                        }
-                    }
+                    const bool own = x >= 4 && x < TX + 4 && y >= 4 && y < TZ + 4 && (!edge || (i < NX && j < NZ));
+                    if (edge) vel_pml(i, j, own, qx, qz, h1, h2, h3, h4);
                     if (own) {
                         const long long c = off + (long long)(j + EFWI_GZ) * pitch + (i + EFWI_GX);
                         a.out.vx[c] = vx;
                         a.out.vz[c] = vz;
                         if (!edge || (i >= PP - 1 && i <= PP + w && j >= PP - 1 && j <= NZ - PP)) {
-                            const int u = (yv - 2) * TX + (xv - 2);
+                            const int u = (y - 4) * TX + (x - 4);
                             a.Gbx[c] = sg[3 * NC + u] + wvx[o] * inc_x;
                             a.Gbz[c] = sg[4 * NC + u] + wvz[o] * inc_z;
                         }
@@ -250,15 +323,44 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                 // each thread reads only its own staged v^ before writing e^ over it
                 svx[o] = h1; svz[o] = h3;
                 if (edge) { e2w[o] = h2; e4w[o] = h4; }
+            };
+            if constexpr (VEC == 1) {
+                constexpr int VX = TX + 4, VZ = TZ + 4;
+                for (int q = tid; q < VX * VZ; q += kThreads) {
+                    const int yv = q / VX, xv = q - yv * VX;
+                    vcell(xv + 2, yv + 2);
+                }
+            } else {
+                // every thread: at most one cell of the ring (rows 2, 3, TZ+4, TZ+5 over the
+                // velocity width, columns 2, 3, TX+4, TX+5 between them), then one cell pair of
+                // the tile, whose x-stencils share their inputs (64-bit shared-memory accesses)
+                constexpr int RW = TX + 4, NRING = 4 * RW + 4 * TZ;
+                for (int q = tid; q < NRING; q += kThreads) {
+                    int x, y;
+                    if (q < 4 * RW) {
+                        const int r = q / RW;
+                        x = 2 + (q - r * RW);
+                        y = r < 2 ? 2 + r : TZ + 2 + r;
+                    } else {
+                        const int r = q - 4 * RW, cc = r & 3;
+                        y = 4 + (r >> 2);
+                        x = cc < 2 ? 2 + cc : TX + 2 + cc;
+                    }
+                    vcell(x, y);
+                }
+                for (int q = tid; q < (TX / 2) * TZ; q += kThreads) {
+                    const int yy = q / (TX / 2);
+                    vpair(4 + 2 * (q - yy * (TX / 2)), 4 + yy);
+                }
             }
             __syncthreads();
             const float *e1r = svx, *e3r = svz, *e2r = e2w, *e4r = e4w;
 
-            // 3. F += dt C (-D^T e^) on the tile, with the imaging in F
-            for (int q = tid; q < NC; q += kThreads) {
-                const int y = q / TX, x = q - y * TX;
+            // 3. F += dt C (-D^T e^) on the tile, with the imaging in F; one cell (x, y) of the tile
+            auto scell = [&](const int x, const int y) {
+                const int q = y * TX + x;
                 const int i = i0 + x, j = j0 + y;
-                if (edge && (i >= NX || j >= NZ)) continue;
+                if (edge && (i >= NX || j >= NZ)) return;
                 const long long c = off + (long long)(j + EFWI_GZ) * pitch + (i + EFWI_GX);
                 const int o = (y + 4) * SX + (x + 4);
                 const float Fxx = edge ? txx[q] : fxx[o];
@@ -266,24 +368,101 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                 const float Fxz = edge ? txz[q] : fxz[o];
                 const float *fvx = wvx + o, *fvz = wvz + o;
                 if (!edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP)) {
-                    const float fx = (C1 * (fvx[0] - fvx[-1]) + C2 * (fvx[1] - fvx[-2])) * rdx;
-                    const float fz = (C1 * (fvz[0] - fvz[-SX]) + C2 * (fvz[SX] - fvz[-2 * SX])) * rdz;
+                    const float fx = st4(fvx[0], fvx[-1], fvx[1], fvx[-2]) * rdx;
+                    const float fz = st4(fvz[0], fvz[-SX], fvz[SX], fvz[-2 * SX]) * rdz;
                     a.Glam[c] = sg[q] + (Fxx + Fzz) * (fx + fz);
                     a.Gmu[c] = sg[NC + q] + (Fxx - Fzz) * (fx - fz);
                 }
                 if (!edge || (i >= PP - 1 && i < PP + w && j >= PP - 1 && j < NZ - PP)) {
-                    const float fxzv = (C1 * (fvx[SX] - fvx[0]) + C2 * (fvx[2 * SX] - fvx[-SX])) * rdz +
-                                       (C1 * (fvz[1] - fvz[0]) + C2 * (fvz[2] - fvz[-1])) * rdx;
+                    const float fxzv = st4(fvx[SX], fvx[0], fvx[2 * SX], fvx[-SX]) * rdz +
+                                       st4(fvz[1], fvz[0], fvz[2], fvz[-1]) * rdx;
                     a.Gmuxz[c] = sg[2 * NC + q] + Fxz * fxzv;
                 }
-                const float dxx = -(C1 * (e1r[o] - e1r[o - 1]) + C2 * (e1r[o + 1] - e1r[o - 2])) * rdx;
-                const float dzz = -(C1 * (e4r[o] - e4r[o - SX]) + C2 * (e4r[o + SX] - e4r[o - 2 * SX])) * rdz;
-                const float dxz = -(C1 * (e2r[o + SX] - e2r[o]) + C2 * (e2r[o + 2 * SX] - e2r[o - SX])) * rdz
-                                  - (C1 * (e3r[o + 1] - e3r[o]) + C2 * (e3r[o + 2] - e3r[o - 1])) * rdx;
+                const float dxx = -st4(e1r[o], e1r[o - 1], e1r[o + 1], e1r[o - 2]) * rdx;
+                const float dzz = -st4(e4r[o], e4r[o - SX], e4r[o + SX], e4r[o - 2 * SX]) * rdz;
+                const float dxz = -st4(e2r[o + SX], e2r[o], e2r[o + 2 * SX], e2r[o - SX]) * rdz
+                                  - st4(e3r[o + 1], e3r[o], e3r[o + 2], e3r[o - 1]) * rdx;
                 const float lam = slam[q], l2m = lam + 2.f * smu[q];
                 a.out.sxx[c] = Fxx + dt * (l2m * dxx + lam * dzz);
                 a.out.szz[c] = Fzz + dt * (lam * dxx + l2m * dzz);
                 a.out.sxz[c] = Fxz + dt * (smxz[q] * dxz);
+            };
+            if constexpr (VEC == 1) {
+                for (int q = tid; q < NC; q += kThreads) {
+                    const int y = q / TX;
+                    scell(q - y * TX, y);
+                }
+            } else {
+                // cell pairs (x, x+1), x even: every cell's expression is scell's, term by term
+                for (int q2 = tid; q2 < NC / 2; q2 += kThreads) {
+                    const int y = q2 / (TX / 2), x = 2 * (q2 - y * (TX / 2));
+                    const int i = i0 + x, j = j0 + y;
+                    if (edge && (i >= NX || j >= NZ)) continue;
+                    const int q = y * TX + x;
+                    const long long c = off + (long long)(j + EFWI_GZ) * pitch + (i + EFWI_GX);
+                    const int o = (y + 4) * SX + (x + 4);
+                    const float2 Fx2 = edge ? ld2(txx + q) : ld2(fxx + o);
+                    const float2 Fz2 = edge ? ld2(tzz + q) : ld2(fzz + o);
+                    const float2 Fs2 = edge ? ld2(txz + q) : ld2(fxz + o);
+                    const float2 pm2 = ld2(wvx + o - 2), p0 = ld2(wvx + o), p2 = ld2(wvx + o + 2),
+                                 pS = ld2(wvx + o + SX), p2S = ld2(wvx + o + 2 * SX), pmS = ld2(wvx + o - SX);
+                    const float2 qm2 = ld2(wvz + o - 2), q0 = ld2(wvz + o), q2v = ld2(wvz + o + 2),
+                                 qS = ld2(wvz + o + SX), qmS = ld2(wvz + o - SX), qm2S = ld2(wvz + o - 2 * SX);
+                    const float fx[2] = {st4(p0.x, pm2.y, p0.y, pm2.x) * rdx, st4(p0.y, p0.x, p2.x, pm2.y) * rdx};
+                    const float fz[2] = {st4(q0.x, qmS.x, qS.x, qm2S.x) * rdz, st4(q0.y, qmS.y, qS.y, qm2S.y) * rdz};
+                    const float fxzv[2] = {
+                        st4(pS.x, p0.x, p2S.x, pmS.x) * rdz + st4(q0.y, q0.x, q2v.x, qm2.y) * rdx,
+                        st4(pS.y, p0.y, p2S.y, pmS.y) * rdz + st4(q2v.x, q0.y, q2v.y, q0.x) * rdx};
+                    const float2 Em2 = ld2(e1r + o - 2), E0 = ld2(e1r + o), E2 = ld2(e1r + o + 2);
+                    const float2 R0 = ld2(e4r + o), RmS = ld2(e4r + o - SX), RS = ld2(e4r + o + SX),
+                                 Rm2S = ld2(e4r + o - 2 * SX);
+                    const float2 W0 = ld2(e2r + o), WS = ld2(e2r + o + SX), W2S = ld2(e2r + o + 2 * SX),
+                                 WmS = ld2(e2r + o - SX);
+                    const float2 Tm2 = ld2(e3r + o - 2), T0 = ld2(e3r + o), T2 = ld2(e3r + o + 2);
+                    const float dxx[2] = {-st4(E0.x, Em2.y, E0.y, Em2.x) * rdx, -st4(E0.y, E0.x, E2.x, Em2.y) * rdx};
+                    const float dzz[2] = {-st4(R0.x, RmS.x, RS.x, Rm2S.x) * rdz, -st4(R0.y, RmS.y, RS.y, Rm2S.y) * rdz};
+                    const float dxz[2] = {
+                        -st4(WS.x, W0.x, W2S.x, WmS.x) * rdz - st4(T0.y, T0.x, T2.x, Tm2.y) * rdx,
+                        -st4(WS.y, W0.y, W2S.y, WmS.y) * rdz - st4(T2.x, T0.y, T2.y, T0.x) * rdx};
+                    const float2 la = ld2(slam + q), mu2 = ld2(smu + q), mx2 = ld2(smxz + q);
+                    const float2 gl = ld2(sg + q), gm = ld2(sg + NC + q), gs = ld2(sg + 2 * NC + q);
+                    const float Fxx[2] = {Fx2.x, Fx2.y}, Fzz[2] = {Fz2.x, Fz2.y}, Fxz[2] = {Fs2.x, Fs2.y};
+                    const float lam[2] = {la.x, la.y}, muv[2] = {mu2.x, mu2.y}, mxz[2] = {mx2.x, mx2.y};
+                    const float glv[2] = {gl.x, gl.y}, gmv[2] = {gm.x, gm.y}, gsv[2] = {gs.x, gs.y};
+                    float nl[2], nm[2], ns[2], oxx[2], ozz[2], oxz[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        nl[h] = glv[h] + (Fxx[h] + Fzz[h]) * (fx[h] + fz[h]);
+                        nm[h] = gmv[h] + (Fxx[h] - Fzz[h]) * (fx[h] - fz[h]);
+                        ns[h] = gsv[h] + Fxz[h] * fxzv[h];
+                        const float l2m = lam[h] + 2.f * muv[h];
+                        oxx[h] = Fxx[h] + dt * (l2m * dxx[h] + lam[h] * dzz[h]);
+                        ozz[h] = Fzz[h] + dt * (lam[h] * dxx[h] + l2m * dzz[h]);
+                        oxz[h] = Fxz[h] + dt * (mxz[h] * dxz[h]);
+                    }
+                    if (!edge) {
+                        st2g(a.Glam + c, make_float2(nl[0], nl[1]));
+                        st2g(a.Gmu + c, make_float2(nm[0], nm[1]));
+                        st2g(a.Gmuxz + c, make_float2(ns[0], ns[1]));
+                        st2g(a.out.sxx + c, make_float2(oxx[0], oxx[1]));
+                        st2g(a.out.szz + c, make_float2(ozz[0], ozz[1]));
+                        st2g(a.out.sxz + c, make_float2(oxz[0], oxz[1]));
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int ih = i + h;
+                            if (ih >= NX) continue;
+                            if (ih >= PP && ih < PP + w && j >= PP && j < NZ - PP) {
+                                a.Glam[c + h] = nl[h];
+                                a.Gmu[c + h] = nm[h];
+                            }
+                            if (ih >= PP - 1 && ih < PP + w && j >= PP - 1 && j < NZ - PP) a.Gmuxz[c + h] = ns[h];
+                            a.out.sxx[c + h] = oxx[h];
+                            a.out.szz[c + h] = ozz[h];
+                            a.out.sxz[c + h] = oxz[h];
+                        }
+                    }
+                }
             }
         };
         if (tl.w & 4) tile(std::true_type{});
@@ -291,13 +470,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
     }
 }
 
-template <int TX, int TZ>
+template <int TX, int TZ, int VEC>
 int attrs_and_blocks() {
     constexpr int sm = (int)AdjsLayout<TX, TZ>::smem();
-    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_scaled_tma<TX, TZ>, kThreads, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_scaled_tma<TX, TZ, VEC>, kThreads, sm);
     return nb;
 }
 
@@ -305,8 +484,8 @@ int attrs_and_blocks() {
 
 bool adj_scaled_tma_shape_ok(int tx, int tz) { return tx == 32 && tz == 16; }
 
-int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz) {
-    if (!adj_scaled_tma_shape_ok(tx, tz) || !p->seg) return EFWI_ERR_ARG;
+int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz, int vec) {
+    if (!adj_scaled_tma_shape_ok(tx, tz) || !p->seg || (vec != 1 && vec != 2)) return EFWI_ERR_ARG;
     std::vector<AdjsMaps> h(p->d.ns);
     const long long F = p->fsz_total;
     for (int s = 0; s < p->d.ns; ++s) {
@@ -326,9 +505,10 @@ int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz) {
     if (!p->adjs_maps && cudaMalloc((void **)&p->adjs_maps, sizeof(AdjsMaps) * p->d.ns) != cudaSuccess)
         return EFWI_ERR_OOM;
     cudaMemcpy(p->adjs_maps, h.data(), sizeof(AdjsMaps) * p->d.ns, cudaMemcpyHostToDevice);
-    const int nb = attrs_and_blocks<32, 16>();
+    const int nb = vec == 2 ? attrs_and_blocks<32, 16, 2>() : attrs_and_blocks<32, 16, 1>();
     p->tma_adj_grid = std::max(1, nb) * std::max(1, p->n_sms);
     p->tma_adj_stages = 2;
+    p->adjs_vec = vec;
     return EFWI_OK;
 }
 
@@ -349,7 +529,8 @@ void launch_adj_scaled_tma(efwi_plan *p, const SnapIn &si, cudaStream_t st) {
     a.dt = f.dt; a.rdx = f.rdx; a.rdz = f.rdz;
     a.err = p->dev_err;
     const int grid = std::min(p->grid_adj_override > 0 ? p->grid_adj_override : p->tma_adj_grid, a.ntiles);
-    k_adj_scaled_tma<32, 16><<<grid, kThreads, AdjsLayout<32, 16>::smem(), st>>>(a);
+    if (p->adjs_vec == 2) k_adj_scaled_tma<32, 16, 2><<<grid, kThreads, AdjsLayout<32, 16>::smem(), st>>>(a);
+    else k_adj_scaled_tma<32, 16, 1><<<grid, kThreads, AdjsLayout<32, 16>::smem(), st>>>(a);
 }
 
 }  // namespace efwi

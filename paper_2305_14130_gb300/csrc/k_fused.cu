@@ -735,7 +735,7 @@ int select_adj(efwi_plan *p, const Variant &v) {
     }
     int rc = upload_tiles(p, p->adj_tiles, v.tx, v.tz);
     if (!rc && v.kind == EFWI_STENCIL_TMA)
-        rc = p->adj_form == EFWI_ADJ_FORM_SCALED ? adj_scaled_tma_prepare(p, v.tx, v.tz)
+        rc = p->adj_form == EFWI_ADJ_FORM_SCALED ? adj_scaled_tma_prepare(p, v.tx, v.tz, v.vec)
                                                  : tma_prepare_adj(p, v.tx, v.tz, v.nst);
     p->adj_tile_x = v.tx;
     p->adj_tile_z = v.tz;
@@ -801,8 +801,12 @@ int efwi_autotune(efwi_plan *p) {
             if (only_p <= 0 || !(s.tx == 32 && s.tz == 16)) adj.push_back({EFWI_STENCIL_LOADS, s.tx, s.tz, 0});
             if (s.tx == 32 && s.tz == 16 && only_p != 0) adj.push_back({EFWI_STENCIL_LOADS, 32, 16, 0, 2});
         }
+        // TMA staging, one cell or a cell pair per thread (EFWI_ADJ_VEC=1|2 keeps only one)
+        const char *fa = getenv("EFWI_ADJ_VEC");
+        const int only_av = fa ? atoi(fa) : 0;
         if (want_a != EFWI_STENCIL_LOADS && fp32v && adj_scaled_tma_shape_ok(s.tx, s.tz))
-            adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, 2});
+            for (int av = 1; av <= 2; ++av)
+                if (!only_av || av == only_av) adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, 2, av});
     }
     if (scaled && adj.empty()) {
         p->err = "no scaled-stress adjoint variant matches the request (per-thread loads: tiles 32x8 32x16 64x8 "
@@ -861,8 +865,8 @@ int efwi_autotune(efwi_plan *p) {
         for (auto &v : adj) {
             if (select_adj(p, v)) continue;
             const float t = time_steps(p, true, st, e0, e1);
-            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d persistent %d: %.1f us\n", v.kind,
-                             v.tx, v.tz, v.nst, v.vec == 2, t * 1e3f / 3);
+            if (log) fprintf(stderr, "efwi autotune adj kind %d tile %dx%d param %d vec/persistent %d: %.1f us\n",
+                             v.kind, v.tx, v.tz, v.nst, v.vec, t * 1e3f / 3);
             if (t < best) { best = t; ba = v; }
         }
         cudaEventDestroy(e0);

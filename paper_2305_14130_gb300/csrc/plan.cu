@@ -652,6 +652,7 @@ extern "C" int efwi_plan_info(const efwi_plan *p, efwi_plan_info_t *info) {
     info->snap_store = p->snap_store;
     info->prefetch = (p->stencil >= EFWI_STENCIL_TMA && p->tma_pf ? 1 : 0) | (p->adj_pf ? 2 : 0);
     info->adj_form = p->adj_form;
+    info->adj_layout = p->adj_form == EFWI_ADJ_FORM_SCALED && p->adj_stencil == EFWI_STENCIL_TMA ? p->adjs_vec : 0;
     return EFWI_OK;
 }
 

@@ -357,7 +357,7 @@ VARIANTS = [("loads", s) for s in SHAPES] + [(k, s) for k in ("tma", "tma_pairs"
 # the scaled-stress adjoint: per-thread loads on every tile, one CTA per tile or on a
 # persistent grid, and TMA staging (32x16, persistent grid)
 SCALED_VARIANTS = [((32, 8), 0, "loads"), ((32, 16), 0, "loads"), ((32, 16), 1, "loads"), ((64, 8), 0, "loads"),
-                   ((64, 16), 0, "loads"), ((32, 16), 0, "tma")]
+                   ((64, 16), 0, "loads"), ((32, 16), 0, "tma:1"), ((32, 16), 0, "tma:2")]
 
 
 @pytest.mark.parametrize("source", ["moment_tensor", "force"])
@@ -385,6 +385,12 @@ def test_stencil_variants_do_not_change_results(efwi, source, monkeypatch):
             monkeypatch.delenv("EFWI_TMA_VEC", raising=False)
         adjp = layout == "adjp" if persist is None else persist == 1
         monkeypatch.setenv("EFWI_ADJ_PERSIST", "1" if adjp else "0")
+        # "tma:v": the TMA scaled-stress adjoint with one cell (1) or a cell pair (2) per thread
+        adj_stencil, _, adj_vec = adj_stencil.partition(":")
+        if adj_vec:
+            monkeypatch.setenv("EFWI_ADJ_VEC", adj_vec)
+        else:
+            monkeypatch.delenv("EFWI_ADJ_VEC", raising=False)
         plan = efwi.Plan(p.acq, exec="batched", tile=(tx, tz), stencil=stencil, adj_form=form,
                          adj_tile=adj_tile or (0, 0), adj_stencil=adj_stencil)
         info = plan.info()
@@ -394,6 +400,7 @@ def test_stencil_variants_do_not_change_results(efwi, source, monkeypatch):
         assert info["adj_form"] == {"stress": 1, "scaled": 2}[form]
         if adj_tile:
             assert (info["adj_tile_x"], info["adj_tile_z"], info["adj_persistent"]) == (*adj_tile, persist)
+        assert info["adj_layout"] == (int(adj_vec) if adj_vec else 0)
         out = [t.clone() for t in plan.gradient(*args, return_data=True)]
         plan.sync_status()
         plan.close()
@@ -424,10 +431,13 @@ def test_tma_full_size_matches_loads(efwi, monkeypatch):
     outs = []
     d_obs = torch.zeros((acq.ntr, acq.nt), device="cuda")
     for stencil in ("loads", "tma", "tma_pairs", "tma_staged", "tma_pairs:split", "tma_pairs:split:scaled-loads",
-                    "tma_pairs:split:scaled-tma"):
+                    "tma_pairs:split:scaled-tma1", "tma_pairs:split:scaled-tma2"):
         stencil, _, layout = stencil.partition(":")
         layout, _, form = layout.partition(":")
         form, _, adj_stencil = form.partition("-")
+        if adj_stencil.startswith("tma"):
+            monkeypatch.setenv("EFWI_ADJ_VEC", adj_stencil[3:])
+            adj_stencil = "tma"
         if layout == "split":
             monkeypatch.setenv("EFWI_TMA_VEC", "3")
         plan = efwi.Plan(acq, exec="batched", stencil=stencil, ckpt_interval=30, adj_form=form or "stress",
@@ -438,13 +448,14 @@ def test_tma_full_size_matches_loads(efwi, monkeypatch):
         plan.sync_status()
         plan.close()
     # the stress-form runs (TMA adjoint with the TMA forward steps) bit for bit
-    for o in outs[1:-2]:
+    for o in outs[1:-3]:
         for a, b in zip(outs[0], o):
             assert torch.equal(a, b)
-    # the scaled-stress adjoint's two stagings bit for bit, and against the stress form the
-    # same data and misfit, gradients within FP32 rounding
-    for a, b in zip(outs[-2], outs[-1]):
-        assert torch.equal(a, b)
+    # the scaled-stress adjoint's stagings and layouts bit for bit, and against the stress
+    # form the same data and misfit, gradients within FP32 rounding
+    for o in outs[-2:]:
+        for a, b in zip(outs[-3], o):
+            assert torch.equal(a, b)
     a, b = outs[0], outs[-1]
     assert torch.equal(a[0], b[0]) and torch.equal(a[4], b[4])
     for x, y in zip(a[1:4], b[1:4]):
