@@ -65,10 +65,11 @@ struct AdjsLayout {
     static_assert(A2 % 32 == 0 && NC % 32 == 0, "arrays must keep 128-byte alignment");
 };
 
+// tl: the tile's work item, already in a register (no global load on the issuing thread's
+// path between the tile's barriers)
 template <int TX, int TZ>
-__device__ __forceinline__ void issue_adjs(const TmaAdjsArgs &a, int t, float *buf, uint64_t *bar) {
+__device__ __forceinline__ void issue_adjs(const TmaAdjsArgs &a, const int4 tl, float *buf, uint64_t *bar) {
     using L = AdjsLayout<TX, TZ>;
-    const int4 tl = a.tiles[t];
     const AdjsMaps *m = a.maps + tl.x;
     mbar_expect_tx(bar, L::LOADED);
     // element x = cell i + GX (halo-4 column 0 = cell i0 - 4), row y = cell j + GZ: halo-4 row r
@@ -105,10 +106,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0 && (int)blockIdx.x < a.ntiles) issue_adjs<TX, TZ>(a, blockIdx.x, smb, &bar[0]);
     uint32_t phase = 0;
     int t = blockIdx.x;
     int4 tl_next = t < a.ntiles ? __ldg(a.tiles + t) : make_int4(0, 0, 0, 0);
+    if (tid == 0 && t < a.ntiles) issue_adjs<TX, TZ>(a, tl_next, smb, &bar[0]);
+    // the work item of the tile the next refill copies (thread 0), loaded one tile ahead
+    int4 tl_fill = make_int4(0, 0, 0, 0);
+    if (tid == 0 && t + (int)gridDim.x < a.ntiles) tl_fill = __ldg(a.tiles + t + gridDim.x);
     for (int k = 0; t < a.ntiles; t += gridDim.x, ++k) {
         const int b = k & 1;
         float *buf = smb + b * L::BUF;
@@ -133,8 +137,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
         phase ^= 1u << b;
         // refill the other stage with the CTA's next tile: every thread has passed the barrier
         // above, so none still reads that stage (it held the previous tile)
-        if (tid == 0 && t + (int)gridDim.x < a.ntiles)
-            issue_adjs<TX, TZ>(a, t + gridDim.x, smb + (b ^ 1) * L::BUF, &bar[b ^ 1]);
+        if (tid == 0 && t + (int)gridDim.x < a.ntiles) {
+            issue_adjs<TX, TZ>(a, tl_fill, smb + (b ^ 1) * L::BUF, &bar[b ^ 1]);   // tile t + gridDim.x
+            if (t + 2 * (int)gridDim.x < a.ntiles) tl_fill = __ldg(a.tiles + t + 2 * gridDim.x);
+        }
 
         auto tile = [&](auto edge_c) {
             constexpr bool edge = decltype(edge_c)::value;   // 4-cell halo touches a strip or the grid edge

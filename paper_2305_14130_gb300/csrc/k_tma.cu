@@ -70,10 +70,11 @@ struct FwdLayout {
     static_assert(2 * NC <= 2 * A2, "staged velocities must fit over b_x, b_z");
 };
 
+// tl: the tile's work item, already in a register (the issuing thread's refill then has no
+// dependent global load between the tile's barriers)
 template <int TX, int TZ, int NST, int VEC>
-__device__ __forceinline__ void issue_fwd(const TmaFwdArgs &a, int t, float *buf, uint64_t *bar) {
+__device__ __forceinline__ void issue_fwd(const TmaFwdArgs &a, const int4 tl, float *buf, uint64_t *bar) {
     using L = FwdLayout<TX, TZ, NST, VEC>;
-    const int4 tl = a.tiles[t];
     const FwdMaps *m = a.maps + tl.x;
     mbar_expect_tx(bar, L::LOADED);
     // element x = cell i + GX (halo-4 column 0 = cell i0 - 4), row y = cell j + GZ: halo-4 row r
@@ -139,8 +140,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
     if (tid == 0)
         for (int b = 0; b < NST - 1; ++b) {
             const int tb = blockIdx.x + b * gridDim.x;
-            if (tb < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, tb, smb + b * L::BUF, &bar[b]);
+            if (tb < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, __ldg(a.tiles + tb), smb + b * L::BUF, &bar[b]);
         }
+    // the work item of the tile the next refill copies (thread 0), loaded one tile ahead
+    int4 tl_fill = make_int4(0, 0, 0, 0);
+    if (tid == 0 && blockIdx.x + (NST - 1) * gridDim.x < a.ntiles)
+        tl_fill = __ldg(a.tiles + blockIdx.x + (NST - 1) * gridDim.x);
     uint32_t phase = 0;
     int t = blockIdx.x;
     // the work item of the next tile is loaded one tile ahead, and its shot scalars
@@ -188,8 +193,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_step_tma(TmaFwdArgs a) {
                 store_fwd<TX, TZ, NST>(a, tl_prev, smb + bn * L::BUF);   // stage bn held tile k - 1
                 bulk_wait_read0();
             }
-            if (tn < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, tn, smb + bn * L::BUF, &bar[bn]);
+            if (tn < a.ntiles) issue_fwd<TX, TZ, NST, VEC>(a, tl_fill, smb + bn * L::BUF, &bar[bn]);
             if (a.pf && tp < a.ntiles) prefetch_fwd(a, tl_pf);
+            if (tn + (int)gridDim.x < a.ntiles) tl_fill = __ldg(a.tiles + tn + gridDim.x);   // next refill
         }
         tl_prev = tl;
 
