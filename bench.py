@@ -193,11 +193,12 @@ def kernel_bytes(exec_, info, nt):
 # capture, reports traffic null.
 TRAFFIC_PER_CELL = {
     # forward step, TMA cell pairs, tile 32x16
-    ("step", 3, 32, 16, 3, 0, 0): {"pass": 54.99, "keep": 60.31},
+    ("step", 3, 32, 16, 3, 0, 0): {"pass": 55.23, "keep": 60.44},
+    # adjoint step, scaled-stress form, TMA staging, cell pairs, tile 32x16, FP32 velocities
+    ("adj", 2, 32, 16, 2, 2, 0): 98.06,
     # adjoint step (stress form), per-thread loads, tile 32x16, persistent grid, FP32 velocities
     ("adj", 1, 32, 16, 1, 1, 0): 94.97,
-    # the same two with FP16 snapshots (every step stored)
-    ("step", 3, 32, 16, 3, 0, 1): {"keep": 57.57},
+    # the stress-form adjoint with FP16 snapshots (every step stored)
     ("adj", 1, 32, 16, 1, 1, 1): 90.35,
 }
 
@@ -253,6 +254,8 @@ def roofline(exec_, info, prof, nt, ns):
                 staging += ", halo ring as single cells"
             if k == "adj" and kind == 1 and info["adj_persistent"]:
                 staging += ", persistent grid"
+            if k == "adj" and kind == 2 and info.get("adj_layout", 0) == 2:
+                staging += ", cell pairs"
             if k == "adj" and info.get("adj_form", 1) == 2:
                 staging = "scaled-stress form, " + staging
             name = f"{name.split(' ')[0]} [{staging}, tile {tile[0]}x{tile[1]}] {' '.join(name.split(' ')[1:])}"
@@ -266,7 +269,7 @@ def roofline(exec_, info, prof, nt, ns):
             if k == "step" and info["stencil"] >= 2:
                 key = key + (info["layout"], info["staged_stores"])
             if k == "adj":
-                key = key + ((info["adj_persistent"],) if info["adj_stencil"] == 1 else ()) + \
+                key = key + ((info["adj_persistent"],) if info["adj_stencil"] == 1 else (info.get("adj_layout", 0),)) + \
                     (info.get("adj_form", 1),)
             key = key + (info.get("snap_store", 0),)
             t = TRAFFIC_PER_CELL.get(key)

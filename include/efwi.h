@@ -104,15 +104,14 @@ enum efwi_stencil { EFWI_STENCIL_AUTO = 0, EFWI_STENCIL_LOADS = 1, EFWI_STENCIL_
  *   STRESS  sigma^ itself (every staging and tile of the adjoint; EXEC_PLAIN always)
  *   SCALED  F = dt C sigma^ (C the cell's stiffness), which the transposed step only
  *           ever uses through C, so a step needs the stiffness on the tile alone and
- *           no pass over the 4-cell halo to form C sigma^ (per-thread loads, or TMA
- *           staging with FP32 snapshots; the imaging sums are converted back once
- *           per gradient).  Needs lambda + mu > 0
+ *           no pass over the 4-cell halo to form C sigma^ (per-thread loads or TMA
+ *           staging; the imaging sums are converted back once per gradient).  Needs lambda + mu > 0
  *           (Vp > Vs) and mu > 0 on the physical cells and the half cells next to
  *           them; a gradient of a model without it is flagged (efwi_sync_status:
  *           EFWI_ERR_NAN).  Either form's chain rule needs mu > 0 on the physical
  *           cells, which every gradient call checks.
- *   AUTO    SCALED with EXEC_BATCHED unless adj_stencil asks for TMA with FP16/BF16
- *           snapshots or for a TMA_PAIRS/TMA_STAGED staging, else STRESS
+ *   AUTO    SCALED with EXEC_BATCHED unless adj_stencil asks for TMA_PAIRS or
+ *           TMA_STAGED (stagings of the stress form only), else STRESS
  * The two forms agree up to FP32 rounding (not bit for bit); all tiles of one form
  * give bitwise-identical results.                                                */
 enum efwi_adj_form { EFWI_ADJ_FORM_AUTO = 0, EFWI_ADJ_FORM_STRESS = 1, EFWI_ADJ_FORM_SCALED = 2 };

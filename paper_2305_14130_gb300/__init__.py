@@ -77,7 +77,7 @@ class Plan:
     recompute.  ``snap_store``: precision of those stored forward
     velocities ("fp32", "fp16", "bf16"; the latter two need exec="batched").
     ``adj_form``: the adjoint step's stress variable -- "scaled" (F = dt C
-    sigma^; per-thread loads, or TMA staging with FP32 snapshots; needs Vp > Vs
+    sigma^; per-thread loads or TMA staging; needs Vp > Vs
     on the imaging area), "stress" (sigma^ itself, every staging) or "auto"
     (scaled with exec="batched" unless the requested adjoint staging exists in
     the stress form only).

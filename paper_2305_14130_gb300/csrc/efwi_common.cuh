@@ -6,8 +6,9 @@
 //   Each field of shot s is a block of (NZ + 2*GZ) rows x pitch floats; cell
 //   (i, j) of the padded grid sits at  off_s + (j + GZ) * pitch + (i + GX).
 //   GX = 4 left ghost columns keep every row's first interior cell 16-byte
-//   aligned (float4); pitch = roundup(NX, 4) + 8 leaves >= 4 zero columns on
-//   the right; GZ = 2 zero rows above and below.  Ghost cells are zero and
+//   aligned (float4); pitch = roundup(NX, 8) + 8 leaves >= 4 zero columns on
+//   the right and keeps rows of 2-byte snapshot elements 16-byte aligned too
+//   (tensor copies); GZ = 2 zero rows above and below.  Ghost cells are zero and
 //   never written, so the radius-2 staggered stencils need no bounds checks
 //   and the discrete derivative operators are exact transposes up to sign.
 //   Field kinds (vx, vz, sxx, szz, sxz, materials, adjoint fields, imaging

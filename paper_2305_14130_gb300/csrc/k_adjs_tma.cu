@@ -2,7 +2,8 @@
 // k_adjs.cu (adjoint stresses carried as F = dt C sigma^) on a persistent grid whose
 // CTAs copy every input of a tile into shared memory with cp.async.bulk.tensor, one
 // tile ahead (two stages completing on mbarriers):
-//   * v^x, v^z, b_x, b_z and the forward v_x, v_z of the step on the tile + 4-cell halo
+//   * v^x, v^z, b_x, b_z and the forward v_x, v_z of the step (FP32, or the 2-byte
+//     FP16/BF16 snapshot elements, scaled when read) on the tile + 4-cell halo
 //     in x and the tile + 2 rows in z, F_xx on the same rows, F_zz and F_xz on the rows
 //     the velocity sub-step reads (tile + 3 rows on one side, 4 on the other);
 //   * lambda, mu, mu_xz and the five imaging sums on the tile.
@@ -42,22 +43,27 @@ struct TmaAdjsArgs {
     float *Glam, *Gmu, *Gmuxz, *Gbx, *Gbz;
     float dt, rdx, rdz;
     int *err;
+    const float *hmax;          // snapshot maxima of the step (SK != 0): the power-of-two scales
+    int ns;
 };
 
 // One stage (halo-4 coordinates: column x = cell i - i0 + 4, row y = cell j - j0 + 4):
 // R2 arrays hold rows 2 .. TZ+5, F_zz rows 1 .. TZ+7, F_xz rows 0 .. TZ+6 (R3 rows each,
 // padded to 128 bytes); tile arrays TX x TZ.  Every array starts 128-byte aligned.
-template <int TX, int TZ>
+template <int TX, int TZ, int SK>
 struct AdjsLayout {
     static constexpr int SX = TX + 8;
     static constexpr int R2 = TZ + 4, R3 = TZ + 7;
     static constexpr int A2 = SX * R2;
     static constexpr int A3 = SX * R3, A3P = (A3 + 31) & ~31;
     static constexpr int NC = TX * TZ;
+    // forward velocities: FP32, or 2-byte FP16/BF16 snapshot elements (SK != 0)
+    static constexpr int WB = SK ? 2 : 4, AW = A2 * WB / 4;                    // floats of one of them
     static constexpr int OVX = 0, OVZ = A2, OFXX = 2 * A2, OFZZ = 3 * A2, OFXZ = OFZZ + A3P, OBX = OFXZ + A3P,
-                         OBZ = OBX + A2, OWX = OBZ + A2, OWZ = OWX + A2, OLAM = OWZ + A2, OG = OLAM + 3 * NC;
+                         OBZ = OBX + A2, OWX = OBZ + A2, OWZ = OWX + AW, OLAM = (OWZ + AW + 31) & ~31,
+                         OG = OLAM + 3 * NC;
     static constexpr int BUF = (OG + 5 * NC + 31) & ~31;                      // floats per stage
-    static constexpr unsigned LOADED = (7u * A2 + 2u * A3 + 8u * NC) * 4u;    // bytes the copies bring
+    static constexpr unsigned LOADED = (5u * A2 + 2u * A3 + 8u * NC) * 4u + 2u * A2 * WB;   // bytes the copies bring
     // per CTA, edge tiles only: F_xz with its x-strip CPML term (g4), e^2, e^4 (R2 rows)
     // and F of the tile before its update
     static constexpr int EXTRA = 3 * A2 + 3 * NC;
@@ -67,9 +73,9 @@ struct AdjsLayout {
 
 // tl: the tile's work item, already in a register (no global load on the issuing thread's
 // path between the tile's barriers)
-template <int TX, int TZ>
+template <int TX, int TZ, int SK>
 __device__ __forceinline__ void issue_adjs(const TmaAdjsArgs &a, const int4 tl, float *buf, uint64_t *bar) {
-    using L = AdjsLayout<TX, TZ>;
+    using L = AdjsLayout<TX, TZ, SK>;
     const AdjsMaps *m = a.maps + tl.x;
     mbar_expect_tx(bar, L::LOADED);
     // element x = cell i + GX (halo-4 column 0 = cell i0 - 4), row y = cell j + GZ: halo-4 row r
@@ -84,14 +90,48 @@ __device__ __forceinline__ void issue_adjs(const TmaAdjsArgs &a, const int4 tl, 
     tma_load_3d(buf + L::OG, &m->gi, bar, tl.y + 4, tl.z + 2, 0);        // imaging sums: tile
 }
 
+// A 2-byte snapshot element as a float (the conversion of the per-thread-load kernels).
+template <int SK>
+__device__ __forceinline__ float h2f(unsigned short u) {
+    if constexpr (SK == EFWI_STORE_FP16) return __half2float(__ushort_as_half(u));
+    else return __bfloat162float(__ushort_as_bfloat16(u));
+}
+
+// Read access to a tile's staged forward velocity: FP32 (SK = 0), or 2-byte FP16/BF16
+// snapshot elements times the snapshot's power-of-two scale s, the value the per-thread
+// kernels compute from the same element.  at(base, o0, s): element o0 of the array that
+// starts at base (shared memory).
+template <int SK>
+struct FvView {
+    using T = typename std::conditional<SK == 0, float, unsigned short>::type;
+    const T *p;
+    float s;
+    __device__ __forceinline__ static FvView at(const float *base, int o0, float s) {
+        return {reinterpret_cast<const T *>(base) + o0, s};
+    }
+    __device__ __forceinline__ FvView operator+(int o) const { return {p + o, s}; }
+    __device__ __forceinline__ float operator[](int o) const {
+        if constexpr (SK == 0) return p[o];
+        else return h2f<SK>(p[o]) * s;
+    }
+    __device__ __forceinline__ float2 pair(int o) const {   // elements o, o + 1; o even
+        if constexpr (SK == 0) {
+            return ld2(p + o);
+        } else {
+            const unsigned int w = *reinterpret_cast<const unsigned int *>(p + o);
+            return make_float2(h2f<SK>((unsigned short)(w & 0xffffu)) * s, h2f<SK>((unsigned short)(w >> 16)) * s);
+        }
+    }
+};
+
 // C1 (a - b) + C2 (c - d): the 4th-order staggered difference, one rounding per operation
 __device__ __forceinline__ float st4(float a, float b, float c, float d) { return C1 * (a - b) + C2 * (c - d); }
 
 // VEC = 1: one cell per thread and iteration; VEC = 2: cell pairs with 64-bit shared-memory
 // accesses (one pair of the tile per thread, the velocity halo ring as single cells)
-template <int TX, int TZ, int VEC>
+template <int TX, int TZ, int VEC, int SK>
 __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
-    using L = AdjsLayout<TX, TZ>;
+    using L = AdjsLayout<TX, TZ, SK>;
     constexpr int SX = L::SX, NC = L::NC;
     extern __shared__ float4 smem_raw[];
     float *smb = align128(smem_raw);
@@ -109,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
     uint32_t phase = 0;
     int t = blockIdx.x;
     int4 tl_next = t < a.ntiles ? __ldg(a.tiles + t) : make_int4(0, 0, 0, 0);
-    if (tid == 0 && t < a.ntiles) issue_adjs<TX, TZ>(a, tl_next, smb, &bar[0]);
+    if (tid == 0 && t < a.ntiles) issue_adjs<TX, TZ, SK>(a, tl_next, smb, &bar[0]);
     // the work item of the tile the next refill copies (thread 0), loaded one tile ahead
     int4 tl_fill = make_int4(0, 0, 0, 0);
     if (tid == 0 && t + (int)gridDim.x < a.ntiles) tl_fill = __ldg(a.tiles + t + gridDim.x);
@@ -121,6 +161,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
         const int NX = __ldg(&sp->NX), NZ = __ldg(&sp->NZ), PP = __ldg(&sp->P), profx = __ldg(&sp->profx),
                   pitch = __ldg(&sp->pitch), w = __ldg(&sp->w);
         const long long off = __ldg(&sp->off), psx = __ldg(&sp->psx), psz = __ldg(&sp->psz);
+        // power-of-two scales of the shot's reduced-precision snapshot (loaded before the wait)
+        const float dnx = SK ? snap_scale_down(a.hmax, 0, tl.x, a.ns) : 1.f;
+        const float dnz = SK ? snap_scale_down(a.hmax, 1, tl.x, a.ns) : 1.f;
         if (t + (int)gridDim.x < a.ntiles) tl_next = __ldg(a.tiles + t + gridDim.x);
         if (tid == 0) ok_s = mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
         __syncthreads();
@@ -138,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
         // refill the other stage with the CTA's next tile: every thread has passed the barrier
         // above, so none still reads that stage (it held the previous tile)
         if (tid == 0 && t + (int)gridDim.x < a.ntiles) {
-            issue_adjs<TX, TZ>(a, tl_fill, smb + (b ^ 1) * L::BUF, &bar[b ^ 1]);   // tile t + gridDim.x
+            issue_adjs<TX, TZ, SK>(a, tl_fill, smb + (b ^ 1) * L::BUF, &bar[b ^ 1]);   // tile t + gridDim.x
             if (t + 2 * (int)gridDim.x < a.ntiles) tl_fill = __ldg(a.tiles + t + 2 * gridDim.x);
         }
 
@@ -150,7 +193,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
             float *svx = buf + L::OVX - 2 * SX, *svz = buf + L::OVZ - 2 * SX;
             float *fxx = buf + L::OFXX - 2 * SX, *fzz = buf + L::OFZZ - SX, *fxz = buf + L::OFXZ;
             const float *sbx = buf + L::OBX - 2 * SX, *sbz = buf + L::OBZ - 2 * SX;
-            const float *wvx = buf + L::OWX - 2 * SX, *wvz = buf + L::OWZ - 2 * SX;
+            const FvView<SK> wvx = FvView<SK>::at(buf + L::OWX, -2 * SX, dnx),
+                             wvz = FvView<SK>::at(buf + L::OWZ, -2 * SX, dnz);
             const float *slam = buf + L::OLAM, *smu = slam + NC, *smxz = smu + NC;
             const float *sg = buf + L::OG;                    // [5][NC]: lambda, mu, mu_xz, b_x, b_z sums
             float *g4 = edge ? xg4 - 2 * SX : fxz;            // f^4 == f^3 away from the CPML
@@ -268,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                 const long long c = off + (long long)(j + EFWI_GZ) * pitch + (i + EFWI_GX);
                 const int u = (y - 4) * TX + (x - 4);
                 const float2 gbx = ld2(sg + 3 * NC + u), gbz = ld2(sg + 4 * NC + u);
-                const float2 fvx = ld2(wvx + o), fvz = ld2(wvz + o);
+                const float2 fvx = wvx.pair(o), fvz = wvz.pair(o);
                 if (!edge) {
                     st2g(a.out.vx + c, make_float2(vx[0], vx[1]));
                     st2g(a.out.vz + c, make_float2(vz[0], vz[1]));
@@ -372,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                 const float Fxx = edge ? txx[q] : fxx[o];
                 const float Fzz = edge ? tzz[q] : fzz[o];
                 const float Fxz = edge ? txz[q] : fxz[o];
-                const float *fvx = wvx + o, *fvz = wvz + o;
+                const FvView<SK> fvx = wvx + o, fvz = wvz + o;
                 if (!edge || (i >= PP && i < PP + w && j >= PP && j < NZ - PP)) {
                     const float fx = st4(fvx[0], fvx[-1], fvx[1], fvx[-2]) * rdx;
                     const float fz = st4(fvz[0], fvz[-SX], fvz[SX], fvz[-2 * SX]) * rdz;
@@ -410,10 +454,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                     const float2 Fx2 = edge ? ld2(txx + q) : ld2(fxx + o);
                     const float2 Fz2 = edge ? ld2(tzz + q) : ld2(fzz + o);
                     const float2 Fs2 = edge ? ld2(txz + q) : ld2(fxz + o);
-                    const float2 pm2 = ld2(wvx + o - 2), p0 = ld2(wvx + o), p2 = ld2(wvx + o + 2),
-                                 pS = ld2(wvx + o + SX), p2S = ld2(wvx + o + 2 * SX), pmS = ld2(wvx + o - SX);
-                    const float2 qm2 = ld2(wvz + o - 2), q0 = ld2(wvz + o), q2v = ld2(wvz + o + 2),
-                                 qS = ld2(wvz + o + SX), qmS = ld2(wvz + o - SX), qm2S = ld2(wvz + o - 2 * SX);
+                    const float2 pm2 = wvx.pair(o - 2), p0 = wvx.pair(o), p2 = wvx.pair(o + 2),
+                                 pS = wvx.pair(o + SX), p2S = wvx.pair(o + 2 * SX), pmS = wvx.pair(o - SX);
+                    const float2 qm2 = wvz.pair(o - 2), q0 = wvz.pair(o), q2v = wvz.pair(o + 2),
+                                 qS = wvz.pair(o + SX), qmS = wvz.pair(o - SX), qm2S = wvz.pair(o - 2 * SX);
                     const float fx[2] = {st4(p0.x, pm2.y, p0.y, pm2.x) * rdx, st4(p0.y, p0.x, p2.x, pm2.y) * rdx};
                     const float fz[2] = {st4(q0.x, qmS.x, qS.x, qm2S.x) * rdz, st4(q0.y, qmS.y, qS.y, qm2S.y) * rdz};
                     const float fxzv[2] = {
@@ -476,14 +520,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
     }
 }
 
-template <int TX, int TZ, int VEC>
+template <int TX, int TZ, int VEC, int SK>
 int attrs_and_blocks() {
-    constexpr int sm = (int)AdjsLayout<TX, TZ>::smem();
-    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    constexpr int sm = (int)AdjsLayout<TX, TZ, SK>::smem();
+    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC, SK>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_scaled_tma<TX, TZ, VEC>, kThreads, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_scaled_tma<TX, TZ, VEC, SK>, kThreads, sm);
     return nb;
+}
+
+template <int VEC>
+int blocks_sk(int sk) {
+    return sk == EFWI_STORE_FP16   ? attrs_and_blocks<32, 16, VEC, EFWI_STORE_FP16>()
+           : sk == EFWI_STORE_BF16 ? attrs_and_blocks<32, 16, VEC, EFWI_STORE_BF16>()
+                                   : attrs_and_blocks<32, 16, VEC, 0>();
+}
+
+template <int VEC, int SK>
+void launch_v(const TmaAdjsArgs &a, int grid, cudaStream_t st) {
+    k_adj_scaled_tma<32, 16, VEC, SK><<<grid, kThreads, AdjsLayout<32, 16, SK>::smem(), st>>>(a);
 }
 
 }  // namespace
@@ -491,7 +547,8 @@ int attrs_and_blocks() {
 bool adj_scaled_tma_shape_ok(int tx, int tz) { return tx == 32 && tz == 16; }
 
 int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz, int vec) {
-    if (!adj_scaled_tma_shape_ok(tx, tz) || !p->seg || (vec != 1 && vec != 2)) return EFWI_ERR_ARG;
+    const bool half = p->snap_store != EFWI_STORE_FP32;
+    if (!adj_scaled_tma_shape_ok(tx, tz) || (half ? !p->segh : !p->seg) || (vec != 1 && vec != 2)) return EFWI_ERR_ARG;
     std::vector<AdjsMaps> h(p->d.ns);
     const long long F = p->fsz_total;
     for (int s = 0; s < p->d.ns; ++s) {
@@ -501,7 +558,8 @@ int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz, int vec) {
         if (!rc) rc = encode_map(&h[s].a3, p->adj[0], sh, F, 10, tx + 8, tz + 7, 1);
         if (!rc) rc = encode_map(&h[s].mb, p->mat, sh, F, 5, tx + 8, tz + 4, 2);
         if (!rc) rc = encode_map(&h[s].mc, p->mat, sh, F, 5, tx, tz, 3);
-        if (!rc) rc = encode_map(&h[s].sv, p->seg, sh, F, 2 * p->nslots, tx + 8, tz + 4, 2);
+        if (!rc) rc = half ? encode_map(&h[s].sv, p->segh, sh, F, 2 * p->nslots, tx + 8, tz + 4, 2, 2)
+                           : encode_map(&h[s].sv, p->seg, sh, F, 2 * p->nslots, tx + 8, tz + 4, 2);
         if (!rc) rc = encode_map(&h[s].gi, p->G, sh, F, 5, tx, tz, 5);
         if (rc) {
             p->err = "cuTensorMapEncodeTiled failed for the scaled-stress adjoint maps";
@@ -511,7 +569,7 @@ int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz, int vec) {
     if (!p->adjs_maps && cudaMalloc((void **)&p->adjs_maps, sizeof(AdjsMaps) * p->d.ns) != cudaSuccess)
         return EFWI_ERR_OOM;
     cudaMemcpy(p->adjs_maps, h.data(), sizeof(AdjsMaps) * p->d.ns, cudaMemcpyHostToDevice);
-    const int nb = vec == 2 ? attrs_and_blocks<32, 16, 2>() : attrs_and_blocks<32, 16, 1>();
+    const int nb = vec == 2 ? blocks_sk<2>(p->snap_store) : blocks_sk<1>(p->snap_store);
     p->tma_adj_grid = std::max(1, nb) * std::max(1, p->n_sms);
     p->tma_adj_stages = 2;
     p->adjs_vec = vec;
@@ -526,7 +584,12 @@ void launch_adj_scaled_tma(efwi_plan *p, const SnapIn &si, cudaStream_t st) {
     a.maps = p->adjs_maps;
     a.ntiles = p->adj_tiles.n;
     a.af = 5 * p->acur;
-    a.vf = (int)(2 * ((si.fx - p->seg) / (2 * p->fsz_total)));
+    // field of the step's vx in the snapshot map: 2 x its slot
+    a.vf = si.sr.h ? (int)(2 * ((static_cast<const char *>(si.sr.h) - static_cast<const char *>(p->segh)) /
+                                 (2 * 2 * p->fsz_total)))
+                   : (int)(2 * ((si.fx - p->seg) / (2 * p->fsz_total)));
+    a.hmax = si.sr.hmax;
+    a.ns = p->d.ns;
     a.out = f.out;
     a.pml = f.pml;
     a.n1 = f.n1; a.n3 = f.n3; a.n2 = f.n2; a.n4 = f.n4;
@@ -535,8 +598,16 @@ void launch_adj_scaled_tma(efwi_plan *p, const SnapIn &si, cudaStream_t st) {
     a.dt = f.dt; a.rdx = f.rdx; a.rdz = f.rdz;
     a.err = p->dev_err;
     const int grid = std::min(p->grid_adj_override > 0 ? p->grid_adj_override : p->tma_adj_grid, a.ntiles);
-    if (p->adjs_vec == 2) k_adj_scaled_tma<32, 16, 2><<<grid, kThreads, AdjsLayout<32, 16>::smem(), st>>>(a);
-    else k_adj_scaled_tma<32, 16, 1><<<grid, kThreads, AdjsLayout<32, 16>::smem(), st>>>(a);
+    const int sk = p->snap_store;
+    if (p->adjs_vec == 2) {
+        if (sk == EFWI_STORE_FP16) launch_v<2, EFWI_STORE_FP16>(a, grid, st);
+        else if (sk == EFWI_STORE_BF16) launch_v<2, EFWI_STORE_BF16>(a, grid, st);
+        else launch_v<2, 0>(a, grid, st);
+    } else {
+        if (sk == EFWI_STORE_FP16) launch_v<1, EFWI_STORE_FP16>(a, grid, st);
+        else if (sk == EFWI_STORE_BF16) launch_v<1, EFWI_STORE_BF16>(a, grid, st);
+        else launch_v<1, 0>(a, grid, st);
+    }
 }
 
 }  // namespace efwi

@@ -779,13 +779,11 @@ int efwi_autotune(efwi_plan *p) {
     }
     // the adjoint's stress variable: the scaled form (per-thread loads) unless the stress
     // form is asked for, or a TMA adjoint (which exists in the stress form only)
-    //  (TMA staging of the scaled form reads FP32 forward velocities only)
-    const bool fp32v = p->snap_store == EFWI_STORE_FP32;
     p->adj_form = p->d.adj_form == EFWI_ADJ_FORM_STRESS ? EFWI_ADJ_FORM_STRESS
                   : p->d.adj_form == EFWI_ADJ_FORM_SCALED ? EFWI_ADJ_FORM_SCALED
-                  : (want_a == EFWI_STENCIL_AUTO || want_a == EFWI_STENCIL_LOADS ||
-                     (want_a == EFWI_STENCIL_TMA && fp32v)) ? EFWI_ADJ_FORM_SCALED
-                                                            : EFWI_ADJ_FORM_STRESS;
+                  : (want_a == EFWI_STENCIL_AUTO || want_a == EFWI_STENCIL_LOADS || want_a == EFWI_STENCIL_TMA)
+                      ? EFWI_ADJ_FORM_SCALED
+                      : EFWI_ADJ_FORM_STRESS;
     const bool scaled = p->adj_form == EFWI_ADJ_FORM_SCALED;
     if (scaled) adj_scaled_set_attrs();
     // the adjoint follows its own request, or the forward one when it has none
@@ -804,13 +802,13 @@ int efwi_autotune(efwi_plan *p) {
         // TMA staging, one cell or a cell pair per thread (EFWI_ADJ_VEC=1|2 keeps only one)
         const char *fa = getenv("EFWI_ADJ_VEC");
         const int only_av = fa ? atoi(fa) : 0;
-        if (want_a != EFWI_STENCIL_LOADS && fp32v && adj_scaled_tma_shape_ok(s.tx, s.tz))
+        if (want_a != EFWI_STENCIL_LOADS && adj_scaled_tma_shape_ok(s.tx, s.tz))
             for (int av = 1; av <= 2; ++av)
                 if (!only_av || av == only_av) adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, 2, av});
     }
     if (scaled && adj.empty()) {
         p->err = "no scaled-stress adjoint variant matches the request (per-thread loads: tiles 32x8 32x16 64x8 "
-                 "64x16; TMA: 32x16 with FP32 snapshots)";
+                 "64x16; TMA: 32x16)";
         return EFWI_ERR_ARG;
     }
     for (auto &s : kShapes) {

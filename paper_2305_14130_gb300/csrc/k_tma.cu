@@ -663,14 +663,17 @@ int occupancy() {
 
 // 3D tensor map over a stack of nfield arrays (stride F floats) of one shot:
 // dims {pitch, rows, nfield}, box {bx, by, bz}.
-int encode_map(CUtensorMap *m, float *base, const ShotDev &s, long long F, int nfield, int bx, int by, int bz) {
+int encode_map(CUtensorMap *m, void *base, const ShotDev &s, long long F, int nfield, int bx, int by, int bz,
+               int elem_bytes) {
     auto enc = encode_fn();
-    if (!enc) return EFWI_ERR_CUDA;
+    if (!enc || (elem_bytes != 4 && elem_bytes != 2)) return EFWI_ERR_CUDA;
+    const cuuint64_t eb = (cuuint64_t)elem_bytes;
     cuuint64_t dims[3] = {(cuuint64_t)s.pitch, (cuuint64_t)(s.NZ + 2 * EFWI_GZ), (cuuint64_t)nfield};
-    cuuint64_t strides[2] = {(cuuint64_t)s.pitch * 4, (cuuint64_t)F * 4};
+    cuuint64_t strides[2] = {(cuuint64_t)s.pitch * eb, (cuuint64_t)F * eb};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base + s.off, dims, strides, box, es,
+    CUresult r = enc(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 3,
+                     static_cast<char *>(base) + s.off * elem_bytes, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? EFWI_OK : EFWI_ERR_CUDA;

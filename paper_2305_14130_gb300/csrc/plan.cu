@@ -402,7 +402,7 @@ extern "C" int efwi_plan_create(efwi_plan **out, const efwi_plan_desc *d) {
         memset(&sh, 0, sizeof sh);
         sh.P = P; sh.x0 = x0; sh.w = w;
         sh.NX = w + 2 * P; sh.NZ = NZ;
-        sh.pitch = ((sh.NX + 3) / 4) * 4 + 8;
+        sh.pitch = ((sh.NX + 7) / 8) * 8 + 8;
         sh.off = off;
         off += (((long long)(NZ + 2 * EFWI_GZ) * sh.pitch + 63) / 64) * 64;
         sh.psx = psx; psx += (long long)NZ * 2 * P;

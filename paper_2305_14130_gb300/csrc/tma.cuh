@@ -38,9 +38,11 @@ struct __align__(64) AdjsMaps {
 };
 
 struct ShotDev;
-// Encode a 3D map (x, row, field) over nfield arrays of F floats of the shot's block with
-// box bx x by x bz (k_tma.cu).
-int encode_map(CUtensorMap *m, float *base, const ShotDev &s, long long F, int nfield, int bx, int by, int bz);
+// Encode a 3D map (x, row, field) over nfield arrays of F elements (4-byte floats, or 2-byte
+// FP16/BF16 snapshot elements copied as raw 16-bit words) of the shot's block with box
+// bx x by x bz (k_tma.cu).
+int encode_map(CUtensorMap *m, void *base, const ShotDev &s, long long F, int nfield, int bx, int by, int bz,
+               int elem_bytes = 4);
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);

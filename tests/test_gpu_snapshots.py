@@ -140,6 +140,35 @@ def test_snapshot_forward_variants_are_bitwise_identical(efwi, store, monkeypatc
                 assert torch.equal(a, b), (stencil, layout, tx, tz)
 
 
+@pytest.mark.parametrize("store", ["fp16", "bf16"])
+@pytest.mark.parametrize("ckpt", ["full", "segments"])
+def test_snapshot_adjoint_variants_are_bitwise_identical(efwi, store, ckpt, monkeypatch):
+    """The scaled-stress adjoint reads the 2-byte snapshots with per-thread loads or
+    through TMA copies (one cell or a cell pair per thread), every step stored or
+    recomputed per segment: the gradients are bit for bit the same."""
+    p = rounded(W.tiny(nx=70, nz=41, ns=3, nt=40, npml=5, win=[[0, 45], [13, 57], [30, 40]]))
+    d_obs = observed(p)
+    args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
+    ref = None
+    K = p.acq.nt if ckpt == "full" else 7
+    for adj_stencil, vec in (("loads", None), ("tma", "1"), ("tma", "2")):
+        if vec:
+            monkeypatch.setenv("EFWI_ADJ_VEC", vec)
+        plan = efwi.Plan(p.acq, exec="batched", tile=(32, 16), stencil="tma_pairs", adj_tile=(32, 16),
+                         adj_stencil=adj_stencil, ckpt_interval=K, snap_store=store)
+        info = plan.info()
+        assert info["adj_form"] == 2 and info["adj_stencil"] == {"loads": 1, "tma": 2}[adj_stencil]
+        assert info["adj_layout"] == (int(vec) if vec else 0)
+        out = [t.clone() for t in plan.gradient(*args, return_data=True)]
+        plan.sync_status()
+        plan.close()
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(ref, out):
+                assert torch.equal(a, b), (adj_stencil, vec)
+
+
 def test_auto_schedule_and_replays(efwi):
     """ckpt_interval="auto" stores every step of a small problem; repeated calls
     (graph replays) are bitwise identical; the plan reports what it chose."""
