@@ -102,6 +102,9 @@ def _desc(p, **over):
     ({"snap_store": 2, "overlap": 2}, -1, "FP32 snapshots"),
     ({"stored_steps": -1}, -1, "stored_steps"),
     ({"stored_steps": 10, "overlap": 2}, -1, "forced overlap"),
+    ({"adj_form": 3}, -1, "adj_form"),
+    ({"adj_form": 2, "exec": 0}, -1, "scaled-stress"),
+    ({"adj_form": 2, "adj_stencil": 3}, -1, "scaled-stress"),
 ])
 def test_plan_create_rejects_bad_descriptions(lib, over, code, msg):
     d, keep = _desc(W.tiny(), **over)
@@ -167,6 +170,7 @@ def test_enum_values_match_binding(tmp_path):
     names = list(_abi.STATUS.values())
     names += [f"EFWI_STORE_{k.upper()}" for k in _abi.STORE] + [f"EFWI_EXEC_{k.upper()}" for k in _abi.EXEC]
     names += [f"EFWI_STENCIL_{k.upper()}" for k in _abi.STENCIL] + [f"EFWI_OVERLAP_{k.upper()}" for k in _abi.OVERLAP]
+    names += [f"EFWI_ADJ_FORM_{k.upper()}" for k in _abi.ADJ_FORM]
     names += ["EFWI_DAS_STRAIN", "EFWI_DAS_STRAIN_RATE", "EFWI_DAS_VELOCITY", "EFWI_CKPT_AUTO"]
     prog = tmp_path / "enums.c"
     prog.write_text("\n".join(['#include <stdio.h>', '#include "efwi.h"', 'int main(void) {']
@@ -178,7 +182,7 @@ def test_enum_values_match_binding(tmp_path):
     for code, n in _abi.STATUS.items():
         assert got[n] == code, n
     for table, prefix in ((_abi.STORE, "STORE"), (_abi.EXEC, "EXEC"), (_abi.STENCIL, "STENCIL"),
-                          (_abi.OVERLAP, "OVERLAP")):
+                          (_abi.OVERLAP, "OVERLAP"), (_abi.ADJ_FORM, "ADJ_FORM")):
         for k, v in table.items():
             assert got[f"EFWI_{prefix}_{k.upper()}"] == v, k
     assert (got["EFWI_DAS_STRAIN"], got["EFWI_DAS_STRAIN_RATE"], got["EFWI_DAS_VELOCITY"]) == \
