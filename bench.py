@@ -198,6 +198,7 @@ TRAFFIC_PER_CELL = {
     ("step", 3, 32, 16, 3, 0, 1): {"keep": 57.31},
     # adjoint step, scaled-stress form, TMA staging, cell pairs, tile 32x16, FP32 velocities / FP16 snapshots
     ("adj", 2, 32, 16, 2, 2, 0): 97.62,
+    ("adj", 2, 32, 16, 3, 2, 0): 97.60,    # the same cell pairs in 512-thread CTAs
     ("adj", 2, 32, 16, 2, 2, 1): 92.78,
     # adjoint step (stress form), per-thread loads, tile 32x16, persistent grid, FP32 velocities
     ("adj", 1, 32, 16, 1, 1, 0): 94.97,
@@ -257,8 +258,8 @@ def roofline(exec_, info, prof, nt, ns):
                 staging += ", halo ring as single cells"
             if k == "adj" and kind == 1 and info["adj_persistent"]:
                 staging += ", persistent grid"
-            if k == "adj" and kind == 2 and info.get("adj_layout", 0) == 2:
-                staging += ", cell pairs"
+            if k == "adj" and kind == 2 and info.get("adj_layout", 0) >= 2:
+                staging += ", cell pairs" + (", 512 threads" if info["adj_layout"] == 3 else "")
             if k == "adj" and info.get("adj_form", 1) == 2:
                 staging = "scaled-stress form, " + staging
             name = f"{name.split(' ')[0]} [{staging}, tile {tile[0]}x{tile[1]}] {' '.join(name.split(' ')[1:])}"

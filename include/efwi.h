@@ -245,7 +245,9 @@ typedef struct efwi_plan_info_t {
                                    (nt with every step stored, 0 for the sqrt(nt) schedule) */
     int adj_form;               /* EFWI_ADJ_FORM_STRESS or _SCALED: the adjoint step in use */
     int adj_layout;             /* TMA scaled-stress adjoint: 1 = one cell per thread, 2 = cell
-                                   pairs (64-bit shared-memory accesses); 0 otherwise */
+                                   pairs (64-bit shared-memory accesses), 3 = cell pairs in
+                                   512-thread CTAs (tile pairs and halo ring on separate
+                                   threads); 0 otherwise */
 } efwi_plan_info_t;
 
 /* Zone-of-influence description (eq. 10), host memory.  Per source s:
@@ -273,7 +275,8 @@ typedef struct efwi_zoi_desc {
  *   EFWI_TMA_VEC=v        only forward layout v (1 single cells, 2 cell pairs,
  *                         3 cell pairs with the halo ring as single cells)
  *   EFWI_ADJ_PERSIST=0|1  only the one-CTA-per-tile / persistent-grid adjoint
- *   EFWI_ADJ_VEC=1|2      only the single-cell / cell-pair TMA scaled-stress adjoint
+ *   EFWI_ADJ_VEC=1|2|3    only the single-cell / cell-pair / 512-thread cell-pair TMA
+ *                         scaled-stress adjoint
  *   EFWI_PREFETCH=0|1     L2 prefetch one tile ahead off / on (else timed)
  *   EFWI_AUTOTUNE_LOG=1   print every timed variant on stderr
  *   EFWI_TEST_FAIL_ALLOC=k  make the k-th workspace allocation fail with

@@ -129,8 +129,12 @@ __device__ __forceinline__ float st4(float a, float b, float c, float d) { retur
 
 // VEC = 1: one cell per thread and iteration; VEC = 2: cell pairs with 64-bit shared-memory
 // accesses (one pair of the tile per thread, the velocity halo ring as single cells)
-template <int TX, int TZ, int VEC, int SK>
-__global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
+// NT: threads per CTA: 256, or 512 with cell pairs (the tile's pairs and the halo ring on separate
+// threads: 32 warps per SM at the same shared memory)
+template <int TX, int TZ, int VEC, int SK, int NT = kThreads>
+__global__ void __launch_bounds__(NT, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
+    static_assert(NT == kThreads || (VEC == 2 && (TX / 2) * TZ + 4 * (TX + 4) + 4 * TZ <= NT),
+                  "512-thread CTAs: one tile pair or one ring cell per thread");
     using L = AdjsLayout<TX, TZ, SK>;
     constexpr int SX = L::SX, NC = L::NC;
     extern __shared__ float4 smem_raw[];
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
             // 1. edge tiles: the stress-sub-step CPML terms over the staged F, in place, and the
             //    tile's stress-sub-step adjoint CPML memory; F of the tile kept for its update
             if constexpr (edge) {
-                for (int q = tid; q < SX * (TZ + 8); q += kThreads) {
+                for (int q = tid; q < SX * (TZ + 8); q += NT) {
                     const int y = q / SX, x = q - y * SX;
                     const int i = i0 - 4 + x, j = j0 - 4 + y;
                     const int o = y * SX + x;
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
             };
             if constexpr (VEC == 1) {
                 constexpr int VX = TX + 4, VZ = TZ + 4;
-                for (int q = tid; q < VX * VZ; q += kThreads) {
+                for (int q = tid; q < VX * VZ; q += NT) {
                     const int yv = q / VX, xv = q - yv * VX;
                     vcell(xv + 2, yv + 2);
                 }
@@ -384,8 +388,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                 // every thread: at most one cell of the ring (rows 2, 3, TZ+4, TZ+5 over the
                 // velocity width, columns 2, 3, TX+4, TX+5 between them), then one cell pair of
                 // the tile, whose x-stencils share their inputs (64-bit shared-memory accesses)
-                constexpr int RW = TX + 4, NRING = 4 * RW + 4 * TZ;
-                for (int q = tid; q < NRING; q += kThreads) {
+                constexpr int RW = TX + 4, NRING = 4 * RW + 4 * TZ, NPAIR = (TX / 2) * TZ;
+                // 512 threads: pairs on threads 0 .. NPAIR-1, the ring on the next NRING threads
+                const int rq0 = NT == kThreads ? tid : tid - NPAIR;
+                for (int q = rq0; q >= 0 && q < NRING; q += NT) {
                     int x, y;
                     if (q < 4 * RW) {
                         const int r = q / RW;
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                     }
                     vcell(x, y);
                 }
-                for (int q = tid; q < (TX / 2) * TZ; q += kThreads) {
+                for (int q = tid; q < (TX / 2) * TZ; q += NT) {
                     const int yy = q / (TX / 2);
                     vpair(4 + 2 * (q - yy * (TX / 2)), 4 + yy);
                 }
@@ -438,13 +444,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
                 a.out.sxz[c] = Fxz + dt * (smxz[q] * dxz);
             };
             if constexpr (VEC == 1) {
-                for (int q = tid; q < NC; q += kThreads) {
+                for (int q = tid; q < NC; q += NT) {
                     const int y = q / TX;
                     scell(q - y * TX, y);
                 }
             } else {
                 // cell pairs (x, x+1), x even: every cell's expression is scell's, term by term
-                for (int q2 = tid; q2 < NC / 2; q2 += kThreads) {
+                for (int q2 = tid; q2 < NC / 2; q2 += NT) {
                     const int y = q2 / (TX / 2), x = 2 * (q2 - y * (TX / 2));
                     const int i = i0 + x, j = j0 + y;
                     if (edge && (i >= NX || j >= NZ)) continue;
@@ -520,26 +526,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_scaled_tma(TmaAdjsArgs a) {
     }
 }
 
-template <int TX, int TZ, int VEC, int SK>
+template <int TX, int TZ, int VEC, int SK, int NT>
 int attrs_and_blocks() {
     constexpr int sm = (int)AdjsLayout<TX, TZ, SK>::smem();
-    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC, SK>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC, SK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_adj_scaled_tma<TX, TZ, VEC, SK, NT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_scaled_tma<TX, TZ, VEC, SK>, kThreads, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_adj_scaled_tma<TX, TZ, VEC, SK, NT>, NT, sm);
     return nb;
 }
 
-template <int VEC>
+template <int VEC, int NT>
 int blocks_sk(int sk) {
-    return sk == EFWI_STORE_FP16   ? attrs_and_blocks<32, 16, VEC, EFWI_STORE_FP16>()
-           : sk == EFWI_STORE_BF16 ? attrs_and_blocks<32, 16, VEC, EFWI_STORE_BF16>()
-                                   : attrs_and_blocks<32, 16, VEC, 0>();
+    return sk == EFWI_STORE_FP16   ? attrs_and_blocks<32, 16, VEC, EFWI_STORE_FP16, NT>()
+           : sk == EFWI_STORE_BF16 ? attrs_and_blocks<32, 16, VEC, EFWI_STORE_BF16, NT>()
+                                   : attrs_and_blocks<32, 16, VEC, 0, NT>();
 }
 
-template <int VEC, int SK>
+template <int VEC, int SK, int NT>
 void launch_v(const TmaAdjsArgs &a, int grid, cudaStream_t st) {
-    k_adj_scaled_tma<32, 16, VEC, SK><<<grid, kThreads, AdjsLayout<32, 16, SK>::smem(), st>>>(a);
+    k_adj_scaled_tma<32, 16, VEC, SK, NT><<<grid, NT, AdjsLayout<32, 16, SK>::smem(), st>>>(a);
+}
+
+template <int VEC, int NT>
+void launch_sk(const TmaAdjsArgs &a, int grid, cudaStream_t st, int sk) {
+    if (sk == EFWI_STORE_FP16) launch_v<VEC, EFWI_STORE_FP16, NT>(a, grid, st);
+    else if (sk == EFWI_STORE_BF16) launch_v<VEC, EFWI_STORE_BF16, NT>(a, grid, st);
+    else launch_v<VEC, 0, NT>(a, grid, st);
 }
 
 }  // namespace
@@ -548,7 +561,7 @@ bool adj_scaled_tma_shape_ok(int tx, int tz) { return tx == 32 && tz == 16; }
 
 int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz, int vec) {
     const bool half = p->snap_store != EFWI_STORE_FP32;
-    if (!adj_scaled_tma_shape_ok(tx, tz) || (half ? !p->segh : !p->seg) || (vec != 1 && vec != 2)) return EFWI_ERR_ARG;
+    if (!adj_scaled_tma_shape_ok(tx, tz) || (half ? !p->segh : !p->seg) || vec < 1 || vec > 3) return EFWI_ERR_ARG;
     std::vector<AdjsMaps> h(p->d.ns);
     const long long F = p->fsz_total;
     for (int s = 0; s < p->d.ns; ++s) {
@@ -569,7 +582,8 @@ int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz, int vec) {
     if (!p->adjs_maps && cudaMalloc((void **)&p->adjs_maps, sizeof(AdjsMaps) * p->d.ns) != cudaSuccess)
         return EFWI_ERR_OOM;
     cudaMemcpy(p->adjs_maps, h.data(), sizeof(AdjsMaps) * p->d.ns, cudaMemcpyHostToDevice);
-    const int nb = vec == 2 ? blocks_sk<2>(p->snap_store) : blocks_sk<1>(p->snap_store);
+    const int nb = vec == 3   ? blocks_sk<2, 512>(p->snap_store)
+                   : vec == 2 ? blocks_sk<2, kThreads>(p->snap_store) : blocks_sk<1, kThreads>(p->snap_store);
     p->tma_adj_grid = std::max(1, nb) * std::max(1, p->n_sms);
     p->tma_adj_stages = 2;
     p->adjs_vec = vec;
@@ -598,16 +612,9 @@ void launch_adj_scaled_tma(efwi_plan *p, const SnapIn &si, cudaStream_t st) {
     a.dt = f.dt; a.rdx = f.rdx; a.rdz = f.rdz;
     a.err = p->dev_err;
     const int grid = std::min(p->grid_adj_override > 0 ? p->grid_adj_override : p->tma_adj_grid, a.ntiles);
-    const int sk = p->snap_store;
-    if (p->adjs_vec == 2) {
-        if (sk == EFWI_STORE_FP16) launch_v<2, EFWI_STORE_FP16>(a, grid, st);
-        else if (sk == EFWI_STORE_BF16) launch_v<2, EFWI_STORE_BF16>(a, grid, st);
-        else launch_v<2, 0>(a, grid, st);
-    } else {
-        if (sk == EFWI_STORE_FP16) launch_v<1, EFWI_STORE_FP16>(a, grid, st);
-        else if (sk == EFWI_STORE_BF16) launch_v<1, EFWI_STORE_BF16>(a, grid, st);
-        else launch_v<1, 0>(a, grid, st);
-    }
+    if (p->adjs_vec == 3) launch_sk<2, 512>(a, grid, st, p->snap_store);
+    else if (p->adjs_vec == 2) launch_sk<2, kThreads>(a, grid, st, p->snap_store);
+    else launch_sk<1, kThreads>(a, grid, st, p->snap_store);
 }
 
 }  // namespace efwi

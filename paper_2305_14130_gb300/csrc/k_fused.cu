@@ -803,7 +803,7 @@ int efwi_autotune(efwi_plan *p) {
         const char *fa = getenv("EFWI_ADJ_VEC");
         const int only_av = fa ? atoi(fa) : 0;
         if (want_a != EFWI_STENCIL_LOADS && adj_scaled_tma_shape_ok(s.tx, s.tz))
-            for (int av = 1; av <= 2; ++av)
+            for (int av = 1; av <= 3; ++av)   // 3: cell pairs, 512-thread CTAs
                 if (!only_av || av == only_av) adj.push_back({EFWI_STENCIL_TMA, s.tx, s.tz, 2, av});
     }
     if (scaled && adj.empty()) {

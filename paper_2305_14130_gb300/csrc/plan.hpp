@@ -137,7 +137,8 @@ struct efwi_plan {
     int adj_form = EFWI_ADJ_FORM_STRESS;   // adjoint stress variable in use (EFWI_ADJ_FORM_STRESS / _SCALED)
     efwi::AdjMaps *adj_maps = nullptr;
     efwi::AdjsMaps *adjs_maps = nullptr;   // [ns] tensor maps of the TMA scaled-stress adjoint
-    int adjs_vec = 1;                      // its layout: 1 = one cell per thread, 2 = cell pairs
+    int adjs_vec = 1;                      // its layout: 1 = one cell per thread, 2 = cell pairs,
+                                           // 3 = cell pairs in 512-thread CTAs
     int tma_adj_grid = 0, tma_adj_stages = 1;
     int adj_grid = 0;                      // per-thread-load adjoint: persistent grid (0 = one CTA per tile)
     int *dev_err = nullptr;                // device flag: a bounded wait expired
@@ -227,7 +228,8 @@ void launch_adj_scaled(efwi_plan *p, const SnapIn &si, cudaStream_t st);
 void launch_imag_unscale(efwi_plan *p, float *G, cudaStream_t st);
 // --- k_adjs_tma.cu (the same step with TMA staging, FP32 forward velocities) ----
 bool adj_scaled_tma_shape_ok(int tx, int tz);
-int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz, int vec);   // tensor maps, grid; vec 1|2 (cell pairs)
+// tensor maps and grid; vec 1 (single cells), 2 (cell pairs), 3 (cell pairs, 512-thread CTAs)
+int adj_scaled_tma_prepare(efwi_plan *p, int tx, int tz, int vec);
 void launch_adj_scaled_tma(efwi_plan *p, const SnapIn &si, cudaStream_t st);
 
 // --- k_fused.cu --------------------------------------------------------------

@@ -357,7 +357,7 @@ VARIANTS = [("loads", s) for s in SHAPES] + [(k, s) for k in ("tma", "tma_pairs"
 # the scaled-stress adjoint: per-thread loads on every tile, one CTA per tile or on a
 # persistent grid, and TMA staging (32x16, persistent grid)
 SCALED_VARIANTS = [((32, 8), 0, "loads"), ((32, 16), 0, "loads"), ((32, 16), 1, "loads"), ((64, 8), 0, "loads"),
-                   ((64, 16), 0, "loads"), ((32, 16), 0, "tma:1"), ((32, 16), 0, "tma:2")]
+                   ((64, 16), 0, "loads"), ((32, 16), 0, "tma:1"), ((32, 16), 0, "tma:2"), ((32, 16), 0, "tma:3")]
 
 
 @pytest.mark.parametrize("source", ["moment_tensor", "force"])

@@ -151,7 +151,7 @@ def test_snapshot_adjoint_variants_are_bitwise_identical(efwi, store, ckpt, monk
     args = (dev(p.vp), dev(p.vs), dev(p.rho), dev(d_obs))
     ref = None
     K = p.acq.nt if ckpt == "full" else 7
-    for adj_stencil, vec in (("loads", None), ("tma", "1"), ("tma", "2")):
+    for adj_stencil, vec in (("loads", None), ("tma", "1"), ("tma", "2"), ("tma", "3")):
         if vec:
             monkeypatch.setenv("EFWI_ADJ_VEC", vec)
         plan = efwi.Plan(p.acq, exec="batched", tile=(32, 16), stencil="tma_pairs", adj_tile=(32, 16),
